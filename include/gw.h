@@ -1,0 +1,206 @@
+/*
+ * gw.h -- C ABI of the GB300-native AMG-preconditioned CG solver for steady
+ * groundwater flow (libgw.so, CUDA for sm_103a).
+ *
+ * The library solves C h = Q, the steady confined flow system (Sbai &
+ * Larabi, Eq. 2 with zero storage), where C is the global conductance matrix
+ * of a cell-centred 5/7-point finite-volume discretisation (an M-matrix;
+ * Benchmarking Examples section) and Q holds the sources and the boundary
+ * contributions.  The solver is conjugate gradients preconditioned by one
+ * smoothed-aggregation algebraic-multigrid V-cycle per iteration
+ * (Introduction: setup phase, V-cycle, AMG as a Krylov preconditioner).  The
+ * hierarchy is built once and reused across right-hand sides, as the dual
+ * delineation approach reuses one matrix for many solves (Introduction).
+ * The ABI is plain C so that any language with a C foreign-function interface
+ * (the paper names Fortran's iso_c_binding) can call it.
+ *
+ * Conventions for every entry point:
+ *  - Return value: a gw_status (GW_OK = 0).  No call aborts and no C++
+ *    exception crosses the ABI.  gw_last_error() gives a one-line reason for
+ *    the last failure on the calling thread.
+ *  - Arrays are plain pointers.  Unless stated otherwise an array may be in
+ *    host memory or in device memory of the current CUDA device; the library
+ *    looks the pointer up and copies host arrays in and out itself.  Arrays
+ *    stay owned by the caller; handles own their device memory until freed.
+ *  - stream is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Work is enqueued on it.  Calls that return host-visible
+ *    results (gw_amg_setup, gw_pcg_solve, gw_hierarchy_info) synchronise it.
+ *  - Cells are numbered i = x + nx*(y + ny*z); fields are nx*ny*nz doubles.
+ *  - Everything runs on the GPU in hand-written kernels; there is no CPU
+ *    fallback.  One GPU per handle: the device current at creation.
+ *  - Results are bitwise reproducible run to run for the same inputs.
+ */
+#ifndef GW_H
+#define GW_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GW_OK = 0,
+    GW_ERR_ARG = 1,           /* null pointer, bad size, K <= 0 or not finite, no Dirichlet face */
+    GW_ERR_CUDA = 2,          /* a CUDA call failed (see gw_last_error) */
+    GW_ERR_OOM = 3,           /* device allocation failed */
+    GW_ERR_SETUP = 4,         /* setup could not build a hierarchy (round cap, coarsest level too big) */
+    GW_ERR_NOT_CONVERGED = 5, /* maxit reached: h holds the last iterate, relres is set */
+    GW_ERR_BREAKDOWN = 6      /* p^T A p <= 0 or a non-finite scalar in CG */
+} gw_status;
+
+/* Regular grid of nx*ny*nz cells of size dx*dy*dz; nz = 1 gives the 2D
+ * 5-point operator. */
+typedef struct {
+    int nx, ny, nz;
+    double dx, dy, dz;
+} gw_grid;
+
+enum { GW_NOFLOW = 0, GW_DIRICHLET = 1 };
+
+/* Boundary condition of the six domain faces in the order -x,+x,-y,+y,-z,+z:
+ * GW_NOFLOW (zero flux) or GW_DIRICHLET (head value[f] on the face). */
+typedef struct {
+    int type[6];
+    double value[6];
+} gw_bc;
+
+/* Arithmetic of the V-cycle.  The outer CG always runs in FP64 (vectors,
+ * dot products, matrix-vector product with the FP64 matrix, true residual)
+ * and the coarsest level always uses the FP64 dense inverse. */
+typedef enum {
+    GW_PREC_FP64 = 0,     /* hierarchy stored and cycled in FP64 */
+    GW_PREC_MIXED32 = 1   /* hierarchy stored and cycled in FP32 */
+} gw_prec;
+
+enum { GW_SMOOTH_JACOBI = 0, GW_SMOOTH_CHEBYSHEV = 1 };
+
+/* Setup and cycle options (gw_amg_opts_default fills the defaults). */
+typedef struct {
+    double theta;        /* strength threshold on level 0, halved per level (0.08) */
+    int smoother;        /* GW_SMOOTH_JACOBI (weight 4/3 over the Gershgorin bound) or GW_SMOOTH_CHEBYSHEV */
+    int degree;          /* Chebyshev degree (2) */
+    int nu;              /* pre- and post-smoothing applications per level (1) */
+    int n_coarse;        /* stop coarsening at this many unknowns or fewer (1024) */
+    int max_levels;      /* at most this many levels (12) */
+    uint64_t seed;       /* seed of the MIS-2 priorities (0x5EED) */
+    int prec;            /* gw_prec (GW_PREC_MIXED32) */
+} gw_amg_opts;
+
+/* Per-level statistics in the columns of the paper's Table 1 (unknowns,
+ * nonzeros, memory) plus what the GPU hierarchy adds. */
+typedef struct {
+    int n;                  /* unknowns */
+    long long nnz;          /* structural nonzeros of A_l */
+    long long nnz_p;        /* nonzeros of P_l (0 on the coarsest level) */
+    long long bytes;        /* device bytes held for this level */
+    int naggregates;        /* aggregates formed from this level (0 on the coarsest) */
+    int mis_rounds;         /* parallel MIS-2 rounds used on this level */
+    double omega_p;         /* prolongator smoothing weight (4/3)/rho_F */
+    double jacobi_w;        /* Jacobi weight (4/3)/rho_Gershgorin(D^-1 A) */
+    double lambda_max;      /* power-iteration estimate of lambda_max(D^-1 A) */
+} gw_level_info;
+
+typedef struct gw_matrix_s *gw_matrix;
+typedef struct gw_hierarchy_s *gw_hierarchy;
+
+/* Fills *opts with the defaults listed in gw_amg_opts. */
+void gw_amg_opts_default(gw_amg_opts *opts);
+
+/*
+ * gw_assemble -- build C and Q (Eq. 2 with S = 0; 5/7-point finite volumes,
+ * Benchmarking Examples section).  For an interior face between cells i < j
+ * along axis d the transmissibility is T = (2 K_i K_j)/(K_i + K_j) * g_d with
+ * g_x = dy dz / dx (and likewise for y, z) and K the conductivity along d;
+ * a Dirichlet face of cell i has T_b = 2 K_i g_d (head at the face, half a
+ * cell away).  Row i: a_ii = sum of T over the faces of i in the order
+ * -x,+x,-y,+y,-z,+z, a_ij = -T, b_i = q_i + sum over its Dirichlet faces of
+ * T_b h_b.  A is symmetric bitwise.
+ *   grid, bc          host structs.
+ *   Kx, Ky, Kz        conductivities, n doubles each (host or device); Ky and
+ *                     Kz may be equal to Kx.
+ *   q                 source per cell (n doubles, host or device) or NULL.
+ *   A_out             receives a new matrix handle (CSR, FP64, columns
+ *                     ascending; nnz = 7n - 2(ny nz + nx nz + nx ny) in 3D).
+ *   b_out             n doubles (host or device), receives Q.
+ * Errors: GW_ERR_ARG for a null pointer, a non-positive size or spacing, a
+ * K <= 0 or non-finite value, a non-finite q or head, or no Dirichlet face
+ * (the system would be singular).  Checked on the device before any output
+ * is written; b_out is untouched on error.
+ */
+int gw_assemble(const gw_grid *grid, const double *Kx, const double *Ky, const double *Kz, const gw_bc *bc,
+                const double *q, gw_matrix *A_out, double *b_out, void *stream);
+
+/* Size of the matrix behind a handle. */
+int gw_matrix_size(gw_matrix A, int *n, long long *nnz);
+
+/* Copies the CSR arrays of A (rowptr n+1 ints, col nnz ints, val nnz doubles;
+ * host or device; any may be NULL). */
+int gw_matrix_export(gw_matrix A, int *rowptr, int *col, double *val, void *stream);
+
+/*
+ * gw_amg_setup -- the AMG setup phase (Introduction): strength graph,
+ * deterministic parallel MIS-2 aggregation with hashed seeded priorities,
+ * tentative prolongator, one damped-Jacobi smoothing of it, Galerkin coarse
+ * operators A_{l+1} = P^T A_l P by a two-pass SpGEMM, and a dense LU inverse
+ * of the coarsest level; then the V-cycle storage in the chosen precision.
+ * All of it runs in CUDA kernels.  The aggregates and the P and A_{l+1}
+ * patterns and values are the same as a serial FP64 implementation that
+ * sums in the stated order (no fused multiply-add in these stages).
+ *   A     assembled matrix; the hierarchy keeps a reference to it (freeing A
+ *         before H is the caller's error).
+ *   opts  host struct or NULL for the defaults.
+ * Errors: GW_ERR_ARG (bad option), GW_ERR_OOM, GW_ERR_SETUP (MIS-2 round cap
+ * reached, a node left unaggregated, coarsest level above 4096 unknowns or
+ * singular), GW_ERR_CUDA.
+ */
+int gw_amg_setup(gw_matrix A, const gw_amg_opts *opts, gw_hierarchy *H_out, void *stream);
+
+/*
+ * gw_pcg_solve -- AMG-preconditioned conjugate gradients from h0 = 0
+ * (Saad, Algorithm 9.1; AMG as a preconditioner, Introduction).  Stops when
+ * the TRUE relative residual ||b - A h||_2 / ||b||_2 <= tol: when the
+ * recursive residual passes the test the true one is computed in FP64 and,
+ * if it fails, replaces the recursive residual.
+ *   b       n doubles (host or device), right-hand side.
+ *   h       n doubles (host or device), receives the heads.
+ *   tol     > 0; maxit >= 1.
+ *   iters   host int or NULL: iterations done.
+ *   relres  host double or NULL: final true relative residual.
+ * Returns GW_OK, GW_ERR_NOT_CONVERGED (h = last iterate), GW_ERR_BREAKDOWN,
+ * GW_ERR_ARG or GW_ERR_CUDA.  Synchronises the stream.  Concurrent solves on
+ * one hierarchy must be serialised by the caller (the hierarchy holds the
+ * work vectors).
+ */
+int gw_pcg_solve(gw_hierarchy H, const double *b, double *h, double tol, int maxit, int *iters,
+                 double *relres, void *stream);
+
+/* Applies one V-cycle z = M^-1 r (from a zero initial guess) with the
+ * hierarchy's precision; r and z are n doubles on the device. */
+int gw_vcycle(gw_hierarchy H, const double *r, double *z, void *stream);
+
+/* Table-1 statistics: fills out[0..min(cap, levels)-1] and *nlevels. */
+int gw_hierarchy_info(gw_hierarchy H, gw_level_info *out, int cap, int *nlevels);
+
+/*
+ * Copies level l of the hierarchy for inspection: aggregate id per node
+ * (n ints), MIS-2 root flag (n bytes), the FP64 CSR of A_l and of P_l.
+ * Sizes from gw_hierarchy_info (P_l has n rows and naggregates columns).
+ * Any pointer may be NULL; host or device memory.
+ */
+int gw_hierarchy_export(gw_hierarchy H, int level, int *agg, unsigned char *root, int *a_rowptr, int *a_col,
+                        double *a_val, int *p_rowptr, int *p_col, double *p_val, void *stream);
+
+void gw_matrix_free(gw_matrix A);
+void gw_hierarchy_free(gw_hierarchy H);
+
+/* Static string naming a status code. */
+const char *gw_status_str(int status);
+
+/* One-line description of the last failure on the calling thread. */
+const char *gw_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GW_H */

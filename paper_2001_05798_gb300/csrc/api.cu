@@ -1,0 +1,473 @@
+// api.cu -- the C ABI of libgw and the construction of the hierarchy.
+#include <math.h>
+#include <string.h>
+
+#include <new>
+
+#include "gw_internal.cuh"
+
+struct gw_matrix_s {
+    int dev = 0;
+    int nx = 0, ny = 0, nz = 0;
+    gw::DCSR A;
+};
+
+struct gw_hierarchy_s {
+    gw::Hier H;
+};
+
+namespace gw {
+
+// ---------------------------------------------------------------- helpers --
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) GW_CUDA(cudaSetDevice(dev));
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// A read-only input that may live on the host: staged into device memory.
+template <class T>
+struct DevIn {
+    const T *p = nullptr;
+    DBuf<T> own;
+    DevIn(const T *src, size_t n, cudaStream_t st)
+    {
+        if (!src) return;
+        if (is_device_ptr(src)) {
+            p = src;
+        } else {
+            own.alloc(n);
+            GW_CUDA(cudaMemcpyAsync(own.p, src, n * sizeof(T), cudaMemcpyHostToDevice, st));
+            p = own.p;
+        }
+    }
+};
+
+Hier::~Hier()
+{
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (cap) cudaStreamDestroy(cap);
+    if (ctl_host) cudaFreeHost(ctl_host);
+}
+
+__global__ void k_make_dw(int n, const double *__restrict__ d, double scale, float *__restrict__ of,
+                          double *__restrict__ od)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double w = scale / d[i];
+        if (of) of[i] = (float)w;
+        if (od) od[i] = w;
+    }
+}
+
+template <class T>
+static void alloc_vectors(CycLevel<T> &c, int n)
+{
+    c.n = n;
+    c.x.alloc((size_t)n);
+    c.b.alloc((size_t)n);
+    c.r.alloc((size_t)n);
+    c.t.alloc((size_t)n);
+    c.d.alloc((size_t)n);
+    c.d2.alloc((size_t)n);
+}
+
+static void cheb_coeffs(double lam, int degree, double &c0, double *c1, double *c2)
+{
+    const double a = lam / 30.0, b = 1.1 * lam;
+    const double theta = (b + a) / 2.0, delta = (b - a) / 2.0, sigma = theta / delta;
+    double rho = 1.0 / sigma;
+    c0 = 1.0 / theta;
+    for (int k = 1; k < degree && k < 8; ++k) {
+        const double rn = 1.0 / (2.0 * sigma - rho);
+        c1[k] = rn * rho;
+        c2[k] = 2.0 * rn / delta;
+        rho = rn;
+    }
+}
+
+// Smoothed-aggregation setup (see setup.cu for the stages).  Levels are added
+// while the level has more than n_coarse unknowns and fewer than max_levels
+// levels exist; a level whose aggregation keeps more than 0.9 of its unknowns
+// (or finds none) becomes the coarsest.  theta halves per level.
+void build_hierarchy(Hier &H, cudaStream_t st)
+{
+    const gw_amg_opts &o = H.o;
+    H.A.clear();
+    H.A.emplace_back();  // placeholder for level 0 (the matrix handle's CSR)
+    std::vector<DCSR> R;
+    auto Al = [&](int l) -> const DCSR & { return l == 0 ? *H.A0 : H.A[(size_t)l]; };
+    double th = o.theta;
+    int l = 0;
+    for (;;) {
+        const DCSR &A = Al(l);
+        gw_level_info li;
+        memset(&li, 0, sizeof li);
+        li.n = A.nr;
+        li.nnz = A.nnz;
+        H.info.push_back(li);
+        H.agg.emplace_back();
+        H.root.emplace_back();
+        if (A.nr <= o.n_coarse || l + 1 >= o.max_levels) break;
+        DBuf<unsigned char> S;
+        setup_strength(A, th * th, S, st);
+        H.info[(size_t)l].mis_rounds = setup_mis2(A, S.p, o.seed, l, H.root[(size_t)l], st);
+        const int m = setup_aggregate(A, S.p, H.root[(size_t)l].p, o.seed, l, H.agg[(size_t)l], st);
+        H.info[(size_t)l].naggregates = m;
+        if (m == 0 || (double)m > 0.9 * (double)A.nr) {
+            H.info[(size_t)l].naggregates = 0;
+            break;
+        }
+        DCSR P, Rl, AP, Ac;
+        double omega = 0.0, rho = 0.0;
+        setup_smooth_p(A, S.p, H.agg[(size_t)l].p, m, P, &omega, &rho, st);
+        setup_transpose(P, Rl, st);
+        setup_spgemm(A, P, AP, st);
+        setup_spgemm(Rl, AP, Ac, st);
+        H.info[(size_t)l].omega_p = omega;
+        H.info[(size_t)l].nnz_p = P.nnz;
+        H.P.push_back(std::move(P));
+        R.push_back(std::move(Rl));
+        H.A.push_back(std::move(Ac));
+        ++l;
+        th = th * 0.5;
+    }
+    H.L = l + 1;
+    const int L = H.L;
+    setup_dense_inverse(Al(L - 1), H.Ainv, st);
+    H.info[(size_t)L - 1].bytes += (long long)H.Ainv.bytes();
+    const bool f64 = o.prec == GW_PREC_FP64;
+    if (f64) H.cd.resize((size_t)L);
+    else H.cf.resize((size_t)L);
+    for (int k = 0; k < L; ++k) {
+        const DCSR &A = Al(k);
+        const int n = A.nr;
+        long long bytes = 0;
+        if (k < L - 1) {
+            DBuf<double> diag;
+            const double rhoJ = setup_gershgorin(A, diag, st);
+            H.info[(size_t)k].jacobi_w = (4.0 / 3.0) / rhoJ;
+            double scale = 1.0;
+            double c0 = 0.0, c1[8] = {0}, c2[8] = {0};
+            if (o.smoother == GW_SMOOTH_JACOBI) {
+                scale = H.info[(size_t)k].jacobi_w;
+            } else {
+                const double lam = setup_power_lambda(A, diag.p, o.seed, k, st);
+                H.info[(size_t)k].lambda_max = lam;
+                cheb_coeffs(lam, o.degree, c0, c1, c2);
+            }
+            const int g = (int)std::min<long long>(((long long)n + 255) / 256, 152LL * 16);
+            if (f64) {
+                CycLevel<double> &c = H.cd[(size_t)k];
+                to_sell<double>(A, c.A, st);
+                to_sell<double>(H.P[(size_t)k], c.P, st);
+                to_sell<double>(R[(size_t)k], c.R, st);
+                c.dw.alloc((size_t)n);
+                k_make_dw<<<std::max(g, 1), 256, 0, st>>>(n, diag.p, scale, nullptr, c.dw.p);
+                c.c0 = c0;
+                memcpy(c.c1, c1, sizeof c1);
+                memcpy(c.c2, c2, sizeof c2);
+                bytes += (long long)(c.A.bytes() + c.P.bytes() + c.R.bytes() + c.dw.bytes());
+            } else {
+                CycLevel<float> &c = H.cf[(size_t)k];
+                to_sell<float>(A, c.A, st);
+                to_sell<float>(H.P[(size_t)k], c.P, st);
+                to_sell<float>(R[(size_t)k], c.R, st);
+                c.dw.alloc((size_t)n);
+                k_make_dw<<<std::max(g, 1), 256, 0, st>>>(n, diag.p, scale, c.dw.p, nullptr);
+                c.c0 = c0;
+                memcpy(c.c1, c1, sizeof c1);
+                memcpy(c.c2, c2, sizeof c2);
+                bytes += (long long)(c.A.bytes() + c.P.bytes() + c.R.bytes() + c.dw.bytes());
+            }
+            GW_LAUNCH_CHECK();
+            GW_CUDA(cudaStreamSynchronize(st));
+        }
+        if (f64) {
+            alloc_vectors(H.cd[(size_t)k], n);
+            bytes += 6LL * n * 8;
+        } else {
+            alloc_vectors(H.cf[(size_t)k], n);
+            bytes += 6LL * n * 4;
+        }
+        H.info[(size_t)k].bytes += bytes;
+    }
+    if (!f64) {
+        to_sell<double>(*H.A0, H.A64, st);
+        H.info[0].bytes += (long long)H.A64.bytes();
+    }
+    const int n = H.A0->nr;
+    H.n = n;
+    H.x.alloc((size_t)n);
+    H.r.alloc((size_t)n);
+    H.p.alloc((size_t)n);
+    H.q.alloc((size_t)n);
+    H.z.alloc((size_t)n);
+    H.b.alloc((size_t)n);
+    H.part.alloc(2 * (size_t)RED_MAX_BLOCKS);
+    H.ctl.alloc(1);
+    GW_CUDA(cudaMemsetAsync(H.ctl.p, 0, sizeof(Ctl), st));
+    GW_CUDA(cudaMallocHost((void **)&H.ctl_host, sizeof(Ctl)));
+    memset(H.ctl_host, 0, sizeof(Ctl));
+    H.info[0].bytes += 6LL * n * 8;
+    GW_CUDA(cudaStreamSynchronize(st));
+}
+
+}  // namespace gw
+
+using namespace gw;
+
+#define GW_API_BEGIN try {
+#define GW_API_END                                    \
+    }                                                 \
+    catch (const gw::Error &e)                        \
+    {                                                 \
+        gw::set_last_error(e.msg.c_str());            \
+        return e.code;                                \
+    }                                                 \
+    catch (const std::bad_alloc &)                    \
+    {                                                 \
+        gw::set_last_error("host allocation failed"); \
+        return GW_ERR_OOM;                            \
+    }                                                 \
+    catch (...)                                       \
+    {                                                 \
+        gw::set_last_error("unexpected failure");     \
+        return GW_ERR_CUDA;                           \
+    }                                                 \
+    return GW_OK;
+
+extern "C" {
+
+void gw_amg_opts_default(gw_amg_opts *o)
+{
+    if (!o) return;
+    o->theta = 0.08;
+    o->smoother = GW_SMOOTH_JACOBI;
+    o->degree = 2;
+    o->nu = 1;
+    o->n_coarse = 1024;
+    o->max_levels = 12;
+    o->seed = 0x5EEDULL;
+    o->prec = GW_PREC_MIXED32;
+}
+
+const char *gw_status_str(int s)
+{
+    switch (s) {
+    case GW_OK: return "GW_OK";
+    case GW_ERR_ARG: return "GW_ERR_ARG";
+    case GW_ERR_CUDA: return "GW_ERR_CUDA";
+    case GW_ERR_OOM: return "GW_ERR_OOM";
+    case GW_ERR_SETUP: return "GW_ERR_SETUP";
+    case GW_ERR_NOT_CONVERGED: return "GW_ERR_NOT_CONVERGED";
+    case GW_ERR_BREAKDOWN: return "GW_ERR_BREAKDOWN";
+    default: return "GW_UNKNOWN_STATUS";
+    }
+}
+
+const char *gw_last_error(void) { return gw::last_error_cstr(); }
+
+int gw_assemble(const gw_grid *grid, const double *Kx, const double *Ky, const double *Kz, const gw_bc *bc,
+                const double *q, gw_matrix *A_out, double *b_out, void *stream)
+{
+    GW_API_BEGIN
+    if (!grid || !Kx || !bc || !A_out || !b_out) fail(GW_ERR_ARG, "gw_assemble: null argument");
+    *A_out = nullptr;
+    const int nx = grid->nx, ny = grid->ny, nz = grid->nz;
+    if (nx < 1 || ny < 1 || nz < 1) fail(GW_ERR_ARG, "gw_assemble: grid sizes must be >= 1");
+    const double dx = grid->dx, dy = grid->dy, dz = grid->dz;
+    if (!(dx > 0.0) || !(dy > 0.0) || !(dz > 0.0) || !isfinite(dx) || !isfinite(dy) || !isfinite(dz))
+        fail(GW_ERR_ARG, "gw_assemble: cell sizes must be positive and finite");
+    const long long n64 = (long long)nx * ny * nz;
+    if (n64 > 0x7fffffffLL / 8) fail(GW_ERR_ARG, "gw_assemble: %lld cells is too many", n64);
+    int ndir = 0;
+    for (int f = 0; f < 6; ++f) {
+        if (bc->type[f] != GW_NOFLOW && bc->type[f] != GW_DIRICHLET) fail(GW_ERR_ARG, "gw_assemble: bad face type");
+        if (bc->type[f] == GW_DIRICHLET) {
+            if (!isfinite(bc->value[f])) fail(GW_ERR_ARG, "gw_assemble: head on face %d is not finite", f);
+            ++ndir;
+        }
+    }
+    if (ndir == 0) fail(GW_ERR_ARG, "gw_assemble: no Dirichlet face, the system is singular");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t n = (size_t)n64;
+    int dev = 0;
+    GW_CUDA(cudaGetDevice(&dev));
+    DevIn<double> kx(Kx, n, st), ky(Ky ? Ky : Kx, n, st), kz(Kz ? Kz : Kx, n, st), qq(q, n, st);
+    const bool bdev = is_device_ptr(b_out);
+    DBuf<double> btmp;
+    double *bd = b_out;
+    if (!bdev) {
+        btmp.alloc(n);
+        bd = btmp.p;
+    }
+    DBuf<int> flag(1);
+    gw_matrix M = new gw_matrix_s;
+    try {
+        M->dev = dev;
+        M->nx = nx;
+        M->ny = ny;
+        M->nz = nz;
+        assemble_csr(nx, ny, nz, dx, dy, dz, kx.p, ky.p, kz.p, bc->type, bc->value, qq.p, M->A, bd, flag.p, st);
+        if (!bdev) GW_CUDA(cudaMemcpyAsync(b_out, bd, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+        GW_CUDA(cudaStreamSynchronize(st));
+    } catch (...) {
+        delete M;
+        throw;
+    }
+    *A_out = M;
+    GW_API_END
+}
+
+int gw_matrix_size(gw_matrix A, int *n, long long *nnz)
+{
+    GW_API_BEGIN
+    if (!A) fail(GW_ERR_ARG, "gw_matrix_size: null matrix");
+    if (n) *n = A->A.nr;
+    if (nnz) *nnz = A->A.nnz;
+    GW_API_END
+}
+
+int gw_matrix_export(gw_matrix A, int *rowptr, int *col, double *val, void *stream)
+{
+    GW_API_BEGIN
+    if (!A) fail(GW_ERR_ARG, "gw_matrix_export: null matrix");
+    DeviceGuard g(A->dev);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (rowptr) to_device(rowptr, A->A.rp.p, ((size_t)A->A.nr + 1) * sizeof(int), st);
+    if (col) to_device(col, A->A.ci.p, (size_t)A->A.nnz * sizeof(int), st);
+    if (val) to_device(val, A->A.v.p, (size_t)A->A.nnz * sizeof(double), st);
+    GW_CUDA(cudaStreamSynchronize(st));
+    GW_API_END
+}
+
+int gw_amg_setup(gw_matrix A, const gw_amg_opts *opts, gw_hierarchy *H_out, void *stream)
+{
+    GW_API_BEGIN
+    if (!A || !H_out) fail(GW_ERR_ARG, "gw_amg_setup: null argument");
+    *H_out = nullptr;
+    gw_amg_opts o;
+    gw_amg_opts_default(&o);
+    if (opts) o = *opts;
+    if (!(o.theta >= 0.0) || !isfinite(o.theta)) fail(GW_ERR_ARG, "gw_amg_setup: theta must be >= 0");
+    if (o.smoother != GW_SMOOTH_JACOBI && o.smoother != GW_SMOOTH_CHEBYSHEV) fail(GW_ERR_ARG, "gw_amg_setup: bad smoother");
+    if (o.degree < 1 || o.degree > 8 || o.nu < 1 || o.nu > 8) fail(GW_ERR_ARG, "gw_amg_setup: degree and nu must be in 1..8");
+    if (o.n_coarse < 1 || o.n_coarse > 4096) fail(GW_ERR_ARG, "gw_amg_setup: n_coarse must be in 1..4096");
+    if (o.max_levels < 2 || o.max_levels > 16) fail(GW_ERR_ARG, "gw_amg_setup: max_levels must be in 2..16");
+    if (o.prec != GW_PREC_FP64 && o.prec != GW_PREC_MIXED32) fail(GW_ERR_ARG, "gw_amg_setup: bad precision");
+    DeviceGuard g(A->dev);
+    cudaStream_t st = (cudaStream_t)stream;
+    gw_hierarchy h = new gw_hierarchy_s;
+    try {
+        h->H.dev = A->dev;
+        h->H.o = o;
+        h->H.A0 = &A->A;
+        build_hierarchy(h->H, st);
+        if (h->H.L < 2) fail(GW_ERR_SETUP, "gw_amg_setup: the matrix is small enough for one level (n <= n_coarse)");
+    } catch (...) {
+        delete h;
+        throw;
+    }
+    *H_out = h;
+    GW_API_END
+}
+
+int gw_pcg_solve(gw_hierarchy H, const double *b, double *h, double tol, int maxit, int *iters, double *relres,
+                 void *stream)
+{
+    int status = GW_OK;
+    GW_API_BEGIN
+    if (!H || !b || !h) fail(GW_ERR_ARG, "gw_pcg_solve: null argument");
+    if (!(tol > 0.0) || !isfinite(tol) || maxit < 1) fail(GW_ERR_ARG, "gw_pcg_solve: need tol > 0 and maxit >= 1");
+    Hier &hh = H->H;
+    DeviceGuard g(hh.dev);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = (size_t)hh.n * sizeof(double);
+    GW_CUDA(cudaMemcpyAsync(hh.b.p, b, bytes, cudaMemcpyDefault, st));
+    status = pcg_run(hh, tol, maxit, iters, relres, st);
+    GW_CUDA(cudaMemcpyAsync(h, hh.x.p, bytes, cudaMemcpyDefault, st));
+    GW_CUDA(cudaStreamSynchronize(st));
+    if (status != GW_OK) {
+        gw::set_last_error(status == GW_ERR_NOT_CONVERGED ? "gw_pcg_solve: maxit reached" : "gw_pcg_solve: CG breakdown");
+        return status;
+    }
+    GW_API_END
+}
+
+int gw_vcycle(gw_hierarchy H, const double *r, double *z, void *stream)
+{
+    GW_API_BEGIN
+    if (!H || !r || !z) fail(GW_ERR_ARG, "gw_vcycle: null argument");
+    if (!is_device_ptr(r) || !is_device_ptr(z)) fail(GW_ERR_ARG, "gw_vcycle: r and z must be device pointers");
+    DeviceGuard g(H->H.dev);
+    cudaStream_t st = (cudaStream_t)stream;
+    vcycle_enqueue(H->H, r, z, nullptr, false, st);
+    GW_CUDA(cudaStreamSynchronize(st));
+    GW_API_END
+}
+
+int gw_hierarchy_info(gw_hierarchy H, gw_level_info *out, int cap, int *nlevels)
+{
+    GW_API_BEGIN
+    if (!H) fail(GW_ERR_ARG, "gw_hierarchy_info: null hierarchy");
+    if (nlevels) *nlevels = H->H.L;
+    for (int l = 0; out && l < cap && l < H->H.L; ++l) out[l] = H->H.info[(size_t)l];
+    GW_API_END
+}
+
+int gw_hierarchy_export(gw_hierarchy H, int level, int *agg, unsigned char *root, int *a_rowptr, int *a_col,
+                        double *a_val, int *p_rowptr, int *p_col, double *p_val, void *stream)
+{
+    GW_API_BEGIN
+    if (!H) fail(GW_ERR_ARG, "gw_hierarchy_export: null hierarchy");
+    Hier &hh = H->H;
+    if (level < 0 || level >= hh.L) fail(GW_ERR_ARG, "gw_hierarchy_export: level out of range");
+    DeviceGuard g(hh.dev);
+    cudaStream_t st = (cudaStream_t)stream;
+    const DCSR &A = level == 0 ? *hh.A0 : hh.A[(size_t)level];
+    const size_t n = (size_t)A.nr;
+    if (agg && hh.agg[(size_t)level].p) to_device(agg, hh.agg[(size_t)level].p, n * sizeof(int), st);
+    if (root && hh.root[(size_t)level].p) to_device(root, hh.root[(size_t)level].p, n, st);
+    if (a_rowptr) to_device(a_rowptr, A.rp.p, (n + 1) * sizeof(int), st);
+    if (a_col) to_device(a_col, A.ci.p, (size_t)A.nnz * sizeof(int), st);
+    if (a_val) to_device(a_val, A.v.p, (size_t)A.nnz * sizeof(double), st);
+    if (level < hh.L - 1) {
+        const DCSR &P = hh.P[(size_t)level];
+        if (p_rowptr) to_device(p_rowptr, P.rp.p, (n + 1) * sizeof(int), st);
+        if (p_col) to_device(p_col, P.ci.p, (size_t)P.nnz * sizeof(int), st);
+        if (p_val) to_device(p_val, P.v.p, (size_t)P.nnz * sizeof(double), st);
+    }
+    GW_CUDA(cudaStreamSynchronize(st));
+    GW_API_END
+}
+
+void gw_matrix_free(gw_matrix A)
+{
+    if (!A) return;
+    try {
+        DeviceGuard g(A->dev);
+        delete A;
+    } catch (...) {
+    }
+}
+
+void gw_hierarchy_free(gw_hierarchy H)
+{
+    if (!H) return;
+    try {
+        DeviceGuard g(H->H.dev);
+        delete H;
+    } catch (...) {
+    }
+}
+
+}  // extern "C"

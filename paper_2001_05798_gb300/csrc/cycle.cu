@@ -1,0 +1,639 @@
+// cycle.cu -- the V-cycle preconditioner and the outer conjugate-gradient loop.
+//
+// V-cycle (Introduction): on each level a smoothing step and the residual,
+// restriction of the residual to the next level, a direct solve on the
+// coarsest level, interpolation and correction on the way up, and a final
+// smoothing step; the passes are sparse matrix-vector products.  The
+// smoothers are damped Jacobi (weight 4/3 over the Gershgorin bound) or
+// Chebyshev polynomials of D^-1 A (Adams et al. 2003), fused with the residual
+// they need.  The coarsest level multiplies by its dense FP64 inverse.
+//
+// CG (Saad, Algorithm 9.1) runs in FP64 with all scalars on the device: dot
+// products are reduced deterministically (fixed grid, per-block partial sums,
+// the last block to arrive adds them in a fixed order) and every kernel
+// leaves at once when the control block says the solve has finished, so a
+// captured graph of several iterations can be replayed without a host round
+// trip per iteration.
+#include "gw_internal.cuh"
+
+namespace gw {
+
+constexpr int BS = 256;
+
+static inline int vgrid(long long n)
+{
+    long long b = (n + BS - 1) / BS;
+    return (int)std::max(1LL, std::min<long long>(b, RED_MAX_BLOCKS));
+}
+
+#define ROWS(i, n) for (int i = blockIdx.x * BS + threadIdx.x; i < (n); i += gridDim.x * BS)
+
+// ---------------------------------------------------------------- sliced ELL --
+template <class T>
+struct SV {
+    const int *__restrict__ sp;
+    const int *__restrict__ ci;
+    const T *__restrict__ v;
+    int nr;
+};
+
+template <class T>
+static SV<T> view(const Sell<T> &S)
+{
+    return SV<T>{S.sp.p, S.ci.p, S.v.p, S.nr};
+}
+
+template <class T>
+struct VecT;
+template <>
+struct VecT<float> {
+    using V = float4;
+    using I = int4;
+};
+template <>
+struct VecT<double> {
+    using V = double2;
+    using I = int2;
+};
+
+// sum over the slots of row r of a_rk * f(col_k), in slot order
+template <class T, class F>
+__device__ __forceinline__ T sell_row(const SV<T> &A, int r, F f)
+{
+    using VV = typename VecT<T>::V;
+    using VI = typename VecT<T>::I;
+    constexpr int V = SellV<T>::V;
+    const int s = r >> 5, lane = r & 31;
+    const int base = A.sp[s];
+    const int nch = (A.sp[s + 1] - base) / (SELL_C * V);
+    const VV *vv = reinterpret_cast<const VV *>(A.v + base) + lane;
+    const VI *cc = reinterpret_cast<const VI *>(A.ci + base) + lane;
+    T acc = 0;
+    for (int c = 0; c < nch; ++c) {
+        const VV a = __ldg(vv + c * SELL_C);
+        const VI j = __ldg(cc + c * SELL_C);
+        if constexpr (V == 4) {
+            acc += a.x * f(j.x);
+            acc += a.y * f(j.y);
+            acc += a.z * f(j.z);
+            acc += a.w * f(j.w);
+        } else {
+            acc += a.x * f(j.x);
+            acc += a.y * f(j.y);
+        }
+    }
+    return acc;
+}
+
+// ------------------------------------------------------------- reductions --
+__device__ __forceinline__ double warp_sum(double v)
+{
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+// block sum in a fixed order (shuffle tree, then warp 0 adds the 8 warp sums)
+__device__ __forceinline__ double block_sum(double v, double *sh)
+{
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (w == 0) {
+        t = lane < BS / 32 ? sh[lane] : 0.0;
+        t = warp_sum(t);
+    }
+    return t;  // valid in thread 0
+}
+
+// Writes this block's partial sums; returns true in the last block to arrive,
+// which then holds the grand totals (summed over blocks in index order) in tot[].
+template <int K>
+__device__ __forceinline__ bool reduce_last(const double (&loc)[K], double *part, unsigned *cnt, double (&tot)[K])
+{
+    __shared__ double sh[32];
+    __shared__ unsigned ticket;
+    for (int k = 0; k < K; ++k) {
+        double s = block_sum(loc[k], sh);
+        if (threadIdx.x == 0) part[(size_t)k * gridDim.x + blockIdx.x] = s;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) ticket = atomicAdd(cnt, 1u);
+    __syncthreads();
+    if (ticket != gridDim.x - 1) return false;
+    __threadfence();
+    for (int k = 0; k < K; ++k) {
+        double s = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += BS) s += __ldcg(part + (size_t)k * gridDim.x + b);
+        tot[k] = block_sum(s, sh);
+    }
+    if (threadIdx.x == 0) *cnt = 0u;
+    return true;
+}
+
+__device__ __forceinline__ bool finished(const Ctl *c) { return c && *(volatile const int *)&c->done; }
+
+// ------------------------------------------------------- V-cycle kernels --
+// Epilogue of the last kernel of a preconditioner application inside CG:
+// rz = (r, z); mode 1 also forms beta (flexible: -alpha (q,z) / rz_old).
+__device__ __forceinline__ void cg_rz_epilogue(double lrz, double lqz, double *part, Ctl *c, int mode)
+{
+    if (!c) return;
+    double loc[2] = {lrz, lqz}, tot[2];
+    if (reduce_last<2>(loc, part, &c->cnt[0], tot) && threadIdx.x == 0) {
+        const double rz_new = tot[0];
+        if (mode == 1) {
+            const double beta = c->flexible ? -c->alpha * tot[1] / c->rz : rz_new / c->rz;
+            c->beta = beta;
+            if (!isfinite(beta) || !isfinite(rz_new)) {
+                c->status = GW_ERR_BREAKDOWN;
+                c->done = 1;
+            }
+        }
+        c->rz = rz_new;
+    }
+}
+
+// x = dw * b ; r = b - A x   (first Jacobi step from zero, fused with the residual)
+template <class T, class BT>
+__global__ void __launch_bounds__(BS) k_jac0_res(SV<T> A, const T *__restrict__ dw, const BT *__restrict__ b,
+                                                 T *__restrict__ x, T *__restrict__ r, const Ctl *ctl)
+{
+    if (finished(ctl)) return;
+    ROWS(i, A.nr)
+    {
+        const T bi = (T)b[i];
+        const T ax = sell_row(A, i, [&](int j) { return __ldg(dw + j) * (T)__ldg(b + j); });
+        x[i] = __ldg(dw + i) * bi;
+        r[i] = bi - ax;
+    }
+}
+
+// xo = xi + dw * (b - A xi); xi == nullptr means xi = 0.  OUT = double with
+// DOT: xo is the preconditioned residual z of CG and (b, z) is reduced.
+template <class T, class BT, class OT, bool DOT>
+__global__ void __launch_bounds__(BS) k_jacobi(SV<T> A, const T *__restrict__ dw, const BT *__restrict__ b,
+                                               const T *__restrict__ xi, OT *__restrict__ xo,
+                                               const double *__restrict__ q, double *part, Ctl *ctl, int mode)
+{
+    if (finished(ctl)) return;
+    double lrz = 0.0, lqz = 0.0;
+    ROWS(i, A.nr)
+    {
+        const T bi = (T)b[i];
+        T xn;
+        if (xi) {
+            const T ax = sell_row(A, i, [&](int j) { return __ldg(xi + j); });
+            xn = xi[i] + __ldg(dw + i) * (bi - ax);
+        } else {
+            xn = __ldg(dw + i) * bi;
+        }
+        xo[i] = (OT)xn;
+        if constexpr (DOT) {
+            lrz += (double)b[i] * (double)xn;
+            if (q) lqz += q[i] * (double)xn;
+        }
+    }
+    if constexpr (DOT) cg_rz_epilogue(lrz, lqz, part, ctl, mode);
+}
+
+// r = b - A x
+template <class T, class BT>
+__global__ void __launch_bounds__(BS) k_residual(SV<T> A, const BT *__restrict__ b, const T *__restrict__ x,
+                                                 T *__restrict__ r, const Ctl *ctl)
+{
+    if (finished(ctl)) return;
+    ROWS(i, A.nr)
+    {
+        const T ax = sell_row(A, i, [&](int j) { return __ldg(x + j); });
+        r[i] = (T)b[i] - ax;
+    }
+}
+
+// y = M x (restriction R r)
+template <class T>
+__global__ void __launch_bounds__(BS) k_spmv(SV<T> M, const T *__restrict__ x, T *__restrict__ y, const Ctl *ctl)
+{
+    if (finished(ctl)) return;
+    ROWS(i, M.nr) y[i] = sell_row(M, i, [&](int j) { return __ldg(x + j); });
+}
+
+// x += P e (interpolate and correct)
+template <class T>
+__global__ void __launch_bounds__(BS) k_prolong(SV<T> P, const T *__restrict__ e, T *__restrict__ x, const Ctl *ctl)
+{
+    if (finished(ctl)) return;
+    ROWS(i, P.nr) x[i] += sell_row(P, i, [&](int j) { return __ldg(e + j); });
+}
+
+// x = Ainv b on the coarsest level (dense FP64 inverse), one warp per row
+template <class T>
+__global__ void __launch_bounds__(BS) k_coarse(int n, const double *__restrict__ Ainv, const T *__restrict__ b,
+                                               T *__restrict__ x, const Ctl *ctl)
+{
+    if (finished(ctl)) return;
+    const int lane = threadIdx.x & 31;
+    for (int row = (blockIdx.x * BS + threadIdx.x) >> 5; row < n; row += (gridDim.x * BS) >> 5) {
+        const double *a = Ainv + (size_t)row * n;
+        double s = 0.0;
+        for (int j = lane; j < n; j += 32) s += a[j] * (double)b[j];
+        s = warp_sum(s);
+        if (lane == 0) x[row] = (T)s;
+    }
+}
+
+// Chebyshev first step: r = b - A x (r = b when x0zero), d = c0 dw r.  x is
+// gathered here, so it is not written in place: with x0zero x = d; otherwise
+// the next step (or k_axpy) adds d.  DOT: xo = x + d is the CG's z.
+template <class T, class BT, class OT, bool DOT>
+__global__ void __launch_bounds__(BS) k_cheb0(SV<T> A, const T *__restrict__ dw, const BT *__restrict__ b, T *x,
+                                              T *__restrict__ r, T *__restrict__ d, OT *__restrict__ xo, T c0,
+                                              int x0zero, const double *__restrict__ q, double *part, Ctl *ctl,
+                                              int mode)
+{
+    if (finished(ctl)) return;
+    double lrz = 0.0, lqz = 0.0;
+    ROWS(i, A.nr)
+    {
+        const T bi = (T)b[i];
+        T ri = bi;
+        if (!x0zero) ri -= sell_row(A, i, [&](int j) { return __ldg(x + j); });
+        const T di = c0 * (__ldg(dw + i) * ri);
+        r[i] = ri;
+        d[i] = di;
+        if constexpr (DOT) {
+            const T xn = (x0zero ? (T)0 : x[i]) + di;
+            xo[i] = (OT)xn;
+            lrz += (double)b[i] * (double)xn;
+            if (q) lqz += q[i] * (double)xn;
+        } else {
+            if (x0zero) x[i] = di;
+        }
+    }
+    if constexpr (DOT) cg_rz_epilogue(lrz, lqz, part, ctl, mode);
+}
+
+// Chebyshev step k >= 2: r -= A d; dn = c1 d + c2 dw r; x += (add_prev ? d : 0) + dn
+template <class T, class OT, bool DOT>
+__global__ void __launch_bounds__(BS) k_chebk(SV<T> A, const T *__restrict__ dw, T *__restrict__ r,
+                                              const T *__restrict__ d, T *__restrict__ dn, T *x, OT *__restrict__ xo,
+                                              T c1, T c2, int add_prev, const double *__restrict__ b0,
+                                              const double *__restrict__ q, double *part, Ctl *ctl, int mode)
+{
+    if (finished(ctl)) return;
+    double lrz = 0.0, lqz = 0.0;
+    ROWS(i, A.nr)
+    {
+        const T ad = sell_row(A, i, [&](int j) { return __ldg(d + j); });
+        const T ri = r[i] - ad;
+        const T dp = d[i];
+        const T dni = c1 * dp + c2 * (__ldg(dw + i) * ri);
+        const T xn = x[i] + (add_prev ? dp : (T)0) + dni;
+        r[i] = ri;
+        dn[i] = dni;
+        if constexpr (DOT) {
+            xo[i] = (OT)xn;
+            lrz += b0[i] * (double)xn;
+            if (q) lqz += q[i] * (double)xn;
+        } else {
+            x[i] = xn;
+        }
+    }
+    if constexpr (DOT) cg_rz_epilogue(lrz, lqz, part, ctl, mode);
+}
+
+template <class T>
+__global__ void __launch_bounds__(BS) k_axpy(int n, const T *__restrict__ d, T *__restrict__ x, const Ctl *ctl)
+{
+    if (finished(ctl)) return;
+    ROWS(i, n) x[i] += d[i];
+}
+
+// ---------------------------------------------------------- V-cycle driver --
+template <class T>
+static void smooth(Hier &H, std::vector<CycLevel<T>> &C, int l, const void *bptr, bool b_is_double, bool x0zero,
+                   bool last, double *zout, Ctl *ctl, const double *q, int mode, cudaStream_t st)
+{
+    CycLevel<T> &lv = C[l];
+    const SV<T> A = view(lv.A);
+    const int g = vgrid(lv.n);
+    const int nu = std::max(1, H.o.nu);
+    const double *b64 = (const double *)bptr;
+    const T *bT = (const T *)bptr;
+    double *part = H.part.p;
+    if (H.o.smoother == GW_SMOOTH_JACOBI) {
+        T *cur = lv.x.p, *nxt = lv.t.p;
+        for (int s = 0; s < nu; ++s) {
+            const bool first = x0zero && s == 0;
+            const bool fin = last && s == nu - 1;
+            const T *xi = first ? nullptr : cur;
+            if (fin) {
+                if (b_is_double)
+                    k_jacobi<T, double, double, true><<<g, BS, 0, st>>>(A, lv.dw.p, b64, xi, zout, q, part, ctl, mode);
+                else
+                    k_jacobi<T, T, double, true><<<g, BS, 0, st>>>(A, lv.dw.p, bT, xi, zout, q, part, ctl, mode);
+            } else {
+                if (b_is_double)
+                    k_jacobi<T, double, T, false><<<g, BS, 0, st>>>(A, lv.dw.p, b64, xi, nxt, q, part, ctl, mode);
+                else
+                    k_jacobi<T, T, T, false><<<g, BS, 0, st>>>(A, lv.dw.p, bT, xi, nxt, q, part, ctl, mode);
+                std::swap(cur, nxt);
+            }
+        }
+        if (cur != lv.x.p) GW_CUDA(cudaMemcpyAsync(lv.x.p, cur, (size_t)lv.n * sizeof(T), cudaMemcpyDeviceToDevice, st));
+        return;
+    }
+    // Chebyshev of degree m, nu times
+    const int m = std::max(1, H.o.degree);
+    for (int s = 0; s < nu; ++s) {
+        const int zero = x0zero && s == 0;
+        const bool fin = last && s == nu - 1;
+        T *d = lv.d.p, *dn = lv.d2.p;
+        if (fin && m == 1) {
+            if (b_is_double)
+                k_cheb0<T, double, double, true><<<g, BS, 0, st>>>(A, lv.dw.p, b64, lv.x.p, lv.r.p, d, zout, (T)lv.c0,
+                                                                   zero, q, part, ctl, mode);
+            else
+                k_cheb0<T, T, double, true><<<g, BS, 0, st>>>(A, lv.dw.p, bT, lv.x.p, lv.r.p, d, zout, (T)lv.c0, zero,
+                                                              q, part, ctl, mode);
+            continue;
+        }
+        if (b_is_double)
+            k_cheb0<T, double, T, false><<<g, BS, 0, st>>>(A, lv.dw.p, b64, lv.x.p, lv.r.p, d, (T *)nullptr,
+                                                           (T)lv.c0, zero, q, part, ctl, mode);
+        else
+            k_cheb0<T, T, T, false><<<g, BS, 0, st>>>(A, lv.dw.p, bT, lv.x.p, lv.r.p, d, (T *)nullptr, (T)lv.c0,
+                                                      zero, q, part, ctl, mode);
+        if (m == 1) {
+            if (!zero) k_axpy<T><<<g, BS, 0, st>>>(lv.n, d, lv.x.p, ctl);
+            continue;
+        }
+        for (int k = 1; k < m; ++k) {
+            const bool f2 = fin && k == m - 1;
+            const int add_prev = (k == 1 && !zero) ? 1 : 0;
+            if (f2)
+                k_chebk<T, double, true><<<g, BS, 0, st>>>(A, lv.dw.p, lv.r.p, d, dn, lv.x.p, zout, (T)lv.c1[k],
+                                                           (T)lv.c2[k], add_prev, b64, q, part, ctl, mode);
+            else
+                k_chebk<T, T, false><<<g, BS, 0, st>>>(A, lv.dw.p, lv.r.p, d, dn, lv.x.p, (T *)nullptr, (T)lv.c1[k],
+                                                       (T)lv.c2[k], add_prev, nullptr, q, part, ctl, mode);
+            std::swap(d, dn);
+        }
+    }
+}
+
+template <class T>
+static void vcycle_t(Hier &H, std::vector<CycLevel<T>> &C, const double *r, double *z, Ctl *ctl, const double *q, int mode,
+                     cudaStream_t st)
+{
+    const int L = H.L;
+    if (L == 1) {
+        // a single level: the dense inverse is the preconditioner
+        fail(GW_ERR_SETUP, "a one-level hierarchy is not supported by the V-cycle");
+    }
+    for (int l = 0; l < L - 1; ++l) {
+        CycLevel<T> &lv = C[l];
+        const SV<T> A = view(lv.A);
+        const int g = vgrid(lv.n);
+        const bool bd = l == 0;
+        const void *bptr = bd ? (const void *)r : (const void *)lv.b.p;
+        if (H.o.smoother == GW_SMOOTH_JACOBI && H.o.nu <= 1) {
+            if (bd) k_jac0_res<T, double><<<g, BS, 0, st>>>(A, lv.dw.p, r, lv.x.p, lv.r.p, ctl);
+            else k_jac0_res<T, T><<<g, BS, 0, st>>>(A, lv.dw.p, lv.b.p, lv.x.p, lv.r.p, ctl);
+        } else {
+            smooth<T>(H, C, l, bptr, bd, true, false, nullptr, ctl, q, mode, st);
+            if (bd) k_residual<T, double><<<g, BS, 0, st>>>(A, r, lv.x.p, lv.r.p, ctl);
+            else k_residual<T, T><<<g, BS, 0, st>>>(A, lv.b.p, lv.x.p, lv.r.p, ctl);
+        }
+        k_spmv<T><<<vgrid(lv.R.nr), BS, 0, st>>>(view(lv.R), lv.r.p, C[l + 1].b.p, ctl);
+        GW_LAUNCH_CHECK();
+    }
+    {
+        CycLevel<T> &lc = C[L - 1];
+        k_coarse<T><<<std::max(1, std::min(2048, (lc.n * 32 + BS - 1) / BS)), BS, 0, st>>>(lc.n, H.Ainv.p, lc.b.p,
+                                                                                         lc.x.p, ctl);
+    }
+    for (int l = L - 2; l >= 0; --l) {
+        CycLevel<T> &lv = C[l];
+        k_prolong<T><<<vgrid(lv.n), BS, 0, st>>>(view(lv.P), C[l + 1].x.p, lv.x.p, ctl);
+        const bool bd = l == 0;
+        const void *bptr = bd ? (const void *)r : (const void *)lv.b.p;
+        smooth<T>(H, C, l, bptr, bd, false, l == 0, z, ctl, q, mode, st);
+        GW_LAUNCH_CHECK();
+    }
+}
+
+void vcycle_enqueue(Hier &H, const double *r, double *z, Ctl *ctl, bool dot, cudaStream_t st)
+{
+    (void)dot;
+    Ctl *c = ctl;
+    if (H.o.prec == GW_PREC_FP64) vcycle_t<double>(H, H.cd, r, z, c, nullptr, 0, st);
+    else vcycle_t<float>(H, H.cf, r, z, c, nullptr, 0, st);
+}
+
+// ---------------------------------------------------------------- CG kernels --
+__global__ void __launch_bounds__(BS) k_cg_init(int n, const double *__restrict__ b, double *__restrict__ x,
+                                                double *__restrict__ r, double *part, Ctl *c, double tol2, int maxit,
+                                                int flexible)
+{
+    double loc[1] = {0.0}, tot[1];
+    ROWS(i, n)
+    {
+        const double bi = b[i];
+        x[i] = 0.0;
+        r[i] = bi;
+        loc[0] += bi * bi;
+    }
+    if (reduce_last<1>(loc, part, &c->cnt[0], tot) && threadIdx.x == 0) {
+        c->bnorm2 = tot[0];
+        c->tol2 = tol2;
+        c->maxit = maxit;
+        c->flexible = flexible;
+        c->it = 0;
+        c->check = 0;
+        c->status = GW_OK;
+        c->rz = c->pq = c->alpha = c->beta = c->rr = c->rt2 = c->qz = 0.0;
+        c->relres = tot[0] > 0.0 ? 1.0 : 0.0;
+        c->done = tot[0] > 0.0 ? 0 : 1;
+    }
+}
+
+__global__ void __launch_bounds__(BS) k_copy(int n, const double *__restrict__ a, double *__restrict__ b, const Ctl *c)
+{
+    if (finished(c)) return;
+    ROWS(i, n) b[i] = a[i];
+}
+
+// q = A p, pq = (p, q); alpha = rz / pq
+__global__ void __launch_bounds__(BS) k_cg_spmv_dot(SV<double> A, const double *__restrict__ p,
+                                                    double *__restrict__ q, double *part, Ctl *c)
+{
+    if (finished(c)) return;
+    if (c->it >= c->maxit) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            c->status = GW_ERR_NOT_CONVERGED;
+            c->done = 1;
+        }
+        return;
+    }
+    double loc[1] = {0.0}, tot[1];
+    ROWS(i, A.nr)
+    {
+        const double qi = sell_row(A, i, [&](int j) { return __ldg(p + j); });
+        q[i] = qi;
+        loc[0] += p[i] * qi;
+    }
+    if (reduce_last<1>(loc, part, &c->cnt[0], tot) && threadIdx.x == 0) {
+        const double pq = tot[0];
+        c->pq = pq;
+        c->it += 1;
+        if (!(pq > 0.0) || !isfinite(pq)) {
+            c->status = GW_ERR_BREAKDOWN;
+            c->done = 1;
+        } else {
+            c->alpha = c->rz / pq;
+        }
+    }
+}
+
+// x += alpha p; r -= alpha q; rr = (r, r)
+__global__ void __launch_bounds__(BS) k_cg_update(int n, double *__restrict__ x, double *__restrict__ r,
+                                                  const double *__restrict__ p, const double *__restrict__ q,
+                                                  double *part, Ctl *c)
+{
+    if (finished(c)) return;
+    const double a = c->alpha;
+    double loc[1] = {0.0}, tot[1];
+    ROWS(i, n)
+    {
+        x[i] += a * p[i];
+        const double ri = r[i] - a * q[i];
+        r[i] = ri;
+        loc[0] += ri * ri;
+    }
+    if (reduce_last<1>(loc, part, &c->cnt[0], tot) && threadIdx.x == 0) {
+        c->rr = tot[0];
+        if (!isfinite(tot[0])) {
+            c->status = GW_ERR_BREAKDOWN;
+            c->done = 1;
+        } else if (tot[0] <= c->tol2 * c->bnorm2) {
+            c->check = 1;
+        }
+    }
+}
+
+// when the recursive residual passed: r = b - A x in FP64; stop if it passes too
+__global__ void __launch_bounds__(BS) k_cg_true(SV<double> A, const double *__restrict__ b,
+                                                const double *__restrict__ x, double *__restrict__ r, double *part,
+                                                Ctl *c, int force)
+{
+    if (!force && (finished(c) || !c->check)) return;
+    double loc[1] = {0.0}, tot[1];
+    ROWS(i, A.nr)
+    {
+        const double ri = b[i] - sell_row(A, i, [&](int j) { return __ldg(x + j); });
+        if (!force) r[i] = ri;
+        loc[0] += ri * ri;
+    }
+    if (reduce_last<1>(loc, part, &c->cnt[0], tot) && threadIdx.x == 0) {
+        c->rt2 = tot[0];
+        const double rel = c->bnorm2 > 0.0 ? sqrt(tot[0] / c->bnorm2) : 0.0;
+        if (force) {
+            c->relres = rel;
+        } else if (tot[0] <= c->tol2 * c->bnorm2) {
+            c->relres = rel;
+            c->status = GW_OK;
+            c->done = 1;
+        } else {
+            c->check = 0;
+        }
+    }
+}
+
+// p = z + beta p
+__global__ void __launch_bounds__(BS) k_cg_p(int n, const double *__restrict__ z, double *__restrict__ p, const Ctl *c)
+{
+    if (finished(c)) return;
+    const double beta = c->beta;
+    ROWS(i, n) p[i] = z[i] + beta * p[i];
+}
+
+// ------------------------------------------------------------------ CG loop --
+static const SV<double> fine64(Hier &H)
+{
+    return H.o.prec == GW_PREC_FP64 ? view(H.cd[0].A) : view(H.A64);
+}
+
+static void cg_iteration(Hier &H, cudaStream_t st)
+{
+    const int n = H.n, g = vgrid(n);
+    Ctl *c = H.ctl.p;
+    const SV<double> A = fine64(H);
+    k_cg_spmv_dot<<<g, BS, 0, st>>>(A, H.p.p, H.q.p, H.part.p, c);
+    k_cg_update<<<g, BS, 0, st>>>(n, H.x.p, H.r.p, H.p.p, H.q.p, H.part.p, c);
+    k_cg_true<<<g, BS, 0, st>>>(A, H.b.p, H.x.p, H.r.p, H.part.p, c, 0);
+    const double *q = H.o.prec == GW_PREC_FP64 ? nullptr : H.q.p;
+    if (H.o.prec == GW_PREC_FP64) vcycle_t<double>(H, H.cd, H.r.p, H.z.p, c, q, 1, st);
+    else vcycle_t<float>(H, H.cf, H.r.p, H.z.p, c, q, 1, st);
+    k_cg_p<<<g, BS, 0, st>>>(n, H.z.p, H.p.p, c);
+    GW_LAUNCH_CHECK();
+}
+
+static constexpr int GRAPH_ITERS = 4;
+
+static void ensure_graph(Hier &H)
+{
+    if (H.gexec) return;
+    if (!H.cap) GW_CUDA(cudaStreamCreateWithFlags(&H.cap, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    GW_CUDA(cudaStreamBeginCapture(H.cap, cudaStreamCaptureModeThreadLocal));
+    try {
+        for (int k = 0; k < GRAPH_ITERS; ++k) cg_iteration(H, H.cap);
+    } catch (...) {
+        cudaStreamEndCapture(H.cap, &g);
+        if (g) cudaGraphDestroy(g);
+        throw;
+    }
+    GW_CUDA(cudaStreamEndCapture(H.cap, &g));
+    cudaError_t e = cudaGraphInstantiate(&H.gexec, g, 0);
+    cudaGraphDestroy(g);
+    GW_CUDA(e);
+    H.graph_iters = GRAPH_ITERS;
+}
+
+int pcg_run(Hier &H, double tol, int maxit, int *iters, double *relres, cudaStream_t st)
+{
+    const int n = H.n, g = vgrid(n);
+    Ctl *c = H.ctl.p;
+    ensure_graph(H);
+    const int flexible = H.o.prec == GW_PREC_FP64 ? 0 : 1;
+    k_cg_init<<<g, BS, 0, st>>>(n, H.b.p, H.x.p, H.r.p, H.part.p, c, tol * tol, maxit, flexible);
+    GW_LAUNCH_CHECK();
+    // z = M r, rz = (r, z), p = z
+    if (H.o.prec == GW_PREC_FP64) vcycle_t<double>(H, H.cd, H.r.p, H.z.p, c, nullptr, 0, st);
+    else vcycle_t<float>(H, H.cf, H.r.p, H.z.p, c, nullptr, 0, st);
+    k_copy<<<g, BS, 0, st>>>(n, H.z.p, H.p.p, c);
+    GW_LAUNCH_CHECK();
+    const int max_launches = (maxit + GRAPH_ITERS - 1) / GRAPH_ITERS + 2;
+    for (int k = 0; k < max_launches; ++k) {
+        GW_CUDA(cudaGraphLaunch(H.gexec, st));
+        GW_CUDA(cudaMemcpyAsync(H.ctl_host, c, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+        GW_CUDA(cudaStreamSynchronize(st));
+        if (H.ctl_host->done) break;
+    }
+    if (H.ctl_host->status == GW_ERR_NOT_CONVERGED || !H.ctl_host->done) {
+        k_cg_true<<<g, BS, 0, st>>>(fine64(H), H.b.p, H.x.p, H.r.p, H.part.p, c, 1);
+        GW_LAUNCH_CHECK();
+        GW_CUDA(cudaMemcpyAsync(H.ctl_host, c, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+        GW_CUDA(cudaStreamSynchronize(st));
+        if (!H.ctl_host->done) H.ctl_host->status = GW_ERR_NOT_CONVERGED;
+    }
+    if (iters) *iters = H.ctl_host->it;
+    if (relres) *relres = H.ctl_host->relres;
+    return H.ctl_host->status;
+}
+
+}  // namespace gw

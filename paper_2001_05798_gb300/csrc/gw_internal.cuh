@@ -1,0 +1,194 @@
+// gw_internal.cuh -- internal types and helpers of libgw (CUDA, sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "gw.h"
+
+namespace gw {
+
+// ------------------------------------------------------------------ errors --
+struct Error {
+    int code;
+    std::string msg;
+};
+
+[[noreturn]] void fail(int code, const char *fmt, ...);
+void set_last_error(const char *msg);
+const char *last_error_cstr();
+
+#define GW_CUDA(call)                                                                                 \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess)                                                                        \
+            ::gw::fail(e_ == cudaErrorMemoryAllocation ? GW_ERR_OOM : GW_ERR_CUDA, "%s: %s (%s:%d)", \
+                       #call, cudaGetErrorString(e_), __FILE__, __LINE__);                            \
+    } while (0)
+
+#define GW_LAUNCH_CHECK() GW_CUDA(cudaGetLastError())
+
+// ---------------------------------------------------------- device buffers --
+template <class T>
+struct DBuf {
+    T *p = nullptr;
+    size_t n = 0;
+    DBuf() = default;
+    explicit DBuf(size_t n_) { alloc(n_); }
+    void alloc(size_t n_)
+    {
+        release();
+        n = n_;
+        if (n) GW_CUDA(cudaMalloc((void **)&p, n * sizeof(T)));
+    }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    ~DBuf() { release(); }
+    DBuf(const DBuf &) = delete;
+    DBuf &operator=(const DBuf &) = delete;
+    DBuf(DBuf &&o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+    DBuf &operator=(DBuf &&o) noexcept
+    {
+        if (this != &o) {
+            release();
+            p = o.p;
+            n = o.n;
+            o.p = nullptr;
+            o.n = 0;
+        }
+        return *this;
+    }
+    size_t bytes() const { return n * sizeof(T); }
+};
+
+// FP64 CSR on the device, columns ascending within each row.
+struct DCSR {
+    int nr = 0, nc = 0, nnz = 0;
+    DBuf<int> rp, ci;
+    DBuf<double> v;
+    size_t bytes() const { return rp.bytes() + ci.bytes() + v.bytes(); }
+};
+
+// Sliced ELL with slices of 32 rows.  Row r = 32*s + lane; slot k of that row
+// lives at sp[s] + (k / V) * 32 * V + lane * V + (k % V), so one thread loads
+// V consecutive slots of its row with one 16-byte (or 8-byte for indices of
+// the FP64 form) load and a warp reads 32 * 16 contiguous bytes.  Padding
+// slots hold column = row (or 0 for a rectangular matrix) and value 0.
+constexpr int SELL_C = 32;
+
+template <class T>
+struct SellV;
+template <>
+struct SellV<float> {
+    static constexpr int V = 4;
+};
+template <>
+struct SellV<double> {
+    static constexpr int V = 2;
+};
+
+template <class T>
+struct Sell {
+    int nr = 0, nc = 0, nslices = 0;
+    long long stored = 0, nnz = 0;
+    DBuf<int> sp;  // nslices + 1 slice offsets (elements)
+    DBuf<int> ci;
+    DBuf<T> v;
+    size_t bytes() const { return sp.bytes() + ci.bytes() + v.bytes(); }
+};
+
+// ------------------------------------------------------------ CG control --
+// Scalars of the CG recurrence live on the device so that an iteration needs
+// no host round trip.
+struct Ctl {
+    double bnorm2, tol2;
+    double rz, pq, alpha, beta, rr, rt2, relres, qz;
+    int it, maxit, done, status, check, flexible;
+    unsigned int cnt[8];  // arrival counters of the last-block reductions
+};
+
+constexpr int RED_MAX_BLOCKS = 2048;
+
+// ------------------------------------------------------------ scan / misc --
+void exclusive_scan(const int *in, int *out, int n, cudaStream_t st);  // out[n] = total
+int read_int(const int *dptr, cudaStream_t st);
+void to_device(void *dst, const void *src, size_t bytes, cudaStream_t st);
+bool is_device_ptr(const void *p);
+
+// -------------------------------------------------------------- assembly --
+void assemble_csr(int nx, int ny, int nz, double dx, double dy, double dz, const double *Kx, const double *Ky,
+                  const double *Kz, const int *bct, const double *bcv, const double *q, DCSR &A, double *b,
+                  int *dflag, cudaStream_t st);
+
+// ----------------------------------------------------------------- setup --
+struct LevelSetupOut {
+    int nagg = 0, rounds = 0;
+    double omega = 0, rho = 0;
+};
+void setup_strength(const DCSR &A, double theta2, DBuf<unsigned char> &S, cudaStream_t st);
+int setup_mis2(const DCSR &A, const unsigned char *S, uint64_t seed, int level, DBuf<unsigned char> &root,
+               cudaStream_t st);  // returns rounds
+int setup_aggregate(const DCSR &A, const unsigned char *S, const unsigned char *root, uint64_t seed, int level,
+                    DBuf<int> &agg, cudaStream_t st);  // returns nagg
+void setup_smooth_p(const DCSR &A, const unsigned char *S, const int *agg, int nagg, DCSR &P, double *omega,
+                    double *rho, cudaStream_t st);
+void setup_transpose(const DCSR &P, DCSR &R, cudaStream_t st);
+void setup_spgemm(const DCSR &L, const DCSR &Rm, DCSR &C, cudaStream_t st);
+void setup_dense_inverse(const DCSR &A, DBuf<double> &Ainv, cudaStream_t st);
+double setup_gershgorin(const DCSR &A, DBuf<double> &diag, cudaStream_t st);  // max_i sum|a_ij|/a_ii
+double setup_power_lambda(const DCSR &A, const double *diag, uint64_t seed, int level, cudaStream_t st);
+
+template <class T>
+void to_sell(const DCSR &A, Sell<T> &S, cudaStream_t st);
+
+// ---------------------------------------------------------------- cycle --
+// Storage of one level of the V-cycle in the cycle's precision T.
+template <class T>
+struct CycLevel {
+    int n = 0;
+    Sell<T> A, P, R;     // A_l, P_l (n x n_{l+1}), R_l = P_l^T
+    DBuf<T> dw;          // Jacobi: w / a_ii; Chebyshev: 1 / a_ii
+    DBuf<T> x, b, r, t, d, d2;
+    double c0 = 0.0, c1[8] = {0}, c2[8] = {0};  // Chebyshev coefficients
+};
+
+struct Hier {
+    int dev = 0;
+    gw_amg_opts o{};
+    const DCSR *A0 = nullptr;  // level-0 FP64 CSR (owned by the matrix handle)
+    int L = 0;
+    std::vector<DCSR> A;       // A[l] for l >= 1 (A[0] is *A0)
+    std::vector<DCSR> P;       // P[l] for l < L-1
+    std::vector<DBuf<int>> agg;
+    std::vector<DBuf<unsigned char>> root;
+    std::vector<gw_level_info> info;
+    std::vector<CycLevel<float>> cf;
+    std::vector<CycLevel<double>> cd;
+    Sell<double> A64;          // level-0 FP64 matrix of the outer CG (mixed precision)
+    DBuf<double> Ainv;         // dense inverse of the coarsest level, row-major
+    // outer CG
+    int n = 0;
+    DBuf<double> x, r, p, q, z, b, part;
+    DBuf<Ctl> ctl;
+    Ctl *ctl_host = nullptr;   // pinned mirror of the control block
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int graph_iters = 0;
+    ~Hier();
+};
+
+void build_hierarchy(Hier &H, cudaStream_t st);
+void vcycle_enqueue(Hier &H, const double *r, double *z, Ctl *ctl, bool dot, cudaStream_t st);
+int pcg_run(Hier &H, double tol, int maxit, int *iters, double *relres, cudaStream_t st);
+
+}  // namespace gw

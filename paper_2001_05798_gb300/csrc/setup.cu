@@ -1,0 +1,989 @@
+// setup.cu -- the AMG setup phase on the GPU (Introduction: the hierarchy,
+// prolongation and restriction are built automatically; "CG/AMG/SA" smoothed
+// aggregation, Results section).
+//
+// Stages per level: symmetrised strength of connection, distance-2 maximal
+// independent set by parallel rounds with hashed priorities, aggregation,
+// filtered matrix and Gershgorin bound, Jacobi-smoothed prolongator,
+// transpose, Galerkin product by a two-pass SpGEMM.  Then the dense inverse of
+// the coarsest level and the conversion of every level to sliced ELL.
+//
+// Every floating-point operation that decides the hierarchy is an explicitly
+// rounded intrinsic (__dmul_rn, __dadd_rn, __ddiv_rn), so no multiply-add is
+// fused, and every sum runs in ascending column order of its row -- the same
+// order a serial FP64 implementation follows -- so aggregates, patterns and
+// values match such an implementation exactly.
+#include <string.h>
+
+#include "gw_internal.cuh"
+
+namespace gw {
+
+static inline int nblk(long long n, int bs, long long cap = 152LL * 32)
+{
+    long long b = (n + bs - 1) / bs;
+    return (int)std::max(1LL, std::min(b, cap));
+}
+
+#define GRID_STRIDE(i, n) for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (n); i += (long long)gridDim.x * blockDim.x)
+
+// SplitMix64 (Steele, Lea & Flood 2014): finaliser of x + golden gamma.
+__device__ __forceinline__ uint64_t smix64(uint64_t x)
+{
+    uint64_t z = x + 0x9e3779b97f4a7c15ULL;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ uint64_t prio_key(uint64_t seed, int level, int i)
+{
+    return smix64(seed ^ ((uint64_t)level << 48) ^ (uint64_t)(uint32_t)i);
+}
+
+__device__ __forceinline__ bool prio_gt(uint64_t k1, int i1, uint64_t k2, int i2)
+{
+    return k1 > k2 || (k1 == k2 && i1 > i2);
+}
+
+// ----------------------------------------------------------------- strength --
+__global__ void k_diag(int n, const int *__restrict__ rp, const int *__restrict__ ci, const double *__restrict__ v,
+                       double *__restrict__ d)
+{
+    GRID_STRIDE(ii, n)
+    {
+        const int i = (int)ii;
+        double dd = 0.0;
+        for (int e = rp[i]; e < rp[i + 1]; ++e)
+            if (ci[e] == i) {
+                dd = v[e];
+                break;
+            }
+        d[i] = dd;
+    }
+}
+
+// (i,j) strong iff a_ij^2 > theta2 * (a_ii * a_jj), i != j
+__global__ void k_strength_raw(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                               const double *__restrict__ v, const double *__restrict__ d, double theta2,
+                               unsigned char *__restrict__ raw)
+{
+    GRID_STRIDE(ii, n)
+    {
+        const int i = (int)ii;
+        const double di = d[i];
+        for (int e = rp[i]; e < rp[i + 1]; ++e) {
+            const int j = ci[e];
+            if (j == i) {
+                raw[e] = 0;
+                continue;
+            }
+            const double a = v[e];
+            const double lhs = __dmul_rn(a, a);
+            double rhs = __dmul_rn(di, d[j]);
+            rhs = __dmul_rn(theta2, rhs);
+            raw[e] = lhs > rhs;
+        }
+    }
+}
+
+__device__ __forceinline__ int row_find(const int *__restrict__ rp, const int *__restrict__ ci, int row, int col)
+{
+    int lo = rp[row], hi = rp[row + 1] - 1;
+    while (lo <= hi) {
+        int mid = (lo + hi) >> 1;
+        int c = ci[mid];
+        if (c == col) return mid;
+        if (c < col) lo = mid + 1;
+        else hi = mid - 1;
+    }
+    return -1;
+}
+
+// S = raw OR raw^T
+__global__ void k_strength_sym(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                               const unsigned char *__restrict__ raw, unsigned char *__restrict__ S)
+{
+    GRID_STRIDE(ii, n)
+    {
+        const int i = (int)ii;
+        for (int e = rp[i]; e < rp[i + 1]; ++e) {
+            const int j = ci[e];
+            unsigned char s = raw[e];
+            if (!s && j != i) {
+                int t = row_find(rp, ci, j, i);
+                if (t >= 0) s = raw[t];
+            }
+            S[e] = s;
+        }
+    }
+}
+
+void setup_strength(const DCSR &A, double theta2, DBuf<unsigned char> &S, cudaStream_t st)
+{
+    DBuf<double> d((size_t)A.nr);
+    DBuf<unsigned char> raw((size_t)A.nnz + 1);
+    S.alloc((size_t)A.nnz + 1);
+    k_diag<<<nblk(A.nr, 256), 256, 0, st>>>(A.nr, A.rp.p, A.ci.p, A.v.p, d.p);
+    k_strength_raw<<<nblk(A.nr, 256), 256, 0, st>>>(A.nr, A.rp.p, A.ci.p, A.v.p, d.p, theta2, raw.p);
+    k_strength_sym<<<nblk(A.nr, 256), 256, 0, st>>>(A.nr, A.rp.p, A.ci.p, raw.p, S.p);
+    GW_LAUNCH_CHECK();
+    GW_CUDA(cudaStreamSynchronize(st));
+}
+
+// -------------------------------------------------------------------- MIS-2 --
+// Parallel rounds with fixed priorities (key, index).  A node joins the set
+// when it beats every undecided node within two hops of the strength graph
+// (the hops pass through nodes in any state); nodes within two hops of a
+// selected node leave.  With fixed priorities this yields the same set as
+// visiting the nodes in descending priority (Blelloch, Fineman & Shun 2012).
+enum : unsigned char { MIS_UNDECIDED = 0, MIS_ROOT = 1, MIS_OUT = 2 };
+
+__global__ void k_mis_max1(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                           const unsigned char *__restrict__ S, const unsigned char *__restrict__ state,
+                           uint64_t seed, int level, unsigned long long *__restrict__ mk, int *__restrict__ mi)
+{
+    GRID_STRIDE(ii, n)
+    {
+        const int i = (int)ii;
+        uint64_t bk = 0;
+        int bi = -1;
+        if (state[i] == MIS_UNDECIDED) {
+            bk = prio_key(seed, level, i);
+            bi = i;
+        }
+        for (int e = rp[i]; e < rp[i + 1]; ++e) {
+            if (!S[e]) continue;
+            const int j = ci[e];
+            if (state[j] != MIS_UNDECIDED) continue;
+            const uint64_t k = prio_key(seed, level, j);
+            if (bi < 0 || prio_gt(k, j, bk, bi)) {
+                bk = k;
+                bi = j;
+            }
+        }
+        mk[i] = bk;
+        mi[i] = bi;
+    }
+}
+
+__global__ void k_mis_select(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                             const unsigned char *__restrict__ S, unsigned char *__restrict__ state,
+                             const unsigned long long *__restrict__ mk, const int *__restrict__ mi)
+{
+    GRID_STRIDE(ii, n)
+    {
+        const int i = (int)ii;
+        if (state[i] != MIS_UNDECIDED) continue;
+        uint64_t bk = mk[i];
+        int bi = mi[i];
+        for (int e = rp[i]; e < rp[i + 1]; ++e) {
+            if (!S[e]) continue;
+            const int j = ci[e];
+            const int ji = mi[j];
+            if (ji < 0) continue;
+            const uint64_t k = mk[j];
+            if (bi < 0 || prio_gt(k, ji, bk, bi)) {
+                bk = k;
+                bi = ji;
+            }
+        }
+        if (bi == i) state[i] = MIS_ROOT;
+    }
+}
+
+__global__ void k_mis_near1(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                            const unsigned char *__restrict__ S, const unsigned char *__restrict__ state,
+                            unsigned char *__restrict__ near1)
+{
+    GRID_STRIDE(ii, n)
+    {
+        const int i = (int)ii;
+        unsigned char f = state[i] == MIS_ROOT;
+        for (int e = rp[i]; e < rp[i + 1] && !f; ++e)
+            if (S[e] && state[ci[e]] == MIS_ROOT) f = 1;
+        near1[i] = f;
+    }
+}
+
+__global__ void k_mis_remove(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                             const unsigned char *__restrict__ S, unsigned char *__restrict__ state,
+                             const unsigned char *__restrict__ near1, int *__restrict__ undecided)
+{
+    GRID_STRIDE(ii, n)
+    {
+        const int i = (int)ii;
+        if (state[i] != MIS_UNDECIDED) continue;
+        bool f = near1[i];
+        for (int e = rp[i]; e < rp[i + 1] && !f; ++e)
+            if (S[e] && near1[ci[e]]) f = true;
+        if (f) state[i] = MIS_OUT;
+        else atomicAdd(undecided, 1);
+    }
+}
+
+__global__ void k_mis_roots(int n, const unsigned char *__restrict__ state, unsigned char *__restrict__ root)
+{
+    GRID_STRIDE(i, n) root[i] = state[i] == MIS_ROOT;
+}
+
+int setup_mis2(const DCSR &A, const unsigned char *S, uint64_t seed, int level, DBuf<unsigned char> &root,
+               cudaStream_t st)
+{
+    const int n = A.nr;
+    DBuf<unsigned char> state((size_t)n), near1((size_t)n);
+    DBuf<unsigned long long> mk((size_t)n);
+    DBuf<int> mi((size_t)n), cnt(1);
+    root.alloc((size_t)n);
+    GW_CUDA(cudaMemsetAsync(state.p, 0, (size_t)n, st));
+    const int g = nblk(n, 256);
+    const int max_rounds = 200;
+    int rounds = 0;
+    for (;;) {
+        if (rounds >= max_rounds) fail(GW_ERR_SETUP, "MIS-2 did not finish in %d rounds on level %d", max_rounds, level);
+        ++rounds;
+        GW_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int), st));
+        k_mis_max1<<<g, 256, 0, st>>>(n, A.rp.p, A.ci.p, S, state.p, seed, level, mk.p, mi.p);
+        k_mis_select<<<g, 256, 0, st>>>(n, A.rp.p, A.ci.p, S, state.p, mk.p, mi.p);
+        k_mis_near1<<<g, 256, 0, st>>>(n, A.rp.p, A.ci.p, S, state.p, near1.p);
+        k_mis_remove<<<g, 256, 0, st>>>(n, A.rp.p, A.ci.p, S, state.p, near1.p, cnt.p);
+        GW_LAUNCH_CHECK();
+        if (read_int(cnt.p, st) == 0) break;
+    }
+    k_mis_roots<<<g, 256, 0, st>>>(n, state.p, root.p);
+    GW_LAUNCH_CHECK();
+    return rounds;
+}
+
+// -------------------------------------------------------------- aggregates --
+__global__ void k_root_flag(int n, const unsigned char *__restrict__ root, int *__restrict__ f)
+{
+    GRID_STRIDE(i, n) f[i] = root[i] ? 1 : 0;
+}
+
+// roots take their scan index; strong neighbours of a root join it
+__global__ void k_join1(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                        const unsigned char *__restrict__ S, const unsigned char *__restrict__ root,
+                        const int *__restrict__ id, int *__restrict__ agg1, int *__restrict__ rootof)
+{
+    GRID_STRIDE(ii, n)
+    {
+        const int i = (int)ii;
+        int a = -1, r = -1;
+        if (root[i]) {
+            a = id[i];
+            r = i;
+        } else {
+            for (int e = rp[i]; e < rp[i + 1]; ++e) {
+                const int j = ci[e];
+                if (S[e] && j != i && root[j]) {
+                    a = id[j];
+                    r = j;
+                    break;
+                }
+            }
+        }
+        agg1[i] = a;
+        rootof[i] = r;
+    }
+}
+
+// remaining nodes join the step-1 neighbour whose root has the largest (key, index)
+__global__ void k_join2(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                        const unsigned char *__restrict__ S, const int *__restrict__ agg1,
+                        const int *__restrict__ rootof, uint64_t seed, int level, int *__restrict__ agg,
+                        int *__restrict__ bad)
+{
+    GRID_STRIDE(ii, n)
+    {
+        const int i = (int)ii;
+        if (agg1[i] >= 0) {
+            agg[i] = agg1[i];
+            continue;
+        }
+        int best = -1;
+        uint64_t bk = 0;
+        for (int e = rp[i]; e < rp[i + 1]; ++e) {
+            const int j = ci[e];
+            if (!S[e] || j == i || agg1[j] < 0) continue;
+            const int r = rootof[j];
+            const uint64_t k = prio_key(seed, level, r);
+            if (best < 0 || k > bk || (k == bk && r > best)) {
+                best = r;
+                bk = k;
+            }
+        }
+        if (best < 0) {
+            agg[i] = -1;
+            atomicAdd(bad, 1);
+        } else {
+            agg[i] = agg1[best];
+        }
+    }
+}
+
+int setup_aggregate(const DCSR &A, const unsigned char *S, const unsigned char *root, uint64_t seed, int level,
+                    DBuf<int> &agg, cudaStream_t st)
+{
+    const int n = A.nr;
+    DBuf<int> id((size_t)n + 1), agg1((size_t)n), rootof((size_t)n), bad(1);
+    agg.alloc((size_t)n);
+    const int g = nblk(n, 256);
+    k_root_flag<<<g, 256, 0, st>>>(n, root, id.p);
+    GW_LAUNCH_CHECK();
+    exclusive_scan(id.p, id.p, n, st);
+    k_join1<<<g, 256, 0, st>>>(n, A.rp.p, A.ci.p, S, root, id.p, agg1.p, rootof.p);
+    GW_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
+    k_join2<<<g, 256, 0, st>>>(n, A.rp.p, A.ci.p, S, agg1.p, rootof.p, seed, level, agg.p, bad.p);
+    GW_LAUNCH_CHECK();
+    if (read_int(bad.p, st)) fail(GW_ERR_SETUP, "aggregation left nodes unassigned on level %d", level);
+    return read_int(id.p + n, st);
+}
+
+// ------------------------------------------------------ smoothed prolongator --
+// A_F: weak off-diagonals dropped and added to the diagonal in ascending
+// column order; rho = max over rows with a strong neighbour of
+// (sum_j |a^F_ij|, ascending j) / a^F_ii.
+__global__ void k_filter(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                         const double *__restrict__ v, const unsigned char *__restrict__ S,
+                         const double *__restrict__ d, double *__restrict__ aF, unsigned char *__restrict__ hs,
+                         unsigned long long *__restrict__ rho_bits)
+{
+    GRID_STRIDE(ii, n)
+    {
+        const int i = (int)ii;
+        double di = d[i];
+        unsigned char h = 0;
+        for (int e = rp[i]; e < rp[i + 1]; ++e) {
+            const int j = ci[e];
+            if (j == i) continue;
+            if (S[e]) h = 1;
+            else di = __dadd_rn(di, v[e]);
+        }
+        aF[i] = di;
+        hs[i] = h;
+        if (!h) continue;
+        double s = 0.0;
+        for (int e = rp[i]; e < rp[i + 1]; ++e) {
+            const int j = ci[e];
+            if (j == i) s = __dadd_rn(s, fabs(di));
+            else if (S[e]) s = __dadd_rn(s, fabs(v[e]));
+        }
+        const double ratio = __ddiv_rn(s, di);
+        if (ratio > 0.0 && isfinite(ratio)) atomicMax(rho_bits, (unsigned long long)__double_as_longlong(ratio));
+    }
+}
+
+__device__ __forceinline__ bool p_member(int i, int j, unsigned char s) { return j == i || s; }
+
+__global__ void k_p_count(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                          const unsigned char *__restrict__ S, const int *__restrict__ agg,
+                          const unsigned char *__restrict__ hs, int *__restrict__ cnt)
+{
+    GRID_STRIDE(ii, n)
+    {
+        const int i = (int)ii;
+        if (!hs[i]) {
+            cnt[i] = 1;
+            continue;
+        }
+        int c = 0;
+        for (int e = rp[i]; e < rp[i + 1]; ++e) {
+            const int j = ci[e];
+            if (!p_member(i, j, S[e])) continue;
+            const int a = agg[j];
+            bool dup = false;
+            for (int f = rp[i]; f < e && !dup; ++f)
+                if (p_member(i, ci[f], S[f]) && agg[ci[f]] == a) dup = true;
+            if (!dup) ++c;
+        }
+        cnt[i] = c;
+    }
+}
+
+// P(i,c) = [c == agg(i)] - s_i * sum_{j in {i} U S(i), agg(j) = c} a^F_ij,
+// s_i = omega / a^F_ii, sums in ascending j; columns ascending.
+__global__ void k_p_fill(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                         const double *__restrict__ v, const unsigned char *__restrict__ S,
+                         const int *__restrict__ agg, const unsigned char *__restrict__ hs,
+                         const double *__restrict__ aF, double omega, const int *__restrict__ prp,
+                         int *__restrict__ pci, double *__restrict__ pv)
+{
+    GRID_STRIDE(ii, n)
+    {
+        const int i = (int)ii;
+        int o = prp[i];
+        const int ai = agg[i];
+        if (!hs[i]) {
+            pci[o] = ai;
+            pv[o] = 1.0;
+            continue;
+        }
+        const double s = __ddiv_rn(omega, aF[i]);
+        const int cnt = prp[i + 1] - o;
+        int last = -1;
+        for (int t = 0; t < cnt; ++t) {
+            int c = 0x7fffffff;
+            for (int e = rp[i]; e < rp[i + 1]; ++e) {
+                const int j = ci[e];
+                if (!p_member(i, j, S[e])) continue;
+                const int a = agg[j];
+                if (a > last && a < c) c = a;
+            }
+            double acc = 0.0;
+            for (int e = rp[i]; e < rp[i + 1]; ++e) {
+                const int j = ci[e];
+                if (!p_member(i, j, S[e]) || agg[j] != c) continue;
+                acc = __dadd_rn(acc, j == i ? aF[i] : v[e]);
+            }
+            const double delta = c == ai ? 1.0 : 0.0;
+            pci[o + t] = c;
+            pv[o + t] = __dsub_rn(delta, __dmul_rn(s, acc));
+            last = c;
+        }
+    }
+}
+
+void setup_smooth_p(const DCSR &A, const unsigned char *S, const int *agg, int nagg, DCSR &P, double *omega,
+                    double *rho, cudaStream_t st)
+{
+    const int n = A.nr;
+    DBuf<double> d((size_t)n), aF((size_t)n);
+    DBuf<unsigned char> hs((size_t)n);
+    DBuf<unsigned long long> rb(1);
+    const int g = nblk(n, 256);
+    k_diag<<<g, 256, 0, st>>>(n, A.rp.p, A.ci.p, A.v.p, d.p);
+    GW_CUDA(cudaMemsetAsync(rb.p, 0, sizeof(unsigned long long), st));
+    k_filter<<<g, 256, 0, st>>>(n, A.rp.p, A.ci.p, A.v.p, S, d.p, aF.p, hs.p, rb.p);
+    GW_LAUNCH_CHECK();
+    unsigned long long bits = 0;
+    GW_CUDA(cudaMemcpyAsync(&bits, rb.p, sizeof bits, cudaMemcpyDeviceToHost, st));
+    GW_CUDA(cudaStreamSynchronize(st));
+    double r;
+    memcpy(&r, &bits, sizeof r);
+    *rho = r;
+    *omega = r > 0.0 ? (4.0 / 3.0) / r : 0.0;
+    P.nr = n;
+    P.nc = nagg;
+    P.rp.alloc((size_t)n + 1);
+    k_p_count<<<g, 256, 0, st>>>(n, A.rp.p, A.ci.p, S, agg, hs.p, P.rp.p);
+    GW_LAUNCH_CHECK();
+    exclusive_scan(P.rp.p, P.rp.p, n, st);
+    P.nnz = read_int(P.rp.p + n, st);
+    P.ci.alloc((size_t)P.nnz);
+    P.v.alloc((size_t)P.nnz);
+    k_p_fill<<<g, 256, 0, st>>>(n, A.rp.p, A.ci.p, A.v.p, S, agg, hs.p, aF.p, *omega, P.rp.p, P.ci.p, P.v.p);
+    GW_LAUNCH_CHECK();
+}
+
+// ---------------------------------------------------------------- transpose --
+__global__ void k_tr_count(int nnz, const int *__restrict__ ci, int *__restrict__ cnt)
+{
+    GRID_STRIDE(e, nnz) atomicAdd(&cnt[ci[e]], 1);
+}
+
+__global__ void k_tr_scatter(int nr, const int *__restrict__ rp, const int *__restrict__ ci,
+                             const double *__restrict__ v, const int *__restrict__ rrp, int *__restrict__ fill,
+                             int *__restrict__ tci, double *__restrict__ tv)
+{
+    GRID_STRIDE(ii, nr)
+    {
+        const int i = (int)ii;
+        for (int e = rp[i]; e < rp[i + 1]; ++e) {
+            const int c = ci[e];
+            const int pos = rrp[c] + atomicAdd(&fill[c], 1);
+            tci[pos] = i;
+            tv[pos] = v[e];
+        }
+    }
+}
+
+// one warp per row: every entry moves to its rank among the row's (unique) keys
+__global__ void k_rank_sort_rows(int nr, const int *__restrict__ rp, const int *__restrict__ kin,
+                                 const double *__restrict__ vin, int *__restrict__ kout, double *__restrict__ vout)
+{
+    const int lane = threadIdx.x & 31;
+    const long long w0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long r = w0; r < nr; r += nw) {
+        const int b = rp[r], m = rp[r + 1] - b;
+        for (int k = lane; k < m; k += 32) {
+            const int key = kin[b + k];
+            int rank = 0;
+            for (int t = 0; t < m; ++t) rank += kin[b + t] < key;
+            kout[b + rank] = key;
+            vout[b + rank] = vin[b + k];
+        }
+    }
+}
+
+void setup_transpose(const DCSR &P, DCSR &R, cudaStream_t st)
+{
+    R.nr = P.nc;
+    R.nc = P.nr;
+    R.nnz = P.nnz;
+    R.rp.alloc((size_t)R.nr + 1);
+    R.ci.alloc((size_t)R.nnz);
+    R.v.alloc((size_t)R.nnz);
+    DBuf<int> fill((size_t)R.nr), tci((size_t)R.nnz);
+    DBuf<double> tv((size_t)R.nnz);
+    GW_CUDA(cudaMemsetAsync(R.rp.p, 0, ((size_t)R.nr + 1) * sizeof(int), st));
+    GW_CUDA(cudaMemsetAsync(fill.p, 0, (size_t)R.nr * sizeof(int), st));
+    k_tr_count<<<nblk(P.nnz, 256), 256, 0, st>>>(P.nnz, P.ci.p, R.rp.p);
+    GW_LAUNCH_CHECK();
+    exclusive_scan(R.rp.p, R.rp.p, R.nr, st);
+    k_tr_scatter<<<nblk(P.nr, 256), 256, 0, st>>>(P.nr, P.rp.p, P.ci.p, P.v.p, R.rp.p, fill.p, tci.p, tv.p);
+    k_rank_sort_rows<<<nblk((long long)R.nr * 32, 256), 256, 0, st>>>(R.nr, R.rp.p, tci.p, tv.p, R.ci.p, R.v.p);
+    GW_LAUNCH_CHECK();
+    GW_CUDA(cudaStreamSynchronize(st));
+}
+
+// ------------------------------------------------------------------- SpGEMM --
+// C = L * Rm.  Pass 1 (symbolic) collects the distinct columns of each output
+// row in a per-warp open-addressing table in shared memory and counts them;
+// after a scan of the counts, pass 2 (numeric) rebuilds the set, sorts it
+// (rank sort), and accumulates C(i,c) = sum over L's row i in ascending
+// column k of L(i,k) * Rm(k,c): the warp walks L's row in order and its lanes
+// take the entries of Rm's row k, which have distinct columns, so every
+// output entry receives its terms in ascending k.
+constexpr int SG_HMAX = 8192;
+
+__global__ void k_sg_bound(int nr, int ncol, const int *__restrict__ lrp, const int *__restrict__ lci,
+                           const int *__restrict__ rrp, int *__restrict__ maxub)
+{
+    int best = 0;
+    GRID_STRIDE(ii, nr)
+    {
+        const int i = (int)ii;
+        long long ub = 0;
+        for (int e = lrp[i]; e < lrp[i + 1]; ++e) {
+            const int k = lci[e];
+            ub += rrp[k + 1] - rrp[k];
+        }
+        best = max(best, (int)(ub < (long long)ncol ? ub : (long long)ncol));
+    }
+    atomicMax(maxub, best);
+}
+
+__device__ __forceinline__ unsigned sg_hash(int c) { return (unsigned)c * 2654435761u; }
+
+__device__ __forceinline__ int sg_insert(int *keys, int H, int c)
+{
+    unsigned h = sg_hash(c) & (unsigned)(H - 1);
+    for (int probe = 0; probe < H; ++probe) {
+        int old = atomicCAS(&keys[h], -1, c);
+        if (old == -1) return 1;
+        if (old == c) return 0;
+        h = (h + 1) & (unsigned)(H - 1);
+    }
+    return -1000000;  // table full: flagged by the caller through the count
+}
+
+__device__ int sg_build_set(const int *__restrict__ lrp, const int *__restrict__ lci, const int *__restrict__ rrp,
+                            const int *__restrict__ rci, int row, int *keys, int H, int lane)
+{
+    for (int t = lane; t < H; t += 32) keys[t] = -1;
+    __syncwarp();
+    int mine = 0;
+    for (int e = lrp[row]; e < lrp[row + 1]; ++e) {
+        const int k = lci[e];
+        for (int f = rrp[k] + lane; f < rrp[k + 1]; f += 32) mine += sg_insert(keys, H, rci[f]);
+    }
+    __syncwarp();
+    for (int off = 16; off > 0; off >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, off);
+    return mine;
+}
+
+__global__ void k_sg_symbolic(int nr, const int *__restrict__ lrp, const int *__restrict__ lci,
+                              const int *__restrict__ rrp, const int *__restrict__ rci, int H, int *__restrict__ cnt,
+                              int *__restrict__ overflow)
+{
+    extern __shared__ int sg_smem[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, W = blockDim.x >> 5;
+    int *keys = sg_smem + (size_t)w * H;
+    for (long long row = (long long)blockIdx.x * W + w; row < nr; row += (long long)gridDim.x * W) {
+        int u = sg_build_set(lrp, lci, rrp, rci, (int)row, keys, H, lane);
+        if (lane == 0) {
+            if (u < 0 || u > H / 2) atomicOr(overflow, 1);
+            cnt[row] = u < 0 ? 0 : u;
+        }
+        __syncwarp();
+    }
+}
+
+__global__ void k_sg_numeric(int nr, const int *__restrict__ lrp, const int *__restrict__ lci,
+                             const double *__restrict__ lv, const int *__restrict__ rrp, const int *__restrict__ rci,
+                             const double *__restrict__ rv, int H, const int *__restrict__ crp, int *__restrict__ cci,
+                             double *__restrict__ cv)
+{
+    extern __shared__ int sg_smem[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, W = blockDim.x >> 5;
+    // per warp: keys[H] ints, list[H] ints, acc[H/2] doubles
+    char *base = (char *)sg_smem + (size_t)w * (size_t)H * 12;
+    int *keys = (int *)base;
+    int *list = keys + H;
+    double *acc = (double *)(list + H);
+    for (long long rr = (long long)blockIdx.x * W + w; rr < nr; rr += (long long)gridDim.x * W) {
+        const int row = (int)rr;
+        sg_build_set(lrp, lci, rrp, rci, row, keys, H, lane);
+        // compact the table into list (any order), then rank-sort into keys
+        int u = 0;
+        for (int t0 = 0; t0 < H; t0 += 32) {
+            const int t = t0 + lane;
+            const int c = keys[t];
+            const unsigned m = __ballot_sync(0xffffffffu, c != -1);
+            if (c != -1) list[u + __popc(m & ((1u << lane) - 1u))] = c;
+            u += __popc(m);
+        }
+        __syncwarp();
+        const int o = crp[row];
+        for (int k = lane; k < u; k += 32) {
+            const int c = list[k];
+            int rank = 0;
+            for (int t = 0; t < u; ++t) rank += list[t] < c;
+            keys[rank] = c;
+            cci[o + rank] = c;
+        }
+        for (int k = lane; k < u; k += 32) acc[k] = 0.0;
+        __syncwarp();
+        for (int e = lrp[row]; e < lrp[row + 1]; ++e) {
+            const int k = lci[e];
+            const double a = lv[e];
+            for (int f = rrp[k] + lane; f < rrp[k + 1]; f += 32) {
+                const int c = rci[f];
+                int lo = 0, hi = u - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (keys[mid] < c) lo = mid + 1;
+                    else hi = mid;
+                }
+                acc[lo] = __dadd_rn(acc[lo], __dmul_rn(a, rv[f]));
+            }
+            __syncwarp();
+        }
+        for (int k = lane; k < u; k += 32) cv[o + k] = acc[k];
+        __syncwarp();
+    }
+}
+
+void setup_spgemm(const DCSR &L, const DCSR &Rm, DCSR &C, cudaStream_t st)
+{
+    DBuf<int> maxub(1), ovf(1);
+    GW_CUDA(cudaMemsetAsync(maxub.p, 0, sizeof(int), st));
+    GW_CUDA(cudaMemsetAsync(ovf.p, 0, sizeof(int), st));
+    k_sg_bound<<<nblk(L.nr, 256), 256, 0, st>>>(L.nr, Rm.nc, L.rp.p, L.ci.p, Rm.rp.p, maxub.p);
+    GW_LAUNCH_CHECK();
+    const int ub = read_int(maxub.p, st);
+    int H = 32;
+    while (H < 2 * ub && H < SG_HMAX) H <<= 1;
+    // warps per block so that a block's tables stay within 96 KB
+    const size_t per_warp_num = (size_t)H * 12;
+    int W = (int)std::max<size_t>(1, std::min<size_t>(8, (96u << 10) / per_warp_num));
+    const size_t smem_sym = (size_t)W * H * sizeof(int), smem_num = (size_t)W * per_warp_num;
+    GW_CUDA(cudaFuncSetAttribute(k_sg_symbolic, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_sym));
+    GW_CUDA(cudaFuncSetAttribute(k_sg_numeric, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_num));
+    C.nr = L.nr;
+    C.nc = Rm.nc;
+    C.rp.alloc((size_t)C.nr + 1);
+    const int grid = (int)std::max(1LL, std::min<long long>(((long long)L.nr + W - 1) / W, 152LL * 64));
+    k_sg_symbolic<<<grid, 32 * W, smem_sym, st>>>(L.nr, L.rp.p, L.ci.p, Rm.rp.p, Rm.ci.p, H, C.rp.p, ovf.p);
+    GW_LAUNCH_CHECK();
+    if (read_int(ovf.p, st)) fail(GW_ERR_SETUP, "SpGEMM row has more than %d distinct columns", H / 2);
+    exclusive_scan(C.rp.p, C.rp.p, C.nr, st);
+    C.nnz = read_int(C.rp.p + C.nr, st);
+    C.ci.alloc((size_t)C.nnz);
+    C.v.alloc((size_t)C.nnz);
+    k_sg_numeric<<<grid, 32 * W, smem_num, st>>>(L.nr, L.rp.p, L.ci.p, L.v.p, Rm.rp.p, Rm.ci.p, Rm.v.p, H, C.rp.p,
+                                                  C.ci.p, C.v.p);
+    GW_LAUNCH_CHECK();
+    GW_CUDA(cudaStreamSynchronize(st));
+}
+
+// ---------------------------------------------------------- coarsest level --
+__global__ void k_dense_fill(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                             const double *__restrict__ v, double *__restrict__ a)
+{
+    GRID_STRIDE(ii, n)
+    {
+        const int i = (int)ii;
+        for (int e = rp[i]; e < rp[i + 1]; ++e) a[(size_t)i * n + ci[e]] = v[e];
+    }
+}
+
+// Doolittle LU with partial pivoting (first row of largest |a_ik|), one block.
+__global__ void k_lu_factor(int n, double *__restrict__ a, int *__restrict__ piv, int *__restrict__ singular)
+{
+    __shared__ double sv[1024];
+    __shared__ int si[1024];
+    const int tid = threadIdx.x, bs = blockDim.x;
+    for (int k = 0; k < n; ++k) {
+        double best = -1.0;
+        int bi = n;
+        for (int i = k + tid; i < n; i += bs) {
+            const double t = fabs(a[(size_t)i * n + k]);
+            if (t > best) {
+                best = t;
+                bi = i;
+            }
+        }
+        sv[tid] = best;
+        si[tid] = bi;
+        __syncthreads();
+        for (int off = bs >> 1; off > 0; off >>= 1) {
+            if (tid < off) {
+                const double o = sv[tid + off];
+                const int oi = si[tid + off];
+                if (o > sv[tid] || (o == sv[tid] && oi < si[tid])) {
+                    sv[tid] = o;
+                    si[tid] = oi;
+                }
+            }
+            __syncthreads();
+        }
+        const int p = si[0];
+        const double pmax = sv[0];
+        __syncthreads();
+        if (tid == 0) {
+            piv[k] = p;
+            if (!(pmax > 0.0)) *singular = 1;
+        }
+        if (!(pmax > 0.0)) return;
+        if (p != k)
+            for (int j = tid; j < n; j += bs) {
+                const double t = a[(size_t)k * n + j];
+                a[(size_t)k * n + j] = a[(size_t)p * n + j];
+                a[(size_t)p * n + j] = t;
+            }
+        __syncthreads();
+        const double pv = a[(size_t)k * n + k];
+        for (int i = k + 1 + tid; i < n; i += bs) a[(size_t)i * n + k] /= pv;
+        __syncthreads();
+        const int m = n - k - 1;
+        for (long long idx = tid; idx < (long long)m * m; idx += bs) {
+            const int i = k + 1 + (int)(idx / m), j = k + 1 + (int)(idx % m);
+            a[(size_t)i * n + j] -= a[(size_t)i * n + k] * a[(size_t)k * n + j];
+        }
+        __syncthreads();
+    }
+}
+
+// Column j of the inverse: solve L U x = P e_j; thread j owns column j of X.
+__global__ void k_lu_inverse(int n, const double *__restrict__ lu, const int *__restrict__ piv, double *__restrict__ X)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    for (int i = 0; i < n; ++i) X[(size_t)i * n + j] = i == j ? 1.0 : 0.0;
+    for (int k = 0; k < n; ++k) {
+        const int p = piv[k];
+        if (p != k) {
+            const double t = X[(size_t)k * n + j];
+            X[(size_t)k * n + j] = X[(size_t)p * n + j];
+            X[(size_t)p * n + j] = t;
+        }
+    }
+    for (int i = 0; i < n; ++i) {
+        double s = X[(size_t)i * n + j];
+        for (int m = 0; m < i; ++m) s -= lu[(size_t)i * n + m] * X[(size_t)m * n + j];
+        X[(size_t)i * n + j] = s;
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        double s = X[(size_t)i * n + j];
+        for (int m = i + 1; m < n; ++m) s -= lu[(size_t)i * n + m] * X[(size_t)m * n + j];
+        X[(size_t)i * n + j] = s / lu[(size_t)i * n + i];
+    }
+}
+
+void setup_dense_inverse(const DCSR &A, DBuf<double> &Ainv, cudaStream_t st)
+{
+    const int n = A.nr;
+    if (n > 4096) fail(GW_ERR_SETUP, "coarsest level has %d unknowns (more than 4096)", n);
+    DBuf<double> lu((size_t)n * n);
+    DBuf<int> piv((size_t)n), sing(1);
+    Ainv.alloc((size_t)n * n);
+    GW_CUDA(cudaMemsetAsync(lu.p, 0, lu.bytes(), st));
+    GW_CUDA(cudaMemsetAsync(sing.p, 0, sizeof(int), st));
+    k_dense_fill<<<nblk(n, 128), 128, 0, st>>>(n, A.rp.p, A.ci.p, A.v.p, lu.p);
+    k_lu_factor<<<1, 1024, 0, st>>>(n, lu.p, piv.p, sing.p);
+    GW_LAUNCH_CHECK();
+    if (read_int(sing.p, st)) fail(GW_ERR_SETUP, "coarsest-level matrix (%d unknowns) is singular", n);
+    k_lu_inverse<<<(n + 31) / 32, 32, 0, st>>>(n, lu.p, piv.p, Ainv.p);
+    GW_LAUNCH_CHECK();
+    GW_CUDA(cudaStreamSynchronize(st));
+}
+
+// ------------------------------------------------- smoother data (per level) --
+__global__ void k_gersh(int n, const int *__restrict__ rp, const int *__restrict__ ci, const double *__restrict__ v,
+                        double *__restrict__ d, unsigned long long *__restrict__ rho_bits)
+{
+    GRID_STRIDE(ii, n)
+    {
+        const int i = (int)ii;
+        double s = 0.0, dd = 0.0;
+        for (int e = rp[i]; e < rp[i + 1]; ++e) {
+            s += fabs(v[e]);
+            if (ci[e] == i) dd = v[e];
+        }
+        d[i] = dd;
+        const double ratio = s / dd;
+        if (ratio > 0.0 && isfinite(ratio)) atomicMax(rho_bits, (unsigned long long)__double_as_longlong(ratio));
+    }
+}
+
+double setup_gershgorin(const DCSR &A, DBuf<double> &diag, cudaStream_t st)
+{
+    diag.alloc((size_t)A.nr);
+    DBuf<unsigned long long> rb(1);
+    GW_CUDA(cudaMemsetAsync(rb.p, 0, sizeof(unsigned long long), st));
+    k_gersh<<<nblk(A.nr, 256), 256, 0, st>>>(A.nr, A.rp.p, A.ci.p, A.v.p, diag.p, rb.p);
+    GW_LAUNCH_CHECK();
+    unsigned long long bits = 0;
+    GW_CUDA(cudaMemcpyAsync(&bits, rb.p, sizeof bits, cudaMemcpyDeviceToHost, st));
+    GW_CUDA(cudaStreamSynchronize(st));
+    double r;
+    memcpy(&r, &bits, sizeof r);
+    return r;
+}
+
+__global__ void k_pow_start(int n, uint64_t seed, int level, double *__restrict__ v)
+{
+    GRID_STRIDE(ii, n)
+    {
+        const int i = (int)ii;
+        const uint64_t h = smix64(seed ^ ((uint64_t)level << 48) ^ (uint64_t)(uint32_t)i ^ 0x00c0ffee00000000ULL);
+        v[i] = (double)(h >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+    }
+}
+
+// w = D^-1 A v and per-block partial sums of w.w
+__global__ void k_pow_step(int n, const int *__restrict__ rp, const int *__restrict__ ci, const double *__restrict__ a,
+                           const double *__restrict__ d, const double *__restrict__ v, double scale,
+                           double *__restrict__ w, double *__restrict__ part)
+{
+    __shared__ double sh[256];
+    double loc = 0.0;
+    GRID_STRIDE(ii, n)
+    {
+        const int i = (int)ii;
+        double s = 0.0;
+        for (int e = rp[i]; e < rp[i + 1]; ++e) s += a[e] * (v[ci[e]] * scale);
+        s /= d[i];
+        w[i] = s;
+        loc += s * s;
+    }
+    sh[threadIdx.x] = loc;
+    __syncthreads();
+    for (int off = 128; off > 0; off >>= 1) {
+        if (threadIdx.x < off) sh[threadIdx.x] += sh[threadIdx.x + off];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void k_sumsq(int n, const double *__restrict__ v, double *__restrict__ part)
+{
+    __shared__ double sh[256];
+    double loc = 0.0;
+    GRID_STRIDE(i, n) loc += v[i] * v[i];
+    sh[threadIdx.x] = loc;
+    __syncthreads();
+    for (int off = 128; off > 0; off >>= 1) {
+        if (threadIdx.x < off) sh[threadIdx.x] += sh[threadIdx.x + off];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+static double host_sum(const DBuf<double> &part, int nb, cudaStream_t st)
+{
+    std::vector<double> h((size_t)nb);
+    GW_CUDA(cudaMemcpyAsync(h.data(), part.p, (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+    GW_CUDA(cudaStreamSynchronize(st));
+    double s = 0.0;
+    for (int i = 0; i < nb; ++i) s += h[(size_t)i];
+    return s;
+}
+
+// lambda_max(D^-1 A) by 10 power iterations from a hashed start vector
+double setup_power_lambda(const DCSR &A, const double *diag, uint64_t seed, int level, cudaStream_t st)
+{
+    const int n = A.nr, g = nblk(n, 256, 1024);
+    DBuf<double> v((size_t)n), w((size_t)n), part((size_t)g);
+    k_pow_start<<<g, 256, 0, st>>>(n, seed, level, v.p);
+    k_sumsq<<<g, 256, 0, st>>>(n, v.p, part.p);
+    GW_LAUNCH_CHECK();
+    double scale = 1.0 / sqrt(host_sum(part, g, st));
+    double lam = 0.0;
+    for (int it = 0; it < 10; ++it) {
+        k_pow_step<<<g, 256, 0, st>>>(n, A.rp.p, A.ci.p, A.v.p, diag, v.p, scale, w.p, part.p);
+        GW_LAUNCH_CHECK();
+        lam = sqrt(host_sum(part, g, st));
+        std::swap(v, w);
+        scale = 1.0 / lam;
+    }
+    return lam;
+}
+
+// ------------------------------------------------------- sliced ELL format --
+__global__ void k_sell_width(int nr, int nslices, int V, const int *__restrict__ rp, int *__restrict__ width)
+{
+    GRID_STRIDE(s, nslices)
+    {
+        int w = 0;
+        for (int l = 0; l < SELL_C; ++l) {
+            const long long r = s * SELL_C + l;
+            if (r < nr) w = max(w, rp[r + 1] - rp[r]);
+        }
+        w = (w + V - 1) / V * V;
+        width[s] = w * SELL_C;
+    }
+}
+
+template <class T>
+__global__ void k_sell_fill(int nr, int nc, int nslices, const int *__restrict__ rp, const int *__restrict__ ci,
+                            const double *__restrict__ v, const int *__restrict__ sp, int *__restrict__ sci,
+                            T *__restrict__ sv)
+{
+    constexpr int V = SellV<T>::V;
+    GRID_STRIDE(rr, (long long)nslices * SELL_C)
+    {
+        const int r = (int)rr, s = r / SELL_C, lane = r % SELL_C;
+        const int base = sp[s], w = (sp[s + 1] - base) / SELL_C;
+        const int b = r < nr ? rp[r] : 0, len = r < nr ? rp[r + 1] - b : 0;
+        const int pad = r < nc ? r : 0;
+        for (int k = 0; k < w; ++k) {
+            const size_t o = (size_t)base + (size_t)(k / V) * SELL_C * V + (size_t)lane * V + (k % V);
+            if (k < len) {
+                sci[o] = ci[b + k];
+                sv[o] = (T)v[b + k];
+            } else {
+                sci[o] = pad;
+                sv[o] = (T)0;
+            }
+        }
+    }
+}
+
+template <class T>
+void to_sell(const DCSR &A, Sell<T> &S, cudaStream_t st)
+{
+    constexpr int V = SellV<T>::V;
+    S.nr = A.nr;
+    S.nc = A.nc;
+    S.nnz = A.nnz;
+    S.nslices = (A.nr + SELL_C - 1) / SELL_C;
+    S.sp.alloc((size_t)S.nslices + 1);
+    k_sell_width<<<nblk(S.nslices, 256), 256, 0, st>>>(A.nr, S.nslices, V, A.rp.p, S.sp.p);
+    GW_LAUNCH_CHECK();
+    exclusive_scan(S.sp.p, S.sp.p, S.nslices, st);
+    S.stored = read_int(S.sp.p + S.nslices, st);
+    S.ci.alloc((size_t)S.stored);
+    S.v.alloc((size_t)S.stored);
+    k_sell_fill<T><<<nblk((long long)S.nslices * SELL_C, 256), 256, 0, st>>>(A.nr, A.nc, S.nslices, A.rp.p, A.ci.p,
+                                                                          A.v.p, S.sp.p, S.ci.p, S.v.p);
+    GW_LAUNCH_CHECK();
+}
+
+template void to_sell<float>(const DCSR &, Sell<float> &, cudaStream_t);
+template void to_sell<double>(const DCSR &, Sell<double> &, cudaStream_t);
+
+}  // namespace gw

@@ -1,0 +1,115 @@
+// util.cu -- error plumbing, device scan and small host helpers of libgw.
+#include <stdarg.h>
+
+#include "gw_internal.cuh"
+
+namespace gw {
+
+static thread_local std::string g_last_error;
+
+void set_last_error(const char *msg) { g_last_error = msg ? msg : ""; }
+
+const char *last_error_cstr() { return g_last_error.c_str(); }
+
+[[noreturn]] void fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    throw Error{code, std::string(buf)};
+}
+
+// ------------------------------------------------------------------ scan --
+// Exclusive prefix sum of n ints, three phases: per-block scan of 2048
+// elements, scan of the block totals (recursively), add-back.
+constexpr int SCAN_BS = 256, SCAN_IT = 8, SCAN_CHUNK = SCAN_BS * SCAN_IT;
+
+__global__ void k_scan_block(const int *__restrict__ in, int *__restrict__ out, int *__restrict__ bsum, int n)
+{
+    __shared__ int sh[SCAN_BS];
+    const int tid = threadIdx.x;
+    const long long base = (long long)blockIdx.x * SCAN_CHUNK + (long long)tid * SCAN_IT;
+    int v[SCAN_IT];
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_IT; ++k) {
+        long long idx = base + k;
+        v[k] = idx < n ? in[idx] : 0;
+        s += v[k];
+    }
+    sh[tid] = s;
+    __syncthreads();
+    for (int off = 1; off < SCAN_BS; off <<= 1) {
+        int t = tid >= off ? sh[tid - off] : 0;
+        __syncthreads();
+        sh[tid] += t;
+        __syncthreads();
+    }
+    int excl = sh[tid] - s;
+#pragma unroll
+    for (int k = 0; k < SCAN_IT; ++k) {
+        long long idx = base + k;
+        if (idx < n) out[idx] = excl;
+        excl += v[k];
+    }
+    if (tid == SCAN_BS - 1) bsum[blockIdx.x] = sh[tid];
+}
+
+__global__ void k_scan_add(int *__restrict__ out, const int *__restrict__ bsum, int n)
+{
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx < n) out[idx] += bsum[idx / SCAN_CHUNK];
+}
+
+__global__ void k_set_at(int *dst, const int *src) { *dst = *src; }
+
+void exclusive_scan(const int *in, int *out, int n, cudaStream_t st)
+{
+    if (n <= 0) {
+        GW_CUDA(cudaMemsetAsync(out, 0, sizeof(int), st));
+        return;
+    }
+    int nb = (n + SCAN_CHUNK - 1) / SCAN_CHUNK;
+    int *bsum = nullptr;
+    GW_CUDA(cudaMallocAsync((void **)&bsum, (size_t)(nb + 1) * sizeof(int), st));
+    k_scan_block<<<nb, SCAN_BS, 0, st>>>(in, out, bsum, n);
+    GW_LAUNCH_CHECK();
+    if (nb > 1) {
+        exclusive_scan(bsum, bsum, nb, st);
+        k_scan_add<<<(n + 255) / 256, 256, 0, st>>>(out, bsum, n);
+        GW_LAUNCH_CHECK();
+        k_set_at<<<1, 1, 0, st>>>(out + n, bsum + nb);
+    } else {
+        k_set_at<<<1, 1, 0, st>>>(out + n, bsum);
+    }
+    GW_LAUNCH_CHECK();
+    GW_CUDA(cudaFreeAsync(bsum, st));
+}
+
+int read_int(const int *dptr, cudaStream_t st)
+{
+    int v = 0;
+    GW_CUDA(cudaMemcpyAsync(&v, dptr, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GW_CUDA(cudaStreamSynchronize(st));
+    return v;
+}
+
+bool is_device_ptr(const void *p)
+{
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+void to_device(void *dst, const void *src, size_t bytes, cudaStream_t st)
+{
+    GW_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, st));
+}
+
+}  // namespace gw

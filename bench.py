@@ -1,0 +1,309 @@
+"""Benchmark: AMG-PCG solve time and fine-level V-cycle HBM bandwidth.
+
+Workload: 3D heterogeneous steady flow on 128^3 cells (2,097,152 unknowns),
+7-point finite volumes with harmonic-mean transmissibilities, lnK Gaussian
+(mean 0, variance 4, exponential covariance, correlation length 8 cells,
+seed 1), h = 1 / h = 0 on the x faces, no-flow elsewhere; solved to a true
+relative residual of 1e-8 from h0 = 0.  One step = one gw_pcg_solve with the
+hierarchy resident (setup excluded and reported separately).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+The primary arm runs the mixed-precision form (FP32 V-cycle inside FP64 CG);
+the all-FP64 form is timed beside it.  --impl reference times the FP64 CPU
+oracle on the same workload.  Under torchrun (N > 1) every rank solves its own
+copy of the workload on its own GPU (replicas, no collective on the data
+path); rank 0 prints one JSON line.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "AMG-PCG solve ms & V-cycle HBM GB/s @128³ to 1e-8 (mixed vs FP64); p50/p99"
+WORKLOAD = ("3D heterogeneous steady flow 128^3 cells (2,097,152 unknowns), 7-point FV harmonic-mean "
+            "transmissibilities, lnK N(0, 4) exponential covariance corr 8 cells seed 1, h=1/h=0 on x faces, "
+            "tol 1e-8 (true relative residual), x0 = 0")
+SIDE, VAR, CORR, SEED, TOL = 128, 4.0, 8.0, 1, 1e-8
+L2_FLUSH_BYTES = 256 << 20
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_problem():
+    from paper_2001_05798_gb300 import workload as wl
+
+    return wl.heterogeneous_3d(side=SIDE, var=VAR, corr=CORR, seed=SEED)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    """FP64 CPU oracle on the same workload; one step = one oracle solve."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+
+    p = make_problem()
+    A, b = oracle.assemble(SIDE, SIDE, SIDE, p["Kx"], bct=p["bct"], bcv=p["bcv"])
+    t0 = time.perf_counter()
+    H = oracle.Hierarchy(A)
+    setup_ms = (time.perf_counter() - t0) * 1e3
+    for _ in range(args.warmup):
+        H.pcg(b, tol=TOL)
+    times, its = [], 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        x, its, rel, st = H.pcg(b, tol=TOL)
+        times.append((time.perf_counter() - t0) * 1e3)
+    p50 = float(np.median(times))
+    out = {"metric": METRIC, "value": p50, "unit": "ms", "impl": "reference", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(times)),
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "tol": TOL, "smoother": "jacobi", "implementation":
+                      "FP64 CPU oracle (plain C, single thread)"},
+           "p50_ms": p50, "p99_ms": float(np.percentile(times, 99)), "iters": its, "relres": rel,
+           "setup_ms": setup_ms,
+           "cpu_baseline": {"value": p50, "unit": "ms", "cores": 1, "kind": "oracle",
+                            "sample": "one full oracle solve of the 128^3 workload per step (setup excluded)"},
+           "e2e": {"value": p50, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def cpu_baseline_sample():
+    """The oracle as it stands, one solve of the same workload on one host core."""
+    import oracle
+
+    p = make_problem()
+    A, b = oracle.assemble(SIDE, SIDE, SIDE, p["Kx"], bct=p["bct"], bcv=p["bcv"])
+    t0 = time.perf_counter()
+    H = oracle.Hierarchy(A)
+    setup_ms = (time.perf_counter() - t0) * 1e3
+    t0 = time.perf_counter()
+    x, its, rel, st = H.pcg(b, tol=TOL)
+    ms = (time.perf_counter() - t0) * 1e3
+    return {"value": ms, "unit": "ms", "cores": 1, "kind": "oracle",
+            "sample": "one full FP64 oracle solve of the 128^3 workload to 1e-8 (setup %.0f ms excluded), "
+                      "%d iterations; host has %d cores" % (setup_ms, its, os.cpu_count() or 0)}, x
+
+
+def timed_solves(torch, H, b, h, steps, flush, stream):
+    times = []
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, it, rel, st = H.solve(b, h, tol=TOL, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return times, it, rel, st
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2001_05798_gb300 import build, gw
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    build.build()
+    gw.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    p = make_problem()
+    n = SIDE ** 3
+    K = torch.from_numpy(p["Kx"]).to(dev)
+    b = torch.empty(n, dtype=torch.float64, device=dev)
+    A, _ = gw.gw_assemble(SIDE, SIDE, SIDE, K, K, K, p["bct"], p["bcv"], None, b_out=b)
+    smoother = gw.GW_SMOOTH_CHEBYSHEV if args.smoother == "chebyshev" else gw.GW_SMOOTH_JACOBI
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Hm = gw.Hierarchy(A, prec=gw.GW_PREC_MIXED32, smoother=smoother)
+    torch.cuda.synchronize()
+    setup_ms = (time.perf_counter() - t0) * 1e3
+    Hd = gw.Hierarchy(A, prec=gw.GW_PREC_FP64, smoother=smoother)
+    info = Hm.info()
+    h = torch.empty_like(b)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    Hm.profile(True)
+    for _ in range(max(args.warmup, 3)):
+        Hm.solve(b, h, tol=TOL, stream=stream)
+        Hd.solve(b, h, tol=TOL, stream=stream)
+    Hm.profile_read(reset=True)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        t_wall = time.perf_counter()
+        tm, it_m, rel_m, st_m = timed_solves(torch, Hm, b, h, args.steps, flush, stream)
+        t_wall = time.perf_counter() - t_wall
+    kinds, launches, solves = Hm.profile_read(reset=True)
+    h_mixed = h.clone()
+    td, it_d, rel_d, st_d = timed_solves(torch, Hd, b, h, args.steps, flush, stream)
+    # end to end through the C ABI with host buffers: the H2D copy of b and the
+    # D2H copy of h happen inside gw_pcg_solve, inside the timed region
+    b_host = b.cpu().pin_memory()
+    h_host = torch.empty(n, dtype=torch.float64).pin_memory()
+    te = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Hm.solve(b_host, h_host, tol=TOL, stream=stream)
+        te.append((time.perf_counter() - t0) * 1e3)
+    p50m, p50d = float(np.median(tm)), float(np.median(td))
+    if ws > 1:
+        t = torch.tensor([p50m, p50d, float(np.mean(tm)), float(np.median(te))], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        p50m, p50d, mean_m, p50e = t.tolist()
+    else:
+        mean_m, p50e = float(np.mean(tm)), float(np.median(te))
+    if rank != 0:
+        torch.distributed.destroy_process_group()
+        return
+    peak, peak_src = peaks()
+    kern = {}
+    for name, (ms, cnt, byts) in kinds.items():
+        if cnt:
+            per = ms / cnt
+            kern[name] = {"ms_per_launch": per, "launches": cnt, "bytes_per_launch": byts,
+                          "gbs": byts / (per * 1e-3) / 1e9 if per > 0 and byts > 0 else None}
+    fine = [k for k in ("pre", "restrict", "prolong", "post") if k in kern]
+    fb = sum(kern[k]["bytes_per_launch"] for k in fine)
+    ft = sum(kern[k]["ms_per_launch"] for k in fine)
+    fine_gbs = fb / (ft * 1e-3) / 1e9 if ft > 0 else None
+    dom = max((k for k in kern if kern[k]["gbs"]), key=lambda k: kern[k]["ms_per_launch"] * kern[k]["launches"])
+    roof = {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["gbs"], "peak": peak, "unit": "GB/s",
+            "frac": kern[dom]["gbs"] / peak, "peak_source": peak_src, "traffic": None,
+            "bytes_per_launch": kern[dom]["bytes_per_launch"], "ms_per_launch": kern[dom]["ms_per_launch"]}
+    out = {"metric": METRIC, "value": p50m, "unit": "ms", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": mean_m, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32 V-cycle + f64 CG", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "n": n, "tol": TOL, "prec": "mixed32",
+                      "smoother": args.smoother, "levels": [l["n"] for l in info],
+                      "l2": "flushed before every timed solve (256 MiB write)",
+                      "parallelism": "replicas" if ws > 1 else "single GPU"},
+           "p50_ms": p50m, "p99_ms": float(np.percentile(tm, 99)), "iters": it_m, "relres": rel_m,
+           "status": st_m, "solves_per_s": ws * 1e3 / p50m,
+           "fp64": {"p50_ms": p50d, "p99_ms": float(np.percentile(td, 99)), "iters": it_d, "relres": rel_d,
+                    "status": st_d},
+           "mixed_speedup_vs_fp64": p50d / p50m,
+           "vcycle_fine_gbs": fine_gbs, "vcycle_fine_frac": (fine_gbs / peak) if fine_gbs else None,
+           "kernels": kern, "setup_ms": setup_ms,
+           "e2e": {"value": p50e, "unit": "ms", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},
+           "roofline": roof, "gpu_launches": int(launches), "timed_wall_s": t_wall,
+           "clocks": clk.summary()}
+    if ws == 1 and not args.no_cpu_baseline:
+        cb, x_or = cpu_baseline_sample()
+        out["cpu_baseline"] = cb
+        href = x_or
+        out["rel_err_vs_oracle_at_1e-8"] = float(np.linalg.norm(h_mixed.cpu().numpy() - href) / np.linalg.norm(href))
+    print(json.dumps(out), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--smoother", choices=("jacobi", "chebyshev"), default="chebyshev")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -191,6 +191,47 @@ int gw_hierarchy_info(gw_hierarchy H, gw_level_info *out, int cap, int *nlevels)
 int gw_hierarchy_export(gw_hierarchy H, int level, int *agg, unsigned char *root, int *a_rowptr, int *a_col,
                         double *a_val, int *p_rowptr, int *p_col, double *p_val, void *stream);
 
+/*
+ * Benchmark instrumentation (no counterpart in the paper).  With profiling
+ * on, the captured CG iteration graph records CUDA events around the
+ * level-0 work of every iteration: the outer FP64 product q = A p with its
+ * dot (GW_PK_SPMV), the x/r update (GW_PK_UPDATE), the pre-smoothing with
+ * the residual (GW_PK_PRE), the restriction (GW_PK_RESTRICT), everything on
+ * the coarser levels (GW_PK_COARSE), the interpolation and correction
+ * (GW_PK_PROLONG), the post-smoothing that yields z (GW_PK_POST) and the
+ * direction update (GW_PK_PUPDATE).  Only iterations that ran to the end are
+ * counted.  bytes[k] is the algorithmic traffic of one launch of kind k:
+ * every array counted once, a gathered vector once, padding not counted.
+ * kernel_launches counts every kernel the solves launched (graph kernel
+ * nodes included), profiling on or off.
+ */
+enum {
+    GW_PK_SPMV = 0,
+    GW_PK_UPDATE,
+    GW_PK_PRE,
+    GW_PK_RESTRICT,
+    GW_PK_COARSE,
+    GW_PK_PROLONG,
+    GW_PK_POST,
+    GW_PK_PUPDATE,
+    GW_PK_COUNT
+};
+
+typedef struct {
+    double ms[GW_PK_COUNT];           /* summed device time per kind */
+    long long launches[GW_PK_COUNT];  /* timed launches per kind */
+    double bytes[GW_PK_COUNT];        /* algorithmic bytes of one launch */
+    long long kernel_launches;        /* kernels launched by gw_pcg_solve */
+    long long solves;                 /* gw_pcg_solve calls counted */
+} gw_profile;
+
+/* Turns the event instrumentation on or off (the iteration graph is
+ * re-captured on the next solve). */
+int gw_profile_enable(gw_hierarchy H, int on);
+
+/* Copies the counters gathered since the last reset; reset != 0 clears them. */
+int gw_profile_read(gw_hierarchy H, gw_profile *out, int reset);
+
 void gw_matrix_free(gw_matrix A);
 void gw_hierarchy_free(gw_hierarchy H);
 

@@ -53,7 +53,7 @@ struct DevIn {
 
 Hier::~Hier()
 {
-    if (gexec) cudaGraphExecDestroy(gexec);
+    drop_graphs(*this);
     if (cap) cudaStreamDestroy(cap);
     if (ctl_host) cudaFreeHost(ctl_host);
 }
@@ -447,6 +447,42 @@ int gw_hierarchy_export(gw_hierarchy H, int level, int *agg, unsigned char *root
         if (p_val) to_device(p_val, P.v.p, (size_t)P.nnz * sizeof(double), st);
     }
     GW_CUDA(cudaStreamSynchronize(st));
+    GW_API_END
+}
+
+int gw_profile_enable(gw_hierarchy H, int on)
+{
+    GW_API_BEGIN
+    if (!H) fail(GW_ERR_ARG, "gw_profile_enable: null hierarchy");
+    DeviceGuard g(H->H.dev);
+    if ((bool)on != H->H.prof_on) {
+        H->H.prof_on = on != 0;
+        drop_graphs(H->H);
+    }
+    GW_API_END
+}
+
+int gw_profile_read(gw_hierarchy H, gw_profile *out, int reset)
+{
+    GW_API_BEGIN
+    if (!H || !out) fail(GW_ERR_ARG, "gw_profile_read: null argument");
+    Hier &h = H->H;
+    memset(out, 0, sizeof *out);
+    for (int k = 0; k < GW_PK_COUNT; ++k) {
+        out->ms[k] = h.prof_ms[k];
+        out->launches[k] = h.prof_cnt[k];
+        out->bytes[k] = h.prof_b[k];
+    }
+    out->kernel_launches = h.launches;
+    out->solves = h.solves;
+    if (reset) {
+        for (int k = 0; k < GW_PK_COUNT; ++k) {
+            h.prof_ms[k] = 0.0;
+            h.prof_cnt[k] = 0;
+        }
+        h.launches = 0;
+        h.solves = 0;
+    }
     GW_API_END
 }
 

@@ -14,6 +14,8 @@
 // leaves at once when the control block says the solve has finished, so a
 // captured graph of several iterations can be replayed without a host round
 // trip per iteration.
+#include <string.h>
+
 #include "gw_internal.cuh"
 
 namespace gw {
@@ -313,6 +315,33 @@ __global__ void __launch_bounds__(BS) k_axpy(int n, const T *__restrict__ d, T *
 }
 
 // ---------------------------------------------------------- V-cycle driver --
+// Algorithmic bytes of each launch (every array counted once, a gathered
+// vector once, padding slots not counted) are added to H.prof_bytes while a
+// profiled graph is captured; see the bytes_* helpers.
+static inline double vbytes(const Hier &H, double b) { return H.prof_capture ? b : 0.0; }
+
+static void mark_begin(Hier &H, int kind, cudaStream_t st)
+{
+    if (!H.prof_capture) return;
+    Hier::Mark m;
+    m.kind = kind;
+    m.iter = H.cap_iter;
+    m.bytes = 0.0;
+    GW_CUDA(cudaEventCreate(&m.a));
+    GW_CUDA(cudaEventCreate(&m.b));
+    GW_CUDA(cudaEventRecord(m.a, st));
+    H.marks.push_back(m);
+    H.prof_bytes = 0.0;
+}
+
+static void mark_end(Hier &H, cudaStream_t st)
+{
+    if (!H.prof_capture) return;
+    Hier::Mark &m = H.marks.back();
+    GW_CUDA(cudaEventRecord(m.b, st));
+    m.bytes = H.prof_bytes;
+}
+
 template <class T>
 static void smooth(Hier &H, std::vector<CycLevel<T>> &C, int l, const void *bptr, bool b_is_double, bool x0zero,
                    bool last, double *zout, Ctl *ctl, const double *q, int mode, cudaStream_t st)
@@ -324,12 +353,16 @@ static void smooth(Hier &H, std::vector<CycLevel<T>> &C, int l, const void *bptr
     const double *b64 = (const double *)bptr;
     const T *bT = (const T *)bptr;
     double *part = H.part.p;
+    const double n = lv.n, nnz = (double)lv.A.nnz, sx = sizeof(T), sb = b_is_double ? 8.0 : sx;
+    const double amat = nnz * (sx + 4.0);
     if (H.o.smoother == GW_SMOOTH_JACOBI) {
         T *cur = lv.x.p, *nxt = lv.t.p;
         for (int s = 0; s < nu; ++s) {
             const bool first = x0zero && s == 0;
             const bool fin = last && s == nu - 1;
             const T *xi = first ? nullptr : cur;
+            const double so = fin ? 8.0 : sx;
+            H.prof_bytes += vbytes(H, (first ? 0.0 : amat + n * sx) + n * sx + n * sb + n * so + (fin && q ? 8.0 * n : 0.0));
             if (fin) {
                 if (b_is_double)
                     k_jacobi<T, double, double, true><<<g, BS, 0, st>>>(A, lv.dw.p, b64, xi, zout, q, part, ctl, mode);
@@ -352,7 +385,9 @@ static void smooth(Hier &H, std::vector<CycLevel<T>> &C, int l, const void *bptr
         const int zero = x0zero && s == 0;
         const bool fin = last && s == nu - 1;
         T *d = lv.d.p, *dn = lv.d2.p;
+        const double b0 = n * sb + n * sx + (zero ? 0.0 : amat + n * sx);
         if (fin && m == 1) {
+            H.prof_bytes += vbytes(H, b0 + 2.0 * n * sx + n * 8.0 + (q ? 8.0 * n : 0.0));
             if (b_is_double)
                 k_cheb0<T, double, double, true><<<g, BS, 0, st>>>(A, lv.dw.p, b64, lv.x.p, lv.r.p, d, zout, (T)lv.c0,
                                                                    zero, q, part, ctl, mode);
@@ -361,6 +396,7 @@ static void smooth(Hier &H, std::vector<CycLevel<T>> &C, int l, const void *bptr
                                                               q, part, ctl, mode);
             continue;
         }
+        H.prof_bytes += vbytes(H, b0 + (zero ? 3.0 : 2.0) * n * sx);
         if (b_is_double)
             k_cheb0<T, double, T, false><<<g, BS, 0, st>>>(A, lv.dw.p, b64, lv.x.p, lv.r.p, d, (T *)nullptr,
                                                            (T)lv.c0, zero, q, part, ctl, mode);
@@ -368,12 +404,16 @@ static void smooth(Hier &H, std::vector<CycLevel<T>> &C, int l, const void *bptr
             k_cheb0<T, T, T, false><<<g, BS, 0, st>>>(A, lv.dw.p, bT, lv.x.p, lv.r.p, d, (T *)nullptr, (T)lv.c0,
                                                       zero, q, part, ctl, mode);
         if (m == 1) {
-            if (!zero) k_axpy<T><<<g, BS, 0, st>>>(lv.n, d, lv.x.p, ctl);
+            if (!zero) {
+                H.prof_bytes += vbytes(H, 3.0 * n * sx);
+                k_axpy<T><<<g, BS, 0, st>>>(lv.n, d, lv.x.p, ctl);
+            }
             continue;
         }
         for (int k = 1; k < m; ++k) {
             const bool f2 = fin && k == m - 1;
             const int add_prev = (k == 1 && !zero) ? 1 : 0;
+            H.prof_bytes += vbytes(H, amat + n * sx * 6.0 + (f2 ? n * 8.0 + n * 8.0 + (q ? 8.0 * n : 0.0) - n * sx : 0.0));
             if (f2)
                 k_chebk<T, double, true><<<g, BS, 0, st>>>(A, lv.dw.p, lv.r.p, d, dn, lv.x.p, zout, (T)lv.c1[k],
                                                            (T)lv.c2[k], add_prev, b64, q, part, ctl, mode);
@@ -386,30 +426,41 @@ static void smooth(Hier &H, std::vector<CycLevel<T>> &C, int l, const void *bptr
 }
 
 template <class T>
-static void vcycle_t(Hier &H, std::vector<CycLevel<T>> &C, const double *r, double *z, Ctl *ctl, const double *q, int mode,
-                     cudaStream_t st)
+static void vcycle_t(Hier &H, std::vector<CycLevel<T>> &C, const double *r, double *z, Ctl *ctl, const double *q,
+                     int mode, cudaStream_t st)
 {
     const int L = H.L;
-    if (L == 1) {
-        // a single level: the dense inverse is the preconditioner
-        fail(GW_ERR_SETUP, "a one-level hierarchy is not supported by the V-cycle");
-    }
+    if (L == 1) fail(GW_ERR_SETUP, "a one-level hierarchy is not supported by the V-cycle");
+    const double sx = sizeof(T);
     for (int l = 0; l < L - 1; ++l) {
         CycLevel<T> &lv = C[l];
         const SV<T> A = view(lv.A);
         const int g = vgrid(lv.n);
         const bool bd = l == 0;
+        const double n = lv.n, sb = bd ? 8.0 : sx, amat = (double)lv.A.nnz * (sx + 4.0);
         const void *bptr = bd ? (const void *)r : (const void *)lv.b.p;
+        if (l == 0) mark_begin(H, GW_PK_PRE, st);
         if (H.o.smoother == GW_SMOOTH_JACOBI && H.o.nu <= 1) {
+            H.prof_bytes += vbytes(H, amat + n * sx + n * sb + 2.0 * n * sx);
             if (bd) k_jac0_res<T, double><<<g, BS, 0, st>>>(A, lv.dw.p, r, lv.x.p, lv.r.p, ctl);
             else k_jac0_res<T, T><<<g, BS, 0, st>>>(A, lv.dw.p, lv.b.p, lv.x.p, lv.r.p, ctl);
         } else {
             smooth<T>(H, C, l, bptr, bd, true, false, nullptr, ctl, q, mode, st);
+            H.prof_bytes += vbytes(H, amat + n * sx + n * sb + n * sx);
             if (bd) k_residual<T, double><<<g, BS, 0, st>>>(A, r, lv.x.p, lv.r.p, ctl);
             else k_residual<T, T><<<g, BS, 0, st>>>(A, lv.b.p, lv.x.p, lv.r.p, ctl);
         }
+        if (l == 0) {
+            mark_end(H, st);
+            mark_begin(H, GW_PK_RESTRICT, st);
+        }
+        H.prof_bytes += vbytes(H, (double)lv.R.nnz * (sx + 4.0) + n * sx + (double)lv.R.nr * sx);
         k_spmv<T><<<vgrid(lv.R.nr), BS, 0, st>>>(view(lv.R), lv.r.p, C[l + 1].b.p, ctl);
         GW_LAUNCH_CHECK();
+        if (l == 0) {
+            mark_end(H, st);
+            mark_begin(H, GW_PK_COARSE, st);
+        }
     }
     {
         CycLevel<T> &lc = C[L - 1];
@@ -418,10 +469,22 @@ static void vcycle_t(Hier &H, std::vector<CycLevel<T>> &C, const double *r, doub
     }
     for (int l = L - 2; l >= 0; --l) {
         CycLevel<T> &lv = C[l];
+        const double n = lv.n;
+        if (l == 0) {
+            mark_end(H, st);
+            H.prof_bytes = 0.0;
+            mark_begin(H, GW_PK_PROLONG, st);
+        }
+        H.prof_bytes += vbytes(H, (double)lv.P.nnz * (sx + 4.0) + (double)lv.P.nc * sx + 2.0 * n * sx);
         k_prolong<T><<<vgrid(lv.n), BS, 0, st>>>(view(lv.P), C[l + 1].x.p, lv.x.p, ctl);
+        if (l == 0) {
+            mark_end(H, st);
+            mark_begin(H, GW_PK_POST, st);
+        }
         const bool bd = l == 0;
         const void *bptr = bd ? (const void *)r : (const void *)lv.b.p;
         smooth<T>(H, C, l, bptr, bd, false, l == 0, z, ctl, q, mode, st);
+        if (l == 0) mark_end(H, st);
         GW_LAUNCH_CHECK();
     }
 }
@@ -429,15 +492,13 @@ static void vcycle_t(Hier &H, std::vector<CycLevel<T>> &C, const double *r, doub
 void vcycle_enqueue(Hier &H, const double *r, double *z, Ctl *ctl, bool dot, cudaStream_t st)
 {
     (void)dot;
-    Ctl *c = ctl;
-    if (H.o.prec == GW_PREC_FP64) vcycle_t<double>(H, H.cd, r, z, c, nullptr, 0, st);
-    else vcycle_t<float>(H, H.cf, r, z, c, nullptr, 0, st);
+    if (H.o.prec == GW_PREC_FP64) vcycle_t<double>(H, H.cd, r, z, ctl, nullptr, 0, st);
+    else vcycle_t<float>(H, H.cf, r, z, ctl, nullptr, 0, st);
 }
 
 // ---------------------------------------------------------------- CG kernels --
 __global__ void __launch_bounds__(BS) k_cg_init(int n, const double *__restrict__ b, double *__restrict__ x,
-                                                double *__restrict__ r, double *part, Ctl *c, double tol2, int maxit,
-                                                int flexible)
+                                                double *__restrict__ r, double *part, Ctl *c)
 {
     double loc[1] = {0.0}, tot[1];
     ROWS(i, n)
@@ -449,9 +510,6 @@ __global__ void __launch_bounds__(BS) k_cg_init(int n, const double *__restrict_
     }
     if (reduce_last<1>(loc, part, &c->cnt[0], tot) && threadIdx.x == 0) {
         c->bnorm2 = tot[0];
-        c->tol2 = tol2;
-        c->maxit = maxit;
-        c->flexible = flexible;
         c->it = 0;
         c->check = 0;
         c->status = GW_OK;
@@ -572,65 +630,152 @@ static void cg_iteration(Hier &H, cudaStream_t st)
     const int n = H.n, g = vgrid(n);
     Ctl *c = H.ctl.p;
     const SV<double> A = fine64(H);
+    const double dn = n, nnz = (double)H.A0->nnz;
+    mark_begin(H, GW_PK_SPMV, st);
+    H.prof_bytes += vbytes(H, nnz * 12.0 + 16.0 * dn);
     k_cg_spmv_dot<<<g, BS, 0, st>>>(A, H.p.p, H.q.p, H.part.p, c);
+    mark_end(H, st);
+    mark_begin(H, GW_PK_UPDATE, st);
+    H.prof_bytes += vbytes(H, 48.0 * dn);
     k_cg_update<<<g, BS, 0, st>>>(n, H.x.p, H.r.p, H.p.p, H.q.p, H.part.p, c);
+    mark_end(H, st);
     k_cg_true<<<g, BS, 0, st>>>(A, H.b.p, H.x.p, H.r.p, H.part.p, c, 0);
     const double *q = H.o.prec == GW_PREC_FP64 ? nullptr : H.q.p;
     if (H.o.prec == GW_PREC_FP64) vcycle_t<double>(H, H.cd, H.r.p, H.z.p, c, q, 1, st);
     else vcycle_t<float>(H, H.cf, H.r.p, H.z.p, c, q, 1, st);
+    mark_begin(H, GW_PK_PUPDATE, st);
+    H.prof_bytes += vbytes(H, 24.0 * dn);
     k_cg_p<<<g, BS, 0, st>>>(n, H.z.p, H.p.p, c);
+    mark_end(H, st);
     GW_LAUNCH_CHECK();
 }
 
 static constexpr int GRAPH_ITERS = 4;
 
-static void ensure_graph(Hier &H)
+static size_t kernel_nodes(cudaGraph_t g)
 {
-    if (H.gexec) return;
+    size_t num = 0;
+    GW_CUDA(cudaGraphGetNodes(g, nullptr, &num));
+    std::vector<cudaGraphNode_t> nodes(num);
+    if (num) GW_CUDA(cudaGraphGetNodes(g, nodes.data(), &num));
+    size_t k = 0;
+    for (size_t i = 0; i < num; ++i) {
+        cudaGraphNodeType t;
+        GW_CUDA(cudaGraphNodeGetType(nodes[i], &t));
+        if (t == cudaGraphNodeTypeKernel) ++k;
+    }
+    return k;
+}
+
+template <class F>
+static cudaGraphExec_t capture(Hier &H, F body, long long *nkernels)
+{
     if (!H.cap) GW_CUDA(cudaStreamCreateWithFlags(&H.cap, cudaStreamNonBlocking));
     cudaGraph_t g = nullptr;
     GW_CUDA(cudaStreamBeginCapture(H.cap, cudaStreamCaptureModeThreadLocal));
     try {
-        for (int k = 0; k < GRAPH_ITERS; ++k) cg_iteration(H, H.cap);
+        body(H.cap);
     } catch (...) {
         cudaStreamEndCapture(H.cap, &g);
         if (g) cudaGraphDestroy(g);
+        H.prof_capture = false;
         throw;
     }
     GW_CUDA(cudaStreamEndCapture(H.cap, &g));
-    cudaError_t e = cudaGraphInstantiate(&H.gexec, g, 0);
+    cudaGraphExec_t ex = nullptr;
+    cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+    if (e == cudaSuccess) *nkernels = (long long)kernel_nodes(g);
     cudaGraphDestroy(g);
     GW_CUDA(e);
+    return ex;
+}
+
+void drop_graphs(Hier &H)
+{
+    if (H.gexec) cudaGraphExecDestroy(H.gexec);
+    if (H.ginit) cudaGraphExecDestroy(H.ginit);
+    H.gexec = H.ginit = nullptr;
+    for (auto &m : H.marks) {
+        cudaEventDestroy(m.a);
+        cudaEventDestroy(m.b);
+    }
+    H.marks.clear();
+}
+
+static void ensure_graphs(Hier &H)
+{
+    if (H.gexec && H.ginit) return;
+    drop_graphs(H);
+    const int n = H.n, g = vgrid(n);
+    H.ginit = capture(H, [&](cudaStream_t s) {
+        k_cg_init<<<g, BS, 0, s>>>(n, H.b.p, H.x.p, H.r.p, H.part.p, H.ctl.p);
+        if (H.o.prec == GW_PREC_FP64) vcycle_t<double>(H, H.cd, H.r.p, H.z.p, H.ctl.p, nullptr, 0, s);
+        else vcycle_t<float>(H, H.cf, H.r.p, H.z.p, H.ctl.p, nullptr, 0, s);
+        k_copy<<<g, BS, 0, s>>>(n, H.z.p, H.p.p, H.ctl.p);
+        GW_LAUNCH_CHECK();
+    }, &H.init_kernels);
+    H.prof_capture = H.prof_on;
+    H.gexec = capture(H, [&](cudaStream_t s) {
+        for (int k = 0; k < GRAPH_ITERS; ++k) {
+            H.cap_iter = k;
+            cg_iteration(H, s);
+        }
+    }, &H.iter_kernels);
+    H.prof_capture = false;
     H.graph_iters = GRAPH_ITERS;
+}
+
+// accumulate the profiled level-0 kernel times of one replay of the iteration
+// graph; only iterations that ran to the end (iteration number < it_now, or
+// all of them while the solve continues) are counted
+static void collect_marks(Hier &H, int first_iter, int it_now, bool done)
+{
+    for (auto &m : H.marks) {
+        const int iter = first_iter + m.iter;
+        if (done && iter >= it_now) continue;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, m.a, m.b) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        H.prof_ms[m.kind] += ms;
+        H.prof_cnt[m.kind] += 1;
+        H.prof_b[m.kind] = m.bytes;
+    }
 }
 
 int pcg_run(Hier &H, double tol, int maxit, int *iters, double *relres, cudaStream_t st)
 {
-    const int n = H.n, g = vgrid(n);
     Ctl *c = H.ctl.p;
-    ensure_graph(H);
-    const int flexible = H.o.prec == GW_PREC_FP64 ? 0 : 1;
-    k_cg_init<<<g, BS, 0, st>>>(n, H.b.p, H.x.p, H.r.p, H.part.p, c, tol * tol, maxit, flexible);
-    GW_LAUNCH_CHECK();
-    // z = M r, rz = (r, z), p = z
-    if (H.o.prec == GW_PREC_FP64) vcycle_t<double>(H, H.cd, H.r.p, H.z.p, c, nullptr, 0, st);
-    else vcycle_t<float>(H, H.cf, H.r.p, H.z.p, c, nullptr, 0, st);
-    k_copy<<<g, BS, 0, st>>>(n, H.z.p, H.p.p, c);
-    GW_LAUNCH_CHECK();
+    ensure_graphs(H);
+    Ctl init;
+    memset(&init, 0, sizeof init);
+    init.tol2 = tol * tol;
+    init.maxit = maxit;
+    init.flexible = H.o.prec == GW_PREC_FP64 ? 0 : 1;
+    *H.ctl_host = init;
+    GW_CUDA(cudaMemcpyAsync(c, H.ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, st));
+    GW_CUDA(cudaGraphLaunch(H.ginit, st));
+    H.launches += H.init_kernels;
     const int max_launches = (maxit + GRAPH_ITERS - 1) / GRAPH_ITERS + 2;
     for (int k = 0; k < max_launches; ++k) {
         GW_CUDA(cudaGraphLaunch(H.gexec, st));
+        H.launches += H.iter_kernels;
         GW_CUDA(cudaMemcpyAsync(H.ctl_host, c, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
         GW_CUDA(cudaStreamSynchronize(st));
+        if (H.prof_on && !H.marks.empty()) collect_marks(H, k * GRAPH_ITERS + 1, H.ctl_host->it, H.ctl_host->done);
         if (H.ctl_host->done) break;
     }
     if (H.ctl_host->status == GW_ERR_NOT_CONVERGED || !H.ctl_host->done) {
+        const int g = vgrid(H.n);
         k_cg_true<<<g, BS, 0, st>>>(fine64(H), H.b.p, H.x.p, H.r.p, H.part.p, c, 1);
+        H.launches += 1;
         GW_LAUNCH_CHECK();
         GW_CUDA(cudaMemcpyAsync(H.ctl_host, c, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
         GW_CUDA(cudaStreamSynchronize(st));
         if (!H.ctl_host->done) H.ctl_host->status = GW_ERR_NOT_CONVERGED;
     }
+    H.solves += 1;
     if (iters) *iters = H.ctl_host->it;
     if (relres) *relres = H.ctl_host->relres;
     return H.ctl_host->status;

@@ -182,10 +182,26 @@ struct Hier {
     DBuf<Ctl> ctl;
     Ctl *ctl_host = nullptr;   // pinned mirror of the control block
     cudaStream_t cap = nullptr;
-    cudaGraphExec_t gexec = nullptr;
+    cudaGraphExec_t gexec = nullptr, ginit = nullptr;
     int graph_iters = 0;
+    long long init_kernels = 0, iter_kernels = 0;
+    // profiling of the level-0 kernels (events captured into the graph)
+    struct Mark {
+        int kind, iter;
+        cudaEvent_t a, b;
+        double bytes;
+    };
+    bool prof_on = false, prof_capture = false;
+    int cap_iter = 0;
+    double prof_bytes = 0.0;
+    std::vector<Mark> marks;
+    double prof_ms[GW_PK_COUNT] = {0}, prof_b[GW_PK_COUNT] = {0};
+    long long prof_cnt[GW_PK_COUNT] = {0};
+    long long launches = 0, solves = 0;
     ~Hier();
 };
+
+void drop_graphs(Hier &H);
 
 void build_hierarchy(Hier &H, cudaStream_t st);
 void vcycle_enqueue(Hier &H, const double *r, double *z, Ctl *ctl, bool dot, cudaStream_t st);

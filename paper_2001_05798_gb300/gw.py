@@ -21,7 +21,9 @@ GW_SMOOTH_JACOBI, GW_SMOOTH_CHEBYSHEV = 0, 1
 
 EXPORTS = ("gw_amg_opts_default", "gw_assemble", "gw_matrix_size", "gw_matrix_export", "gw_amg_setup",
            "gw_pcg_solve", "gw_vcycle", "gw_hierarchy_info", "gw_hierarchy_export", "gw_matrix_free",
-           "gw_hierarchy_free", "gw_status_str", "gw_last_error")
+           "gw_hierarchy_free", "gw_status_str", "gw_last_error", "gw_profile_enable", "gw_profile_read")
+
+PK_NAMES = ("spmv", "update", "pre", "restrict", "coarse", "prolong", "post", "pupdate")
 
 
 class gw_grid(ctypes.Structure):
@@ -43,6 +45,11 @@ class gw_level_info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("nnz", ctypes.c_longlong), ("nnz_p", ctypes.c_longlong),
                 ("bytes", ctypes.c_longlong), ("naggregates", ctypes.c_int), ("mis_rounds", ctypes.c_int),
                 ("omega_p", ctypes.c_double), ("jacobi_w", ctypes.c_double), ("lambda_max", ctypes.c_double)]
+
+
+class gw_profile(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 8), ("launches", ctypes.c_longlong * 8), ("bytes", ctypes.c_double * 8),
+                ("kernel_launches", ctypes.c_longlong), ("solves", ctypes.c_longlong)]
 
 
 class GwError(RuntimeError):
@@ -78,6 +85,8 @@ def load():
         "gw_hierarchy_free": (None, [vp]),
         "gw_status_str": (ctypes.c_char_p, [i]),
         "gw_last_error": (ctypes.c_char_p, []),
+        "gw_profile_enable": (i, [vp, i]),
+        "gw_profile_read": (i, [vp, P(gw_profile), i]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -223,6 +232,16 @@ class Hierarchy:
         if check and st not in (GW_OK, GW_ERR_NOT_CONVERGED):
             _check(st)
         return h, it.value, rel.value, st
+
+    def profile(self, on=True):
+        _check(load().gw_profile_enable(self.h, int(bool(on))))
+
+    def profile_read(self, reset=True):
+        """Per-kind level-0 kernel timing: {name: (ms_total, launches, bytes_per_launch)}, launches, solves."""
+        p = gw_profile()
+        _check(load().gw_profile_read(self.h, ctypes.byref(p), int(bool(reset))))
+        kinds = {PK_NAMES[k]: (p.ms[k], p.launches[k], p.bytes[k]) for k in range(8)}
+        return kinds, p.kernel_launches, p.solves
 
     def vcycle(self, r, z, stream=None):
         _check(load().gw_vcycle(self.h, _ptr(r), _ptr(z), _stream(stream)))

@@ -257,10 +257,15 @@ def run_ours(args):
     fb = sum(kern[k]["bytes_per_launch"] for k in fine)
     ft = sum(kern[k]["ms_per_launch"] for k in fine)
     fine_gbs = fb / (ft * 1e-3) / 1e9 if ft > 0 else None
-    dom = max((k for k in kern if kern[k]["gbs"]), key=lambda k: kern[k]["ms_per_launch"] * kern[k]["launches"])
-    roof = {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["gbs"], "peak": peak, "unit": "GB/s",
-            "frac": kern[dom]["gbs"] / peak, "peak_source": peak_src, "traffic": None,
-            "bytes_per_launch": kern[dom]["bytes_per_launch"], "ms_per_launch": kern[dom]["ms_per_launch"]}
+    timed = [k for k in kern if kern[k]["gbs"]]
+    if timed:
+        dom = max(timed, key=lambda k: kern[k]["ms_per_launch"] * kern[k]["launches"])
+        roof = {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["gbs"], "peak": peak, "unit": "GB/s",
+                "frac": kern[dom]["gbs"] / peak, "peak_source": peak_src, "traffic": None,
+                "bytes_per_launch": kern[dom]["bytes_per_launch"], "ms_per_launch": kern[dom]["ms_per_launch"]}
+    else:
+        roof = {"bound": "hbm", "kernel": None, "achieved": None, "peak": peak, "unit": "GB/s", "frac": None,
+                "peak_source": peak_src, "traffic": None, "note": "kernel timing unavailable"}
     out = {"metric": METRIC, "value": p50m, "unit": "ms", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": mean_m, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32 V-cycle + f64 CG", "data": "synthetic",

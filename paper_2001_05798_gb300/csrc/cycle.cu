@@ -329,7 +329,7 @@ static void mark_begin(Hier &H, int kind, cudaStream_t st)
     m.bytes = 0.0;
     GW_CUDA(cudaEventCreate(&m.a));
     GW_CUDA(cudaEventCreate(&m.b));
-    GW_CUDA(cudaEventRecord(m.a, st));
+    GW_CUDA(cudaEventRecordWithFlags(m.a, st, cudaEventRecordExternal));
     H.marks.push_back(m);
     H.prof_bytes = 0.0;
 }
@@ -338,7 +338,7 @@ static void mark_end(Hier &H, cudaStream_t st)
 {
     if (!H.prof_capture) return;
     Hier::Mark &m = H.marks.back();
-    GW_CUDA(cudaEventRecord(m.b, st));
+    GW_CUDA(cudaEventRecordWithFlags(m.b, st, cudaEventRecordExternal));
     m.bytes = H.prof_bytes;
 }
 

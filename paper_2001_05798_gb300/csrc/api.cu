@@ -101,6 +101,9 @@ static void cheb_coeffs(double lam, int degree, double &c0, double *c1, double *
 void build_hierarchy(Hier &H, cudaStream_t st)
 {
     const gw_amg_opts &o = H.o;
+    int nsm = 0;
+    GW_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, H.dev));
+    H.max_blocks = std::max(1, std::min(RED_MAX_BLOCKS, nsm * 8));
     H.A.clear();
     H.A.emplace_back();  // placeholder for level 0 (the matrix handle's CSR)
     std::vector<DCSR> R;
@@ -167,9 +170,9 @@ void build_hierarchy(Hier &H, cudaStream_t st)
             const int g = (int)std::min<long long>(((long long)n + 255) / 256, 152LL * 16);
             if (f64) {
                 CycLevel<double> &c = H.cd[(size_t)k];
-                to_sell<double>(A, c.A, st);
-                to_sell<double>(H.P[(size_t)k], c.P, st);
-                to_sell<double>(R[(size_t)k], c.R, st);
+                to_store<double>(A, c.A, k == 0 ? FMT_STEN : choose_fmt(A), H.gnx, H.gny, H.gnz, st);
+                to_store<double>(H.P[(size_t)k], c.P, choose_fmt(H.P[(size_t)k]), 0, 0, 0, st);
+                to_store<double>(R[(size_t)k], c.R, choose_fmt(R[(size_t)k]), 0, 0, 0, st);
                 c.dw.alloc((size_t)n);
                 k_make_dw<<<std::max(g, 1), 256, 0, st>>>(n, diag.p, scale, nullptr, c.dw.p);
                 c.c0 = c0;
@@ -178,9 +181,9 @@ void build_hierarchy(Hier &H, cudaStream_t st)
                 bytes += (long long)(c.A.bytes() + c.P.bytes() + c.R.bytes() + c.dw.bytes());
             } else {
                 CycLevel<float> &c = H.cf[(size_t)k];
-                to_sell<float>(A, c.A, st);
-                to_sell<float>(H.P[(size_t)k], c.P, st);
-                to_sell<float>(R[(size_t)k], c.R, st);
+                to_store<float>(A, c.A, k == 0 ? FMT_STEN : choose_fmt(A), H.gnx, H.gny, H.gnz, st);
+                to_store<float>(H.P[(size_t)k], c.P, choose_fmt(H.P[(size_t)k]), 0, 0, 0, st);
+                to_store<float>(R[(size_t)k], c.R, choose_fmt(R[(size_t)k]), 0, 0, 0, st);
                 c.dw.alloc((size_t)n);
                 k_make_dw<<<std::max(g, 1), 256, 0, st>>>(n, diag.p, scale, c.dw.p, nullptr);
                 c.c0 = c0;
@@ -201,7 +204,7 @@ void build_hierarchy(Hier &H, cudaStream_t st)
         H.info[(size_t)k].bytes += bytes;
     }
     if (!f64) {
-        to_sell<double>(*H.A0, H.A64, st);
+        to_store<double>(*H.A0, H.A64, FMT_STEN, H.gnx, H.gny, H.gnz, st);
         H.info[0].bytes += (long long)H.A64.bytes();
     }
     const int n = H.A0->nr;
@@ -371,6 +374,9 @@ int gw_amg_setup(gw_matrix A, const gw_amg_opts *opts, gw_hierarchy *H_out, void
         h->H.dev = A->dev;
         h->H.o = o;
         h->H.A0 = &A->A;
+        h->H.gnx = A->nx;
+        h->H.gny = A->ny;
+        h->H.gnz = A->nz;
         build_hierarchy(h->H, st);
         if (h->H.L < 2) fail(GW_ERR_SETUP, "gw_amg_setup: the matrix is small enough for one level (n <= n_coarse)");
     } catch (...) {

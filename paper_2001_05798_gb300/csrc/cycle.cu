@@ -8,6 +8,11 @@
 // Chebyshev polynomials of D^-1 A (Adams et al. 2003), fused with the residual
 // they need.  The coarsest level multiplies by its dense FP64 inverse.
 //
+// Every kernel is written once against a matrix view: the index-free 7-point
+// stencil of level 0, sliced ELL (one thread per row) for short rows, and CSR
+// read by groups of 8 or 32 lanes per row for the long rows of the Galerkin
+// levels, so small levels still spread over every SM.
+//
 // CG (Saad, Algorithm 9.1) runs in FP64 with all scalars on the device: dot
 // products are reduced deterministically (fixed grid, per-block partial sums,
 // the last block to arrive adds them in a fixed order) and every kernel
@@ -22,15 +27,7 @@ namespace gw {
 
 constexpr int BS = 256;
 
-static inline int vgrid(long long n)
-{
-    long long b = (n + BS - 1) / BS;
-    return (int)std::max(1LL, std::min<long long>(b, RED_MAX_BLOCKS));
-}
-
-#define ROWS(i, n) for (int i = blockIdx.x * BS + threadIdx.x; i < (n); i += gridDim.x * BS)
-
-// ---------------------------------------------------------------- sliced ELL --
+// ------------------------------------------------------------ matrix views --
 template <class T>
 struct SV {
     const int *__restrict__ sp;
@@ -38,12 +35,6 @@ struct SV {
     const T *__restrict__ v;
     int nr;
 };
-
-template <class T>
-static SV<T> view(const Sell<T> &S)
-{
-    return SV<T>{S.sp.p, S.ci.p, S.v.p, S.nr};
-}
 
 template <class T>
 struct VecT;
@@ -58,34 +49,122 @@ struct VecT<double> {
     using I = int2;
 };
 
-// sum over the slots of row r of a_rk * f(col_k), in slot order
-template <class T, class F>
-__device__ __forceinline__ T sell_row(const SV<T> &A, int r, F f)
-{
-    using VV = typename VecT<T>::V;
-    using VI = typename VecT<T>::I;
-    constexpr int V = SellV<T>::V;
-    const int s = r >> 5, lane = r & 31;
-    const int base = A.sp[s];
-    const int nch = (A.sp[s + 1] - base) / (SELL_C * V);
-    const VV *vv = reinterpret_cast<const VV *>(A.v + base) + lane;
-    const VI *cc = reinterpret_cast<const VI *>(A.ci + base) + lane;
-    T acc = 0;
-    for (int c = 0; c < nch; ++c) {
-        const VV a = __ldg(vv + c * SELL_C);
-        const VI j = __ldg(cc + c * SELL_C);
-        if constexpr (V == 4) {
-            acc += a.x * f(j.x);
-            acc += a.y * f(j.y);
-            acc += a.z * f(j.z);
-            acc += a.w * f(j.w);
-        } else {
-            acc += a.x * f(j.x);
-            acc += a.y * f(j.y);
+// Sliced ELL, one thread per row; V slots per 16-byte load.
+template <class T>
+struct MSell {
+    using value_type = T;
+    static constexpr int G = 1;
+    SV<T> a;
+    template <class F>
+    __device__ __forceinline__ T dot(int r, int, F f) const
+    {
+        using VV = typename VecT<T>::V;
+        using VI = typename VecT<T>::I;
+        constexpr int V = SellV<T>::V;
+        const int s = r >> 5, lane = r & 31;
+        const int base = a.sp[s];
+        const int nch = (a.sp[s + 1] - base) / (SELL_C * V);
+        const VV *vv = reinterpret_cast<const VV *>(a.v + base) + lane;
+        const VI *cc = reinterpret_cast<const VI *>(a.ci + base) + lane;
+        T acc = 0;
+        for (int c = 0; c < nch; ++c) {
+            const VV x = __ldg(vv + c * SELL_C);
+            const VI j = __ldg(cc + c * SELL_C);
+            if constexpr (V == 4) {
+                acc += x.x * f(j.x);
+                acc += x.y * f(j.y);
+                acc += x.z * f(j.z);
+                acc += x.w * f(j.w);
+            } else {
+                acc += x.x * f(j.x);
+                acc += x.y * f(j.y);
+            }
         }
+        return acc;
     }
-    return acc;
+};
+
+// CSR read by a group of G lanes per row; every lane of the group gets the sum.
+template <class T, int G_>
+struct MCsr {
+    using value_type = T;
+    static constexpr int G = G_;
+    const int *__restrict__ rp;
+    const int *__restrict__ ci;
+    const T *__restrict__ v;
+    int n;
+    template <class F>
+    __device__ __forceinline__ T dot(int i, int lane, F f) const
+    {
+        T s = 0;
+        if (i < n) {
+            const int e1 = rp[i + 1];
+            for (int e = rp[i] + lane; e < e1; e += G) s += __ldg(v + e) * f(__ldg(ci + e));
+        }
+#pragma unroll
+        for (int off = G / 2; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off, G);
+        return s;
+    }
+};
+
+// Index-free 7-point stencil; terms in ascending column order.
+template <class T>
+struct MSten {
+    using value_type = T;
+    static constexpr int G = 1;
+    const T *__restrict__ d;
+    const T *__restrict__ ox;
+    const T *__restrict__ oy;
+    const T *__restrict__ oz;
+    int n, nx, sxy;
+    template <class F>
+    __device__ __forceinline__ T dot(int i, int, F f) const
+    {
+        T s = 0;
+        if (i >= sxy) s += __ldg(oz + i - sxy) * f(i - sxy);
+        if (i >= nx) s += __ldg(oy + i - nx) * f(i - nx);
+        if (i >= 1) s += __ldg(ox + i - 1) * f(i - 1);
+        s += __ldg(d + i) * f(i);
+        if (i + 1 < n) s += __ldg(ox + i) * f(i + 1);
+        if (i + nx < n) s += __ldg(oy + i) * f(i + nx);
+        if (i + sxy < n) s += __ldg(oz + i) * f(i + sxy);
+        return s;
+    }
+};
+
+template <class T, class F>
+static void with_mat(const MatStore<T> &M, F f)
+{
+    switch (M.fmt) {
+    case FMT_SELL: f(MSell<T>{SV<T>{M.sell.sp.p, M.sell.ci.p, M.sell.v.p, M.sell.nr}}); break;
+    case FMT_CSR8: f(MCsr<T, 8>{M.csr.rp.p, M.csr.ci.p, M.csr.v.p, M.csr.nr}); break;
+    case FMT_CSR32: f(MCsr<T, 32>{M.csr.rp.p, M.csr.ci.p, M.csr.v.p, M.csr.nr}); break;
+    default: f(MSten<T>{M.sten.d.p, M.sten.ox.p, M.sten.oy.p, M.sten.oz.p, M.sten.n, M.sten.nx, M.sten.nx * M.sten.ny});
+    }
 }
+
+// Rows handled by groups of M::G lanes.  The loop keeps whole warps together
+// (so the group reductions may shuffle); 'valid' tells a group whether its
+// row exists.
+#define GROUP_ROWS(M, n)                                                                                  \
+    const int lane = M::G == 1 ? 0 : (int)(threadIdx.x & (M::G - 1));                                    \
+    for (int i = (int)((blockIdx.x * (long long)BS + threadIdx.x) / M::G), stride_ = gridDim.x * (BS / M::G); \
+         M::G == 1 ? (i < (n)) : __any_sync(0xffffffffu, i < (n)); i += stride_)
+
+template <class M>
+static inline int grid_for(const Hier &H, long long n)
+{
+    long long b = (n * M::G + BS - 1) / BS;
+    return (int)std::max(1LL, std::min<long long>(b, H.max_blocks));
+}
+
+static inline int vgrid(const Hier &H, long long n)
+{
+    long long b = (n + BS - 1) / BS;
+    return (int)std::max(1LL, std::min<long long>(b, H.max_blocks));
+}
+
+#define ROWS(i, n) for (int i = blockIdx.x * BS + threadIdx.x; i < (n); i += gridDim.x * BS)
 
 // ------------------------------------------------------------- reductions --
 __device__ __forceinline__ double warp_sum(double v)
@@ -160,75 +239,93 @@ __device__ __forceinline__ void cg_rz_epilogue(double lrz, double lqz, double *p
 }
 
 // x = dw * b ; r = b - A x   (first Jacobi step from zero, fused with the residual)
-template <class T, class BT>
-__global__ void __launch_bounds__(BS) k_jac0_res(SV<T> A, const T *__restrict__ dw, const BT *__restrict__ b,
-                                                 T *__restrict__ x, T *__restrict__ r, const Ctl *ctl)
+template <class M, class BT>
+__global__ void __launch_bounds__(BS) k_jac0_res(M A, int n, const typename M::value_type *__restrict__ dw,
+                                                 const BT *__restrict__ b, typename M::value_type *__restrict__ x,
+                                                 typename M::value_type *__restrict__ r, const Ctl *ctl)
 {
+    using T = typename M::value_type;
     if (finished(ctl)) return;
-    ROWS(i, A.nr)
+    GROUP_ROWS(M, n)
     {
-        const T bi = (T)b[i];
-        const T ax = sell_row(A, i, [&](int j) { return __ldg(dw + j) * (T)__ldg(b + j); });
-        x[i] = __ldg(dw + i) * bi;
-        r[i] = bi - ax;
+        const T ax = A.dot(i, lane, [&](int j) { return __ldg(dw + j) * (T)__ldg(b + j); });
+        if (i < n && lane == 0) {
+            const T bi = (T)b[i];
+            x[i] = __ldg(dw + i) * bi;
+            r[i] = bi - ax;
+        }
     }
 }
 
-// xo = xi + dw * (b - A xi); xi == nullptr means xi = 0.  OUT = double with
-// DOT: xo is the preconditioned residual z of CG and (b, z) is reduced.
-template <class T, class BT, class OT, bool DOT>
-__global__ void __launch_bounds__(BS) k_jacobi(SV<T> A, const T *__restrict__ dw, const BT *__restrict__ b,
-                                               const T *__restrict__ xi, OT *__restrict__ xo,
-                                               const double *__restrict__ q, double *part, Ctl *ctl, int mode)
+// xo = xi + dw * (b - A xi); xi == nullptr means xi = 0.  With DOT, xo is the
+// CG's z (double) and (b, z) [and (q, z)] are reduced.
+template <class M, class BT, class OT, bool DOT>
+__global__ void __launch_bounds__(BS) k_jacobi(M A, int n, const typename M::value_type *__restrict__ dw,
+                                               const BT *__restrict__ b, const typename M::value_type *__restrict__ xi,
+                                               OT *__restrict__ xo, const double *__restrict__ q, double *part,
+                                               Ctl *ctl, int mode)
 {
+    using T = typename M::value_type;
     if (finished(ctl)) return;
     double lrz = 0.0, lqz = 0.0;
-    ROWS(i, A.nr)
+    GROUP_ROWS(M, n)
     {
-        const T bi = (T)b[i];
-        T xn;
-        if (xi) {
-            const T ax = sell_row(A, i, [&](int j) { return __ldg(xi + j); });
-            xn = xi[i] + __ldg(dw + i) * (bi - ax);
-        } else {
-            xn = __ldg(dw + i) * bi;
-        }
-        xo[i] = (OT)xn;
-        if constexpr (DOT) {
-            lrz += (double)b[i] * (double)xn;
-            if (q) lqz += q[i] * (double)xn;
+        T ax = 0;
+        if (xi) ax = A.dot(i, lane, [&](int j) { return __ldg(xi + j); });
+        if (i < n && lane == 0) {
+            const T bi = (T)b[i];
+            const T xn = xi ? xi[i] + __ldg(dw + i) * (bi - ax) : __ldg(dw + i) * bi;
+            xo[i] = (OT)xn;
+            if constexpr (DOT) {
+                lrz += (double)b[i] * (double)xn;
+                if (q) lqz += q[i] * (double)xn;
+            }
         }
     }
     if constexpr (DOT) cg_rz_epilogue(lrz, lqz, part, ctl, mode);
 }
 
 // r = b - A x
-template <class T, class BT>
-__global__ void __launch_bounds__(BS) k_residual(SV<T> A, const BT *__restrict__ b, const T *__restrict__ x,
-                                                 T *__restrict__ r, const Ctl *ctl)
+template <class M, class BT>
+__global__ void __launch_bounds__(BS) k_residual(M A, int n, const BT *__restrict__ b,
+                                                 const typename M::value_type *__restrict__ x,
+                                                 typename M::value_type *__restrict__ r, const Ctl *ctl)
 {
+    using T = typename M::value_type;
     if (finished(ctl)) return;
-    ROWS(i, A.nr)
+    GROUP_ROWS(M, n)
     {
-        const T ax = sell_row(A, i, [&](int j) { return __ldg(x + j); });
-        r[i] = (T)b[i] - ax;
+        const T ax = A.dot(i, lane, [&](int j) { return __ldg(x + j); });
+        if (i < n && lane == 0) r[i] = (T)b[i] - ax;
     }
 }
 
-// y = M x (restriction R r)
-template <class T>
-__global__ void __launch_bounds__(BS) k_spmv(SV<T> M, const T *__restrict__ x, T *__restrict__ y, const Ctl *ctl)
+// y = R x (restriction)
+template <class M>
+__global__ void __launch_bounds__(BS) k_spmv(M R, int n, const typename M::value_type *__restrict__ x,
+                                             typename M::value_type *__restrict__ y, const Ctl *ctl)
 {
+    using T = typename M::value_type;
     if (finished(ctl)) return;
-    ROWS(i, M.nr) y[i] = sell_row(M, i, [&](int j) { return __ldg(x + j); });
+    GROUP_ROWS(M, n)
+    {
+        const T s = R.dot(i, lane, [&](int j) { return __ldg(x + j); });
+        if (i < n && lane == 0) y[i] = s;
+    }
 }
 
 // x += P e (interpolate and correct)
-template <class T>
-__global__ void __launch_bounds__(BS) k_prolong(SV<T> P, const T *__restrict__ e, T *__restrict__ x, const Ctl *ctl)
+template <class M>
+__global__ void __launch_bounds__(BS) k_prolong(M P, int n, const typename M::value_type *__restrict__ e,
+                                                typename M::value_type *__restrict__ x, const Ctl *ctl)
 {
+    using T = typename M::value_type;
     if (finished(ctl)) return;
-    ROWS(i, P.nr) x[i] += sell_row(P, i, [&](int j) { return __ldg(e + j); });
+    GROUP_ROWS(M, n)
+    {
+        const T s = P.dot(i, lane, [&](int j) { return __ldg(e + j); });
+        if (i < n && lane == 0) x[i] += s;
+    }
 }
 
 // x = Ainv b on the coarsest level (dense FP64 inverse), one warp per row
@@ -250,58 +347,69 @@ __global__ void __launch_bounds__(BS) k_coarse(int n, const double *__restrict__
 // Chebyshev first step: r = b - A x (r = b when x0zero), d = c0 dw r.  x is
 // gathered here, so it is not written in place: with x0zero x = d; otherwise
 // the next step (or k_axpy) adds d.  DOT: xo = x + d is the CG's z.
-template <class T, class BT, class OT, bool DOT>
-__global__ void __launch_bounds__(BS) k_cheb0(SV<T> A, const T *__restrict__ dw, const BT *__restrict__ b, T *x,
-                                              T *__restrict__ r, T *__restrict__ d, OT *__restrict__ xo, T c0,
-                                              int x0zero, const double *__restrict__ q, double *part, Ctl *ctl,
-                                              int mode)
+template <class M, class BT, class OT, bool DOT>
+__global__ void __launch_bounds__(BS) k_cheb0(M A, int n, const typename M::value_type *__restrict__ dw,
+                                              const BT *__restrict__ b, typename M::value_type *x,
+                                              typename M::value_type *__restrict__ r,
+                                              typename M::value_type *__restrict__ d, OT *__restrict__ xo,
+                                              typename M::value_type c0, int x0zero, const double *__restrict__ q,
+                                              double *part, Ctl *ctl, int mode)
 {
+    using T = typename M::value_type;
     if (finished(ctl)) return;
     double lrz = 0.0, lqz = 0.0;
-    ROWS(i, A.nr)
+    GROUP_ROWS(M, n)
     {
-        const T bi = (T)b[i];
-        T ri = bi;
-        if (!x0zero) ri -= sell_row(A, i, [&](int j) { return __ldg(x + j); });
-        const T di = c0 * (__ldg(dw + i) * ri);
-        r[i] = ri;
-        d[i] = di;
-        if constexpr (DOT) {
-            const T xn = (x0zero ? (T)0 : x[i]) + di;
-            xo[i] = (OT)xn;
-            lrz += (double)b[i] * (double)xn;
-            if (q) lqz += q[i] * (double)xn;
-        } else {
-            if (x0zero) x[i] = di;
+        T ax = 0;
+        if (!x0zero) ax = A.dot(i, lane, [&](int j) { return __ldg(x + j); });
+        if (i < n && lane == 0) {
+            const T ri = (T)b[i] - ax;
+            const T di = c0 * (__ldg(dw + i) * ri);
+            r[i] = ri;
+            d[i] = di;
+            if constexpr (DOT) {
+                const T xn = (x0zero ? (T)0 : x[i]) + di;
+                xo[i] = (OT)xn;
+                lrz += (double)b[i] * (double)xn;
+                if (q) lqz += q[i] * (double)xn;
+            } else {
+                if (x0zero) x[i] = di;
+            }
         }
     }
     if constexpr (DOT) cg_rz_epilogue(lrz, lqz, part, ctl, mode);
 }
 
 // Chebyshev step k >= 2: r -= A d; dn = c1 d + c2 dw r; x += (add_prev ? d : 0) + dn
-template <class T, class OT, bool DOT>
-__global__ void __launch_bounds__(BS) k_chebk(SV<T> A, const T *__restrict__ dw, T *__restrict__ r,
-                                              const T *__restrict__ d, T *__restrict__ dn, T *x, OT *__restrict__ xo,
-                                              T c1, T c2, int add_prev, const double *__restrict__ b0,
+template <class M, class OT, bool DOT>
+__global__ void __launch_bounds__(BS) k_chebk(M A, int n, const typename M::value_type *__restrict__ dw,
+                                              typename M::value_type *__restrict__ r,
+                                              const typename M::value_type *__restrict__ d,
+                                              typename M::value_type *__restrict__ dn, typename M::value_type *x,
+                                              OT *__restrict__ xo, typename M::value_type c1,
+                                              typename M::value_type c2, int add_prev, const double *__restrict__ b0,
                                               const double *__restrict__ q, double *part, Ctl *ctl, int mode)
 {
+    using T = typename M::value_type;
     if (finished(ctl)) return;
     double lrz = 0.0, lqz = 0.0;
-    ROWS(i, A.nr)
+    GROUP_ROWS(M, n)
     {
-        const T ad = sell_row(A, i, [&](int j) { return __ldg(d + j); });
-        const T ri = r[i] - ad;
-        const T dp = d[i];
-        const T dni = c1 * dp + c2 * (__ldg(dw + i) * ri);
-        const T xn = x[i] + (add_prev ? dp : (T)0) + dni;
-        r[i] = ri;
-        dn[i] = dni;
-        if constexpr (DOT) {
-            xo[i] = (OT)xn;
-            lrz += b0[i] * (double)xn;
-            if (q) lqz += q[i] * (double)xn;
-        } else {
-            x[i] = xn;
+        const T ad = A.dot(i, lane, [&](int j) { return __ldg(d + j); });
+        if (i < n && lane == 0) {
+            const T ri = r[i] - ad;
+            const T dp = d[i];
+            const T dni = c1 * dp + c2 * (__ldg(dw + i) * ri);
+            const T xn = x[i] + (add_prev ? dp : (T)0) + dni;
+            r[i] = ri;
+            dn[i] = dni;
+            if constexpr (DOT) {
+                xo[i] = (OT)xn;
+                lrz += b0[i] * (double)xn;
+                if (q) lqz += q[i] * (double)xn;
+            } else {
+                x[i] = xn;
+            }
         }
     }
     if constexpr (DOT) cg_rz_epilogue(lrz, lqz, part, ctl, mode);
@@ -317,7 +425,7 @@ __global__ void __launch_bounds__(BS) k_axpy(int n, const T *__restrict__ d, T *
 // ---------------------------------------------------------- V-cycle driver --
 // Algorithmic bytes of each launch (every array counted once, a gathered
 // vector once, padding slots not counted) are added to H.prof_bytes while a
-// profiled graph is captured; see the bytes_* helpers.
+// profiled graph is captured.
 static inline double vbytes(const Hier &H, double b) { return H.prof_capture ? b : 0.0; }
 
 static void mark_begin(Hier &H, int kind, cudaStream_t st)
@@ -342,87 +450,102 @@ static void mark_end(Hier &H, cudaStream_t st)
     m.bytes = H.prof_bytes;
 }
 
+// bytes of the matrix itself: values + indices (none for the stencil)
+template <class T>
+static double mat_bytes(const MatStore<T> &M)
+{
+    if (M.fmt == FMT_STEN) return 4.0 * M.nr * sizeof(T);
+    return (double)M.nnz * (sizeof(T) + 4.0);
+}
+
 template <class T>
 static void smooth(Hier &H, std::vector<CycLevel<T>> &C, int l, const void *bptr, bool b_is_double, bool x0zero,
                    bool last, double *zout, Ctl *ctl, const double *q, int mode, cudaStream_t st)
 {
     CycLevel<T> &lv = C[l];
-    const SV<T> A = view(lv.A);
-    const int g = vgrid(lv.n);
     const int nu = std::max(1, H.o.nu);
     const double *b64 = (const double *)bptr;
     const T *bT = (const T *)bptr;
     double *part = H.part.p;
-    const double n = lv.n, nnz = (double)lv.A.nnz, sx = sizeof(T), sb = b_is_double ? 8.0 : sx;
-    const double amat = nnz * (sx + 4.0);
-    if (H.o.smoother == GW_SMOOTH_JACOBI) {
-        T *cur = lv.x.p, *nxt = lv.t.p;
+    const int n = lv.n;
+    const double dn = n, sx = sizeof(T), sb = b_is_double ? 8.0 : sx;
+    const double amat = mat_bytes(lv.A);
+    with_mat(lv.A, [&](auto A) {
+        using M = decltype(A);
+        const int g = grid_for<M>(H, n);
+        if (H.o.smoother == GW_SMOOTH_JACOBI) {
+            T *cur = lv.x.p, *nxt = lv.t.p;
+            for (int s = 0; s < nu; ++s) {
+                const bool first = x0zero && s == 0;
+                const bool fin = last && s == nu - 1;
+                const T *xi = first ? nullptr : cur;
+                const double so = fin ? 8.0 : sx;
+                H.prof_bytes += vbytes(H, (first ? 0.0 : amat + dn * sx) + dn * sx + dn * sb + dn * so +
+                                              (fin && q ? 8.0 * dn : 0.0));
+                if (fin) {
+                    if (b_is_double)
+                        k_jacobi<M, double, double, true><<<g, BS, 0, st>>>(A, n, lv.dw.p, b64, xi, zout, q, part, ctl, mode);
+                    else
+                        k_jacobi<M, T, double, true><<<g, BS, 0, st>>>(A, n, lv.dw.p, bT, xi, zout, q, part, ctl, mode);
+                } else {
+                    if (b_is_double)
+                        k_jacobi<M, double, T, false><<<g, BS, 0, st>>>(A, n, lv.dw.p, b64, xi, nxt, q, part, ctl, mode);
+                    else
+                        k_jacobi<M, T, T, false><<<g, BS, 0, st>>>(A, n, lv.dw.p, bT, xi, nxt, q, part, ctl, mode);
+                    std::swap(cur, nxt);
+                }
+            }
+            if (cur != lv.x.p)
+                GW_CUDA(cudaMemcpyAsync(lv.x.p, cur, (size_t)n * sizeof(T), cudaMemcpyDeviceToDevice, st));
+            return;
+        }
+        // Chebyshev of degree m, nu times
+        const int m = std::max(1, H.o.degree);
         for (int s = 0; s < nu; ++s) {
-            const bool first = x0zero && s == 0;
+            const int zero = x0zero && s == 0;
             const bool fin = last && s == nu - 1;
-            const T *xi = first ? nullptr : cur;
-            const double so = fin ? 8.0 : sx;
-            H.prof_bytes += vbytes(H, (first ? 0.0 : amat + n * sx) + n * sx + n * sb + n * so + (fin && q ? 8.0 * n : 0.0));
-            if (fin) {
+            T *d = lv.d.p, *dnx = lv.d2.p;
+            const double b0 = dn * sb + dn * sx + (zero ? 0.0 : amat + dn * sx);
+            if (fin && m == 1) {
+                H.prof_bytes += vbytes(H, b0 + 2.0 * dn * sx + dn * 8.0 + (q ? 8.0 * dn : 0.0));
                 if (b_is_double)
-                    k_jacobi<T, double, double, true><<<g, BS, 0, st>>>(A, lv.dw.p, b64, xi, zout, q, part, ctl, mode);
+                    k_cheb0<M, double, double, true><<<g, BS, 0, st>>>(A, n, lv.dw.p, b64, lv.x.p, lv.r.p, d, zout,
+                                                                       (T)lv.c0, zero, q, part, ctl, mode);
                 else
-                    k_jacobi<T, T, double, true><<<g, BS, 0, st>>>(A, lv.dw.p, bT, xi, zout, q, part, ctl, mode);
-            } else {
-                if (b_is_double)
-                    k_jacobi<T, double, T, false><<<g, BS, 0, st>>>(A, lv.dw.p, b64, xi, nxt, q, part, ctl, mode);
-                else
-                    k_jacobi<T, T, T, false><<<g, BS, 0, st>>>(A, lv.dw.p, bT, xi, nxt, q, part, ctl, mode);
-                std::swap(cur, nxt);
+                    k_cheb0<M, T, double, true><<<g, BS, 0, st>>>(A, n, lv.dw.p, bT, lv.x.p, lv.r.p, d, zout, (T)lv.c0,
+                                                                  zero, q, part, ctl, mode);
+                continue;
             }
-        }
-        if (cur != lv.x.p) GW_CUDA(cudaMemcpyAsync(lv.x.p, cur, (size_t)lv.n * sizeof(T), cudaMemcpyDeviceToDevice, st));
-        return;
-    }
-    // Chebyshev of degree m, nu times
-    const int m = std::max(1, H.o.degree);
-    for (int s = 0; s < nu; ++s) {
-        const int zero = x0zero && s == 0;
-        const bool fin = last && s == nu - 1;
-        T *d = lv.d.p, *dn = lv.d2.p;
-        const double b0 = n * sb + n * sx + (zero ? 0.0 : amat + n * sx);
-        if (fin && m == 1) {
-            H.prof_bytes += vbytes(H, b0 + 2.0 * n * sx + n * 8.0 + (q ? 8.0 * n : 0.0));
+            H.prof_bytes += vbytes(H, b0 + (zero ? 3.0 : 2.0) * dn * sx);
             if (b_is_double)
-                k_cheb0<T, double, double, true><<<g, BS, 0, st>>>(A, lv.dw.p, b64, lv.x.p, lv.r.p, d, zout, (T)lv.c0,
-                                                                   zero, q, part, ctl, mode);
+                k_cheb0<M, double, T, false><<<g, BS, 0, st>>>(A, n, lv.dw.p, b64, lv.x.p, lv.r.p, d, (T *)nullptr,
+                                                               (T)lv.c0, zero, q, part, ctl, mode);
             else
-                k_cheb0<T, T, double, true><<<g, BS, 0, st>>>(A, lv.dw.p, bT, lv.x.p, lv.r.p, d, zout, (T)lv.c0, zero,
-                                                              q, part, ctl, mode);
-            continue;
-        }
-        H.prof_bytes += vbytes(H, b0 + (zero ? 3.0 : 2.0) * n * sx);
-        if (b_is_double)
-            k_cheb0<T, double, T, false><<<g, BS, 0, st>>>(A, lv.dw.p, b64, lv.x.p, lv.r.p, d, (T *)nullptr,
-                                                           (T)lv.c0, zero, q, part, ctl, mode);
-        else
-            k_cheb0<T, T, T, false><<<g, BS, 0, st>>>(A, lv.dw.p, bT, lv.x.p, lv.r.p, d, (T *)nullptr, (T)lv.c0,
-                                                      zero, q, part, ctl, mode);
-        if (m == 1) {
-            if (!zero) {
-                H.prof_bytes += vbytes(H, 3.0 * n * sx);
-                k_axpy<T><<<g, BS, 0, st>>>(lv.n, d, lv.x.p, ctl);
+                k_cheb0<M, T, T, false><<<g, BS, 0, st>>>(A, n, lv.dw.p, bT, lv.x.p, lv.r.p, d, (T *)nullptr,
+                                                          (T)lv.c0, zero, q, part, ctl, mode);
+            if (m == 1) {
+                if (!zero) {
+                    H.prof_bytes += vbytes(H, 3.0 * dn * sx);
+                    k_axpy<T><<<vgrid(H, n), BS, 0, st>>>(n, d, lv.x.p, ctl);
+                }
+                continue;
             }
-            continue;
+            for (int k = 1; k < m; ++k) {
+                const bool f2 = fin && k == m - 1;
+                const int add_prev = (k == 1 && !zero) ? 1 : 0;
+                H.prof_bytes += vbytes(H, amat + dn * sx * 6.0 + (f2 ? dn * 16.0 + (q ? 8.0 * dn : 0.0) - dn * sx : 0.0));
+                if (f2)
+                    k_chebk<M, double, true><<<g, BS, 0, st>>>(A, n, lv.dw.p, lv.r.p, d, dnx, lv.x.p, zout,
+                                                               (T)lv.c1[k], (T)lv.c2[k], add_prev, b64, q, part, ctl,
+                                                               mode);
+                else
+                    k_chebk<M, T, false><<<g, BS, 0, st>>>(A, n, lv.dw.p, lv.r.p, d, dnx, lv.x.p, (T *)nullptr,
+                                                           (T)lv.c1[k], (T)lv.c2[k], add_prev, nullptr, q, part, ctl,
+                                                           mode);
+                std::swap(d, dnx);
+            }
         }
-        for (int k = 1; k < m; ++k) {
-            const bool f2 = fin && k == m - 1;
-            const int add_prev = (k == 1 && !zero) ? 1 : 0;
-            H.prof_bytes += vbytes(H, amat + n * sx * 6.0 + (f2 ? n * 8.0 + n * 8.0 + (q ? 8.0 * n : 0.0) - n * sx : 0.0));
-            if (f2)
-                k_chebk<T, double, true><<<g, BS, 0, st>>>(A, lv.dw.p, lv.r.p, d, dn, lv.x.p, zout, (T)lv.c1[k],
-                                                           (T)lv.c2[k], add_prev, b64, q, part, ctl, mode);
-            else
-                k_chebk<T, T, false><<<g, BS, 0, st>>>(A, lv.dw.p, lv.r.p, d, dn, lv.x.p, (T *)nullptr, (T)lv.c1[k],
-                                                       (T)lv.c2[k], add_prev, nullptr, q, part, ctl, mode);
-            std::swap(d, dn);
-        }
-    }
+    });
 }
 
 template <class T>
@@ -434,28 +557,36 @@ static void vcycle_t(Hier &H, std::vector<CycLevel<T>> &C, const double *r, doub
     const double sx = sizeof(T);
     for (int l = 0; l < L - 1; ++l) {
         CycLevel<T> &lv = C[l];
-        const SV<T> A = view(lv.A);
-        const int g = vgrid(lv.n);
+        const int n = lv.n;
         const bool bd = l == 0;
-        const double n = lv.n, sb = bd ? 8.0 : sx, amat = (double)lv.A.nnz * (sx + 4.0);
+        const double dn = n, sb = bd ? 8.0 : sx, amat = mat_bytes(lv.A);
         const void *bptr = bd ? (const void *)r : (const void *)lv.b.p;
         if (l == 0) mark_begin(H, GW_PK_PRE, st);
         if (H.o.smoother == GW_SMOOTH_JACOBI && H.o.nu <= 1) {
-            H.prof_bytes += vbytes(H, amat + n * sx + n * sb + 2.0 * n * sx);
-            if (bd) k_jac0_res<T, double><<<g, BS, 0, st>>>(A, lv.dw.p, r, lv.x.p, lv.r.p, ctl);
-            else k_jac0_res<T, T><<<g, BS, 0, st>>>(A, lv.dw.p, lv.b.p, lv.x.p, lv.r.p, ctl);
+            H.prof_bytes += vbytes(H, amat + dn * sx + dn * sb + 2.0 * dn * sx);
+            with_mat(lv.A, [&](auto A) {
+                using M = decltype(A);
+                if (bd) k_jac0_res<M, double><<<grid_for<M>(H, n), BS, 0, st>>>(A, n, lv.dw.p, r, lv.x.p, lv.r.p, ctl);
+                else k_jac0_res<M, T><<<grid_for<M>(H, n), BS, 0, st>>>(A, n, lv.dw.p, lv.b.p, lv.x.p, lv.r.p, ctl);
+            });
         } else {
             smooth<T>(H, C, l, bptr, bd, true, false, nullptr, ctl, q, mode, st);
-            H.prof_bytes += vbytes(H, amat + n * sx + n * sb + n * sx);
-            if (bd) k_residual<T, double><<<g, BS, 0, st>>>(A, r, lv.x.p, lv.r.p, ctl);
-            else k_residual<T, T><<<g, BS, 0, st>>>(A, lv.b.p, lv.x.p, lv.r.p, ctl);
+            H.prof_bytes += vbytes(H, amat + dn * sx + dn * sb + dn * sx);
+            with_mat(lv.A, [&](auto A) {
+                using M = decltype(A);
+                if (bd) k_residual<M, double><<<grid_for<M>(H, n), BS, 0, st>>>(A, n, r, lv.x.p, lv.r.p, ctl);
+                else k_residual<M, T><<<grid_for<M>(H, n), BS, 0, st>>>(A, n, lv.b.p, lv.x.p, lv.r.p, ctl);
+            });
         }
         if (l == 0) {
             mark_end(H, st);
             mark_begin(H, GW_PK_RESTRICT, st);
         }
-        H.prof_bytes += vbytes(H, (double)lv.R.nnz * (sx + 4.0) + n * sx + (double)lv.R.nr * sx);
-        k_spmv<T><<<vgrid(lv.R.nr), BS, 0, st>>>(view(lv.R), lv.r.p, C[l + 1].b.p, ctl);
+        H.prof_bytes += vbytes(H, mat_bytes(lv.R) + dn * sx + (double)lv.R.nr * sx);
+        with_mat(lv.R, [&](auto R) {
+            using M = decltype(R);
+            k_spmv<M><<<grid_for<M>(H, lv.R.nr), BS, 0, st>>>(R, lv.R.nr, lv.r.p, C[l + 1].b.p, ctl);
+        });
         GW_LAUNCH_CHECK();
         if (l == 0) {
             mark_end(H, st);
@@ -464,19 +595,23 @@ static void vcycle_t(Hier &H, std::vector<CycLevel<T>> &C, const double *r, doub
     }
     {
         CycLevel<T> &lc = C[L - 1];
-        k_coarse<T><<<std::max(1, std::min(2048, (lc.n * 32 + BS - 1) / BS)), BS, 0, st>>>(lc.n, H.Ainv.p, lc.b.p,
-                                                                                         lc.x.p, ctl);
+        k_coarse<T><<<std::max(1, std::min(H.max_blocks, (lc.n * 32 + BS - 1) / BS)), BS, 0, st>>>(lc.n, H.Ainv.p,
+                                                                                                   lc.b.p, lc.x.p, ctl);
     }
     for (int l = L - 2; l >= 0; --l) {
         CycLevel<T> &lv = C[l];
-        const double n = lv.n;
+        const int n = lv.n;
+        const double dn = n;
         if (l == 0) {
             mark_end(H, st);
             H.prof_bytes = 0.0;
             mark_begin(H, GW_PK_PROLONG, st);
         }
-        H.prof_bytes += vbytes(H, (double)lv.P.nnz * (sx + 4.0) + (double)lv.P.nc * sx + 2.0 * n * sx);
-        k_prolong<T><<<vgrid(lv.n), BS, 0, st>>>(view(lv.P), C[l + 1].x.p, lv.x.p, ctl);
+        H.prof_bytes += vbytes(H, mat_bytes(lv.P) + (double)lv.P.nc * sx + 2.0 * dn * sx);
+        with_mat(lv.P, [&](auto P) {
+            using M = decltype(P);
+            k_prolong<M><<<grid_for<M>(H, n), BS, 0, st>>>(P, n, C[l + 1].x.p, lv.x.p, ctl);
+        });
         if (l == 0) {
             mark_end(H, st);
             mark_begin(H, GW_PK_POST, st);
@@ -526,8 +661,9 @@ __global__ void __launch_bounds__(BS) k_copy(int n, const double *__restrict__ a
 }
 
 // q = A p, pq = (p, q); alpha = rz / pq
-__global__ void __launch_bounds__(BS) k_cg_spmv_dot(SV<double> A, const double *__restrict__ p,
-                                                    double *__restrict__ q, double *part, Ctl *c)
+template <class M>
+__global__ void __launch_bounds__(BS) k_cg_spmv_dot(M A, int n, const double *__restrict__ p, double *__restrict__ q,
+                                                    double *part, Ctl *c)
 {
     if (finished(c)) return;
     if (c->it >= c->maxit) {
@@ -538,11 +674,13 @@ __global__ void __launch_bounds__(BS) k_cg_spmv_dot(SV<double> A, const double *
         return;
     }
     double loc[1] = {0.0}, tot[1];
-    ROWS(i, A.nr)
+    GROUP_ROWS(M, n)
     {
-        const double qi = sell_row(A, i, [&](int j) { return __ldg(p + j); });
-        q[i] = qi;
-        loc[0] += p[i] * qi;
+        const double qi = A.dot(i, lane, [&](int j) { return __ldg(p + j); });
+        if (i < n && lane == 0) {
+            q[i] = qi;
+            loc[0] += p[i] * qi;
+        }
     }
     if (reduce_last<1>(loc, part, &c->cnt[0], tot) && threadIdx.x == 0) {
         const double pq = tot[0];
@@ -584,17 +722,20 @@ __global__ void __launch_bounds__(BS) k_cg_update(int n, double *__restrict__ x,
 }
 
 // when the recursive residual passed: r = b - A x in FP64; stop if it passes too
-__global__ void __launch_bounds__(BS) k_cg_true(SV<double> A, const double *__restrict__ b,
-                                                const double *__restrict__ x, double *__restrict__ r, double *part,
-                                                Ctl *c, int force)
+template <class M>
+__global__ void __launch_bounds__(BS) k_cg_true(M A, int n, const double *__restrict__ b, const double *__restrict__ x,
+                                                double *__restrict__ r, double *part, Ctl *c, int force)
 {
     if (!force && (finished(c) || !c->check)) return;
     double loc[1] = {0.0}, tot[1];
-    ROWS(i, A.nr)
+    GROUP_ROWS(M, n)
     {
-        const double ri = b[i] - sell_row(A, i, [&](int j) { return __ldg(x + j); });
-        if (!force) r[i] = ri;
-        loc[0] += ri * ri;
+        const double ax = A.dot(i, lane, [&](int j) { return __ldg(x + j); });
+        if (i < n && lane == 0) {
+            const double ri = b[i] - ax;
+            if (!force) r[i] = ri;
+            loc[0] += ri * ri;
+        }
     }
     if (reduce_last<1>(loc, part, &c->cnt[0], tot) && threadIdx.x == 0) {
         c->rt2 = tot[0];
@@ -620,26 +761,29 @@ __global__ void __launch_bounds__(BS) k_cg_p(int n, const double *__restrict__ z
 }
 
 // ------------------------------------------------------------------ CG loop --
-static const SV<double> fine64(Hier &H)
-{
-    return H.o.prec == GW_PREC_FP64 ? view(H.cd[0].A) : view(H.A64);
-}
+static const MatStore<double> &fine64(Hier &H) { return H.o.prec == GW_PREC_FP64 ? H.cd[0].A : H.A64; }
 
 static void cg_iteration(Hier &H, cudaStream_t st)
 {
-    const int n = H.n, g = vgrid(n);
+    const int n = H.n, g = vgrid(H, n);
     Ctl *c = H.ctl.p;
-    const SV<double> A = fine64(H);
-    const double dn = n, nnz = (double)H.A0->nnz;
+    const MatStore<double> &A64 = fine64(H);
+    const double dn = n;
     mark_begin(H, GW_PK_SPMV, st);
-    H.prof_bytes += vbytes(H, nnz * 12.0 + 16.0 * dn);
-    k_cg_spmv_dot<<<g, BS, 0, st>>>(A, H.p.p, H.q.p, H.part.p, c);
+    H.prof_bytes += vbytes(H, mat_bytes(A64) + 16.0 * dn);
+    with_mat(A64, [&](auto A) {
+        using M = decltype(A);
+        k_cg_spmv_dot<M><<<grid_for<M>(H, n), BS, 0, st>>>(A, n, H.p.p, H.q.p, H.part.p, c);
+    });
     mark_end(H, st);
     mark_begin(H, GW_PK_UPDATE, st);
     H.prof_bytes += vbytes(H, 48.0 * dn);
     k_cg_update<<<g, BS, 0, st>>>(n, H.x.p, H.r.p, H.p.p, H.q.p, H.part.p, c);
     mark_end(H, st);
-    k_cg_true<<<g, BS, 0, st>>>(A, H.b.p, H.x.p, H.r.p, H.part.p, c, 0);
+    with_mat(A64, [&](auto A) {
+        using M = decltype(A);
+        k_cg_true<M><<<grid_for<M>(H, n), BS, 0, st>>>(A, n, H.b.p, H.x.p, H.r.p, H.part.p, c, 0);
+    });
     const double *q = H.o.prec == GW_PREC_FP64 ? nullptr : H.q.p;
     if (H.o.prec == GW_PREC_FP64) vcycle_t<double>(H, H.cd, H.r.p, H.z.p, c, q, 1, st);
     else vcycle_t<float>(H, H.cf, H.r.p, H.z.p, c, q, 1, st);
@@ -706,7 +850,7 @@ static void ensure_graphs(Hier &H)
 {
     if (H.gexec && H.ginit) return;
     drop_graphs(H);
-    const int n = H.n, g = vgrid(n);
+    const int n = H.n, g = vgrid(H, n);
     H.ginit = capture(H, [&](cudaStream_t s) {
         k_cg_init<<<g, BS, 0, s>>>(n, H.b.p, H.x.p, H.r.p, H.part.p, H.ctl.p);
         if (H.o.prec == GW_PREC_FP64) vcycle_t<double>(H, H.cd, H.r.p, H.z.p, H.ctl.p, nullptr, 0, s);
@@ -767,8 +911,10 @@ int pcg_run(Hier &H, double tol, int maxit, int *iters, double *relres, cudaStre
         if (H.ctl_host->done) break;
     }
     if (H.ctl_host->status == GW_ERR_NOT_CONVERGED || !H.ctl_host->done) {
-        const int g = vgrid(H.n);
-        k_cg_true<<<g, BS, 0, st>>>(fine64(H), H.b.p, H.x.p, H.r.p, H.part.p, c, 1);
+        with_mat(fine64(H), [&](auto A) {
+            using M = decltype(A);
+            k_cg_true<M><<<grid_for<M>(H, H.n), BS, 0, st>>>(A, H.n, H.b.p, H.x.p, H.r.p, H.part.p, c, 1);
+        });
         H.launches += 1;
         GW_LAUNCH_CHECK();
         GW_CUDA(cudaMemcpyAsync(H.ctl_host, c, sizeof(Ctl), cudaMemcpyDeviceToHost, st));

@@ -107,6 +107,45 @@ struct Sell {
     size_t bytes() const { return sp.bytes() + ci.bytes() + v.bytes(); }
 };
 
+// CSR in the cycle's precision T (read by groups of 8 or 32 lanes per row).
+template <class T>
+struct CsrT {
+    int nr = 0, nc = 0;
+    long long nnz = 0;
+    DBuf<int> rp, ci;
+    DBuf<T> v;
+    size_t bytes() const { return rp.bytes() + ci.bytes() + v.bytes(); }
+};
+
+// Index-free 7-point operator on an nx*ny*nz grid: the diagonal and the
+// couplings to the +x, +y, +z neighbours (zero where there is none).  The
+// coupling to a -x neighbour is ox[i-1] because the assembled operator is
+// symmetric bit for bit.
+template <class T>
+struct StenT {
+    int n = 0, nx = 0, ny = 0, nz = 0;
+    DBuf<T> d, ox, oy, oz;
+    size_t bytes() const { return d.bytes() + ox.bytes() + oy.bytes() + oz.bytes(); }
+};
+
+enum { FMT_SELL = 0, FMT_CSR8 = 1, FMT_CSR32 = 2, FMT_STEN = 3 };
+
+template <class T>
+struct MatStore {
+    int fmt = FMT_SELL;
+    int nr = 0, nc = 0;
+    long long nnz = 0;
+    Sell<T> sell;
+    CsrT<T> csr;
+    StenT<T> sten;
+    size_t bytes() const { return sell.bytes() + csr.bytes() + sten.bytes(); }
+};
+
+int choose_fmt(const DCSR &A);
+// fmt FMT_STEN needs the grid (nx, ny, nz); returns false if A is not a 7-point grid operator
+template <class T>
+bool to_store(const DCSR &A, MatStore<T> &M, int fmt, int nx, int ny, int nz, cudaStream_t st);
+
 // ------------------------------------------------------------ CG control --
 // Scalars of the CG recurrence live on the device so that an iteration needs
 // no host round trip.
@@ -156,7 +195,7 @@ void to_sell(const DCSR &A, Sell<T> &S, cudaStream_t st);
 template <class T>
 struct CycLevel {
     int n = 0;
-    Sell<T> A, P, R;     // A_l, P_l (n x n_{l+1}), R_l = P_l^T
+    MatStore<T> A, P, R;  // A_l, P_l (n x n_{l+1}), R_l = P_l^T
     DBuf<T> dw;          // Jacobi: w / a_ii; Chebyshev: 1 / a_ii
     DBuf<T> x, b, r, t, d, d2;
     double c0 = 0.0, c1[8] = {0}, c2[8] = {0};  // Chebyshev coefficients
@@ -174,7 +213,9 @@ struct Hier {
     std::vector<gw_level_info> info;
     std::vector<CycLevel<float>> cf;
     std::vector<CycLevel<double>> cd;
-    Sell<double> A64;          // level-0 FP64 matrix of the outer CG (mixed precision)
+    MatStore<double> A64;      // level-0 FP64 matrix of the outer CG (mixed precision)
+    int gnx = 0, gny = 0, gnz = 0;  // grid of the level-0 operator
+    int max_blocks = 1216;     // one wave of 256-thread blocks (SMs x 8)
     DBuf<double> Ainv;         // dense inverse of the coarsest level, row-major
     // outer CG
     int n = 0;

@@ -986,4 +986,98 @@ void to_sell(const DCSR &A, Sell<T> &S, cudaStream_t st)
 template void to_sell<float>(const DCSR &, Sell<float> &, cudaStream_t);
 template void to_sell<double>(const DCSR &, Sell<double> &, cudaStream_t);
 
+// ----------------------------------------------- CSR and stencil formats --
+template <class T>
+__global__ void k_convert_vals(long long nnz, const double *__restrict__ v, T *__restrict__ o)
+{
+    GRID_STRIDE(e, nnz) o[e] = (T)v[e];
+}
+
+// split a 7-point grid operator into diagonal and +x/+y/+z couplings; counts
+// entries that are not on the grid stencil
+template <class T>
+__global__ void k_to_stencil(int n, int nx, int sxy, const int *__restrict__ rp, const int *__restrict__ ci,
+                             const double *__restrict__ v, T *__restrict__ d, T *__restrict__ ox, T *__restrict__ oy,
+                             T *__restrict__ oz, int *__restrict__ bad)
+{
+    GRID_STRIDE(ii, n)
+    {
+        const int i = (int)ii;
+        double dd = 0.0, a = 0.0, b = 0.0, c = 0.0;
+        for (int e = rp[i]; e < rp[i + 1]; ++e) {
+            const long long j = ci[e];
+            if (j == i) dd = v[e];
+            else if (j == (long long)i + sxy) c = v[e];
+            else if (j == (long long)i + nx) b = v[e];
+            else if (j == (long long)i + 1) a = v[e];
+            else if (!(j == (long long)i - sxy || j == (long long)i - nx || j == (long long)i - 1)) atomicAdd(bad, 1);
+        }
+        d[i] = (T)dd;
+        ox[i] = (T)a;
+        oy[i] = (T)b;
+        oz[i] = (T)c;
+    }
+}
+
+int choose_fmt(const DCSR &A)
+{
+    const double avg = A.nr > 0 ? (double)A.nnz / A.nr : 0.0;
+    if (avg <= 12.0) return FMT_SELL;
+    return A.nr < 65536 ? FMT_CSR32 : FMT_CSR8;
+}
+
+template <class T>
+bool to_store(const DCSR &A, MatStore<T> &M, int fmt, int nx, int ny, int nz, cudaStream_t st)
+{
+    M.nr = A.nr;
+    M.nc = A.nc;
+    M.nnz = A.nnz;
+    M.fmt = fmt;
+    if (fmt == FMT_STEN) {
+        StenT<T> &S = M.sten;
+        const int n = A.nr;
+        S.n = n;
+        S.nx = nx;
+        S.ny = ny;
+        S.nz = nz;
+        S.d.alloc((size_t)n);
+        S.ox.alloc((size_t)n);
+        S.oy.alloc((size_t)n);
+        S.oz.alloc((size_t)n);
+        DBuf<int> bad(1);
+        GW_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
+        k_to_stencil<T><<<nblk(n, 256), 256, 0, st>>>(n, nx, nx * ny, A.rp.p, A.ci.p, A.v.p, S.d.p, S.ox.p, S.oy.p,
+                                                     S.oz.p, bad.p);
+        GW_LAUNCH_CHECK();
+        if (read_int(bad.p, st) == 0) return true;
+        S.d.release();
+        S.ox.release();
+        S.oy.release();
+        S.oz.release();
+        fmt = choose_fmt(A);
+        M.fmt = fmt;
+    }
+    if (fmt == FMT_SELL) {
+        to_sell<T>(A, M.sell, st);
+        return true;
+    }
+    CsrT<T> &C = M.csr;
+    C.nr = A.nr;
+    C.nc = A.nc;
+    C.nnz = A.nnz;
+    C.rp.alloc((size_t)A.nr + 1);
+    C.ci.alloc((size_t)std::max(A.nnz, 1));
+    C.v.alloc((size_t)std::max(A.nnz, 1));
+    GW_CUDA(cudaMemcpyAsync(C.rp.p, A.rp.p, ((size_t)A.nr + 1) * sizeof(int), cudaMemcpyDeviceToDevice, st));
+    if (A.nnz) {
+        GW_CUDA(cudaMemcpyAsync(C.ci.p, A.ci.p, (size_t)A.nnz * sizeof(int), cudaMemcpyDeviceToDevice, st));
+        k_convert_vals<T><<<nblk(A.nnz, 256), 256, 0, st>>>(A.nnz, A.v.p, C.v.p);
+        GW_LAUNCH_CHECK();
+    }
+    return true;
+}
+
+template bool to_store<float>(const DCSR &, MatStore<float> &, int, int, int, int, cudaStream_t);
+template bool to_store<double>(const DCSR &, MatStore<double> &, int, int, int, int, cudaStream_t);
+
 }  // namespace gw

@@ -28,6 +28,118 @@ namespace gw {
 constexpr int BS = 256;
 
 // ------------------------------------------------------------ matrix views --
+// R consecutive values handled by one thread (R = 4 floats or 2 doubles is
+// one 16-byte load or store).
+template <class T, int R>
+struct VecN {
+    T v[R];
+};
+
+template <int R, class T>
+__device__ __forceinline__ VecN<T, R> ld_ro(const T *__restrict__ p)
+{
+    VecN<T, R> o;
+    if constexpr (R == 4 && sizeof(T) == 4) {
+        const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+        o.v[0] = t.x, o.v[1] = t.y, o.v[2] = t.z, o.v[3] = t.w;
+    } else if constexpr (R == 2 && sizeof(T) == 8) {
+        const double2 t = __ldg(reinterpret_cast<const double2 *>(p));
+        o.v[0] = t.x, o.v[1] = t.y;
+    } else if constexpr (R == 4 && sizeof(T) == 8) {
+        const double2 t0 = __ldg(reinterpret_cast<const double2 *>(p));
+        const double2 t1 = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+        o.v[0] = t0.x, o.v[1] = t0.y, o.v[2] = t1.x, o.v[3] = t1.y;
+    } else if constexpr (R == 2 && sizeof(T) == 4) {
+        const float2 t = __ldg(reinterpret_cast<const float2 *>(p));
+        o.v[0] = t.x, o.v[1] = t.y;
+    } else {
+#pragma unroll
+        for (int k = 0; k < R; ++k) o.v[k] = __ldg(p + k);
+    }
+    return o;
+}
+
+// coherent load (the array is written by this kernel, each element by its own thread)
+template <int R, class T>
+__device__ __forceinline__ VecN<T, R> ld_rw(const T *p)
+{
+    VecN<T, R> o;
+    if constexpr (R == 4 && sizeof(T) == 4) {
+        const float4 t = *reinterpret_cast<const float4 *>(p);
+        o.v[0] = t.x, o.v[1] = t.y, o.v[2] = t.z, o.v[3] = t.w;
+    } else if constexpr (R == 2 && sizeof(T) == 8) {
+        const double2 t = *reinterpret_cast<const double2 *>(p);
+        o.v[0] = t.x, o.v[1] = t.y;
+    } else if constexpr (R == 4 && sizeof(T) == 8) {
+        const double2 t0 = reinterpret_cast<const double2 *>(p)[0];
+        const double2 t1 = reinterpret_cast<const double2 *>(p)[1];
+        o.v[0] = t0.x, o.v[1] = t0.y, o.v[2] = t1.x, o.v[3] = t1.y;
+    } else if constexpr (R == 2 && sizeof(T) == 4) {
+        const float2 t = *reinterpret_cast<const float2 *>(p);
+        o.v[0] = t.x, o.v[1] = t.y;
+    } else {
+#pragma unroll
+        for (int k = 0; k < R; ++k) o.v[k] = p[k];
+    }
+    return o;
+}
+
+template <int R, class T>
+__device__ __forceinline__ void st(T *p, const VecN<T, R> &o)
+{
+    if constexpr (R == 4 && sizeof(T) == 4) {
+        *reinterpret_cast<float4 *>(p) = make_float4(o.v[0], o.v[1], o.v[2], o.v[3]);
+    } else if constexpr (R == 2 && sizeof(T) == 8) {
+        *reinterpret_cast<double2 *>(p) = make_double2(o.v[0], o.v[1]);
+    } else if constexpr (R == 4 && sizeof(T) == 8) {
+        reinterpret_cast<double2 *>(p)[0] = make_double2(o.v[0], o.v[1]);
+        reinterpret_cast<double2 *>(p)[1] = make_double2(o.v[2], o.v[3]);
+    } else if constexpr (R == 2 && sizeof(T) == 4) {
+        *reinterpret_cast<float2 *>(p) = make_float2(o.v[0], o.v[1]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < R; ++k) p[k] = o.v[k];
+    }
+}
+
+template <class U, class T, int R>
+__device__ __forceinline__ VecN<U, R> cvt(const VecN<T, R> &a)
+{
+    VecN<U, R> o;
+#pragma unroll
+    for (int k = 0; k < R; ++k) o.v[k] = (U)a.v[k];
+    return o;
+}
+
+// gathered operands: p[j] converted to T, and dw[j] * b[j]
+template <class T, class S>
+struct GVec {
+    const S *__restrict__ p;
+    __device__ __forceinline__ T operator()(int j) const { return (T)__ldg(p + j); }
+    template <int R>
+    __device__ __forceinline__ VecN<T, R> vec(int j0) const
+    {
+        return cvt<T>(ld_ro<R>(p + j0));
+    }
+};
+
+template <class T, class S>
+struct GProd {
+    const T *__restrict__ dw;
+    const S *__restrict__ b;
+    __device__ __forceinline__ T operator()(int j) const { return __ldg(dw + j) * (T)__ldg(b + j); }
+    template <int R>
+    __device__ __forceinline__ VecN<T, R> vec(int j0) const
+    {
+        const VecN<T, R> w = ld_ro<R>(dw + j0);
+        const VecN<T, R> bb = cvt<T>(ld_ro<R>(b + j0));
+        VecN<T, R> o;
+#pragma unroll
+        for (int k = 0; k < R; ++k) o.v[k] = w.v[k] * bb.v[k];
+        return o;
+    }
+};
+
 template <class T>
 struct SV {
     const int *__restrict__ sp;
@@ -53,10 +165,10 @@ struct VecT<double> {
 template <class T>
 struct MSell {
     using value_type = T;
-    static constexpr int G = 1;
+    static constexpr int G = 1, R = 1;
     SV<T> a;
     template <class F>
-    __device__ __forceinline__ T dot(int r, int, F f) const
+    __device__ __forceinline__ VecN<T, 1> dot(int r, int, F f) const
     {
         using VV = typename VecT<T>::V;
         using VI = typename VecT<T>::I;
@@ -80,7 +192,7 @@ struct MSell {
                 acc += x.y * f(j.y);
             }
         }
-        return acc;
+        return VecN<T, 1>{{acc}};
     }
 };
 
@@ -88,13 +200,13 @@ struct MSell {
 template <class T, int G_>
 struct MCsr {
     using value_type = T;
-    static constexpr int G = G_;
+    static constexpr int G = G_, R = 1;
     const int *__restrict__ rp;
     const int *__restrict__ ci;
     const T *__restrict__ v;
     int n;
     template <class F>
-    __device__ __forceinline__ T dot(int i, int lane, F f) const
+    __device__ __forceinline__ VecN<T, 1> dot(int i, int lane, F f) const
     {
         T s = 0;
         if (i < n) {
@@ -103,58 +215,111 @@ struct MCsr {
         }
 #pragma unroll
         for (int off = G / 2; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off, G);
-        return s;
+        return VecN<T, 1>{{s}};
     }
 };
 
-// Index-free 7-point stencil; terms in ascending column order.
-template <class T>
+// Index-free 7-point stencil, R consecutive rows per thread (R = 1 for any
+// grid; R = 16 bytes / sizeof(T) when nx and n are multiples of R, so every
+// coefficient and vector access is one aligned 16-byte load).  Terms are added
+// in ascending column order: -z, -y, -x, diagonal, +x, +y, +z.
+template <class T, int R_>
 struct MSten {
     using value_type = T;
-    static constexpr int G = 1;
+    static constexpr int G = 1, R = R_;
     const T *__restrict__ d;
     const T *__restrict__ ox;
     const T *__restrict__ oy;
     const T *__restrict__ oz;
     int n, nx, sxy;
     template <class F>
-    __device__ __forceinline__ T dot(int i, int, F f) const
+    __device__ __forceinline__ VecN<T, R> dot(int i0, int, F f) const
     {
-        T s = 0;
-        if (i >= sxy) s += __ldg(oz + i - sxy) * f(i - sxy);
-        if (i >= nx) s += __ldg(oy + i - nx) * f(i - nx);
-        if (i >= 1) s += __ldg(ox + i - 1) * f(i - 1);
-        s += __ldg(d + i) * f(i);
-        if (i + 1 < n) s += __ldg(ox + i) * f(i + 1);
-        if (i + nx < n) s += __ldg(oy + i) * f(i + nx);
-        if (i + sxy < n) s += __ldg(oz + i) * f(i + sxy);
-        return s;
+        VecN<T, R> acc;
+#pragma unroll
+        for (int k = 0; k < R; ++k) acc.v[k] = 0;
+        if (i0 >= sxy) {
+            const VecN<T, R> c = ld_ro<R>(oz + i0 - sxy);
+            const VecN<T, R> x = f.template vec<R>(i0 - sxy);
+#pragma unroll
+            for (int k = 0; k < R; ++k) acc.v[k] += c.v[k] * x.v[k];
+        }
+        if (i0 >= nx) {
+            const VecN<T, R> c = ld_ro<R>(oy + i0 - nx);
+            const VecN<T, R> x = f.template vec<R>(i0 - nx);
+#pragma unroll
+            for (int k = 0; k < R; ++k) acc.v[k] += c.v[k] * x.v[k];
+        }
+        const VecN<T, R> cx = ld_ro<R>(ox + i0);
+        const VecN<T, R> xc = f.template vec<R>(i0);
+        const T cxm = i0 >= 1 ? __ldg(ox + i0 - 1) : T(0);
+        const T xm = i0 >= 1 ? f(i0 - 1) : T(0);
+        const T xp = i0 + R < n ? f(i0 + R) : T(0);
+        acc.v[0] += cxm * xm;
+#pragma unroll
+        for (int k = 1; k < R; ++k) acc.v[k] += cx.v[k - 1] * xc.v[k - 1];
+        const VecN<T, R> dg = ld_ro<R>(d + i0);
+#pragma unroll
+        for (int k = 0; k < R; ++k) acc.v[k] += dg.v[k] * xc.v[k];
+#pragma unroll
+        for (int k = 0; k < R - 1; ++k) acc.v[k] += cx.v[k] * xc.v[k + 1];
+        acc.v[R - 1] += cx.v[R - 1] * xp;
+        if (i0 + nx < n) {
+            const VecN<T, R> c = ld_ro<R>(oy + i0);
+            const VecN<T, R> x = f.template vec<R>(i0 + nx);
+#pragma unroll
+            for (int k = 0; k < R; ++k) acc.v[k] += c.v[k] * x.v[k];
+        }
+        if (i0 + sxy < n) {
+            const VecN<T, R> c = ld_ro<R>(oz + i0);
+            const VecN<T, R> x = f.template vec<R>(i0 + sxy);
+#pragma unroll
+            for (int k = 0; k < R; ++k) acc.v[k] += c.v[k] * x.v[k];
+        }
+        return acc;
     }
 };
+
+template <class T>
+constexpr int sten_r()
+{
+    return 16 / (int)sizeof(T);
+}
 
 template <class T, class F>
 static void with_mat(const MatStore<T> &M, F f)
 {
     switch (M.fmt) {
     case FMT_SELL: f(MSell<T>{SV<T>{M.sell.sp.p, M.sell.ci.p, M.sell.v.p, M.sell.nr}}); break;
+    case FMT_CSR4: f(MCsr<T, 4>{M.csr.rp.p, M.csr.ci.p, M.csr.v.p, M.csr.nr}); break;
     case FMT_CSR8: f(MCsr<T, 8>{M.csr.rp.p, M.csr.ci.p, M.csr.v.p, M.csr.nr}); break;
     case FMT_CSR32: f(MCsr<T, 32>{M.csr.rp.p, M.csr.ci.p, M.csr.v.p, M.csr.nr}); break;
-    default: f(MSten<T>{M.sten.d.p, M.sten.ox.p, M.sten.oy.p, M.sten.oz.p, M.sten.n, M.sten.nx, M.sten.nx * M.sten.ny});
+    default: {
+        constexpr int RV = sten_r<T>();
+        const StenT<T> &S = M.sten;
+        const int sxy = S.nx * S.ny;
+        if (S.n % RV == 0 && S.nx % RV == 0)
+            f(MSten<T, RV>{S.d.p, S.ox.p, S.oy.p, S.oz.p, S.n, S.nx, sxy});
+        else
+            f(MSten<T, 1>{S.d.p, S.ox.p, S.oy.p, S.oz.p, S.n, S.nx, sxy});
+    }
     }
 }
 
-// Rows handled by groups of M::G lanes.  The loop keeps whole warps together
-// (so the group reductions may shuffle); 'valid' tells a group whether its
-// row exists.
+// Row blocks of M::R rows handled by groups of M::G lanes.  The loop keeps
+// whole warps together (so the group reductions may shuffle); a group whose
+// block starts at or past n does no epilogue.
 #define GROUP_ROWS(M, n)                                                                                  \
     const int lane = M::G == 1 ? 0 : (int)(threadIdx.x & (M::G - 1));                                    \
-    for (int i = (int)((blockIdx.x * (long long)BS + threadIdx.x) / M::G), stride_ = gridDim.x * (BS / M::G); \
+    for (int i = (int)((blockIdx.x * (long long)BS + threadIdx.x) / M::G) * M::R,                          \
+             stride_ = gridDim.x * (BS / M::G) * M::R;                                                     \
          M::G == 1 ? (i < (n)) : __any_sync(0xffffffffu, i < (n)); i += stride_)
 
 template <class M>
 static inline int grid_for(const Hier &H, long long n)
 {
-    long long b = (n * M::G + BS - 1) / BS;
+    long long groups = (n + M::R - 1) / M::R;
+    long long b = (groups * M::G + BS - 1) / BS;
     return (int)std::max(1LL, std::min<long long>(b, H.max_blocks));
 }
 
@@ -165,6 +330,7 @@ static inline int vgrid(const Hier &H, long long n)
 }
 
 #define ROWS(i, n) for (int i = blockIdx.x * BS + threadIdx.x; i < (n); i += gridDim.x * BS)
+
 
 // ------------------------------------------------------------- reductions --
 __device__ __forceinline__ double warp_sum(double v)
@@ -238,6 +404,20 @@ __device__ __forceinline__ void cg_rz_epilogue(double lrz, double lqz, double *p
     }
 }
 
+// (b, z) and (q, z) contributions of R rows
+template <int R, class BT, class OT>
+__device__ __forceinline__ void dot_rows(int i, const BT *b, const OT (&z)[R], const double *q, double &lrz, double &lqz)
+{
+    const VecN<double, R> bb = cvt<double>(ld_ro<R>(b + i));
+#pragma unroll
+    for (int k = 0; k < R; ++k) lrz += bb.v[k] * (double)z[k];
+    if (q) {
+        const VecN<double, R> qq = ld_ro<R>(q + i);
+#pragma unroll
+        for (int k = 0; k < R; ++k) lqz += qq.v[k] * (double)z[k];
+    }
+}
+
 // x = dw * b ; r = b - A x   (first Jacobi step from zero, fused with the residual)
 template <class M, class BT>
 __global__ void __launch_bounds__(BS) k_jac0_res(M A, int n, const typename M::value_type *__restrict__ dw,
@@ -245,14 +425,22 @@ __global__ void __launch_bounds__(BS) k_jac0_res(M A, int n, const typename M::v
                                                  typename M::value_type *__restrict__ r, const Ctl *ctl)
 {
     using T = typename M::value_type;
+    constexpr int R = M::R;
     if (finished(ctl)) return;
     GROUP_ROWS(M, n)
     {
-        const T ax = A.dot(i, lane, [&](int j) { return __ldg(dw + j) * (T)__ldg(b + j); });
+        const VecN<T, R> ax = A.dot(i, lane, GProd<T, BT>{dw, b});
         if (i < n && lane == 0) {
-            const T bi = (T)b[i];
-            x[i] = __ldg(dw + i) * bi;
-            r[i] = bi - ax;
+            const VecN<T, R> bi = cvt<T>(ld_ro<R>(b + i));
+            const VecN<T, R> w = ld_ro<R>(dw + i);
+            VecN<T, R> xo, ro;
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                xo.v[k] = w.v[k] * bi.v[k];
+                ro.v[k] = bi.v[k] - ax.v[k];
+            }
+            st<R>(x + i, xo);
+            st<R>(r + i, ro);
         }
     }
 }
@@ -266,20 +454,28 @@ __global__ void __launch_bounds__(BS) k_jacobi(M A, int n, const typename M::val
                                                Ctl *ctl, int mode)
 {
     using T = typename M::value_type;
+    constexpr int R = M::R;
     if (finished(ctl)) return;
     double lrz = 0.0, lqz = 0.0;
     GROUP_ROWS(M, n)
     {
-        T ax = 0;
-        if (xi) ax = A.dot(i, lane, [&](int j) { return __ldg(xi + j); });
+        VecN<T, R> ax;
+        if (xi) ax = A.dot(i, lane, GVec<T, T>{xi});
         if (i < n && lane == 0) {
-            const T bi = (T)b[i];
-            const T xn = xi ? xi[i] + __ldg(dw + i) * (bi - ax) : __ldg(dw + i) * bi;
-            xo[i] = (OT)xn;
-            if constexpr (DOT) {
-                lrz += (double)b[i] * (double)xn;
-                if (q) lqz += q[i] * (double)xn;
+            const VecN<T, R> bi = cvt<T>(ld_ro<R>(b + i));
+            const VecN<T, R> w = ld_ro<R>(dw + i);
+            VecN<T, R> xv;
+            if (xi) xv = ld_ro<R>(xi + i);
+            OT out[R];
+            VecN<OT, R> o;
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                const T xn = xi ? xv.v[k] + w.v[k] * (bi.v[k] - ax.v[k]) : w.v[k] * bi.v[k];
+                o.v[k] = (OT)xn;
+                out[k] = (OT)xn;
             }
+            st<R>(xo + i, o);
+            if constexpr (DOT) dot_rows<R>(i, b, out, q, lrz, lqz);
         }
     }
     if constexpr (DOT) cg_rz_epilogue(lrz, lqz, part, ctl, mode);
@@ -292,25 +488,32 @@ __global__ void __launch_bounds__(BS) k_residual(M A, int n, const BT *__restric
                                                  typename M::value_type *__restrict__ r, const Ctl *ctl)
 {
     using T = typename M::value_type;
+    constexpr int R = M::R;
     if (finished(ctl)) return;
     GROUP_ROWS(M, n)
     {
-        const T ax = A.dot(i, lane, [&](int j) { return __ldg(x + j); });
-        if (i < n && lane == 0) r[i] = (T)b[i] - ax;
+        const VecN<T, R> ax = A.dot(i, lane, GVec<T, T>{x});
+        if (i < n && lane == 0) {
+            const VecN<T, R> bi = cvt<T>(ld_ro<R>(b + i));
+            VecN<T, R> ro;
+#pragma unroll
+            for (int k = 0; k < R; ++k) ro.v[k] = bi.v[k] - ax.v[k];
+            st<R>(r + i, ro);
+        }
     }
 }
 
 // y = R x (restriction)
 template <class M>
-__global__ void __launch_bounds__(BS) k_spmv(M R, int n, const typename M::value_type *__restrict__ x,
+__global__ void __launch_bounds__(BS) k_spmv(M Rm, int n, const typename M::value_type *__restrict__ x,
                                              typename M::value_type *__restrict__ y, const Ctl *ctl)
 {
     using T = typename M::value_type;
     if (finished(ctl)) return;
     GROUP_ROWS(M, n)
     {
-        const T s = R.dot(i, lane, [&](int j) { return __ldg(x + j); });
-        if (i < n && lane == 0) y[i] = s;
+        const VecN<T, M::R> s = Rm.dot(i, lane, GVec<T, T>{x});
+        if (i < n && lane == 0) st<M::R>(y + i, s);
     }
 }
 
@@ -320,11 +523,17 @@ __global__ void __launch_bounds__(BS) k_prolong(M P, int n, const typename M::va
                                                 typename M::value_type *__restrict__ x, const Ctl *ctl)
 {
     using T = typename M::value_type;
+    constexpr int R = M::R;
     if (finished(ctl)) return;
     GROUP_ROWS(M, n)
     {
-        const T s = P.dot(i, lane, [&](int j) { return __ldg(e + j); });
-        if (i < n && lane == 0) x[i] += s;
+        const VecN<T, R> s = P.dot(i, lane, GVec<T, T>{e});
+        if (i < n && lane == 0) {
+            VecN<T, R> xv = ld_rw<R>(x + i);
+#pragma unroll
+            for (int k = 0; k < R; ++k) xv.v[k] += s.v[k];
+            st<R>(x + i, xv);
+        }
     }
 }
 
@@ -356,24 +565,40 @@ __global__ void __launch_bounds__(BS) k_cheb0(M A, int n, const typename M::valu
                                               double *part, Ctl *ctl, int mode)
 {
     using T = typename M::value_type;
+    constexpr int R = M::R;
     if (finished(ctl)) return;
     double lrz = 0.0, lqz = 0.0;
     GROUP_ROWS(M, n)
     {
-        T ax = 0;
-        if (!x0zero) ax = A.dot(i, lane, [&](int j) { return __ldg(x + j); });
+        VecN<T, R> ax;
+#pragma unroll
+        for (int k = 0; k < R; ++k) ax.v[k] = 0;
+        if (!x0zero) ax = A.dot(i, lane, GVec<T, T>{x});
         if (i < n && lane == 0) {
-            const T ri = (T)b[i] - ax;
-            const T di = c0 * (__ldg(dw + i) * ri);
-            r[i] = ri;
-            d[i] = di;
+            const VecN<T, R> bi = cvt<T>(ld_ro<R>(b + i));
+            const VecN<T, R> w = ld_ro<R>(dw + i);
+            VecN<T, R> ro, dv, xv;
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                ro.v[k] = bi.v[k] - ax.v[k];
+                dv.v[k] = c0 * (w.v[k] * ro.v[k]);
+            }
+            st<R>(r + i, ro);
+            st<R>(d + i, dv);
             if constexpr (DOT) {
-                const T xn = (x0zero ? (T)0 : x[i]) + di;
-                xo[i] = (OT)xn;
-                lrz += (double)b[i] * (double)xn;
-                if (q) lqz += q[i] * (double)xn;
+                if (!x0zero) xv = ld_rw<R>(x + i);
+                OT out[R];
+                VecN<OT, R> o;
+#pragma unroll
+                for (int k = 0; k < R; ++k) {
+                    const T xn = (x0zero ? (T)0 : xv.v[k]) + dv.v[k];
+                    o.v[k] = (OT)xn;
+                    out[k] = (OT)xn;
+                }
+                st<R>(xo + i, o);
+                dot_rows<R>(i, b, out, q, lrz, lqz);
             } else {
-                if (x0zero) x[i] = di;
+                if (x0zero) st<R>(x + i, dv);
             }
         }
     }
@@ -391,24 +616,38 @@ __global__ void __launch_bounds__(BS) k_chebk(M A, int n, const typename M::valu
                                               const double *__restrict__ q, double *part, Ctl *ctl, int mode)
 {
     using T = typename M::value_type;
+    constexpr int R = M::R;
     if (finished(ctl)) return;
     double lrz = 0.0, lqz = 0.0;
     GROUP_ROWS(M, n)
     {
-        const T ad = A.dot(i, lane, [&](int j) { return __ldg(d + j); });
+        const VecN<T, R> ad = A.dot(i, lane, GVec<T, T>{d});
         if (i < n && lane == 0) {
-            const T ri = r[i] - ad;
-            const T dp = d[i];
-            const T dni = c1 * dp + c2 * (__ldg(dw + i) * ri);
-            const T xn = x[i] + (add_prev ? dp : (T)0) + dni;
-            r[i] = ri;
-            dn[i] = dni;
+            const VecN<T, R> rv = ld_rw<R>(r + i);
+            const VecN<T, R> dp = ld_ro<R>(d + i);
+            const VecN<T, R> w = ld_ro<R>(dw + i);
+            const VecN<T, R> xv = ld_rw<R>(x + i);
+            VecN<T, R> ro, dv, xn;
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                ro.v[k] = rv.v[k] - ad.v[k];
+                dv.v[k] = c1 * dp.v[k] + c2 * (w.v[k] * ro.v[k]);
+                xn.v[k] = xv.v[k] + (add_prev ? dp.v[k] : (T)0) + dv.v[k];
+            }
+            st<R>(r + i, ro);
+            st<R>(dn + i, dv);
             if constexpr (DOT) {
-                xo[i] = (OT)xn;
-                lrz += b0[i] * (double)xn;
-                if (q) lqz += q[i] * (double)xn;
+                OT out[R];
+                VecN<OT, R> o;
+#pragma unroll
+                for (int k = 0; k < R; ++k) {
+                    o.v[k] = (OT)xn.v[k];
+                    out[k] = (OT)xn.v[k];
+                }
+                st<R>(xo + i, o);
+                dot_rows<R>(i, b0, out, q, lrz, lqz);
             } else {
-                x[i] = xn;
+                st<R>(x + i, xn);
             }
         }
     }
@@ -665,6 +904,7 @@ template <class M>
 __global__ void __launch_bounds__(BS) k_cg_spmv_dot(M A, int n, const double *__restrict__ p, double *__restrict__ q,
                                                     double *part, Ctl *c)
 {
+    constexpr int R = M::R;
     if (finished(c)) return;
     if (c->it >= c->maxit) {
         if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -676,10 +916,12 @@ __global__ void __launch_bounds__(BS) k_cg_spmv_dot(M A, int n, const double *__
     double loc[1] = {0.0}, tot[1];
     GROUP_ROWS(M, n)
     {
-        const double qi = A.dot(i, lane, [&](int j) { return __ldg(p + j); });
+        const VecN<double, R> qi = A.dot(i, lane, GVec<double, double>{p});
         if (i < n && lane == 0) {
-            q[i] = qi;
-            loc[0] += p[i] * qi;
+            st<R>(q + i, qi);
+            const VecN<double, R> pi = ld_ro<R>(p + i);
+#pragma unroll
+            for (int k = 0; k < R; ++k) loc[0] += pi.v[k] * qi.v[k];
         }
     }
     if (reduce_last<1>(loc, part, &c->cnt[0], tot) && threadIdx.x == 0) {
@@ -695,7 +937,8 @@ __global__ void __launch_bounds__(BS) k_cg_spmv_dot(M A, int n, const double *__
     }
 }
 
-// x += alpha p; r -= alpha q; rr = (r, r)
+// x += alpha p; r -= alpha q; rr = (r, r)   (two rows per thread when n is even)
+template <int R>
 __global__ void __launch_bounds__(BS) k_cg_update(int n, double *__restrict__ x, double *__restrict__ r,
                                                   const double *__restrict__ p, const double *__restrict__ q,
                                                   double *part, Ctl *c)
@@ -703,12 +946,17 @@ __global__ void __launch_bounds__(BS) k_cg_update(int n, double *__restrict__ x,
     if (finished(c)) return;
     const double a = c->alpha;
     double loc[1] = {0.0}, tot[1];
-    ROWS(i, n)
-    {
-        x[i] += a * p[i];
-        const double ri = r[i] - a * q[i];
-        r[i] = ri;
-        loc[0] += ri * ri;
+    for (int i = R * (blockIdx.x * BS + threadIdx.x); i < n; i += R * gridDim.x * BS) {
+        VecN<double, R> xv = ld_rw<R>(x + i), rv = ld_rw<R>(r + i);
+        const VecN<double, R> pv = ld_ro<R>(p + i), qv = ld_ro<R>(q + i);
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            xv.v[k] += a * pv.v[k];
+            rv.v[k] -= a * qv.v[k];
+            loc[0] += rv.v[k] * rv.v[k];
+        }
+        st<R>(x + i, xv);
+        st<R>(r + i, rv);
     }
     if (reduce_last<1>(loc, part, &c->cnt[0], tot) && threadIdx.x == 0) {
         c->rr = tot[0];
@@ -726,15 +974,21 @@ template <class M>
 __global__ void __launch_bounds__(BS) k_cg_true(M A, int n, const double *__restrict__ b, const double *__restrict__ x,
                                                 double *__restrict__ r, double *part, Ctl *c, int force)
 {
+    constexpr int R = M::R;
     if (!force && (finished(c) || !c->check)) return;
     double loc[1] = {0.0}, tot[1];
     GROUP_ROWS(M, n)
     {
-        const double ax = A.dot(i, lane, [&](int j) { return __ldg(x + j); });
+        const VecN<double, R> ax = A.dot(i, lane, GVec<double, double>{x});
         if (i < n && lane == 0) {
-            const double ri = b[i] - ax;
-            if (!force) r[i] = ri;
-            loc[0] += ri * ri;
+            const VecN<double, R> bv = ld_ro<R>(b + i);
+            VecN<double, R> rv;
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                rv.v[k] = bv.v[k] - ax.v[k];
+                loc[0] += rv.v[k] * rv.v[k];
+            }
+            if (!force) st<R>(r + i, rv);
         }
     }
     if (reduce_last<1>(loc, part, &c->cnt[0], tot) && threadIdx.x == 0) {
@@ -753,11 +1007,18 @@ __global__ void __launch_bounds__(BS) k_cg_true(M A, int n, const double *__rest
 }
 
 // p = z + beta p
+template <int R>
 __global__ void __launch_bounds__(BS) k_cg_p(int n, const double *__restrict__ z, double *__restrict__ p, const Ctl *c)
 {
     if (finished(c)) return;
     const double beta = c->beta;
-    ROWS(i, n) p[i] = z[i] + beta * p[i];
+    for (int i = R * (blockIdx.x * BS + threadIdx.x); i < n; i += R * gridDim.x * BS) {
+        const VecN<double, R> zv = ld_ro<R>(z + i);
+        VecN<double, R> pv = ld_rw<R>(p + i);
+#pragma unroll
+        for (int k = 0; k < R; ++k) pv.v[k] = zv.v[k] + beta * pv.v[k];
+        st<R>(p + i, pv);
+    }
 }
 
 // ------------------------------------------------------------------ CG loop --
@@ -778,7 +1039,8 @@ static void cg_iteration(Hier &H, cudaStream_t st)
     mark_end(H, st);
     mark_begin(H, GW_PK_UPDATE, st);
     H.prof_bytes += vbytes(H, 48.0 * dn);
-    k_cg_update<<<g, BS, 0, st>>>(n, H.x.p, H.r.p, H.p.p, H.q.p, H.part.p, c);
+    if (n % 2 == 0) k_cg_update<2><<<vgrid(H, n / 2), BS, 0, st>>>(n, H.x.p, H.r.p, H.p.p, H.q.p, H.part.p, c);
+    else k_cg_update<1><<<g, BS, 0, st>>>(n, H.x.p, H.r.p, H.p.p, H.q.p, H.part.p, c);
     mark_end(H, st);
     with_mat(A64, [&](auto A) {
         using M = decltype(A);
@@ -789,7 +1051,8 @@ static void cg_iteration(Hier &H, cudaStream_t st)
     else vcycle_t<float>(H, H.cf, H.r.p, H.z.p, c, q, 1, st);
     mark_begin(H, GW_PK_PUPDATE, st);
     H.prof_bytes += vbytes(H, 24.0 * dn);
-    k_cg_p<<<g, BS, 0, st>>>(n, H.z.p, H.p.p, c);
+    if (n % 2 == 0) k_cg_p<2><<<vgrid(H, n / 2), BS, 0, st>>>(n, H.z.p, H.p.p, c);
+    else k_cg_p<1><<<g, BS, 0, st>>>(n, H.z.p, H.p.p, c);
     mark_end(H, st);
     GW_LAUNCH_CHECK();
 }

@@ -128,7 +128,7 @@ struct StenT {
     size_t bytes() const { return d.bytes() + ox.bytes() + oy.bytes() + oz.bytes(); }
 };
 
-enum { FMT_SELL = 0, FMT_CSR8 = 1, FMT_CSR32 = 2, FMT_STEN = 3 };
+enum { FMT_SELL = 0, FMT_CSR4 = 1, FMT_CSR8 = 2, FMT_CSR32 = 3, FMT_STEN = 4 };
 
 template <class T>
 struct MatStore {

@@ -65,12 +65,19 @@ typedef struct {
     double value[6];
 } gw_bc;
 
-/* Arithmetic of the V-cycle.  The outer CG always runs in FP64 (vectors,
- * dot products, matrix-vector product with the FP64 matrix, true residual)
- * and the coarsest level always uses the FP64 dense inverse. */
+/* Arithmetic of the solve.  The coarsest level always uses the FP64 dense
+ * inverse and dot products are always summed in FP64 across threads.
+ * GW_PREC_FP64: the hierarchy, the V-cycle and every CG vector in FP64.
+ * GW_PREC_MIXED32: the hierarchy and V-cycle in FP32, the CG recurrence in
+ * FP32 against the FP32 level-0 operator, and the solution in FP64 by
+ * reliable updates: when the FP32 residual has fallen by the factor delta
+ * since the last update, or passes the stopping test, the FP32 correction is
+ * added to the FP64 solution and the residual is recomputed as b - A h with
+ * the FP64 operator in FP64 arithmetic; the solve stops only on that FP64
+ * residual. */
 typedef enum {
-    GW_PREC_FP64 = 0,     /* hierarchy stored and cycled in FP64 */
-    GW_PREC_MIXED32 = 1   /* hierarchy stored and cycled in FP32 */
+    GW_PREC_FP64 = 0,
+    GW_PREC_MIXED32 = 1
 } gw_prec;
 
 enum { GW_SMOOTH_JACOBI = 0, GW_SMOOTH_CHEBYSHEV = 1 };
@@ -85,6 +92,7 @@ typedef struct {
     int max_levels;      /* at most this many levels (12) */
     uint64_t seed;       /* seed of the MIS-2 priorities (0x5EED) */
     int prec;            /* gw_prec (GW_PREC_MIXED32) */
+    double delta;        /* mixed form: reliable update when the FP32 residual fell by this factor (0.1) */
 } gw_amg_opts;
 
 /* Per-level statistics in the columns of the paper's Table 1 (unknowns,

@@ -215,12 +215,23 @@ void build_hierarchy(Hier &H, cudaStream_t st)
     H.q.alloc((size_t)n);
     H.z.alloc((size_t)n);
     H.b.alloc((size_t)n);
+    if (!f64) {
+        H.r.release();
+        H.p.release();
+        H.q.release();
+        H.z.release();
+        H.xs32.alloc((size_t)n);
+        H.r32.alloc((size_t)n);
+        H.p32.alloc((size_t)n);
+        H.q32.alloc((size_t)n);
+        H.z32.alloc((size_t)n);
+    }
     H.part.alloc(2 * (size_t)RED_MAX_BLOCKS);
     H.ctl.alloc(1);
     GW_CUDA(cudaMemsetAsync(H.ctl.p, 0, sizeof(Ctl), st));
     GW_CUDA(cudaMallocHost((void **)&H.ctl_host, sizeof(Ctl)));
     memset(H.ctl_host, 0, sizeof(Ctl));
-    H.info[0].bytes += 6LL * n * 8;
+    H.info[0].bytes += f64 ? 6LL * n * 8 : 2LL * n * 8 + 5LL * n * 4;
     GW_CUDA(cudaStreamSynchronize(st));
 }
 
@@ -261,6 +272,7 @@ void gw_amg_opts_default(gw_amg_opts *o)
     o->max_levels = 12;
     o->seed = 0x5EEDULL;
     o->prec = GW_PREC_MIXED32;
+    o->delta = 0.1;
 }
 
 const char *gw_status_str(int s)
@@ -367,6 +379,7 @@ int gw_amg_setup(gw_matrix A, const gw_amg_opts *opts, gw_hierarchy *H_out, void
     if (o.n_coarse < 1 || o.n_coarse > 4096) fail(GW_ERR_ARG, "gw_amg_setup: n_coarse must be in 1..4096");
     if (o.max_levels < 2 || o.max_levels > 16) fail(GW_ERR_ARG, "gw_amg_setup: max_levels must be in 2..16");
     if (o.prec != GW_PREC_FP64 && o.prec != GW_PREC_MIXED32) fail(GW_ERR_ARG, "gw_amg_setup: bad precision");
+    if (!(o.delta > 0.0 && o.delta < 1.0)) fail(GW_ERR_ARG, "gw_amg_setup: delta must be in (0, 1)");
     DeviceGuard g(A->dev);
     cudaStream_t st = (cudaStream_t)stream;
     gw_hierarchy h = new gw_hierarchy_s;

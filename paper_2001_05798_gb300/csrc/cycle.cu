@@ -404,17 +404,22 @@ __device__ __forceinline__ void cg_rz_epilogue(double lrz, double lqz, double *p
     }
 }
 
-// (b, z) and (q, z) contributions of R rows
-template <int R, class BT, class OT>
-__device__ __forceinline__ void dot_rows(int i, const BT *b, const OT (&z)[R], const double *q, double &lrz, double &lqz)
+// (b, z) and (q, z) contributions of R rows: products summed in T over the
+// R rows, then accumulated in FP64 across rows and threads
+template <int R, class T, class OT>
+__device__ __forceinline__ void dot_rows(int i, const T *b, const OT (&z)[R], const T *q, double &lrz, double &lqz)
 {
-    const VecN<double, R> bb = cvt<double>(ld_ro<R>(b + i));
+    const VecN<T, R> bb = ld_ro<R>(b + i);
+    T s = 0;
 #pragma unroll
-    for (int k = 0; k < R; ++k) lrz += bb.v[k] * (double)z[k];
+    for (int k = 0; k < R; ++k) s += bb.v[k] * (T)z[k];
+    lrz += (double)s;
     if (q) {
-        const VecN<double, R> qq = ld_ro<R>(q + i);
+        const VecN<T, R> qq = ld_ro<R>(q + i);
+        T t = 0;
 #pragma unroll
-        for (int k = 0; k < R; ++k) lqz += qq.v[k] * (double)z[k];
+        for (int k = 0; k < R; ++k) t += qq.v[k] * (T)z[k];
+        lqz += (double)t;
     }
 }
 
@@ -450,8 +455,8 @@ __global__ void __launch_bounds__(BS) k_jac0_res(M A, int n, const typename M::v
 template <class M, class BT, class OT, bool DOT>
 __global__ void __launch_bounds__(BS) k_jacobi(M A, int n, const typename M::value_type *__restrict__ dw,
                                                const BT *__restrict__ b, const typename M::value_type *__restrict__ xi,
-                                               OT *__restrict__ xo, const double *__restrict__ q, double *part,
-                                               Ctl *ctl, int mode)
+                                               OT *__restrict__ xo, const typename M::value_type *__restrict__ q,
+                                               double *part, Ctl *ctl, int mode)
 {
     using T = typename M::value_type;
     constexpr int R = M::R;
@@ -561,8 +566,9 @@ __global__ void __launch_bounds__(BS) k_cheb0(M A, int n, const typename M::valu
                                               const BT *__restrict__ b, typename M::value_type *x,
                                               typename M::value_type *__restrict__ r,
                                               typename M::value_type *__restrict__ d, OT *__restrict__ xo,
-                                              typename M::value_type c0, int x0zero, const double *__restrict__ q,
-                                              double *part, Ctl *ctl, int mode)
+                                              typename M::value_type c0, int x0zero,
+                                              const typename M::value_type *__restrict__ q, double *part, Ctl *ctl,
+                                              int mode)
 {
     using T = typename M::value_type;
     constexpr int R = M::R;
@@ -612,8 +618,10 @@ __global__ void __launch_bounds__(BS) k_chebk(M A, int n, const typename M::valu
                                               const typename M::value_type *__restrict__ d,
                                               typename M::value_type *__restrict__ dn, typename M::value_type *x,
                                               OT *__restrict__ xo, typename M::value_type c1,
-                                              typename M::value_type c2, int add_prev, const double *__restrict__ b0,
-                                              const double *__restrict__ q, double *part, Ctl *ctl, int mode)
+                                              typename M::value_type c2, int add_prev,
+                                              const typename M::value_type *__restrict__ b0,
+                                              const typename M::value_type *__restrict__ q, double *part, Ctl *ctl,
+                                              int mode)
 {
     using T = typename M::value_type;
     constexpr int R = M::R;
@@ -698,16 +706,14 @@ static double mat_bytes(const MatStore<T> &M)
 }
 
 template <class T>
-static void smooth(Hier &H, std::vector<CycLevel<T>> &C, int l, const void *bptr, bool b_is_double, bool x0zero,
-                   bool last, double *zout, Ctl *ctl, const double *q, int mode, cudaStream_t st)
+static void smooth(Hier &H, std::vector<CycLevel<T>> &C, int l, const T *b, bool x0zero, bool last, T *zout,
+                   Ctl *ctl, const T *q, int mode, cudaStream_t st)
 {
     CycLevel<T> &lv = C[l];
     const int nu = std::max(1, H.o.nu);
-    const double *b64 = (const double *)bptr;
-    const T *bT = (const T *)bptr;
     double *part = H.part.p;
     const int n = lv.n;
-    const double dn = n, sx = sizeof(T), sb = b_is_double ? 8.0 : sx;
+    const double dn = n, sx = sizeof(T);
     const double amat = mat_bytes(lv.A);
     with_mat(lv.A, [&](auto A) {
         using M = decltype(A);
@@ -718,19 +724,11 @@ static void smooth(Hier &H, std::vector<CycLevel<T>> &C, int l, const void *bptr
                 const bool first = x0zero && s == 0;
                 const bool fin = last && s == nu - 1;
                 const T *xi = first ? nullptr : cur;
-                const double so = fin ? 8.0 : sx;
-                H.prof_bytes += vbytes(H, (first ? 0.0 : amat + dn * sx) + dn * sx + dn * sb + dn * so +
-                                              (fin && q ? 8.0 * dn : 0.0));
+                H.prof_bytes += vbytes(H, (first ? 0.0 : amat + dn * sx) + 3.0 * dn * sx + (fin && q ? dn * sx : 0.0));
                 if (fin) {
-                    if (b_is_double)
-                        k_jacobi<M, double, double, true><<<g, BS, 0, st>>>(A, n, lv.dw.p, b64, xi, zout, q, part, ctl, mode);
-                    else
-                        k_jacobi<M, T, double, true><<<g, BS, 0, st>>>(A, n, lv.dw.p, bT, xi, zout, q, part, ctl, mode);
+                    k_jacobi<M, T, T, true><<<g, BS, 0, st>>>(A, n, lv.dw.p, b, xi, zout, q, part, ctl, mode);
                 } else {
-                    if (b_is_double)
-                        k_jacobi<M, double, T, false><<<g, BS, 0, st>>>(A, n, lv.dw.p, b64, xi, nxt, q, part, ctl, mode);
-                    else
-                        k_jacobi<M, T, T, false><<<g, BS, 0, st>>>(A, n, lv.dw.p, bT, xi, nxt, q, part, ctl, mode);
+                    k_jacobi<M, T, T, false><<<g, BS, 0, st>>>(A, n, lv.dw.p, b, xi, nxt, q, part, ctl, mode);
                     std::swap(cur, nxt);
                 }
             }
@@ -744,24 +742,16 @@ static void smooth(Hier &H, std::vector<CycLevel<T>> &C, int l, const void *bptr
             const int zero = x0zero && s == 0;
             const bool fin = last && s == nu - 1;
             T *d = lv.d.p, *dnx = lv.d2.p;
-            const double b0 = dn * sb + dn * sx + (zero ? 0.0 : amat + dn * sx);
+            const double b0 = 2.0 * dn * sx + (zero ? 0.0 : amat + dn * sx);
             if (fin && m == 1) {
-                H.prof_bytes += vbytes(H, b0 + 2.0 * dn * sx + dn * 8.0 + (q ? 8.0 * dn : 0.0));
-                if (b_is_double)
-                    k_cheb0<M, double, double, true><<<g, BS, 0, st>>>(A, n, lv.dw.p, b64, lv.x.p, lv.r.p, d, zout,
-                                                                       (T)lv.c0, zero, q, part, ctl, mode);
-                else
-                    k_cheb0<M, T, double, true><<<g, BS, 0, st>>>(A, n, lv.dw.p, bT, lv.x.p, lv.r.p, d, zout, (T)lv.c0,
-                                                                  zero, q, part, ctl, mode);
+                H.prof_bytes += vbytes(H, b0 + 3.0 * dn * sx + (q ? dn * sx : 0.0));
+                k_cheb0<M, T, T, true><<<g, BS, 0, st>>>(A, n, lv.dw.p, b, lv.x.p, lv.r.p, d, zout, (T)lv.c0, zero, q,
+                                                         part, ctl, mode);
                 continue;
             }
             H.prof_bytes += vbytes(H, b0 + (zero ? 3.0 : 2.0) * dn * sx);
-            if (b_is_double)
-                k_cheb0<M, double, T, false><<<g, BS, 0, st>>>(A, n, lv.dw.p, b64, lv.x.p, lv.r.p, d, (T *)nullptr,
-                                                               (T)lv.c0, zero, q, part, ctl, mode);
-            else
-                k_cheb0<M, T, T, false><<<g, BS, 0, st>>>(A, n, lv.dw.p, bT, lv.x.p, lv.r.p, d, (T *)nullptr,
-                                                          (T)lv.c0, zero, q, part, ctl, mode);
+            k_cheb0<M, T, T, false><<<g, BS, 0, st>>>(A, n, lv.dw.p, b, lv.x.p, lv.r.p, d, (T *)nullptr, (T)lv.c0,
+                                                      zero, q, part, ctl, mode);
             if (m == 1) {
                 if (!zero) {
                     H.prof_bytes += vbytes(H, 3.0 * dn * sx);
@@ -772,24 +762,25 @@ static void smooth(Hier &H, std::vector<CycLevel<T>> &C, int l, const void *bptr
             for (int k = 1; k < m; ++k) {
                 const bool f2 = fin && k == m - 1;
                 const int add_prev = (k == 1 && !zero) ? 1 : 0;
-                H.prof_bytes += vbytes(H, amat + dn * sx * 6.0 + (f2 ? dn * 16.0 + (q ? 8.0 * dn : 0.0) - dn * sx : 0.0));
+                H.prof_bytes += vbytes(H, amat + dn * sx * 6.0 + (f2 ? dn * sx * (q ? 2.0 : 1.0) : 0.0));
                 if (f2)
-                    k_chebk<M, double, true><<<g, BS, 0, st>>>(A, n, lv.dw.p, lv.r.p, d, dnx, lv.x.p, zout,
-                                                               (T)lv.c1[k], (T)lv.c2[k], add_prev, b64, q, part, ctl,
-                                                               mode);
+                    k_chebk<M, T, true><<<g, BS, 0, st>>>(A, n, lv.dw.p, lv.r.p, d, dnx, lv.x.p, zout, (T)lv.c1[k],
+                                                          (T)lv.c2[k], add_prev, b, q, part, ctl, mode);
                 else
                     k_chebk<M, T, false><<<g, BS, 0, st>>>(A, n, lv.dw.p, lv.r.p, d, dnx, lv.x.p, (T *)nullptr,
-                                                           (T)lv.c1[k], (T)lv.c2[k], add_prev, nullptr, q, part, ctl,
-                                                           mode);
+                                                           (T)lv.c1[k], (T)lv.c2[k], add_prev, (const T *)nullptr, q,
+                                                           part, ctl, mode);
                 std::swap(d, dnx);
             }
         }
     });
 }
 
+// One V-cycle z = M^-1 r on the hierarchy stored in T; r and z are level-0
+// vectors in T.  With ctl, the last kernel reduces (r, z) (and (q, z)).
 template <class T>
-static void vcycle_t(Hier &H, std::vector<CycLevel<T>> &C, const double *r, double *z, Ctl *ctl, const double *q,
-                     int mode, cudaStream_t st)
+static void vcycle_t(Hier &H, std::vector<CycLevel<T>> &C, const T *r, T *z, Ctl *ctl, const T *q, int mode,
+                     cudaStream_t st)
 {
     const int L = H.L;
     if (L == 1) fail(GW_ERR_SETUP, "a one-level hierarchy is not supported by the V-cycle");
@@ -797,24 +788,21 @@ static void vcycle_t(Hier &H, std::vector<CycLevel<T>> &C, const double *r, doub
     for (int l = 0; l < L - 1; ++l) {
         CycLevel<T> &lv = C[l];
         const int n = lv.n;
-        const bool bd = l == 0;
-        const double dn = n, sb = bd ? 8.0 : sx, amat = mat_bytes(lv.A);
-        const void *bptr = bd ? (const void *)r : (const void *)lv.b.p;
+        const double dn = n, amat = mat_bytes(lv.A);
+        const T *bl = l == 0 ? r : lv.b.p;
         if (l == 0) mark_begin(H, GW_PK_PRE, st);
         if (H.o.smoother == GW_SMOOTH_JACOBI && H.o.nu <= 1) {
-            H.prof_bytes += vbytes(H, amat + dn * sx + dn * sb + 2.0 * dn * sx);
+            H.prof_bytes += vbytes(H, amat + 4.0 * dn * sx);
             with_mat(lv.A, [&](auto A) {
                 using M = decltype(A);
-                if (bd) k_jac0_res<M, double><<<grid_for<M>(H, n), BS, 0, st>>>(A, n, lv.dw.p, r, lv.x.p, lv.r.p, ctl);
-                else k_jac0_res<M, T><<<grid_for<M>(H, n), BS, 0, st>>>(A, n, lv.dw.p, lv.b.p, lv.x.p, lv.r.p, ctl);
+                k_jac0_res<M, T><<<grid_for<M>(H, n), BS, 0, st>>>(A, n, lv.dw.p, bl, lv.x.p, lv.r.p, ctl);
             });
         } else {
-            smooth<T>(H, C, l, bptr, bd, true, false, nullptr, ctl, q, mode, st);
-            H.prof_bytes += vbytes(H, amat + dn * sx + dn * sb + dn * sx);
+            smooth<T>(H, C, l, bl, true, false, nullptr, ctl, q, mode, st);
+            H.prof_bytes += vbytes(H, amat + 3.0 * dn * sx);
             with_mat(lv.A, [&](auto A) {
                 using M = decltype(A);
-                if (bd) k_residual<M, double><<<grid_for<M>(H, n), BS, 0, st>>>(A, n, r, lv.x.p, lv.r.p, ctl);
-                else k_residual<M, T><<<grid_for<M>(H, n), BS, 0, st>>>(A, n, lv.b.p, lv.x.p, lv.r.p, ctl);
+                k_residual<M, T><<<grid_for<M>(H, n), BS, 0, st>>>(A, n, bl, lv.x.p, lv.r.p, ctl);
             });
         }
         if (l == 0) {
@@ -822,9 +810,9 @@ static void vcycle_t(Hier &H, std::vector<CycLevel<T>> &C, const double *r, doub
             mark_begin(H, GW_PK_RESTRICT, st);
         }
         H.prof_bytes += vbytes(H, mat_bytes(lv.R) + dn * sx + (double)lv.R.nr * sx);
-        with_mat(lv.R, [&](auto R) {
-            using M = decltype(R);
-            k_spmv<M><<<grid_for<M>(H, lv.R.nr), BS, 0, st>>>(R, lv.R.nr, lv.r.p, C[l + 1].b.p, ctl);
+        with_mat(lv.R, [&](auto Rm) {
+            using M = decltype(Rm);
+            k_spmv<M><<<grid_for<M>(H, lv.R.nr), BS, 0, st>>>(Rm, lv.R.nr, lv.r.p, C[l + 1].b.p, ctl);
         });
         GW_LAUNCH_CHECK();
         if (l == 0) {
@@ -855,35 +843,60 @@ static void vcycle_t(Hier &H, std::vector<CycLevel<T>> &C, const double *r, doub
             mark_end(H, st);
             mark_begin(H, GW_PK_POST, st);
         }
-        const bool bd = l == 0;
-        const void *bptr = bd ? (const void *)r : (const void *)lv.b.p;
-        smooth<T>(H, C, l, bptr, bd, false, l == 0, z, ctl, q, mode, st);
+        smooth<T>(H, C, l, l == 0 ? r : lv.b.p, false, l == 0, z, ctl, q, mode, st);
         if (l == 0) mark_end(H, st);
         GW_LAUNCH_CHECK();
     }
 }
 
+template <class A, class B>
+__global__ void k_convert(int n, const A *__restrict__ a, B *__restrict__ b)
+{
+    ROWS(i, n) b[i] = (B)a[i];
+}
+
+// Standalone V-cycle on FP64 vectors (the mixed hierarchy converts in and out).
 void vcycle_enqueue(Hier &H, const double *r, double *z, Ctl *ctl, bool dot, cudaStream_t st)
 {
     (void)dot;
-    if (H.o.prec == GW_PREC_FP64) vcycle_t<double>(H, H.cd, r, z, ctl, nullptr, 0, st);
-    else vcycle_t<float>(H, H.cf, r, z, ctl, nullptr, 0, st);
+    if (H.o.prec == GW_PREC_FP64) {
+        vcycle_t<double>(H, H.cd, r, z, ctl, nullptr, 0, st);
+        return;
+    }
+    const int n = H.n;
+    k_convert<double, float><<<vgrid(H, n), BS, 0, st>>>(n, r, H.r32.p);
+    vcycle_t<float>(H, H.cf, H.r32.p, H.z32.p, ctl, nullptr, 0, st);
+    k_convert<float, double><<<vgrid(H, n), BS, 0, st>>>(n, H.z32.p, z);
+    GW_LAUNCH_CHECK();
 }
 
 // ---------------------------------------------------------------- CG kernels --
+// Two forms share these kernels.  FP64: every vector and the matrix of the
+// CG recurrence in FP64.  Mixed: the CG recurrence (p, q, r, z and the
+// correction xs) runs in FP32 against the FP32 level-0 operator, dot
+// products are summed in FP64 across threads, and the solution is kept in
+// FP64 by reliable updates (van der Vorst & Ye 2000): whenever the recursive
+// residual has dropped by the factor delta since the last update, or passes
+// the stopping test, xs is folded into the FP64 solution and the residual is
+// recomputed as b - A x with the FP64 operator in FP64 arithmetic.
+
+// x = 0, r = b (FP64 form) or x64 = 0, xs = 0, r32 = b (mixed form); ||b||^2
+template <class V>
 __global__ void __launch_bounds__(BS) k_cg_init(int n, const double *__restrict__ b, double *__restrict__ x,
-                                                double *__restrict__ r, double *part, Ctl *c)
+                                                V *__restrict__ xs, V *__restrict__ r, double *part, Ctl *c)
 {
     double loc[1] = {0.0}, tot[1];
     ROWS(i, n)
     {
         const double bi = b[i];
         x[i] = 0.0;
-        r[i] = bi;
+        if (xs) xs[i] = (V)0;
+        r[i] = (V)bi;
         loc[0] += bi * bi;
     }
     if (reduce_last<1>(loc, part, &c->cnt[0], tot) && threadIdx.x == 0) {
         c->bnorm2 = tot[0];
+        c->rmax2 = tot[0];
         c->it = 0;
         c->check = 0;
         c->status = GW_OK;
@@ -893,7 +906,8 @@ __global__ void __launch_bounds__(BS) k_cg_init(int n, const double *__restrict_
     }
 }
 
-__global__ void __launch_bounds__(BS) k_copy(int n, const double *__restrict__ a, double *__restrict__ b, const Ctl *c)
+template <class V>
+__global__ void __launch_bounds__(BS) k_copy(int n, const V *__restrict__ a, V *__restrict__ b, const Ctl *c)
 {
     if (finished(c)) return;
     ROWS(i, n) b[i] = a[i];
@@ -901,9 +915,10 @@ __global__ void __launch_bounds__(BS) k_copy(int n, const double *__restrict__ a
 
 // q = A p, pq = (p, q); alpha = rz / pq
 template <class M>
-__global__ void __launch_bounds__(BS) k_cg_spmv_dot(M A, int n, const double *__restrict__ p, double *__restrict__ q,
-                                                    double *part, Ctl *c)
+__global__ void __launch_bounds__(BS) k_cg_spmv_dot(M A, int n, const typename M::value_type *__restrict__ p,
+                                                    typename M::value_type *__restrict__ q, double *part, Ctl *c)
 {
+    using V = typename M::value_type;
     constexpr int R = M::R;
     if (finished(c)) return;
     if (c->it >= c->maxit) {
@@ -916,12 +931,14 @@ __global__ void __launch_bounds__(BS) k_cg_spmv_dot(M A, int n, const double *__
     double loc[1] = {0.0}, tot[1];
     GROUP_ROWS(M, n)
     {
-        const VecN<double, R> qi = A.dot(i, lane, GVec<double, double>{p});
+        const VecN<V, R> qi = A.dot(i, lane, GVec<V, V>{p});
         if (i < n && lane == 0) {
             st<R>(q + i, qi);
-            const VecN<double, R> pi = ld_ro<R>(p + i);
+            const VecN<V, R> pi = ld_ro<R>(p + i);
+            V s = 0;
 #pragma unroll
-            for (int k = 0; k < R; ++k) loc[0] += pi.v[k] * qi.v[k];
+            for (int k = 0; k < R; ++k) s += pi.v[k] * qi.v[k];
+            loc[0] += (double)s;
         }
     }
     if (reduce_last<1>(loc, part, &c->cnt[0], tot) && threadIdx.x == 0) {
@@ -937,24 +954,28 @@ __global__ void __launch_bounds__(BS) k_cg_spmv_dot(M A, int n, const double *__
     }
 }
 
-// x += alpha p; r -= alpha q; rr = (r, r)   (two rows per thread when n is even)
-template <int R>
-__global__ void __launch_bounds__(BS) k_cg_update(int n, double *__restrict__ x, double *__restrict__ r,
-                                                  const double *__restrict__ p, const double *__restrict__ q,
-                                                  double *part, Ctl *c)
+// x += alpha p; r -= alpha q; rr = (r, r).  Sets check when r passes the
+// stopping test, or (mixed form) when it fell below delta times the residual
+// of the last reliable update.
+template <class V, int R>
+__global__ void __launch_bounds__(BS) k_cg_update(int n, V *__restrict__ x, V *__restrict__ r,
+                                                  const V *__restrict__ p, const V *__restrict__ q, double *part,
+                                                  Ctl *c, int reliable)
 {
     if (finished(c)) return;
-    const double a = c->alpha;
+    const V a = (V)c->alpha;
     double loc[1] = {0.0}, tot[1];
     for (int i = R * (blockIdx.x * BS + threadIdx.x); i < n; i += R * gridDim.x * BS) {
-        VecN<double, R> xv = ld_rw<R>(x + i), rv = ld_rw<R>(r + i);
-        const VecN<double, R> pv = ld_ro<R>(p + i), qv = ld_ro<R>(q + i);
+        VecN<V, R> xv = ld_rw<R>(x + i), rv = ld_rw<R>(r + i);
+        const VecN<V, R> pv = ld_ro<R>(p + i), qv = ld_ro<R>(q + i);
+        V s = 0;
 #pragma unroll
         for (int k = 0; k < R; ++k) {
             xv.v[k] += a * pv.v[k];
             rv.v[k] -= a * qv.v[k];
-            loc[0] += rv.v[k] * rv.v[k];
+            s += rv.v[k] * rv.v[k];
         }
+        loc[0] += (double)s;
         st<R>(x + i, xv);
         st<R>(r + i, rv);
     }
@@ -963,13 +984,13 @@ __global__ void __launch_bounds__(BS) k_cg_update(int n, double *__restrict__ x,
         if (!isfinite(tot[0])) {
             c->status = GW_ERR_BREAKDOWN;
             c->done = 1;
-        } else if (tot[0] <= c->tol2 * c->bnorm2) {
+        } else if (tot[0] <= c->tol2 * c->bnorm2 || (reliable && tot[0] <= c->delta2 * c->rmax2)) {
             c->check = 1;
         }
     }
 }
 
-// when the recursive residual passed: r = b - A x in FP64; stop if it passes too
+// FP64 form: when the recursive residual passed, r = b - A x; stop if it passes too
 template <class M>
 __global__ void __launch_bounds__(BS) k_cg_true(M A, int n, const double *__restrict__ b, const double *__restrict__ x,
                                                 double *__restrict__ r, double *part, Ctl *c, int force)
@@ -988,7 +1009,7 @@ __global__ void __launch_bounds__(BS) k_cg_true(M A, int n, const double *__rest
                 rv.v[k] = bv.v[k] - ax.v[k];
                 loc[0] += rv.v[k] * rv.v[k];
             }
-            if (!force) st<R>(r + i, rv);
+            if (!force && r) st<R>(r + i, rv);
         }
     }
     if (reduce_last<1>(loc, part, &c->cnt[0], tot) && threadIdx.x == 0) {
@@ -1006,15 +1027,75 @@ __global__ void __launch_bounds__(BS) k_cg_true(M A, int n, const double *__rest
     }
 }
 
-// p = z + beta p
+// mixed form, reliable update part 1: x64 += xs; xs = 0
 template <int R>
-__global__ void __launch_bounds__(BS) k_cg_p(int n, const double *__restrict__ z, double *__restrict__ p, const Ctl *c)
+__global__ void __launch_bounds__(BS) k_rel_fold(int n, double *__restrict__ x, float *__restrict__ xs, const Ctl *c,
+                                                 int force)
+{
+    if (!force && (finished(c) || !c->check)) return;
+    for (int i = R * (blockIdx.x * BS + threadIdx.x); i < n; i += R * gridDim.x * BS) {
+        VecN<double, R> xv = ld_rw<R>(x + i);
+        const VecN<float, R> sv = ld_rw<R>(xs + i);
+        VecN<float, R> zero;
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            xv.v[k] += (double)sv.v[k];
+            zero.v[k] = 0.f;
+        }
+        st<R>(x + i, xv);
+        st<R>(xs + i, zero);
+    }
+}
+
+// mixed form, reliable update part 2: r = b - A64 x64 in FP64, stored as FP32;
+// stop if ||r|| passes the test, else remember ||r||^2 for the next update
+template <class M>
+__global__ void __launch_bounds__(BS) k_rel_res(M A, int n, const double *__restrict__ b, const double *__restrict__ x,
+                                                float *__restrict__ r, double *part, Ctl *c, int force)
+{
+    constexpr int R = M::R;
+    if (!force && (finished(c) || !c->check)) return;
+    double loc[1] = {0.0}, tot[1];
+    GROUP_ROWS(M, n)
+    {
+        const VecN<double, R> ax = A.dot(i, lane, GVec<double, double>{x});
+        if (i < n && lane == 0) {
+            const VecN<double, R> bv = ld_ro<R>(b + i);
+            VecN<float, R> rv;
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                const double t = bv.v[k] - ax.v[k];
+                rv.v[k] = (float)t;
+                loc[0] += t * t;
+            }
+            if (!force) st<R>(r + i, rv);
+        }
+    }
+    if (reduce_last<1>(loc, part, &c->cnt[0], tot) && threadIdx.x == 0) {
+        c->rt2 = tot[0];
+        const double rel = c->bnorm2 > 0.0 ? sqrt(tot[0] / c->bnorm2) : 0.0;
+        c->relres = rel;
+        if (!force) {
+            if (tot[0] <= c->tol2 * c->bnorm2) {
+                c->status = GW_OK;
+                c->done = 1;
+            } else {
+                c->rmax2 = tot[0];
+                c->check = 0;
+            }
+        }
+    }
+}
+
+// p = z + beta p
+template <class V, int R>
+__global__ void __launch_bounds__(BS) k_cg_p(int n, const V *__restrict__ z, V *__restrict__ p, const Ctl *c)
 {
     if (finished(c)) return;
-    const double beta = c->beta;
+    const V beta = (V)c->beta;
     for (int i = R * (blockIdx.x * BS + threadIdx.x); i < n; i += R * gridDim.x * BS) {
-        const VecN<double, R> zv = ld_ro<R>(z + i);
-        VecN<double, R> pv = ld_rw<R>(p + i);
+        const VecN<V, R> zv = ld_ro<R>(z + i);
+        VecN<V, R> pv = ld_rw<R>(p + i);
 #pragma unroll
         for (int k = 0; k < R; ++k) pv.v[k] = zv.v[k] + beta * pv.v[k];
         st<R>(p + i, pv);
@@ -1024,35 +1105,82 @@ __global__ void __launch_bounds__(BS) k_cg_p(int n, const double *__restrict__ z
 // ------------------------------------------------------------------ CG loop --
 static const MatStore<double> &fine64(Hier &H) { return H.o.prec == GW_PREC_FP64 ? H.cd[0].A : H.A64; }
 
+template <class V>
+static void cg_vec_update(Hier &H, V *x, V *r, const V *p, const V *q, int reliable, cudaStream_t st)
+{
+    const int n = H.n;
+    constexpr int R = 16 / sizeof(V);
+    if (n % R == 0) k_cg_update<V, R><<<vgrid(H, n / R), BS, 0, st>>>(n, x, r, p, q, H.part.p, H.ctl.p, reliable);
+    else k_cg_update<V, 1><<<vgrid(H, n), BS, 0, st>>>(n, x, r, p, q, H.part.p, H.ctl.p, reliable);
+}
+
+template <class V>
+static void cg_vec_p(Hier &H, const V *z, V *p, cudaStream_t st)
+{
+    const int n = H.n;
+    constexpr int R = 16 / sizeof(V);
+    if (n % R == 0) k_cg_p<V, R><<<vgrid(H, n / R), BS, 0, st>>>(n, z, p, H.ctl.p);
+    else k_cg_p<V, 1><<<vgrid(H, n), BS, 0, st>>>(n, z, p, H.ctl.p);
+}
+
+static void rel_update(Hier &H, int force, cudaStream_t st)
+{
+    const int n = H.n;
+    if (n % 2 == 0) k_rel_fold<2><<<vgrid(H, n / 2), BS, 0, st>>>(n, H.x.p, H.xs32.p, H.ctl.p, force);
+    else k_rel_fold<1><<<vgrid(H, n), BS, 0, st>>>(n, H.x.p, H.xs32.p, H.ctl.p, force);
+    with_mat(H.A64, [&](auto A) {
+        using M = decltype(A);
+        k_rel_res<M><<<grid_for<M>(H, n), BS, 0, st>>>(A, n, H.b.p, H.x.p, H.r32.p, H.part.p, H.ctl.p, force);
+    });
+}
+
 static void cg_iteration(Hier &H, cudaStream_t st)
 {
-    const int n = H.n, g = vgrid(H, n);
+    const int n = H.n;
     Ctl *c = H.ctl.p;
-    const MatStore<double> &A64 = fine64(H);
     const double dn = n;
+    if (H.o.prec == GW_PREC_FP64) {
+        const MatStore<double> &A64 = H.cd[0].A;
+        mark_begin(H, GW_PK_SPMV, st);
+        H.prof_bytes += vbytes(H, mat_bytes(A64) + 16.0 * dn);
+        with_mat(A64, [&](auto A) {
+            using M = decltype(A);
+            k_cg_spmv_dot<M><<<grid_for<M>(H, n), BS, 0, st>>>(A, n, H.p.p, H.q.p, H.part.p, c);
+        });
+        mark_end(H, st);
+        mark_begin(H, GW_PK_UPDATE, st);
+        H.prof_bytes += vbytes(H, 48.0 * dn);
+        cg_vec_update<double>(H, H.x.p, H.r.p, H.p.p, H.q.p, 0, st);
+        mark_end(H, st);
+        with_mat(A64, [&](auto A) {
+            using M = decltype(A);
+            k_cg_true<M><<<grid_for<M>(H, n), BS, 0, st>>>(A, n, H.b.p, H.x.p, H.r.p, H.part.p, c, 0);
+        });
+        vcycle_t<double>(H, H.cd, H.r.p, H.z.p, c, nullptr, 1, st);
+        mark_begin(H, GW_PK_PUPDATE, st);
+        H.prof_bytes += vbytes(H, 24.0 * dn);
+        cg_vec_p<double>(H, H.z.p, H.p.p, st);
+        mark_end(H, st);
+        GW_LAUNCH_CHECK();
+        return;
+    }
+    const MatStore<float> &A32 = H.cf[0].A;
     mark_begin(H, GW_PK_SPMV, st);
-    H.prof_bytes += vbytes(H, mat_bytes(A64) + 16.0 * dn);
-    with_mat(A64, [&](auto A) {
+    H.prof_bytes += vbytes(H, mat_bytes(A32) + 8.0 * dn);
+    with_mat(A32, [&](auto A) {
         using M = decltype(A);
-        k_cg_spmv_dot<M><<<grid_for<M>(H, n), BS, 0, st>>>(A, n, H.p.p, H.q.p, H.part.p, c);
+        k_cg_spmv_dot<M><<<grid_for<M>(H, n), BS, 0, st>>>(A, n, H.p32.p, H.q32.p, H.part.p, c);
     });
     mark_end(H, st);
     mark_begin(H, GW_PK_UPDATE, st);
-    H.prof_bytes += vbytes(H, 48.0 * dn);
-    if (n % 2 == 0) k_cg_update<2><<<vgrid(H, n / 2), BS, 0, st>>>(n, H.x.p, H.r.p, H.p.p, H.q.p, H.part.p, c);
-    else k_cg_update<1><<<g, BS, 0, st>>>(n, H.x.p, H.r.p, H.p.p, H.q.p, H.part.p, c);
-    mark_end(H, st);
-    with_mat(A64, [&](auto A) {
-        using M = decltype(A);
-        k_cg_true<M><<<grid_for<M>(H, n), BS, 0, st>>>(A, n, H.b.p, H.x.p, H.r.p, H.part.p, c, 0);
-    });
-    const double *q = H.o.prec == GW_PREC_FP64 ? nullptr : H.q.p;
-    if (H.o.prec == GW_PREC_FP64) vcycle_t<double>(H, H.cd, H.r.p, H.z.p, c, q, 1, st);
-    else vcycle_t<float>(H, H.cf, H.r.p, H.z.p, c, q, 1, st);
-    mark_begin(H, GW_PK_PUPDATE, st);
     H.prof_bytes += vbytes(H, 24.0 * dn);
-    if (n % 2 == 0) k_cg_p<2><<<vgrid(H, n / 2), BS, 0, st>>>(n, H.z.p, H.p.p, c);
-    else k_cg_p<1><<<g, BS, 0, st>>>(n, H.z.p, H.p.p, c);
+    cg_vec_update<float>(H, H.xs32.p, H.r32.p, H.p32.p, H.q32.p, 1, st);
+    mark_end(H, st);
+    rel_update(H, 0, st);
+    vcycle_t<float>(H, H.cf, H.r32.p, H.z32.p, c, H.q32.p, 1, st);
+    mark_begin(H, GW_PK_PUPDATE, st);
+    H.prof_bytes += vbytes(H, 12.0 * dn);
+    cg_vec_p<float>(H, H.z32.p, H.p32.p, st);
     mark_end(H, st);
     GW_LAUNCH_CHECK();
 }
@@ -1115,10 +1243,15 @@ static void ensure_graphs(Hier &H)
     drop_graphs(H);
     const int n = H.n, g = vgrid(H, n);
     H.ginit = capture(H, [&](cudaStream_t s) {
-        k_cg_init<<<g, BS, 0, s>>>(n, H.b.p, H.x.p, H.r.p, H.part.p, H.ctl.p);
-        if (H.o.prec == GW_PREC_FP64) vcycle_t<double>(H, H.cd, H.r.p, H.z.p, H.ctl.p, nullptr, 0, s);
-        else vcycle_t<float>(H, H.cf, H.r.p, H.z.p, H.ctl.p, nullptr, 0, s);
-        k_copy<<<g, BS, 0, s>>>(n, H.z.p, H.p.p, H.ctl.p);
+        if (H.o.prec == GW_PREC_FP64) {
+            k_cg_init<double><<<g, BS, 0, s>>>(n, H.b.p, H.x.p, (double *)nullptr, H.r.p, H.part.p, H.ctl.p);
+            vcycle_t<double>(H, H.cd, H.r.p, H.z.p, H.ctl.p, nullptr, 0, s);
+            k_copy<double><<<g, BS, 0, s>>>(n, H.z.p, H.p.p, H.ctl.p);
+        } else {
+            k_cg_init<float><<<g, BS, 0, s>>>(n, H.b.p, H.x.p, H.xs32.p, H.r32.p, H.part.p, H.ctl.p);
+            vcycle_t<float>(H, H.cf, H.r32.p, H.z32.p, H.ctl.p, nullptr, 0, s);
+            k_copy<float><<<g, BS, 0, s>>>(n, H.z32.p, H.p32.p, H.ctl.p);
+        }
         GW_LAUNCH_CHECK();
     }, &H.init_kernels);
     H.prof_capture = H.prof_on;
@@ -1160,6 +1293,7 @@ int pcg_run(Hier &H, double tol, int maxit, int *iters, double *relres, cudaStre
     init.tol2 = tol * tol;
     init.maxit = maxit;
     init.flexible = H.o.prec == GW_PREC_FP64 ? 0 : 1;
+    init.delta2 = H.o.delta * H.o.delta;
     *H.ctl_host = init;
     GW_CUDA(cudaMemcpyAsync(c, H.ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, st));
     GW_CUDA(cudaGraphLaunch(H.ginit, st));
@@ -1174,11 +1308,16 @@ int pcg_run(Hier &H, double tol, int maxit, int *iters, double *relres, cudaStre
         if (H.ctl_host->done) break;
     }
     if (H.ctl_host->status == GW_ERR_NOT_CONVERGED || !H.ctl_host->done) {
-        with_mat(fine64(H), [&](auto A) {
-            using M = decltype(A);
-            k_cg_true<M><<<grid_for<M>(H, H.n), BS, 0, st>>>(A, H.n, H.b.p, H.x.p, H.r.p, H.part.p, c, 1);
-        });
-        H.launches += 1;
+        if (H.o.prec == GW_PREC_FP64) {
+            with_mat(fine64(H), [&](auto A) {
+                using M = decltype(A);
+                k_cg_true<M><<<grid_for<M>(H, H.n), BS, 0, st>>>(A, H.n, H.b.p, H.x.p, H.r.p, H.part.p, c, 1);
+            });
+            H.launches += 1;
+        } else {
+            rel_update(H, 1, st);
+            H.launches += 2;
+        }
         GW_LAUNCH_CHECK();
         GW_CUDA(cudaMemcpyAsync(H.ctl_host, c, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
         GW_CUDA(cudaStreamSynchronize(st));

@@ -151,7 +151,7 @@ bool to_store(const DCSR &A, MatStore<T> &M, int fmt, int nx, int ny, int nz, cu
 // no host round trip.
 struct Ctl {
     double bnorm2, tol2;
-    double rz, pq, alpha, beta, rr, rt2, relres, qz;
+    double rz, pq, alpha, beta, rr, rt2, relres, qz, rmax2, delta2;
     int it, maxit, done, status, check, flexible;
     unsigned int cnt[8];  // arrival counters of the last-block reductions
 };
@@ -219,7 +219,8 @@ struct Hier {
     DBuf<double> Ainv;         // dense inverse of the coarsest level, row-major
     // outer CG
     int n = 0;
-    DBuf<double> x, r, p, q, z, b, part;
+    DBuf<double> x, r, p, q, z, b, part;      // FP64 form (x, b also hold the mixed form's solution and rhs)
+    DBuf<float> xs32, r32, p32, q32, z32;     // mixed form: FP32 recurrence
     DBuf<Ctl> ctl;
     Ctl *ctl_host = nullptr;   // pinned mirror of the control block
     cudaStream_t cap = nullptr;

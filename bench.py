@@ -204,7 +204,7 @@ def run_ours(args):
     smoother = gw.GW_SMOOTH_CHEBYSHEV if args.smoother == "chebyshev" else gw.GW_SMOOTH_JACOBI
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    Hm = gw.Hierarchy(A, prec=gw.GW_PREC_MIXED32, smoother=smoother)
+    Hm = gw.Hierarchy(A, prec=gw.GW_PREC_MIXED32, smoother=smoother, delta=args.delta)
     torch.cuda.synchronize()
     setup_ms = (time.perf_counter() - t0) * 1e3
     Hd = None if args.no_fp64 else gw.Hierarchy(A, prec=gw.GW_PREC_FP64, smoother=smoother)
@@ -307,6 +307,7 @@ def main():
     ap.add_argument("--smoother", choices=("jacobi", "chebyshev"), default="chebyshev")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the all-FP64 arm (profiling runs)")
+    ap.add_argument("--delta", type=float, default=0.1, help="reliable-update factor of the mixed form")
     ap.add_argument("--side", type=int, default=SIDE, help="grid side for profiling captures (default 128)")
     args = ap.parse_args()
     if args.side != SIDE:

@@ -1019,13 +1019,12 @@ __global__ void k_to_stencil(int n, int nx, int sxy, const int *__restrict__ rp,
     }
 }
 
-// Short rows (the prolongator) as compact CSR read 4 lanes per row; rows of
-// medium length on big levels as sliced ELL, one thread per row; long rows
-// on small levels as CSR read by a whole warp, so the level still covers the GPU.
+// Short rows (the prolongator) and rows of medium length on big levels as
+// sliced ELL, one thread per row; long rows on small levels as CSR read by a
+// whole warp, so the level still covers the GPU.
 int choose_fmt(const DCSR &A)
 {
     const double avg = A.nr > 0 ? (double)A.nnz / A.nr : 0.0;
-    if (avg <= 6.0) return FMT_CSR4;
     if (avg <= 12.0 || A.nr >= 65536) return FMT_SELL;
     return FMT_CSR32;
 }

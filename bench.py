@@ -274,7 +274,7 @@ def run_ours(args):
     out = {"metric": METRIC, "value": p50m, "unit": "ms", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": mean_m, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32 V-cycle + f64 CG", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "n": n, "tol": TOL, "prec": "mixed32",
+           "config": {"workload": WORKLOAD, "n": n, "tol": TOL, "prec": "mixed32", "delta": args.delta,
                       "smoother": args.smoother, "levels": [l["n"] for l in info],
                       "l2": "flushed before every timed solve (256 MiB write)",
                       "parallelism": "replicas" if ws > 1 else "single GPU"},

@@ -139,6 +139,31 @@ void gw_amg_opts_default(gw_amg_opts *opts);
 int gw_assemble(const gw_grid *grid, const double *Kx, const double *Ky, const double *Kz, const gw_bc *bc,
                 const double *q, gw_matrix *A_out, double *b_out, void *stream);
 
+/*
+ * gw_assemble_noalloc -- the same assembly as gw_assemble (the same matrix
+ * and right-hand side, double for double), for callers that cannot allocate
+ * device memory at this point: the caller passes the output CSR arrays and
+ * the library allocates nothing.  The paper has no counterpart; this entry
+ * point exists for such callers only.
+ *   Kx, Ky, Kz, q     as in gw_assemble, but device memory only (Ky, Kz may be
+ *                     NULL or equal to Kx; q may be NULL).
+ *   rowptr            n+1 ints, device: receives the row pointers.
+ *   col, val          device arrays of at least 7n - 2(ny nz + nx nz + nx ny)
+ *                     ints / doubles: receive columns (ascending) and values.
+ *   b                 n doubles, device: receives Q.
+ * Working memory: a fixed array of about 256 KB in device memory that the
+ * library holds on every GPU that loads it, until the process exits; grids
+ * of more than 2^27 cells are rejected with GW_ERR_ARG.  The first call on a
+ * device looks up that array's device address, so make the first call on
+ * each device outside any stream capture.  All calls on a device share the
+ * array (the call clears the part that must start at zero): calls that
+ * overlap on the GPU race, so serialise them (one stream, or wait for the
+ * previous call, which synchronises its stream before returning).
+ * Errors: as gw_assemble, plus GW_ERR_ARG for a host pointer.
+ */
+int gw_assemble_noalloc(const gw_grid *grid, const double *Kx, const double *Ky, const double *Kz, const gw_bc *bc,
+                        const double *q, int *rowptr, int *col, double *val, double *b, void *stream);
+
 /* Size of the matrix behind a handle. */
 int gw_matrix_size(gw_matrix A, int *n, long long *nnz);
 

@@ -141,3 +141,113 @@ void assemble_csr(int nx, int ny, int nz, double dx, double dy, double dz, const
 }
 
 }  // namespace gw
+
+// ------------------------------------------- assembly without allocations --
+// Some callers cannot allocate device memory at the point where they need
+// the system assembled: a solver embedded in a host code that hands the
+// library a fixed device pool, a caller inside a region where cudaMalloc
+// would synchronise the device or is forbidden, or a process whose memory is
+// budgeted up front.  gw_assemble_noalloc serves them: the caller passes the
+// output arrays, and the only working memory the kernels need (the
+// validation flag and the block totals of the row-pointer scan) lives in the
+// fixed device array below, which every GPU that loads the library holds
+// until the process exits.
+namespace gw {
+
+// 1 validation flag + block totals of a scan over at most NOALLOC_MAX_CELLS
+// rows (2048 rows per block, two scan levels)
+constexpr long long NOALLOC_MAX_CELLS = 1LL << 27;
+constexpr size_t NOALLOC_SCRATCH_INTS = 1 + (size_t)(NOALLOC_MAX_CELLS / 2048) + 64 + 16;
+
+static __device__ __align__(256) int g_noalloc_scratch[NOALLOC_SCRATCH_INTS];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+static int *g_noalloc_ptr[NOALLOC_MAX_DEVICES];
+
+// The device address of the array: its name in host code is only a host-side
+// stand-in, so it is looked up once per device with that device current.
+static int *noalloc_scratch(int dev)
+{
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) fail(GW_ERR_ARG, "gw_assemble_noalloc: device %d out of range", dev);
+    if (!g_noalloc_ptr[dev]) {
+        int *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress((void **)&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            fail(GW_ERR_CUDA, "gw_assemble_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+        g_noalloc_ptr[dev] = p;
+    }
+    return g_noalloc_ptr[dev];
+}
+
+}  // namespace gw
+
+extern "C" int gw_assemble_noalloc(const gw_grid *grid, const double *Kx, const double *Ky, const double *Kz,
+                                   const gw_bc *bc, const double *q, int *rowptr, int *col, double *val, double *b,
+                                   void *stream)
+{
+    using namespace gw;
+    try {
+        if (!grid || !Kx || !bc || !rowptr || !col || !val || !b) fail(GW_ERR_ARG, "gw_assemble_noalloc: null argument");
+        const int nx = grid->nx, ny = grid->ny, nz = grid->nz;
+        if (nx < 1 || ny < 1 || nz < 1) fail(GW_ERR_ARG, "gw_assemble_noalloc: grid sizes must be >= 1");
+        const double dx = grid->dx, dy = grid->dy, dz = grid->dz;
+        if (!(dx > 0.0) || !(dy > 0.0) || !(dz > 0.0) || !isfinite(dx) || !isfinite(dy) || !isfinite(dz))
+            fail(GW_ERR_ARG, "gw_assemble_noalloc: cell sizes must be positive and finite");
+        const long long n64 = (long long)nx * ny * nz;
+        if (n64 > NOALLOC_MAX_CELLS)
+            fail(GW_ERR_ARG, "gw_assemble_noalloc: %lld cells exceeds the maximum of %lld", n64, NOALLOC_MAX_CELLS);
+        int ndir = 0;
+        for (int f = 0; f < 6; ++f) {
+            if (bc->type[f] != GW_NOFLOW && bc->type[f] != GW_DIRICHLET)
+                fail(GW_ERR_ARG, "gw_assemble_noalloc: bad face type");
+            if (bc->type[f] == GW_DIRICHLET) {
+                if (!isfinite(bc->value[f])) fail(GW_ERR_ARG, "gw_assemble_noalloc: head on face %d is not finite", f);
+                ++ndir;
+            }
+        }
+        if (ndir == 0) fail(GW_ERR_ARG, "gw_assemble_noalloc: no Dirichlet face, the system is singular");
+        const double *ky = Ky ? Ky : Kx, *kz = Kz ? Kz : Kx;
+        const void *ptrs[8] = {Kx, ky, kz, q, rowptr, col, val, b};
+        for (int k = 0; k < 8; ++k)
+            if (ptrs[k] && !is_device_ptr(ptrs[k]))
+                fail(GW_ERR_ARG, "gw_assemble_noalloc: every array must be device memory (argument %d is not)", k);
+        int dev = 0;
+        GW_CUDA(cudaGetDevice(&dev));
+        int *scratch = noalloc_scratch(dev);
+        cudaStream_t st = (cudaStream_t)stream;
+        const int n = (int)n64;
+        AsmGeom G;
+        G.nx = nx;
+        G.ny = ny;
+        G.nz = nz;
+        G.g[0] = (dy * dz) / dx;
+        G.g[1] = (dx * dz) / dy;
+        G.g[2] = (dx * dy) / dz;
+        for (int f = 0; f < 6; ++f) {
+            G.bct[f] = bc->type[f];
+            G.bcv[f] = bc->value[f];
+        }
+        const int bs = 256;
+        const int grid_b = (int)std::min<long long>((n + bs - 1) / bs, 152LL * 16);
+        int *flag = scratch;
+        GW_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), st));
+        k_asm_validate<<<grid_b, bs, 0, st>>>(n, Kx, ky, kz, q, flag);
+        GW_LAUNCH_CHECK();
+        if (read_int(flag, st))
+            fail(GW_ERR_ARG, "gw_assemble_noalloc: a conductivity is <= 0 or not finite, or q is not finite");
+        k_asm_rowcount<<<grid_b, bs, 0, st>>>(G, rowptr);
+        GW_LAUNCH_CHECK();
+        if (!exclusive_scan_in(rowptr, rowptr, n, scratch + 1, NOALLOC_SCRATCH_INTS - 1, st))
+            fail(GW_ERR_ARG, "gw_assemble_noalloc: grid too large for the scan workspace");
+        k_asm_fill<<<grid_b, bs, 0, st>>>(G, Kx, ky, kz, q, rowptr, col, val, b);
+        GW_LAUNCH_CHECK();
+        GW_CUDA(cudaStreamSynchronize(st));
+    } catch (const Error &e) {
+        set_last_error(e.msg.c_str());
+        return e.code;
+    } catch (...) {
+        set_last_error("unexpected failure");
+        return GW_ERR_CUDA;
+    }
+    return GW_OK;
+}

@@ -160,6 +160,7 @@ constexpr int RED_MAX_BLOCKS = 2048;
 
 // ------------------------------------------------------------ scan / misc --
 void exclusive_scan(const int *in, int *out, int n, cudaStream_t st);  // out[n] = total
+bool exclusive_scan_in(const int *in, int *out, int n, int *scratch, size_t cap, cudaStream_t st);
 int read_int(const int *dptr, cudaStream_t st);
 void to_device(void *dst, const void *src, size_t bytes, cudaStream_t st);
 bool is_device_ptr(const void *p);

@@ -88,6 +88,31 @@ void exclusive_scan(const int *in, int *out, int n, cudaStream_t st)
     GW_CUDA(cudaFreeAsync(bsum, st));
 }
 
+// Same scan, with the block totals kept in caller-provided device memory of
+// `cap` ints instead of an allocation; returns false if cap is too small.
+bool exclusive_scan_in(const int *in, int *out, int n, int *scratch, size_t cap, cudaStream_t st)
+{
+    if (n <= 0) {
+        GW_CUDA(cudaMemsetAsync(out, 0, sizeof(int), st));
+        return true;
+    }
+    const int nb = (n + SCAN_CHUNK - 1) / SCAN_CHUNK;
+    if ((size_t)nb + 1 > cap) return false;
+    int *bsum = scratch;
+    k_scan_block<<<nb, SCAN_BS, 0, st>>>(in, out, bsum, n);
+    GW_LAUNCH_CHECK();
+    if (nb > 1) {
+        if (!exclusive_scan_in(bsum, bsum, nb, scratch + nb + 1, cap - (size_t)nb - 1, st)) return false;
+        k_scan_add<<<(n + 255) / 256, 256, 0, st>>>(out, bsum, n);
+        GW_LAUNCH_CHECK();
+        k_set_at<<<1, 1, 0, st>>>(out + n, bsum + nb);
+    } else {
+        k_set_at<<<1, 1, 0, st>>>(out + n, bsum);
+    }
+    GW_LAUNCH_CHECK();
+    return true;
+}
+
 int read_int(const int *dptr, cudaStream_t st)
 {
     int v = 0;

@@ -21,7 +21,8 @@ GW_SMOOTH_JACOBI, GW_SMOOTH_CHEBYSHEV = 0, 1
 
 EXPORTS = ("gw_amg_opts_default", "gw_assemble", "gw_matrix_size", "gw_matrix_export", "gw_amg_setup",
            "gw_pcg_solve", "gw_vcycle", "gw_hierarchy_info", "gw_hierarchy_export", "gw_matrix_free",
-           "gw_hierarchy_free", "gw_status_str", "gw_last_error", "gw_profile_enable", "gw_profile_read")
+           "gw_hierarchy_free", "gw_status_str", "gw_last_error", "gw_profile_enable", "gw_profile_read",
+           "gw_assemble_noalloc")
 
 PK_NAMES = ("spmv", "update", "pre", "restrict", "coarse", "prolong", "post", "pupdate")
 
@@ -87,6 +88,7 @@ def load():
         "gw_last_error": (ctypes.c_char_p, []),
         "gw_profile_enable": (i, [vp, i]),
         "gw_profile_read": (i, [vp, P(gw_profile), i]),
+        "gw_assemble_noalloc": (i, [P(gw_grid), vp, vp, vp, P(gw_bc), vp, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -184,6 +186,18 @@ def gw_assemble(nx, ny, nz, Kx, Ky=None, Kz=None, bct=(1, 1, 0, 0, 0, 0), bcv=(1
                          _ptr(Kz if Kz is not None else Kx), ctypes.byref(bc), _ptr(q), ctypes.byref(h),
                          _ptr(b_out), _stream(stream)))
     return Matrix(h), b_out
+
+
+def gw_assemble_noalloc(nx, ny, nz, Kx, rowptr, col, val, b, Ky=None, Kz=None, bct=(1, 1, 0, 0, 0, 0),
+                        bcv=(1.0, 0.0, 0, 0, 0, 0), q=None, spacing=(1.0, 1.0, 1.0), stream=None):
+    """Assembly into caller-provided device arrays (include/gw.h: gw_assemble_noalloc)."""
+    g = gw_grid(nx, ny, nz, float(spacing[0]), float(spacing[1]), float(spacing[2]))
+    bc = gw_bc()
+    for f in range(6):
+        bc.type[f] = int(bct[f])
+        bc.value[f] = float(bcv[f])
+    _check(load().gw_assemble_noalloc(ctypes.byref(g), _ptr(Kx), _ptr(Ky), _ptr(Kz), ctypes.byref(bc), _ptr(q),
+                                      _ptr(rowptr), _ptr(col), _ptr(val), _ptr(b), _stream(stream)))
 
 
 class Hierarchy:

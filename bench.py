@@ -211,7 +211,6 @@ def run_ours(args):
     info = Hm.info()
     h = torch.empty_like(b)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    Hm.profile(True)
     for _ in range(max(args.warmup, 3)):
         Hm.solve(b, h, tol=TOL, stream=stream)
         if Hd is not None:
@@ -220,11 +219,20 @@ def run_ours(args):
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
+    # timed region: the headline solves, instrumentation off
     with ClockSampler(torch.cuda.current_device()) as clk:
         t_wall = time.perf_counter()
         tm, it_m, rel_m, st_m = timed_solves(torch, Hm, b, h, args.steps, flush, stream)
         t_wall = time.perf_counter() - t_wall
-    kinds, launches, solves = Hm.profile_read(reset=True)
+    _, launches, solves = Hm.profile_read(reset=True)
+    # second timed pass with CUDA events captured around the level-0 kernels
+    Hm.profile(True)
+    for _ in range(2):
+        Hm.solve(b, h, tol=TOL, stream=stream)
+    Hm.profile_read(reset=True)
+    tp, _, _, _ = timed_solves(torch, Hm, b, h, args.steps, flush, stream)
+    kinds, _, _ = Hm.profile_read(reset=True)
+    Hm.profile(False)
     h_mixed = h.clone()
     if args.no_fp64:
         td, it_d, rel_d, st_d = [float("nan")], 0, float("nan"), -1
@@ -279,7 +287,7 @@ def run_ours(args):
                       "l2": "flushed before every timed solve (256 MiB write)",
                       "parallelism": "replicas" if ws > 1 else "single GPU"},
            "p50_ms": p50m, "p99_ms": float(np.percentile(tm, 99)), "iters": it_m, "relres": rel_m,
-           "status": st_m, "solves_per_s": ws * 1e3 / p50m,
+           "status": st_m, "solves_per_s": ws * 1e3 / p50m, "profiled_p50_ms": float(np.median(tp)),
            "fp64": {"p50_ms": p50d, "p99_ms": float(np.percentile(td, 99)), "iters": it_d, "relres": rel_d,
                     "status": st_d},
            "mixed_speedup_vs_fp64": p50d / p50m,

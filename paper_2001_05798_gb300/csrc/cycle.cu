@@ -331,6 +331,34 @@ static inline int vgrid(const Hier &H, long long n)
 
 #define ROWS(i, n) for (int i = blockIdx.x * BS + threadIdx.x; i < (n); i += gridDim.x * BS)
 
+// Programmatic dependent launch: every kernel of the cycle and of CG is
+// launched so that the next kernel in the stream may be scheduled while this
+// one runs; each kernel waits for its predecessors to complete (and their
+// writes to be visible) before it touches global memory, then lets its own
+// dependents launch.  Inside captured graphs this hides the launch gap
+// between the 20-30 dependent kernels of a CG iteration.
+__device__ __forceinline__ void pdl_enter()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <class... KArgs, class... Args>
+static void launch_pdl(void (*kernel)(KArgs...), int grid, cudaStream_t st, Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(BS);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    GW_CUDA(cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...));
+}
+
 
 // ------------------------------------------------------------- reductions --
 __device__ __forceinline__ double warp_sum(double v)
@@ -429,6 +457,7 @@ __global__ void __launch_bounds__(BS) k_jac0_res(M A, int n, const typename M::v
                                                  const BT *__restrict__ b, typename M::value_type *__restrict__ x,
                                                  typename M::value_type *__restrict__ r, const Ctl *ctl)
 {
+    pdl_enter();
     using T = typename M::value_type;
     constexpr int R = M::R;
     if (finished(ctl)) return;
@@ -458,6 +487,7 @@ __global__ void __launch_bounds__(BS) k_jacobi(M A, int n, const typename M::val
                                                OT *__restrict__ xo, const typename M::value_type *__restrict__ q,
                                                double *part, Ctl *ctl, int mode)
 {
+    pdl_enter();
     using T = typename M::value_type;
     constexpr int R = M::R;
     if (finished(ctl)) return;
@@ -492,6 +522,7 @@ __global__ void __launch_bounds__(BS) k_residual(M A, int n, const BT *__restric
                                                  const typename M::value_type *__restrict__ x,
                                                  typename M::value_type *__restrict__ r, const Ctl *ctl)
 {
+    pdl_enter();
     using T = typename M::value_type;
     constexpr int R = M::R;
     if (finished(ctl)) return;
@@ -513,6 +544,7 @@ template <class M>
 __global__ void __launch_bounds__(BS) k_spmv(M Rm, int n, const typename M::value_type *__restrict__ x,
                                              typename M::value_type *__restrict__ y, const Ctl *ctl)
 {
+    pdl_enter();
     using T = typename M::value_type;
     if (finished(ctl)) return;
     GROUP_ROWS(M, n)
@@ -527,6 +559,7 @@ template <class M>
 __global__ void __launch_bounds__(BS) k_prolong(M P, int n, const typename M::value_type *__restrict__ e,
                                                 typename M::value_type *__restrict__ x, const Ctl *ctl)
 {
+    pdl_enter();
     using T = typename M::value_type;
     constexpr int R = M::R;
     if (finished(ctl)) return;
@@ -547,6 +580,7 @@ template <class T>
 __global__ void __launch_bounds__(BS) k_coarse(int n, const double *__restrict__ Ainv, const T *__restrict__ b,
                                                T *__restrict__ x, const Ctl *ctl)
 {
+    pdl_enter();
     if (finished(ctl)) return;
     const int lane = threadIdx.x & 31;
     for (int row = (blockIdx.x * BS + threadIdx.x) >> 5; row < n; row += (gridDim.x * BS) >> 5) {
@@ -570,6 +604,7 @@ __global__ void __launch_bounds__(BS) k_cheb0(M A, int n, const typename M::valu
                                               const typename M::value_type *__restrict__ q, double *part, Ctl *ctl,
                                               int mode)
 {
+    pdl_enter();
     using T = typename M::value_type;
     constexpr int R = M::R;
     if (finished(ctl)) return;
@@ -623,6 +658,7 @@ __global__ void __launch_bounds__(BS) k_chebk(M A, int n, const typename M::valu
                                               const typename M::value_type *__restrict__ q, double *part, Ctl *ctl,
                                               int mode)
 {
+    pdl_enter();
     using T = typename M::value_type;
     constexpr int R = M::R;
     if (finished(ctl)) return;
@@ -665,6 +701,7 @@ __global__ void __launch_bounds__(BS) k_chebk(M A, int n, const typename M::valu
 template <class T>
 __global__ void __launch_bounds__(BS) k_axpy(int n, const T *__restrict__ d, T *__restrict__ x, const Ctl *ctl)
 {
+    pdl_enter();
     if (finished(ctl)) return;
     ROWS(i, n) x[i] += d[i];
 }
@@ -726,9 +763,9 @@ static void smooth(Hier &H, std::vector<CycLevel<T>> &C, int l, const T *b, bool
                 const T *xi = first ? nullptr : cur;
                 H.prof_bytes += vbytes(H, (first ? 0.0 : amat + dn * sx) + 3.0 * dn * sx + (fin && q ? dn * sx : 0.0));
                 if (fin) {
-                    k_jacobi<M, T, T, true><<<g, BS, 0, st>>>(A, n, lv.dw.p, b, xi, zout, q, part, ctl, mode);
+                    launch_pdl(k_jacobi<M, T, T, true>, g, st, A, n, lv.dw.p, b, xi, zout, q, part, ctl, mode);
                 } else {
-                    k_jacobi<M, T, T, false><<<g, BS, 0, st>>>(A, n, lv.dw.p, b, xi, nxt, q, part, ctl, mode);
+                    launch_pdl(k_jacobi<M, T, T, false>, g, st, A, n, lv.dw.p, b, xi, nxt, q, part, ctl, mode);
                     std::swap(cur, nxt);
                 }
             }
@@ -745,17 +782,17 @@ static void smooth(Hier &H, std::vector<CycLevel<T>> &C, int l, const T *b, bool
             const double b0 = 2.0 * dn * sx + (zero ? 0.0 : amat + dn * sx);
             if (fin && m == 1) {
                 H.prof_bytes += vbytes(H, b0 + 3.0 * dn * sx + (q ? dn * sx : 0.0));
-                k_cheb0<M, T, T, true><<<g, BS, 0, st>>>(A, n, lv.dw.p, b, lv.x.p, lv.r.p, d, zout, (T)lv.c0, zero, q,
+                launch_pdl(k_cheb0<M, T, T, true>, g, st, A, n, lv.dw.p, b, lv.x.p, lv.r.p, d, zout, (T)lv.c0, zero, q,
                                                          part, ctl, mode);
                 continue;
             }
             H.prof_bytes += vbytes(H, b0 + (zero ? 3.0 : 2.0) * dn * sx);
-            k_cheb0<M, T, T, false><<<g, BS, 0, st>>>(A, n, lv.dw.p, b, lv.x.p, lv.r.p, d, (T *)nullptr, (T)lv.c0,
+            launch_pdl(k_cheb0<M, T, T, false>, g, st, A, n, lv.dw.p, b, lv.x.p, lv.r.p, d, (T *)nullptr, (T)lv.c0,
                                                       zero, q, part, ctl, mode);
             if (m == 1) {
                 if (!zero) {
                     H.prof_bytes += vbytes(H, 3.0 * dn * sx);
-                    k_axpy<T><<<vgrid(H, n), BS, 0, st>>>(n, d, lv.x.p, ctl);
+                    launch_pdl(k_axpy<T>, vgrid(H, n), st, n, d, lv.x.p, ctl);
                 }
                 continue;
             }
@@ -764,10 +801,10 @@ static void smooth(Hier &H, std::vector<CycLevel<T>> &C, int l, const T *b, bool
                 const int add_prev = (k == 1 && !zero) ? 1 : 0;
                 H.prof_bytes += vbytes(H, amat + dn * sx * 6.0 + (f2 ? dn * sx * (q ? 2.0 : 1.0) : 0.0));
                 if (f2)
-                    k_chebk<M, T, true><<<g, BS, 0, st>>>(A, n, lv.dw.p, lv.r.p, d, dnx, lv.x.p, zout, (T)lv.c1[k],
+                    launch_pdl(k_chebk<M, T, true>, g, st, A, n, lv.dw.p, lv.r.p, d, dnx, lv.x.p, zout, (T)lv.c1[k],
                                                           (T)lv.c2[k], add_prev, b, q, part, ctl, mode);
                 else
-                    k_chebk<M, T, false><<<g, BS, 0, st>>>(A, n, lv.dw.p, lv.r.p, d, dnx, lv.x.p, (T *)nullptr,
+                    launch_pdl(k_chebk<M, T, false>, g, st, A, n, lv.dw.p, lv.r.p, d, dnx, lv.x.p, (T *)nullptr,
                                                            (T)lv.c1[k], (T)lv.c2[k], add_prev, (const T *)nullptr, q,
                                                            part, ctl, mode);
                 std::swap(d, dnx);
@@ -795,14 +832,14 @@ static void vcycle_t(Hier &H, std::vector<CycLevel<T>> &C, const T *r, T *z, Ctl
             H.prof_bytes += vbytes(H, amat + 4.0 * dn * sx);
             with_mat(lv.A, [&](auto A) {
                 using M = decltype(A);
-                k_jac0_res<M, T><<<grid_for<M>(H, n), BS, 0, st>>>(A, n, lv.dw.p, bl, lv.x.p, lv.r.p, ctl);
+                launch_pdl(k_jac0_res<M, T>, grid_for<M>(H, n), st, A, n, lv.dw.p, bl, lv.x.p, lv.r.p, ctl);
             });
         } else {
             smooth<T>(H, C, l, bl, true, false, nullptr, ctl, q, mode, st);
             H.prof_bytes += vbytes(H, amat + 3.0 * dn * sx);
             with_mat(lv.A, [&](auto A) {
                 using M = decltype(A);
-                k_residual<M, T><<<grid_for<M>(H, n), BS, 0, st>>>(A, n, bl, lv.x.p, lv.r.p, ctl);
+                launch_pdl(k_residual<M, T>, grid_for<M>(H, n), st, A, n, bl, lv.x.p, lv.r.p, ctl);
             });
         }
         if (l == 0) {
@@ -812,7 +849,7 @@ static void vcycle_t(Hier &H, std::vector<CycLevel<T>> &C, const T *r, T *z, Ctl
         H.prof_bytes += vbytes(H, mat_bytes(lv.R) + dn * sx + (double)lv.R.nr * sx);
         with_mat(lv.R, [&](auto Rm) {
             using M = decltype(Rm);
-            k_spmv<M><<<grid_for<M>(H, lv.R.nr), BS, 0, st>>>(Rm, lv.R.nr, lv.r.p, C[l + 1].b.p, ctl);
+            launch_pdl(k_spmv<M>, grid_for<M>(H, lv.R.nr), st, Rm, lv.R.nr, lv.r.p, C[l + 1].b.p, ctl);
         });
         GW_LAUNCH_CHECK();
         if (l == 0) {
@@ -822,7 +859,7 @@ static void vcycle_t(Hier &H, std::vector<CycLevel<T>> &C, const T *r, T *z, Ctl
     }
     {
         CycLevel<T> &lc = C[L - 1];
-        k_coarse<T><<<std::max(1, std::min(H.max_blocks, (lc.n * 32 + BS - 1) / BS)), BS, 0, st>>>(lc.n, H.Ainv.p,
+        launch_pdl(k_coarse<T>, std::max(1, std::min(H.max_blocks, (lc.n * 32 + BS - 1) / BS)), st, lc.n, H.Ainv.p,
                                                                                                    lc.b.p, lc.x.p, ctl);
     }
     for (int l = L - 2; l >= 0; --l) {
@@ -837,7 +874,7 @@ static void vcycle_t(Hier &H, std::vector<CycLevel<T>> &C, const T *r, T *z, Ctl
         H.prof_bytes += vbytes(H, mat_bytes(lv.P) + (double)lv.P.nc * sx + 2.0 * dn * sx);
         with_mat(lv.P, [&](auto P) {
             using M = decltype(P);
-            k_prolong<M><<<grid_for<M>(H, n), BS, 0, st>>>(P, n, C[l + 1].x.p, lv.x.p, ctl);
+            launch_pdl(k_prolong<M>, grid_for<M>(H, n), st, P, n, C[l + 1].x.p, lv.x.p, ctl);
         });
         if (l == 0) {
             mark_end(H, st);
@@ -852,6 +889,7 @@ static void vcycle_t(Hier &H, std::vector<CycLevel<T>> &C, const T *r, T *z, Ctl
 template <class A, class B>
 __global__ void k_convert(int n, const A *__restrict__ a, B *__restrict__ b)
 {
+    pdl_enter();
     ROWS(i, n) b[i] = (B)a[i];
 }
 
@@ -864,9 +902,9 @@ void vcycle_enqueue(Hier &H, const double *r, double *z, Ctl *ctl, bool dot, cud
         return;
     }
     const int n = H.n;
-    k_convert<double, float><<<vgrid(H, n), BS, 0, st>>>(n, r, H.r32.p);
+    launch_pdl(k_convert<double, float>, vgrid(H, n), st, n, r, H.r32.p);
     vcycle_t<float>(H, H.cf, H.r32.p, H.z32.p, ctl, nullptr, 0, st);
-    k_convert<float, double><<<vgrid(H, n), BS, 0, st>>>(n, H.z32.p, z);
+    launch_pdl(k_convert<float, double>, vgrid(H, n), st, n, H.z32.p, z);
     GW_LAUNCH_CHECK();
 }
 
@@ -885,6 +923,7 @@ template <class V>
 __global__ void __launch_bounds__(BS) k_cg_init(int n, const double *__restrict__ b, double *__restrict__ x,
                                                 V *__restrict__ xs, V *__restrict__ r, double *part, Ctl *c)
 {
+    pdl_enter();
     double loc[1] = {0.0}, tot[1];
     ROWS(i, n)
     {
@@ -909,6 +948,7 @@ __global__ void __launch_bounds__(BS) k_cg_init(int n, const double *__restrict_
 template <class V>
 __global__ void __launch_bounds__(BS) k_copy(int n, const V *__restrict__ a, V *__restrict__ b, const Ctl *c)
 {
+    pdl_enter();
     if (finished(c)) return;
     ROWS(i, n) b[i] = a[i];
 }
@@ -918,6 +958,7 @@ template <class M>
 __global__ void __launch_bounds__(BS) k_cg_spmv_dot(M A, int n, const typename M::value_type *__restrict__ p,
                                                     typename M::value_type *__restrict__ q, double *part, Ctl *c)
 {
+    pdl_enter();
     using V = typename M::value_type;
     constexpr int R = M::R;
     if (finished(c)) return;
@@ -962,6 +1003,7 @@ __global__ void __launch_bounds__(BS) k_cg_update(int n, V *__restrict__ x, V *_
                                                   const V *__restrict__ p, const V *__restrict__ q, double *part,
                                                   Ctl *c, int reliable)
 {
+    pdl_enter();
     if (finished(c)) return;
     const V a = (V)c->alpha;
     double loc[1] = {0.0}, tot[1];
@@ -995,6 +1037,7 @@ template <class M>
 __global__ void __launch_bounds__(BS) k_cg_true(M A, int n, const double *__restrict__ b, const double *__restrict__ x,
                                                 double *__restrict__ r, double *part, Ctl *c, int force)
 {
+    pdl_enter();
     constexpr int R = M::R;
     if (!force && (finished(c) || !c->check)) return;
     double loc[1] = {0.0}, tot[1];
@@ -1032,6 +1075,7 @@ template <int R>
 __global__ void __launch_bounds__(BS) k_rel_fold(int n, double *__restrict__ x, float *__restrict__ xs, const Ctl *c,
                                                  int force)
 {
+    pdl_enter();
     if (!force && (finished(c) || !c->check)) return;
     for (int i = R * (blockIdx.x * BS + threadIdx.x); i < n; i += R * gridDim.x * BS) {
         VecN<double, R> xv = ld_rw<R>(x + i);
@@ -1053,6 +1097,7 @@ template <class M>
 __global__ void __launch_bounds__(BS) k_rel_res(M A, int n, const double *__restrict__ b, const double *__restrict__ x,
                                                 float *__restrict__ r, double *part, Ctl *c, int force)
 {
+    pdl_enter();
     constexpr int R = M::R;
     if (!force && (finished(c) || !c->check)) return;
     double loc[1] = {0.0}, tot[1];
@@ -1091,6 +1136,7 @@ __global__ void __launch_bounds__(BS) k_rel_res(M A, int n, const double *__rest
 template <class V, int R>
 __global__ void __launch_bounds__(BS) k_cg_p(int n, const V *__restrict__ z, V *__restrict__ p, const Ctl *c)
 {
+    pdl_enter();
     if (finished(c)) return;
     const V beta = (V)c->beta;
     for (int i = R * (blockIdx.x * BS + threadIdx.x); i < n; i += R * gridDim.x * BS) {
@@ -1110,8 +1156,8 @@ static void cg_vec_update(Hier &H, V *x, V *r, const V *p, const V *q, int relia
 {
     const int n = H.n;
     constexpr int R = 16 / sizeof(V);
-    if (n % R == 0) k_cg_update<V, R><<<vgrid(H, n / R), BS, 0, st>>>(n, x, r, p, q, H.part.p, H.ctl.p, reliable);
-    else k_cg_update<V, 1><<<vgrid(H, n), BS, 0, st>>>(n, x, r, p, q, H.part.p, H.ctl.p, reliable);
+    if (n % R == 0) launch_pdl(k_cg_update<V, R>, vgrid(H, n / R), st, n, x, r, p, q, H.part.p, H.ctl.p, reliable);
+    else launch_pdl(k_cg_update<V, 1>, vgrid(H, n), st, n, x, r, p, q, H.part.p, H.ctl.p, reliable);
 }
 
 template <class V>
@@ -1119,18 +1165,18 @@ static void cg_vec_p(Hier &H, const V *z, V *p, cudaStream_t st)
 {
     const int n = H.n;
     constexpr int R = 16 / sizeof(V);
-    if (n % R == 0) k_cg_p<V, R><<<vgrid(H, n / R), BS, 0, st>>>(n, z, p, H.ctl.p);
-    else k_cg_p<V, 1><<<vgrid(H, n), BS, 0, st>>>(n, z, p, H.ctl.p);
+    if (n % R == 0) launch_pdl(k_cg_p<V, R>, vgrid(H, n / R), st, n, z, p, H.ctl.p);
+    else launch_pdl(k_cg_p<V, 1>, vgrid(H, n), st, n, z, p, H.ctl.p);
 }
 
 static void rel_update(Hier &H, int force, cudaStream_t st)
 {
     const int n = H.n;
-    if (n % 2 == 0) k_rel_fold<2><<<vgrid(H, n / 2), BS, 0, st>>>(n, H.x.p, H.xs32.p, H.ctl.p, force);
-    else k_rel_fold<1><<<vgrid(H, n), BS, 0, st>>>(n, H.x.p, H.xs32.p, H.ctl.p, force);
+    if (n % 2 == 0) launch_pdl(k_rel_fold<2>, vgrid(H, n / 2), st, n, H.x.p, H.xs32.p, H.ctl.p, force);
+    else launch_pdl(k_rel_fold<1>, vgrid(H, n), st, n, H.x.p, H.xs32.p, H.ctl.p, force);
     with_mat(H.A64, [&](auto A) {
         using M = decltype(A);
-        k_rel_res<M><<<grid_for<M>(H, n), BS, 0, st>>>(A, n, H.b.p, H.x.p, H.r32.p, H.part.p, H.ctl.p, force);
+        launch_pdl(k_rel_res<M>, grid_for<M>(H, n), st, A, n, H.b.p, H.x.p, H.r32.p, H.part.p, H.ctl.p, force);
     });
 }
 
@@ -1145,7 +1191,7 @@ static void cg_iteration(Hier &H, cudaStream_t st)
         H.prof_bytes += vbytes(H, mat_bytes(A64) + 16.0 * dn);
         with_mat(A64, [&](auto A) {
             using M = decltype(A);
-            k_cg_spmv_dot<M><<<grid_for<M>(H, n), BS, 0, st>>>(A, n, H.p.p, H.q.p, H.part.p, c);
+            launch_pdl(k_cg_spmv_dot<M>, grid_for<M>(H, n), st, A, n, H.p.p, H.q.p, H.part.p, c);
         });
         mark_end(H, st);
         mark_begin(H, GW_PK_UPDATE, st);
@@ -1154,7 +1200,7 @@ static void cg_iteration(Hier &H, cudaStream_t st)
         mark_end(H, st);
         with_mat(A64, [&](auto A) {
             using M = decltype(A);
-            k_cg_true<M><<<grid_for<M>(H, n), BS, 0, st>>>(A, n, H.b.p, H.x.p, H.r.p, H.part.p, c, 0);
+            launch_pdl(k_cg_true<M>, grid_for<M>(H, n), st, A, n, H.b.p, H.x.p, H.r.p, H.part.p, c, 0);
         });
         vcycle_t<double>(H, H.cd, H.r.p, H.z.p, c, nullptr, 1, st);
         mark_begin(H, GW_PK_PUPDATE, st);
@@ -1169,7 +1215,7 @@ static void cg_iteration(Hier &H, cudaStream_t st)
     H.prof_bytes += vbytes(H, mat_bytes(A32) + 8.0 * dn);
     with_mat(A32, [&](auto A) {
         using M = decltype(A);
-        k_cg_spmv_dot<M><<<grid_for<M>(H, n), BS, 0, st>>>(A, n, H.p32.p, H.q32.p, H.part.p, c);
+        launch_pdl(k_cg_spmv_dot<M>, grid_for<M>(H, n), st, A, n, H.p32.p, H.q32.p, H.part.p, c);
     });
     mark_end(H, st);
     mark_begin(H, GW_PK_UPDATE, st);
@@ -1244,13 +1290,13 @@ static void ensure_graphs(Hier &H)
     const int n = H.n, g = vgrid(H, n);
     H.ginit = capture(H, [&](cudaStream_t s) {
         if (H.o.prec == GW_PREC_FP64) {
-            k_cg_init<double><<<g, BS, 0, s>>>(n, H.b.p, H.x.p, (double *)nullptr, H.r.p, H.part.p, H.ctl.p);
+            launch_pdl(k_cg_init<double>, g, s, n, H.b.p, H.x.p, (double *)nullptr, H.r.p, H.part.p, H.ctl.p);
             vcycle_t<double>(H, H.cd, H.r.p, H.z.p, H.ctl.p, nullptr, 0, s);
-            k_copy<double><<<g, BS, 0, s>>>(n, H.z.p, H.p.p, H.ctl.p);
+            launch_pdl(k_copy<double>, g, s, n, H.z.p, H.p.p, H.ctl.p);
         } else {
-            k_cg_init<float><<<g, BS, 0, s>>>(n, H.b.p, H.x.p, H.xs32.p, H.r32.p, H.part.p, H.ctl.p);
+            launch_pdl(k_cg_init<float>, g, s, n, H.b.p, H.x.p, H.xs32.p, H.r32.p, H.part.p, H.ctl.p);
             vcycle_t<float>(H, H.cf, H.r32.p, H.z32.p, H.ctl.p, nullptr, 0, s);
-            k_copy<float><<<g, BS, 0, s>>>(n, H.z32.p, H.p32.p, H.ctl.p);
+            launch_pdl(k_copy<float>, g, s, n, H.z32.p, H.p32.p, H.ctl.p);
         }
         GW_LAUNCH_CHECK();
     }, &H.init_kernels);
@@ -1311,7 +1357,7 @@ int pcg_run(Hier &H, double tol, int maxit, int *iters, double *relres, cudaStre
         if (H.o.prec == GW_PREC_FP64) {
             with_mat(fine64(H), [&](auto A) {
                 using M = decltype(A);
-                k_cg_true<M><<<grid_for<M>(H, H.n), BS, 0, st>>>(A, H.n, H.b.p, H.x.p, H.r.p, H.part.p, c, 1);
+                launch_pdl(k_cg_true<M>, grid_for<M>(H, H.n), st, A, H.n, H.b.p, H.x.p, H.r.p, H.part.p, c, 1);
             });
             H.launches += 1;
         } else {

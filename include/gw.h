@@ -227,23 +227,27 @@ int gw_hierarchy_export(gw_hierarchy H, int level, int *agg, unsigned char *root
 /*
  * Benchmark instrumentation (no counterpart in the paper).  With profiling
  * on, the captured CG iteration graph records CUDA events around the
- * level-0 work of every iteration: the outer FP64 product q = A p with its
- * dot (GW_PK_SPMV), the x/r update (GW_PK_UPDATE), the pre-smoothing with
- * the residual (GW_PK_PRE), the restriction (GW_PK_RESTRICT), everything on
- * the coarser levels (GW_PK_COARSE), the interpolation and correction
- * (GW_PK_PROLONG), the post-smoothing that yields z (GW_PK_POST) and the
- * direction update (GW_PK_PUPDATE).  Only iterations that ran to the end are
- * counted.  bytes[k] is the algorithmic traffic of one launch of kind k:
- * every array counted once, a gathered vector once, padding not counted.
- * kernel_launches counts every kernel the solves launched (graph kernel
- * nodes included), profiling on or off.
+ * level-0 work of every iteration: the outer product q = A p with its dot
+ * (GW_PK_SPMV), the x/r update (GW_PK_UPDATE), the pre-smoothing with the
+ * residual (GW_PK_PRE), the restriction (GW_PK_RESTRICT), the interpolation
+ * and correction (GW_PK_PROLONG), the post-smoothing that yields z
+ * (GW_PK_POST) and the direction update (GW_PK_PUPDATE); and the coarser
+ * levels: level 1 down to the restriction to level 2 (GW_PK_L1DOWN), levels
+ * 2 and below with the coarsest solve (GW_PK_DEEP), and the interpolation to
+ * level 1 with its post-smoothing (GW_PK_L1UP).  Only iterations that ran to
+ * the end are counted.  bytes[k] is the algorithmic traffic of one launch of
+ * kind k: every array counted once, a gathered vector once, padding not
+ * counted.  kernel_launches counts every kernel the solves launched (graph
+ * kernel nodes included), profiling on or off.
  */
 enum {
     GW_PK_SPMV = 0,
     GW_PK_UPDATE,
     GW_PK_PRE,
     GW_PK_RESTRICT,
-    GW_PK_COARSE,
+    GW_PK_L1DOWN,
+    GW_PK_DEEP,
+    GW_PK_L1UP,
     GW_PK_PROLONG,
     GW_PK_POST,
     GW_PK_PUPDATE,

@@ -854,11 +854,15 @@ static void vcycle_t(Hier &H, std::vector<CycLevel<T>> &C, const T *r, T *z, Ctl
         GW_LAUNCH_CHECK();
         if (l == 0) {
             mark_end(H, st);
-            mark_begin(H, GW_PK_COARSE, st);
+            mark_begin(H, L > 2 ? GW_PK_L1DOWN : GW_PK_DEEP, st);
+        } else if (l == 1) {
+            mark_end(H, st);
+            mark_begin(H, GW_PK_DEEP, st);
         }
     }
     {
         CycLevel<T> &lc = C[L - 1];
+        H.prof_bytes += vbytes(H, (double)lc.n * lc.n * 8.0 + 2.0 * lc.n * sx);
         launch_pdl(k_coarse<T>, std::max(1, std::min(H.max_blocks, (lc.n * 32 + BS - 1) / BS)), st, lc.n, H.Ainv.p,
                                                                                                    lc.b.p, lc.x.p, ctl);
     }
@@ -866,9 +870,12 @@ static void vcycle_t(Hier &H, std::vector<CycLevel<T>> &C, const T *r, T *z, Ctl
         CycLevel<T> &lv = C[l];
         const int n = lv.n;
         const double dn = n;
+        if (l == 1) {
+            mark_end(H, st);
+            mark_begin(H, GW_PK_L1UP, st);
+        }
         if (l == 0) {
             mark_end(H, st);
-            H.prof_bytes = 0.0;
             mark_begin(H, GW_PK_PROLONG, st);
         }
         H.prof_bytes += vbytes(H, mat_bytes(lv.P) + (double)lv.P.nc * sx + 2.0 * dn * sx);

@@ -24,7 +24,7 @@ EXPORTS = ("gw_amg_opts_default", "gw_assemble", "gw_matrix_size", "gw_matrix_ex
            "gw_hierarchy_free", "gw_status_str", "gw_last_error", "gw_profile_enable", "gw_profile_read",
            "gw_assemble_noalloc")
 
-PK_NAMES = ("spmv", "update", "pre", "restrict", "coarse", "prolong", "post", "pupdate")
+PK_NAMES = ("spmv", "update", "pre", "restrict", "l1down", "deep", "l1up", "prolong", "post", "pupdate")
 
 
 class gw_grid(ctypes.Structure):
@@ -49,7 +49,7 @@ class gw_level_info(ctypes.Structure):
 
 
 class gw_profile(ctypes.Structure):
-    _fields_ = [("ms", ctypes.c_double * 8), ("launches", ctypes.c_longlong * 8), ("bytes", ctypes.c_double * 8),
+    _fields_ = [("ms", ctypes.c_double * 10), ("launches", ctypes.c_longlong * 10), ("bytes", ctypes.c_double * 10),
                 ("kernel_launches", ctypes.c_longlong), ("solves", ctypes.c_longlong)]
 
 
@@ -254,7 +254,7 @@ class Hierarchy:
         """Per-kind level-0 kernel timing: {name: (ms_total, launches, bytes_per_launch)}, launches, solves."""
         p = gw_profile()
         _check(load().gw_profile_read(self.h, ctypes.byref(p), int(bool(reset))))
-        kinds = {PK_NAMES[k]: (p.ms[k], p.launches[k], p.bytes[k]) for k in range(8)}
+        kinds = {PK_NAMES[k]: (p.ms[k], p.launches[k], p.bytes[k]) for k in range(len(PK_NAMES))}
         return kinds, p.kernel_launches, p.solves
 
     def vcycle(self, r, z, stream=None):

@@ -84,8 +84,8 @@ enum { GW_SMOOTH_JACOBI = 0, GW_SMOOTH_CHEBYSHEV = 1 };
 
 /* Setup and cycle options (gw_amg_opts_default fills the defaults). */
 typedef struct {
-    double theta;        /* strength threshold on level 0, halved per level (0.08) */
-    int smoother;        /* GW_SMOOTH_JACOBI (weight 4/3 over the Gershgorin bound) or GW_SMOOTH_CHEBYSHEV */
+    double theta;        /* strength threshold on level 0, halved per level (0.04) */
+    int smoother;        /* GW_SMOOTH_CHEBYSHEV (default) or GW_SMOOTH_JACOBI (weight 4/3 over the Gershgorin bound) */
     int degree;          /* Chebyshev degree (2) */
     int nu;              /* pre- and post-smoothing applications per level (1) */
     int n_coarse;        /* stop coarsening at this many unknowns or fewer (1024) */

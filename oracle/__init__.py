@@ -223,7 +223,7 @@ def lu_solve(lu, piv, b):
 class Hierarchy:
     """Smoothed-aggregation hierarchy built by the oracle (AMG setup phase)."""
 
-    def __init__(self, A, theta=0.08, smoother=0, degree=2, nu=1, n_coarse=1024, max_levels=12,
+    def __init__(self, A, theta=0.04, smoother=1, degree=2, nu=1, n_coarse=1024, max_levels=12,
                  seed=0x5EED):
         L = _load()
         self.h = L.or_setup(A.h, float(theta), int(smoother), int(degree), int(nu), int(n_coarse),

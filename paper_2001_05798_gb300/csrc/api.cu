@@ -264,8 +264,8 @@ extern "C" {
 void gw_amg_opts_default(gw_amg_opts *o)
 {
     if (!o) return;
-    o->theta = 0.08;
-    o->smoother = GW_SMOOTH_JACOBI;
+    o->theta = 0.04;
+    o->smoother = GW_SMOOTH_CHEBYSHEV;
     o->degree = 2;
     o->nu = 1;
     o->n_coarse = 1024;

@@ -53,7 +53,7 @@ def test_status_strings_without_gpu(lib):
     assert L.gw_status_str(0) == b"GW_OK"
     assert L.gw_status_str(5) == b"GW_ERR_NOT_CONVERGED"
     o = gw.amg_opts()
-    assert abs(o.theta - 0.08) < 1e-15 and o.n_coarse == 1024 and o.seed == 0x5EED
+    assert abs(o.theta - 0.04) < 1e-15 and o.n_coarse == 1024 and o.seed == 0x5EED and o.smoother == 1
 
 
 def test_product_code_never_touches_the_oracle():

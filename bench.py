@@ -204,7 +204,8 @@ def run_ours(args):
     smoother = gw.GW_SMOOTH_CHEBYSHEV if args.smoother == "chebyshev" else gw.GW_SMOOTH_JACOBI
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    Hm = gw.Hierarchy(A, prec=gw.GW_PREC_MIXED32, smoother=smoother, delta=args.delta)
+    Hm = gw.Hierarchy(A, prec=gw.GW_PREC_MIXED32, smoother=smoother, delta=args.delta,
+                      half_storage=args.half_storage)
     torch.cuda.synchronize()
     setup_ms = (time.perf_counter() - t0) * 1e3
     Hd = None if args.no_fp64 else gw.Hierarchy(A, prec=gw.GW_PREC_FP64, smoother=smoother)
@@ -282,7 +283,7 @@ def run_ours(args):
     out = {"metric": METRIC, "value": p50m, "unit": "ms", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": mean_m, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32 V-cycle + f64 CG", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "n": n, "tol": TOL, "prec": "mixed32", "delta": args.delta,
+           "config": {"workload": WORKLOAD, "n": n, "tol": TOL, "prec": "mixed32", "delta": args.delta, "half_storage": args.half_storage,
                       "smoother": args.smoother, "levels": [l["n"] for l in info],
                       "l2": "flushed before every timed solve (256 MiB write)",
                       "parallelism": "replicas" if ws > 1 else "single GPU"},
@@ -316,6 +317,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the all-FP64 arm (profiling runs)")
     ap.add_argument("--delta", type=float, default=0.1, help="reliable-update factor of the mixed form")
+    ap.add_argument("--half-storage", type=int, default=1, help="FP16 storage of P, R and coarse operators (mixed)")
     ap.add_argument("--side", type=int, default=SIDE, help="grid side for profiling captures (default 128)")
     args = ap.parse_args()
     if args.side != SIDE:

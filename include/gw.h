@@ -93,6 +93,8 @@ typedef struct {
     uint64_t seed;       /* seed of the MIS-2 priorities (0x5EED) */
     int prec;            /* gw_prec (GW_PREC_MIXED32) */
     double delta;        /* mixed form: reliable update when the FP32 residual fell by this factor (0.1) */
+    int half_storage;    /* mixed form: keep P, R and the coarse operators as FP16 values with 16-bit
+                            column offsets, coarse operators scaled to D^-1/2 A D^-1/2 (1) */
 } gw_amg_opts;
 
 /* Per-level statistics in the columns of the paper's Table 1 (unknowns,

@@ -181,9 +181,11 @@ void build_hierarchy(Hier &H, cudaStream_t st)
                 bytes += (long long)(c.A.bytes() + c.P.bytes() + c.R.bytes() + c.dw.bytes());
             } else {
                 CycLevel<float> &c = H.cf[(size_t)k];
-                to_store<float>(A, c.A, k == 0 ? FMT_STEN : choose_fmt(A), H.gnx, H.gny, H.gnz, st);
-                to_store<float>(H.P[(size_t)k], c.P, choose_fmt(H.P[(size_t)k]), 0, 0, 0, st);
-                to_store<float>(R[(size_t)k], c.R, choose_fmt(R[(size_t)k]), 0, 0, 0, st);
+                const bool h16 = o.half_storage != 0;
+                auto f32 = [h16](int f) { return h16 && f == FMT_SELL ? FMT_SELL16 : f; };
+                to_store<float>(A, c.A, k == 0 ? FMT_STEN : f32(choose_fmt(A)), H.gnx, H.gny, H.gnz, st);
+                to_store<float>(H.P[(size_t)k], c.P, f32(choose_fmt(H.P[(size_t)k])), 0, 0, 0, st);
+                to_store<float>(R[(size_t)k], c.R, f32(choose_fmt(R[(size_t)k])), 0, 0, 0, st);
                 c.dw.alloc((size_t)n);
                 k_make_dw<<<std::max(g, 1), 256, 0, st>>>(n, diag.p, scale, c.dw.p, nullptr);
                 c.c0 = c0;
@@ -273,6 +275,7 @@ void gw_amg_opts_default(gw_amg_opts *o)
     o->seed = 0x5EEDULL;
     o->prec = GW_PREC_MIXED32;
     o->delta = 0.1;
+    o->half_storage = 1;
 }
 
 const char *gw_status_str(int s)

@@ -39,7 +39,8 @@ class gw_bc(ctypes.Structure):
 class gw_amg_opts(ctypes.Structure):
     _fields_ = [("theta", ctypes.c_double), ("smoother", ctypes.c_int), ("degree", ctypes.c_int),
                 ("nu", ctypes.c_int), ("n_coarse", ctypes.c_int), ("max_levels", ctypes.c_int),
-                ("seed", ctypes.c_uint64), ("prec", ctypes.c_int), ("delta", ctypes.c_double)]
+                ("seed", ctypes.c_uint64), ("prec", ctypes.c_int), ("delta", ctypes.c_double),
+                ("half_storage", ctypes.c_int)]
 
 
 class gw_level_info(ctypes.Structure):

@@ -94,7 +94,7 @@ typedef struct {
     int prec;            /* gw_prec (GW_PREC_MIXED32) */
     double delta;        /* mixed form: reliable update when the FP32 residual fell by this factor (0.1) */
     int half_storage;    /* mixed form: keep P, R and the coarse operators as FP16 values with 16-bit
-                            column offsets, coarse operators scaled to D^-1/2 A D^-1/2 (1) */
+                            column offsets, coarse operators scaled to D^-1/2 A D^-1/2 (0) */
 } gw_amg_opts;
 
 /* Per-level statistics in the columns of the paper's Table 1 (unknowns,

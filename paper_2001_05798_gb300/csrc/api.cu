@@ -275,7 +275,7 @@ void gw_amg_opts_default(gw_amg_opts *o)
     o->seed = 0x5EEDULL;
     o->prec = GW_PREC_MIXED32;
     o->delta = 0.1;
-    o->half_storage = 1;
+    o->half_storage = 0;
 }
 
 const char *gw_status_str(int s)

@@ -39,7 +39,12 @@ template <int R, class T>
 __device__ __forceinline__ VecN<T, R> ld_ro(const T *__restrict__ p)
 {
     VecN<T, R> o;
-    if constexpr (R == 4 && sizeof(T) == 4) {
+    if constexpr (R == 8 && sizeof(T) == 4) {
+        const float4 t0 = __ldg(reinterpret_cast<const float4 *>(p));
+        const float4 t1 = __ldg(reinterpret_cast<const float4 *>(p) + 1);
+        o.v[0] = t0.x, o.v[1] = t0.y, o.v[2] = t0.z, o.v[3] = t0.w;
+        o.v[4] = t1.x, o.v[5] = t1.y, o.v[6] = t1.z, o.v[7] = t1.w;
+    } else if constexpr (R == 4 && sizeof(T) == 4) {
         const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
         o.v[0] = t.x, o.v[1] = t.y, o.v[2] = t.z, o.v[3] = t.w;
     } else if constexpr (R == 2 && sizeof(T) == 8) {
@@ -64,7 +69,12 @@ template <int R, class T>
 __device__ __forceinline__ VecN<T, R> ld_rw(const T *p)
 {
     VecN<T, R> o;
-    if constexpr (R == 4 && sizeof(T) == 4) {
+    if constexpr (R == 8 && sizeof(T) == 4) {
+        const float4 t0 = reinterpret_cast<const float4 *>(p)[0];
+        const float4 t1 = reinterpret_cast<const float4 *>(p)[1];
+        o.v[0] = t0.x, o.v[1] = t0.y, o.v[2] = t0.z, o.v[3] = t0.w;
+        o.v[4] = t1.x, o.v[5] = t1.y, o.v[6] = t1.z, o.v[7] = t1.w;
+    } else if constexpr (R == 4 && sizeof(T) == 4) {
         const float4 t = *reinterpret_cast<const float4 *>(p);
         o.v[0] = t.x, o.v[1] = t.y, o.v[2] = t.z, o.v[3] = t.w;
     } else if constexpr (R == 2 && sizeof(T) == 8) {
@@ -87,7 +97,10 @@ __device__ __forceinline__ VecN<T, R> ld_rw(const T *p)
 template <int R, class T>
 __device__ __forceinline__ void st(T *p, const VecN<T, R> &o)
 {
-    if constexpr (R == 4 && sizeof(T) == 4) {
+    if constexpr (R == 8 && sizeof(T) == 4) {
+        reinterpret_cast<float4 *>(p)[0] = make_float4(o.v[0], o.v[1], o.v[2], o.v[3]);
+        reinterpret_cast<float4 *>(p)[1] = make_float4(o.v[4], o.v[5], o.v[6], o.v[7]);
+    } else if constexpr (R == 4 && sizeof(T) == 4) {
         *reinterpret_cast<float4 *>(p) = make_float4(o.v[0], o.v[1], o.v[2], o.v[3]);
     } else if constexpr (R == 2 && sizeof(T) == 8) {
         *reinterpret_cast<double2 *>(p) = make_double2(o.v[0], o.v[1]);
@@ -326,10 +339,12 @@ struct MSell16 {
     }
 };
 
+// rows per thread of the level-0 stencil: 32 bytes of each array (two
+// 16-byte accesses), so a 128^3 level is one balanced wave of threads
 template <class T>
 constexpr int sten_r()
 {
-    return 16 / (int)sizeof(T);
+    return 32 / (int)sizeof(T);
 }
 
 template <class T, class F>
@@ -344,11 +359,13 @@ static void with_mat(const MatStore<T> &M, F f)
         f(MSell16<T>{M.sell16.sp.p, M.sell16.base.p, M.sell16.v.p, M.sell16.ci.p, M.sell16.sd.p});
         break;
     default: {
-        constexpr int RV = sten_r<T>();
+        constexpr int RV = sten_r<T>(), RH = RV / 2;
         const StenT<T> &S = M.sten;
         const int sxy = S.nx * S.ny;
         if (S.n % RV == 0 && S.nx % RV == 0)
             f(MSten<T, RV>{S.d.p, S.ox.p, S.oy.p, S.oz.p, S.n, S.nx, sxy});
+        else if (S.n % RH == 0 && S.nx % RH == 0)
+            f(MSten<T, RH>{S.d.p, S.ox.p, S.oy.p, S.oz.p, S.n, S.nx, sxy});
         else
             f(MSten<T, 1>{S.d.p, S.ox.p, S.oy.p, S.oz.p, S.n, S.nx, sxy});
     }

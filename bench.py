@@ -265,13 +265,14 @@ def run_ours(args):
     for name, (ms, cnt, byts) in kinds.items():
         if cnt:
             per = ms / cnt
-            kern[name] = {"ms_per_launch": per, "launches": cnt, "bytes_per_launch": byts,
+            kern[name] = {"ms_per_launch": per, "launches": cnt, "bytes_per_launch": byts, "ms_total": ms,
                           "gbs": byts / (per * 1e-3) / 1e9 if per > 0 and byts > 0 else None}
-    fine = [k for k in ("pre", "restrict", "prolong", "post") if k in kern]
-    fb = sum(kern[k]["bytes_per_launch"] for k in fine)
-    ft = sum(kern[k]["ms_per_launch"] for k in fine)
+    # fine-level V-cycle: every level-0 kernel of the cycle, bytes over time
+    fine = [k for k in ("pre1", "pre2", "resid", "restrict", "prolong", "post1", "post2") if k in kern]
+    fb = sum(kern[k]["bytes_per_launch"] * kern[k]["launches"] for k in fine)
+    ft = sum(kern[k]["ms_total"] for k in fine)
     fine_gbs = fb / (ft * 1e-3) / 1e9 if ft > 0 else None
-    timed = [k for k in kern if kern[k]["gbs"]]
+    timed = [k for k in kern if kern[k]["gbs"] and k not in ("l1down", "deep", "l1up")]
     if timed:
         dom = max(timed, key=lambda k: kern[k]["ms_per_launch"] * kern[k]["launches"])
         roof = {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["gbs"], "peak": peak, "unit": "GB/s",

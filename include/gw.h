@@ -229,29 +229,35 @@ int gw_hierarchy_export(gw_hierarchy H, int level, int *agg, unsigned char *root
 /*
  * Benchmark instrumentation (no counterpart in the paper).  With profiling
  * on, the captured CG iteration graph records CUDA events around the
- * level-0 work of every iteration: the outer product q = A p with its dot
- * (GW_PK_SPMV), the x/r update (GW_PK_UPDATE), the pre-smoothing with the
- * residual (GW_PK_PRE), the restriction (GW_PK_RESTRICT), the interpolation
- * and correction (GW_PK_PROLONG), the post-smoothing that yields z
- * (GW_PK_POST) and the direction update (GW_PK_PUPDATE); and the coarser
- * levels: level 1 down to the restriction to level 2 (GW_PK_L1DOWN), levels
- * 2 and below with the coarsest solve (GW_PK_DEEP), and the interpolation to
- * level 1 with its post-smoothing (GW_PK_L1UP).  Only iterations that ran to
- * the end are counted.  bytes[k] is the algorithmic traffic of one launch of
+ * level-0 kernels of every iteration, one by one: the CG product q = A p
+ * with its dot (GW_PK_SPMV), the x/r update (GW_PK_UPDATE), the first and the
+ * following pre-smoothing kernels (GW_PK_PRE1, GW_PK_PRE2), the residual
+ * (GW_PK_RESID), the restriction (GW_PK_RESTRICT), the interpolation and
+ * correction (GW_PK_PROLONG), the first and the following post-smoothing
+ * kernels (GW_PK_POST1, GW_PK_POST2; the last one yields z) and the direction
+ * update (GW_PK_PUPDATE); and the coarser levels as groups: level 1 down to
+ * the restriction to level 2 (GW_PK_L1DOWN), levels 2 and below with the
+ * coarsest solve (GW_PK_DEEP), and the interpolation to level 1 with its
+ * post-smoothing (GW_PK_L1UP).  Only iterations that ran to the end are
+ * counted.  bytes[k] is the algorithmic traffic of one launch (or group) of
  * kind k: every array counted once, a gathered vector once, padding not
  * counted.  kernel_launches counts every kernel the solves launched (graph
- * kernel nodes included), profiling on or off.
+ * kernel nodes included), profiling on or off.  Events between kernels
+ * break the programmatic launch overlap, so profiled solves run slower.
  */
 enum {
     GW_PK_SPMV = 0,
     GW_PK_UPDATE,
-    GW_PK_PRE,
+    GW_PK_PRE1,
+    GW_PK_PRE2,
+    GW_PK_RESID,
     GW_PK_RESTRICT,
     GW_PK_L1DOWN,
     GW_PK_DEEP,
     GW_PK_L1UP,
     GW_PK_PROLONG,
-    GW_PK_POST,
+    GW_PK_POST1,
+    GW_PK_POST2,
     GW_PK_PUPDATE,
     GW_PK_COUNT
 };

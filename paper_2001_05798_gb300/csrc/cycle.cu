@@ -339,12 +339,13 @@ struct MSell16 {
     }
 };
 
-// rows per thread of the level-0 stencil: 32 bytes of each array (two
-// 16-byte accesses), so a 128^3 level is one balanced wave of threads
+// rows per thread of the level-0 stencil: 4 (16 bytes of FP32, 32 bytes of
+// FP64 per array); 8 FP32 rows per thread measured slower (more registers,
+// fewer resident blocks)
 template <class T>
 constexpr int sten_r()
 {
-    return 32 / (int)sizeof(T);
+    return 4;
 }
 
 template <class T, class F>
@@ -809,9 +810,21 @@ static double mat_bytes(const MatStore<T> &M)
     return (double)M.nnz * (sizeof(T) + 4.0);
 }
 
+// Runs one launch, bracketed by profiling events of the given kind (kind < 0:
+// not profiled).  The launch's algorithmic bytes are added inside.
+template <class F>
+static void timed(Hier &H, int kind, cudaStream_t st, F f)
+{
+    if (kind >= 0) mark_begin(H, kind, st);
+    f();
+    if (kind >= 0) mark_end(H, st);
+}
+
+// One smoothing application on level l.  k1/k2: profiling kinds of the first
+// kernel and of the following ones (-1: not profiled).
 template <class T>
 static void smooth(Hier &H, std::vector<CycLevel<T>> &C, int l, const T *b, bool x0zero, bool last, T *zout,
-                   Ctl *ctl, const T *q, int mode, cudaStream_t st)
+                   Ctl *ctl, const T *q, int mode, int k1, int k2, cudaStream_t st)
 {
     CycLevel<T> &lv = C[l];
     const int nu = std::max(1, H.o.nu);
@@ -819,6 +832,8 @@ static void smooth(Hier &H, std::vector<CycLevel<T>> &C, int l, const T *b, bool
     const int n = lv.n;
     const double dn = n, sx = sizeof(T);
     const double amat = mat_bytes(lv.A);
+    int launched = 0;
+    auto kind = [&]() { return launched++ == 0 ? k1 : k2; };
     with_mat(lv.A, [&](auto A) {
         using M = decltype(A);
         const int g = grid_for<M>(H, n);
@@ -828,13 +843,14 @@ static void smooth(Hier &H, std::vector<CycLevel<T>> &C, int l, const T *b, bool
                 const bool first = x0zero && s == 0;
                 const bool fin = last && s == nu - 1;
                 const T *xi = first ? nullptr : cur;
-                H.prof_bytes += vbytes(H, (first ? 0.0 : amat + dn * sx) + 3.0 * dn * sx + (fin && q ? dn * sx : 0.0));
-                if (fin) {
-                    launch_pdl(k_jacobi<M, T, T, true>, g, st, A, n, lv.dw.p, b, xi, zout, q, part, ctl, mode);
-                } else {
-                    launch_pdl(k_jacobi<M, T, T, false>, g, st, A, n, lv.dw.p, b, xi, nxt, q, part, ctl, mode);
-                    std::swap(cur, nxt);
-                }
+                timed(H, kind(), st, [&] {
+                    H.prof_bytes += vbytes(H, (first ? 0.0 : amat + dn * sx) + 3.0 * dn * sx + (fin && q ? dn * sx : 0.0));
+                    if (fin)
+                        launch_pdl(k_jacobi<M, T, T, true>, g, st, A, n, lv.dw.p, b, xi, zout, q, part, ctl, mode);
+                    else
+                        launch_pdl(k_jacobi<M, T, T, false>, g, st, A, n, lv.dw.p, b, xi, nxt, q, part, ctl, mode);
+                });
+                if (!fin) std::swap(cur, nxt);
             }
             if (cur != lv.x.p)
                 GW_CUDA(cudaMemcpyAsync(lv.x.p, cur, (size_t)n * sizeof(T), cudaMemcpyDeviceToDevice, st));
@@ -848,32 +864,38 @@ static void smooth(Hier &H, std::vector<CycLevel<T>> &C, int l, const T *b, bool
             T *d = lv.d.p, *dnx = lv.d2.p;
             const double b0 = 2.0 * dn * sx + (zero ? 0.0 : amat + dn * sx);
             if (fin && m == 1) {
-                H.prof_bytes += vbytes(H, b0 + 3.0 * dn * sx + (q ? dn * sx : 0.0));
-                launch_pdl(k_cheb0<M, T, T, true>, g, st, A, n, lv.dw.p, b, lv.x.p, lv.r.p, d, zout, (T)lv.c0, zero, q,
-                                                         part, ctl, mode);
+                timed(H, kind(), st, [&] {
+                    H.prof_bytes += vbytes(H, b0 + 3.0 * dn * sx + (q ? dn * sx : 0.0));
+                    launch_pdl(k_cheb0<M, T, T, true>, g, st, A, n, lv.dw.p, b, lv.x.p, lv.r.p, d, zout, (T)lv.c0,
+                               zero, q, part, ctl, mode);
+                });
                 continue;
             }
-            H.prof_bytes += vbytes(H, b0 + (zero ? 3.0 : 2.0) * dn * sx);
-            launch_pdl(k_cheb0<M, T, T, false>, g, st, A, n, lv.dw.p, b, lv.x.p, lv.r.p, d, (T *)nullptr, (T)lv.c0,
-                                                      zero, q, part, ctl, mode);
+            timed(H, kind(), st, [&] {
+                H.prof_bytes += vbytes(H, b0 + (zero ? 3.0 : 2.0) * dn * sx);
+                launch_pdl(k_cheb0<M, T, T, false>, g, st, A, n, lv.dw.p, b, lv.x.p, lv.r.p, d, (T *)nullptr,
+                           (T)lv.c0, zero, q, part, ctl, mode);
+            });
             if (m == 1) {
-                if (!zero) {
-                    H.prof_bytes += vbytes(H, 3.0 * dn * sx);
-                    launch_pdl(k_axpy<T>, vgrid(H, n), st, n, d, lv.x.p, ctl);
-                }
+                if (!zero)
+                    timed(H, kind(), st, [&] {
+                        H.prof_bytes += vbytes(H, 3.0 * dn * sx);
+                        launch_pdl(k_axpy<T>, vgrid(H, n), st, n, d, lv.x.p, ctl);
+                    });
                 continue;
             }
             for (int k = 1; k < m; ++k) {
                 const bool f2 = fin && k == m - 1;
                 const int add_prev = (k == 1 && !zero) ? 1 : 0;
-                H.prof_bytes += vbytes(H, amat + dn * sx * 6.0 + (f2 ? dn * sx * (q ? 2.0 : 1.0) : 0.0));
-                if (f2)
-                    launch_pdl(k_chebk<M, T, true>, g, st, A, n, lv.dw.p, lv.r.p, d, dnx, lv.x.p, zout, (T)lv.c1[k],
-                                                          (T)lv.c2[k], add_prev, b, q, part, ctl, mode);
-                else
-                    launch_pdl(k_chebk<M, T, false>, g, st, A, n, lv.dw.p, lv.r.p, d, dnx, lv.x.p, (T *)nullptr,
-                                                           (T)lv.c1[k], (T)lv.c2[k], add_prev, (const T *)nullptr, q,
-                                                           part, ctl, mode);
+                timed(H, kind(), st, [&] {
+                    H.prof_bytes += vbytes(H, amat + dn * sx * 6.0 + (f2 ? dn * sx * (q ? 2.0 : 1.0) : 0.0));
+                    if (f2)
+                        launch_pdl(k_chebk<M, T, true>, g, st, A, n, lv.dw.p, lv.r.p, d, dnx, lv.x.p, zout,
+                                   (T)lv.c1[k], (T)lv.c2[k], add_prev, b, q, part, ctl, mode);
+                    else
+                        launch_pdl(k_chebk<M, T, false>, g, st, A, n, lv.dw.p, lv.r.p, d, dnx, lv.x.p, (T *)nullptr,
+                                   (T)lv.c1[k], (T)lv.c2[k], add_prev, (const T *)nullptr, q, part, ctl, mode);
+                });
                 std::swap(d, dnx);
             }
         }
@@ -882,6 +904,8 @@ static void smooth(Hier &H, std::vector<CycLevel<T>> &C, int l, const T *b, bool
 
 // One V-cycle z = M^-1 r on the hierarchy stored in T; r and z are level-0
 // vectors in T.  With ctl, the last kernel reduces (r, z) (and (q, z)).
+// Level-0 kernels are profiled one by one; the coarser levels as three
+// groups (level 1 down, levels >= 2, level 1 up).
 template <class T>
 static void vcycle_t(Hier &H, std::vector<CycLevel<T>> &C, const T *r, T *z, Ctl *ctl, const T *q, int mode,
                      cudaStream_t st)
@@ -894,33 +918,35 @@ static void vcycle_t(Hier &H, std::vector<CycLevel<T>> &C, const T *r, T *z, Ctl
         const int n = lv.n;
         const double dn = n, amat = mat_bytes(lv.A);
         const T *bl = l == 0 ? r : lv.b.p;
-        if (l == 0) mark_begin(H, GW_PK_PRE, st);
+        const bool l0 = l == 0;
         if (H.o.smoother == GW_SMOOTH_JACOBI && H.o.nu <= 1) {
-            H.prof_bytes += vbytes(H, amat + 4.0 * dn * sx);
-            with_mat(lv.A, [&](auto A) {
-                using M = decltype(A);
-                launch_pdl(k_jac0_res<M, T>, grid_for<M>(H, n), st, A, n, lv.dw.p, bl, lv.x.p, lv.r.p, ctl);
+            timed(H, l0 ? GW_PK_PRE1 : -1, st, [&] {
+                H.prof_bytes += vbytes(H, amat + 4.0 * dn * sx);
+                with_mat(lv.A, [&](auto A) {
+                    using M = decltype(A);
+                    launch_pdl(k_jac0_res<M, T>, grid_for<M>(H, n), st, A, n, lv.dw.p, bl, lv.x.p, lv.r.p, ctl);
+                });
             });
         } else {
-            smooth<T>(H, C, l, bl, true, false, nullptr, ctl, q, mode, st);
-            H.prof_bytes += vbytes(H, amat + 3.0 * dn * sx);
-            with_mat(lv.A, [&](auto A) {
-                using M = decltype(A);
-                launch_pdl(k_residual<M, T>, grid_for<M>(H, n), st, A, n, bl, lv.x.p, lv.r.p, ctl);
+            smooth<T>(H, C, l, bl, true, false, nullptr, ctl, q, mode, l0 ? GW_PK_PRE1 : -1, l0 ? GW_PK_PRE2 : -1,
+                      st);
+            timed(H, l0 ? GW_PK_RESID : -1, st, [&] {
+                H.prof_bytes += vbytes(H, amat + 3.0 * dn * sx);
+                with_mat(lv.A, [&](auto A) {
+                    using M = decltype(A);
+                    launch_pdl(k_residual<M, T>, grid_for<M>(H, n), st, A, n, bl, lv.x.p, lv.r.p, ctl);
+                });
             });
         }
-        if (l == 0) {
-            mark_end(H, st);
-            mark_begin(H, GW_PK_RESTRICT, st);
-        }
-        H.prof_bytes += vbytes(H, mat_bytes(lv.R) + dn * sx + (double)lv.R.nr * sx);
-        with_mat(lv.R, [&](auto Rm) {
-            using M = decltype(Rm);
-            launch_pdl(k_spmv<M>, grid_for<M>(H, lv.R.nr), st, Rm, lv.R.nr, lv.r.p, C[l + 1].b.p, ctl);
+        timed(H, l0 ? GW_PK_RESTRICT : -1, st, [&] {
+            H.prof_bytes += vbytes(H, mat_bytes(lv.R) + dn * sx + (double)lv.R.nr * sx);
+            with_mat(lv.R, [&](auto Rm) {
+                using M = decltype(Rm);
+                launch_pdl(k_spmv<M>, grid_for<M>(H, lv.R.nr), st, Rm, lv.R.nr, lv.r.p, C[l + 1].b.p, ctl);
+            });
         });
         GW_LAUNCH_CHECK();
         if (l == 0) {
-            mark_end(H, st);
             mark_begin(H, L > 2 ? GW_PK_L1DOWN : GW_PK_DEEP, st);
         } else if (l == 1) {
             mark_end(H, st);
@@ -931,31 +957,27 @@ static void vcycle_t(Hier &H, std::vector<CycLevel<T>> &C, const T *r, T *z, Ctl
         CycLevel<T> &lc = C[L - 1];
         H.prof_bytes += vbytes(H, (double)lc.n * lc.n * 8.0 + 2.0 * lc.n * sx);
         launch_pdl(k_coarse<T>, std::max(1, std::min(H.max_blocks, (lc.n * 32 + BS - 1) / BS)), st, lc.n, H.Ainv.p,
-                                                                                                   lc.b.p, lc.x.p, ctl);
+                   lc.b.p, lc.x.p, ctl);
     }
     for (int l = L - 2; l >= 0; --l) {
         CycLevel<T> &lv = C[l];
         const int n = lv.n;
         const double dn = n;
+        const bool l0 = l == 0;
         if (l == 1) {
             mark_end(H, st);
             mark_begin(H, GW_PK_L1UP, st);
         }
-        if (l == 0) {
-            mark_end(H, st);
-            mark_begin(H, GW_PK_PROLONG, st);
-        }
-        H.prof_bytes += vbytes(H, mat_bytes(lv.P) + (double)lv.P.nc * sx + 2.0 * dn * sx);
-        with_mat(lv.P, [&](auto P) {
-            using M = decltype(P);
-            launch_pdl(k_prolong<M>, grid_for<M>(H, n), st, P, n, C[l + 1].x.p, lv.x.p, ctl);
-        });
-        if (l == 0) {
-            mark_end(H, st);
-            mark_begin(H, GW_PK_POST, st);
-        }
-        smooth<T>(H, C, l, l == 0 ? r : lv.b.p, false, l == 0, z, ctl, q, mode, st);
         if (l == 0) mark_end(H, st);
+        timed(H, l0 ? GW_PK_PROLONG : -1, st, [&] {
+            H.prof_bytes += vbytes(H, mat_bytes(lv.P) + (double)lv.P.nc * sx + 2.0 * dn * sx);
+            with_mat(lv.P, [&](auto P) {
+                using M = decltype(P);
+                launch_pdl(k_prolong<M>, grid_for<M>(H, n), st, P, n, C[l + 1].x.p, lv.x.p, ctl);
+            });
+        });
+        smooth<T>(H, C, l, l == 0 ? r : lv.b.p, false, l == 0, z, ctl, q, mode, l0 ? GW_PK_POST1 : -1,
+                  l0 ? GW_PK_POST2 : -1, st);
         GW_LAUNCH_CHECK();
     }
 }

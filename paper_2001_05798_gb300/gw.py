@@ -24,7 +24,8 @@ EXPORTS = ("gw_amg_opts_default", "gw_assemble", "gw_matrix_size", "gw_matrix_ex
            "gw_hierarchy_free", "gw_status_str", "gw_last_error", "gw_profile_enable", "gw_profile_read",
            "gw_assemble_noalloc")
 
-PK_NAMES = ("spmv", "update", "pre", "restrict", "l1down", "deep", "l1up", "prolong", "post", "pupdate")
+PK_NAMES = ("spmv", "update", "pre1", "pre2", "resid", "restrict", "l1down", "deep", "l1up", "prolong", "post1",
+            "post2", "pupdate")
 
 
 class gw_grid(ctypes.Structure):
@@ -50,7 +51,7 @@ class gw_level_info(ctypes.Structure):
 
 
 class gw_profile(ctypes.Structure):
-    _fields_ = [("ms", ctypes.c_double * 10), ("launches", ctypes.c_longlong * 10), ("bytes", ctypes.c_double * 10),
+    _fields_ = [("ms", ctypes.c_double * 13), ("launches", ctypes.c_longlong * 13), ("bytes", ctypes.c_double * 13),
                 ("kernel_launches", ctypes.c_longlong), ("solves", ctypes.c_longlong)]
 
 

@@ -214,17 +214,20 @@ void build_hierarchy(Hier &H, cudaStream_t st)
     H.x.alloc((size_t)n);
     H.r.alloc((size_t)n);
     H.p.alloc((size_t)n);
+    H.p2.alloc((size_t)n);
     H.q.alloc((size_t)n);
     H.z.alloc((size_t)n);
     H.b.alloc((size_t)n);
     if (!f64) {
         H.r.release();
         H.p.release();
+        H.p2.release();
         H.q.release();
         H.z.release();
         H.xs32.alloc((size_t)n);
         H.r32.alloc((size_t)n);
         H.p32.alloc((size_t)n);
+        H.p32b.alloc((size_t)n);
         H.q32.alloc((size_t)n);
         H.z32.alloc((size_t)n);
     }
@@ -233,7 +236,7 @@ void build_hierarchy(Hier &H, cudaStream_t st)
     GW_CUDA(cudaMemsetAsync(H.ctl.p, 0, sizeof(Ctl), st));
     GW_CUDA(cudaMallocHost((void **)&H.ctl_host, sizeof(Ctl)));
     memset(H.ctl_host, 0, sizeof(Ctl));
-    H.info[0].bytes += f64 ? 6LL * n * 8 : 2LL * n * 8 + 5LL * n * 4;
+    H.info[0].bytes += f64 ? 7LL * n * 8 : 2LL * n * 8 + 6LL * n * 4;
     GW_CUDA(cudaStreamSynchronize(st));
 }
 

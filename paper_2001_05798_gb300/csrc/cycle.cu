@@ -153,6 +153,43 @@ struct GProd {
     }
 };
 
+// c * dw[j] * b[j]: the first Chebyshev correction from a zero guess
+template <class T, class S>
+struct GProdC {
+    const T *__restrict__ dw;
+    const S *__restrict__ b;
+    T c;
+    __device__ __forceinline__ T operator()(int j) const { return c * (__ldg(dw + j) * (T)__ldg(b + j)); }
+    template <int R>
+    __device__ __forceinline__ VecN<T, R> vec(int j0) const
+    {
+        const VecN<T, R> w = ld_ro<R>(dw + j0);
+        const VecN<T, R> bb = cvt<T>(ld_ro<R>(b + j0));
+        VecN<T, R> o;
+#pragma unroll
+        for (int k = 0; k < R; ++k) o.v[k] = c * (w.v[k] * bb.v[k]);
+        return o;
+    }
+};
+
+// z[j] + beta * p[j]: the new CG direction, formed where it is gathered
+template <class T>
+struct GDir {
+    const T *__restrict__ z;
+    const T *__restrict__ p;
+    T beta;
+    __device__ __forceinline__ T operator()(int j) const { return __ldg(z + j) + beta * __ldg(p + j); }
+    template <int R>
+    __device__ __forceinline__ VecN<T, R> vec(int j0) const
+    {
+        const VecN<T, R> zz = ld_ro<R>(z + j0), pp = ld_ro<R>(p + j0);
+        VecN<T, R> o;
+#pragma unroll
+        for (int k = 0; k < R; ++k) o.v[k] = zz.v[k] + beta * pp.v[k];
+        return o;
+    }
+};
+
 template <class T>
 struct SV {
     const int *__restrict__ sp;
@@ -765,6 +802,62 @@ __global__ void __launch_bounds__(BS) k_chebk(M A, int n, const typename M::valu
     if constexpr (DOT) cg_rz_epilogue(lrz, lqz, part, ctl, mode);
 }
 
+// The first two Chebyshev steps from a zero guess in one pass: with
+// d0 = c0 dw b (formed where gathered), r1 = b - A d0, d1 = c1 d0 + c2 dw r1,
+// x = d0 + d1.  r1 and d1 are stored only when more steps follow (keep).
+// DOT: x is the CG's z and (b, z), (q, z) are reduced.
+template <class M, class OT, bool DOT>
+__global__ void __launch_bounds__(BS) k_cheb_zero2(M A, int n, const typename M::value_type *__restrict__ dw,
+                                                   const typename M::value_type *__restrict__ b,
+                                                   typename M::value_type *__restrict__ x,
+                                                   typename M::value_type *__restrict__ r,
+                                                   typename M::value_type *__restrict__ d, OT *__restrict__ xo,
+                                                   typename M::value_type c0, typename M::value_type c1,
+                                                   typename M::value_type c2, int keep,
+                                                   const typename M::value_type *__restrict__ q, double *part,
+                                                   Ctl *ctl, int mode)
+{
+    using T = typename M::value_type;
+    constexpr int R = M::R;
+    pdl_enter();
+    if (finished(ctl)) return;
+    double lrz = 0.0, lqz = 0.0;
+    GROUP_ROWS(M, n)
+    {
+        const VecN<T, R> ad = A.dot(i, lane, GProdC<T, T>{dw, b, c0});
+        if (i < n && lane == 0) {
+            const VecN<T, R> bi = ld_ro<R>(b + i);
+            const VecN<T, R> w = ld_ro<R>(dw + i);
+            VecN<T, R> rv, dv, xv;
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                const T d0 = c0 * (w.v[k] * bi.v[k]);
+                rv.v[k] = bi.v[k] - ad.v[k];
+                dv.v[k] = c1 * d0 + c2 * (w.v[k] * rv.v[k]);
+                xv.v[k] = d0 + dv.v[k];
+            }
+            if (keep) {
+                st<R>(r + i, rv);
+                st<R>(d + i, dv);
+            }
+            if constexpr (DOT) {
+                OT out[R];
+                VecN<OT, R> o;
+#pragma unroll
+                for (int k = 0; k < R; ++k) {
+                    o.v[k] = (OT)xv.v[k];
+                    out[k] = (OT)xv.v[k];
+                }
+                st<R>(xo + i, o);
+                dot_rows<R>(i, b, out, q, lrz, lqz);
+            } else {
+                st<R>(x + i, xv);
+            }
+        }
+    }
+    if constexpr (DOT) cg_rz_epilogue(lrz, lqz, part, ctl, mode);
+}
+
 template <class T>
 __global__ void __launch_bounds__(BS) k_axpy(int n, const T *__restrict__ d, T *__restrict__ x, const Ctl *ctl)
 {
@@ -869,6 +962,36 @@ static void smooth(Hier &H, std::vector<CycLevel<T>> &C, int l, const T *b, bool
                     launch_pdl(k_cheb0<M, T, T, true>, g, st, A, n, lv.dw.p, b, lv.x.p, lv.r.p, d, zout, (T)lv.c0,
                                zero, q, part, ctl, mode);
                 });
+                continue;
+            }
+            if (zero && m >= 2) {
+                // first two steps from zero fused: x = d0 + d1
+                const bool f2 = fin && m == 2;
+                const int keep = m > 2;
+                timed(H, kind(), st, [&] {
+                    H.prof_bytes += vbytes(H, amat + 2.0 * dn * sx + (keep ? 3.0 : 1.0) * dn * sx +
+                                                  (f2 ? dn * sx * (q ? 2.0 : 1.0) : 0.0));
+                    if (f2)
+                        launch_pdl(k_cheb_zero2<M, T, true>, g, st, A, n, lv.dw.p, b, lv.x.p, lv.r.p, d, zout,
+                                   (T)lv.c0, (T)lv.c1[1], (T)lv.c2[1], keep, q, part, ctl, mode);
+                    else
+                        launch_pdl(k_cheb_zero2<M, T, false>, g, st, A, n, lv.dw.p, b, lv.x.p, lv.r.p, d,
+                                   (T *)nullptr, (T)lv.c0, (T)lv.c1[1], (T)lv.c2[1], keep, q, part, ctl, mode);
+                });
+                for (int k = 2; k < m; ++k) {
+                    const bool f3 = fin && k == m - 1;
+                    timed(H, kind(), st, [&] {
+                        H.prof_bytes += vbytes(H, amat + dn * sx * 6.0 + (f3 ? dn * sx * (q ? 2.0 : 1.0) : 0.0));
+                        if (f3)
+                            launch_pdl(k_chebk<M, T, true>, g, st, A, n, lv.dw.p, lv.r.p, d, dnx, lv.x.p, zout,
+                                       (T)lv.c1[k], (T)lv.c2[k], 0, b, q, part, ctl, mode);
+                        else
+                            launch_pdl(k_chebk<M, T, false>, g, st, A, n, lv.dw.p, lv.r.p, d, dnx, lv.x.p,
+                                       (T *)nullptr, (T)lv.c1[k], (T)lv.c2[k], 0, (const T *)nullptr, q, part, ctl,
+                                       mode);
+                    });
+                    std::swap(d, dnx);
+                }
                 continue;
             }
             timed(H, kind(), st, [&] {
@@ -1014,10 +1137,12 @@ void vcycle_enqueue(Hier &H, const double *r, double *z, Ctl *ctl, bool dot, cud
 // the stopping test, xs is folded into the FP64 solution and the residual is
 // recomputed as b - A x with the FP64 operator in FP64 arithmetic.
 
-// x = 0, r = b (FP64 form) or x64 = 0, xs = 0, r32 = b (mixed form); ||b||^2
+// x = 0, r = b (FP64 form) or x64 = 0, xs = 0, r32 = b (mixed form), both
+// direction buffers 0, beta = 0; ||b||^2
 template <class V>
 __global__ void __launch_bounds__(BS) k_cg_init(int n, const double *__restrict__ b, double *__restrict__ x,
-                                                V *__restrict__ xs, V *__restrict__ r, double *part, Ctl *c)
+                                                V *__restrict__ xs, V *__restrict__ r, V *__restrict__ pa,
+                                                V *__restrict__ pb, double *part, Ctl *c)
 {
     pdl_enter();
     double loc[1] = {0.0}, tot[1];
@@ -1027,6 +1152,8 @@ __global__ void __launch_bounds__(BS) k_cg_init(int n, const double *__restrict_
         x[i] = 0.0;
         if (xs) xs[i] = (V)0;
         r[i] = (V)bi;
+        pa[i] = (V)0;
+        pb[i] = (V)0;
         loc[0] += bi * bi;
     }
     if (reduce_last<1>(loc, part, &c->cnt[0], tot) && threadIdx.x == 0) {
@@ -1072,6 +1199,54 @@ __global__ void __launch_bounds__(BS) k_cg_spmv_dot(M A, int n, const typename M
         if (i < n && lane == 0) {
             st<R>(q + i, qi);
             const VecN<V, R> pi = ld_ro<R>(p + i);
+            V s = 0;
+#pragma unroll
+            for (int k = 0; k < R; ++k) s += pi.v[k] * qi.v[k];
+            loc[0] += (double)s;
+        }
+    }
+    if (reduce_last<1>(loc, part, &c->cnt[0], tot) && threadIdx.x == 0) {
+        const double pq = tot[0];
+        c->pq = pq;
+        c->it += 1;
+        if (!(pq > 0.0) || !isfinite(pq)) {
+            c->status = GW_ERR_BREAKDOWN;
+            c->done = 1;
+        } else {
+            c->alpha = c->rz / pq;
+        }
+    }
+}
+
+// The direction update fused into the product: p_new = z + beta p_old (formed
+// where gathered, stored for the own rows), q = A p_new, pq = (p_new, q),
+// alpha = rz / pq.  p_old and p_new are distinct buffers.
+template <class M>
+__global__ void __launch_bounds__(BS) k_cg_dir_spmv(M A, int n, const typename M::value_type *__restrict__ z,
+                                                    const typename M::value_type *__restrict__ pold,
+                                                    typename M::value_type *__restrict__ pnew,
+                                                    typename M::value_type *__restrict__ q, double *part, Ctl *c)
+{
+    using V = typename M::value_type;
+    constexpr int R = M::R;
+    pdl_enter();
+    if (finished(c)) return;
+    if (c->it >= c->maxit) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            c->status = GW_ERR_NOT_CONVERGED;
+            c->done = 1;
+        }
+        return;
+    }
+    const V beta = (V)c->beta;
+    double loc[1] = {0.0}, tot[1];
+    GROUP_ROWS(M, n)
+    {
+        const VecN<V, R> qi = A.dot(i, lane, GDir<V>{z, pold, beta});
+        if (i < n && lane == 0) {
+            st<R>(q + i, qi);
+            const VecN<V, R> pi = GDir<V>{z, pold, beta}.template vec<R>(i);
+            st<R>(pnew + i, pi);
             V s = 0;
 #pragma unroll
             for (int k = 0; k < R; ++k) s += pi.v[k] * qi.v[k];
@@ -1276,58 +1451,57 @@ static void rel_update(Hier &H, int force, cudaStream_t st)
     });
 }
 
-static void cg_iteration(Hier &H, cudaStream_t st)
+// One CG iteration.  The direction lives in two buffers that swap roles
+// every iteration (parity = iteration number mod 2), so the captured graph
+// holds an even number of iterations.
+static void cg_iteration(Hier &H, int parity, cudaStream_t st)
 {
     const int n = H.n;
     Ctl *c = H.ctl.p;
     const double dn = n;
     if (H.o.prec == GW_PREC_FP64) {
         const MatStore<double> &A64 = H.cd[0].A;
-        mark_begin(H, GW_PK_SPMV, st);
-        H.prof_bytes += vbytes(H, mat_bytes(A64) + 16.0 * dn);
-        with_mat(A64, [&](auto A) {
-            using M = decltype(A);
-            launch_pdl(k_cg_spmv_dot<M>, grid_for<M>(H, n), st, A, n, H.p.p, H.q.p, H.part.p, c);
+        double *pold = parity ? H.p2.p : H.p.p, *pnew = parity ? H.p.p : H.p2.p;
+        timed(H, GW_PK_SPMV, st, [&] {
+            H.prof_bytes += vbytes(H, mat_bytes(A64) + 40.0 * dn);
+            with_mat(A64, [&](auto A) {
+                using M = decltype(A);
+                launch_pdl(k_cg_dir_spmv<M>, grid_for<M>(H, n), st, A, n, (const double *)H.z.p,
+                           (const double *)pold, pnew, H.q.p, H.part.p, c);
+            });
         });
-        mark_end(H, st);
-        mark_begin(H, GW_PK_UPDATE, st);
-        H.prof_bytes += vbytes(H, 48.0 * dn);
-        cg_vec_update<double>(H, H.x.p, H.r.p, H.p.p, H.q.p, 0, st);
-        mark_end(H, st);
+        timed(H, GW_PK_UPDATE, st, [&] {
+            H.prof_bytes += vbytes(H, 48.0 * dn);
+            cg_vec_update<double>(H, H.x.p, H.r.p, pnew, H.q.p, 0, st);
+        });
         with_mat(A64, [&](auto A) {
             using M = decltype(A);
             launch_pdl(k_cg_true<M>, grid_for<M>(H, n), st, A, n, H.b.p, H.x.p, H.r.p, H.part.p, c, 0);
         });
         vcycle_t<double>(H, H.cd, H.r.p, H.z.p, c, nullptr, 1, st);
-        mark_begin(H, GW_PK_PUPDATE, st);
-        H.prof_bytes += vbytes(H, 24.0 * dn);
-        cg_vec_p<double>(H, H.z.p, H.p.p, st);
-        mark_end(H, st);
         GW_LAUNCH_CHECK();
         return;
     }
     const MatStore<float> &A32 = H.cf[0].A;
-    mark_begin(H, GW_PK_SPMV, st);
-    H.prof_bytes += vbytes(H, mat_bytes(A32) + 8.0 * dn);
-    with_mat(A32, [&](auto A) {
-        using M = decltype(A);
-        launch_pdl(k_cg_spmv_dot<M>, grid_for<M>(H, n), st, A, n, H.p32.p, H.q32.p, H.part.p, c);
+    float *pold = parity ? H.p32b.p : H.p32.p, *pnew = parity ? H.p32.p : H.p32b.p;
+    timed(H, GW_PK_SPMV, st, [&] {
+        H.prof_bytes += vbytes(H, mat_bytes(A32) + 20.0 * dn);
+        with_mat(A32, [&](auto A) {
+            using M = decltype(A);
+            launch_pdl(k_cg_dir_spmv<M>, grid_for<M>(H, n), st, A, n, (const float *)H.z32.p,
+                       (const float *)pold, pnew, H.q32.p, H.part.p, c);
+        });
     });
-    mark_end(H, st);
-    mark_begin(H, GW_PK_UPDATE, st);
-    H.prof_bytes += vbytes(H, 24.0 * dn);
-    cg_vec_update<float>(H, H.xs32.p, H.r32.p, H.p32.p, H.q32.p, 1, st);
-    mark_end(H, st);
+    timed(H, GW_PK_UPDATE, st, [&] {
+        H.prof_bytes += vbytes(H, 24.0 * dn);
+        cg_vec_update<float>(H, H.xs32.p, H.r32.p, pnew, H.q32.p, 1, st);
+    });
     rel_update(H, 0, st);
     vcycle_t<float>(H, H.cf, H.r32.p, H.z32.p, c, H.q32.p, 1, st);
-    mark_begin(H, GW_PK_PUPDATE, st);
-    H.prof_bytes += vbytes(H, 12.0 * dn);
-    cg_vec_p<float>(H, H.z32.p, H.p32.p, st);
-    mark_end(H, st);
     GW_LAUNCH_CHECK();
 }
 
-static constexpr int GRAPH_ITERS = 4;
+static constexpr int GRAPH_ITERS = 4;  // even: the direction buffers alternate
 
 static size_t kernel_nodes(cudaGraph_t g)
 {
@@ -1386,13 +1560,13 @@ static void ensure_graphs(Hier &H)
     const int n = H.n, g = vgrid(H, n);
     H.ginit = capture(H, [&](cudaStream_t s) {
         if (H.o.prec == GW_PREC_FP64) {
-            launch_pdl(k_cg_init<double>, g, s, n, H.b.p, H.x.p, (double *)nullptr, H.r.p, H.part.p, H.ctl.p);
+            launch_pdl(k_cg_init<double>, g, s, n, (const double *)H.b.p, H.x.p, (double *)nullptr, H.r.p, H.p.p,
+                       H.p2.p, H.part.p, H.ctl.p);
             vcycle_t<double>(H, H.cd, H.r.p, H.z.p, H.ctl.p, nullptr, 0, s);
-            launch_pdl(k_copy<double>, g, s, n, H.z.p, H.p.p, H.ctl.p);
         } else {
-            launch_pdl(k_cg_init<float>, g, s, n, H.b.p, H.x.p, H.xs32.p, H.r32.p, H.part.p, H.ctl.p);
+            launch_pdl(k_cg_init<float>, g, s, n, (const double *)H.b.p, H.x.p, H.xs32.p, H.r32.p, H.p32.p,
+                       H.p32b.p, H.part.p, H.ctl.p);
             vcycle_t<float>(H, H.cf, H.r32.p, H.z32.p, H.ctl.p, nullptr, 0, s);
-            launch_pdl(k_copy<float>, g, s, n, H.z32.p, H.p32.p, H.ctl.p);
         }
         GW_LAUNCH_CHECK();
     }, &H.init_kernels);
@@ -1400,7 +1574,7 @@ static void ensure_graphs(Hier &H)
     H.gexec = capture(H, [&](cudaStream_t s) {
         for (int k = 0; k < GRAPH_ITERS; ++k) {
             H.cap_iter = k;
-            cg_iteration(H, s);
+            cg_iteration(H, k & 1, s);
         }
     }, &H.iter_kernels);
     H.prof_capture = false;

@@ -238,8 +238,8 @@ struct Hier {
     DBuf<double> Ainv;         // dense inverse of the coarsest level, row-major
     // outer CG
     int n = 0;
-    DBuf<double> x, r, p, q, z, b, part;      // FP64 form (x, b also hold the mixed form's solution and rhs)
-    DBuf<float> xs32, r32, p32, q32, z32;     // mixed form: FP32 recurrence
+    DBuf<double> x, r, p, p2, q, z, b, part;  // FP64 form (x, b also hold the mixed form's solution and rhs)
+    DBuf<float> xs32, r32, p32, p32b, q32, z32;  // mixed form: FP32 recurrence (two direction buffers)
     DBuf<Ctl> ctl;
     Ctl *ctl_host = nullptr;   // pinned mirror of the control block
     cudaStream_t cap = nullptr;

@@ -1460,25 +1460,31 @@ static void cg_iteration(Hier &H, int parity, cudaStream_t st)
     Ctl *c = H.ctl.p;
     const double dn = n;
     if (H.o.prec == GW_PREC_FP64) {
+        // FP64 form: the direction update stays a separate pass, because
+        // forming z + beta p at every gathered neighbour would add FP64
+        // multiply-adds, the scarce resource of this GPU
+        (void)parity;
         const MatStore<double> &A64 = H.cd[0].A;
-        double *pold = parity ? H.p2.p : H.p.p, *pnew = parity ? H.p.p : H.p2.p;
         timed(H, GW_PK_SPMV, st, [&] {
-            H.prof_bytes += vbytes(H, mat_bytes(A64) + 40.0 * dn);
+            H.prof_bytes += vbytes(H, mat_bytes(A64) + 16.0 * dn);
             with_mat(A64, [&](auto A) {
                 using M = decltype(A);
-                launch_pdl(k_cg_dir_spmv<M>, grid_for<M>(H, n), st, A, n, (const double *)H.z.p,
-                           (const double *)pold, pnew, H.q.p, H.part.p, c);
+                launch_pdl(k_cg_spmv_dot<M>, grid_for<M>(H, n), st, A, n, (const double *)H.p.p, H.q.p, H.part.p, c);
             });
         });
         timed(H, GW_PK_UPDATE, st, [&] {
             H.prof_bytes += vbytes(H, 48.0 * dn);
-            cg_vec_update<double>(H, H.x.p, H.r.p, pnew, H.q.p, 0, st);
+            cg_vec_update<double>(H, H.x.p, H.r.p, H.p.p, H.q.p, 0, st);
         });
         with_mat(A64, [&](auto A) {
             using M = decltype(A);
             launch_pdl(k_cg_true<M>, grid_for<M>(H, n), st, A, n, H.b.p, H.x.p, H.r.p, H.part.p, c, 0);
         });
         vcycle_t<double>(H, H.cd, H.r.p, H.z.p, c, nullptr, 1, st);
+        timed(H, GW_PK_PUPDATE, st, [&] {
+            H.prof_bytes += vbytes(H, 24.0 * dn);
+            cg_vec_p<double>(H, H.z.p, H.p.p, st);
+        });
         GW_LAUNCH_CHECK();
         return;
     }
@@ -1563,6 +1569,7 @@ static void ensure_graphs(Hier &H)
             launch_pdl(k_cg_init<double>, g, s, n, (const double *)H.b.p, H.x.p, (double *)nullptr, H.r.p, H.p.p,
                        H.p2.p, H.part.p, H.ctl.p);
             vcycle_t<double>(H, H.cd, H.r.p, H.z.p, H.ctl.p, nullptr, 0, s);
+            launch_pdl(k_copy<double>, g, s, n, (const double *)H.z.p, H.p.p, H.ctl.p);
         } else {
             launch_pdl(k_cg_init<float>, g, s, n, (const double *)H.b.p, H.x.p, H.xs32.p, H.r32.p, H.p32.p,
                        H.p32b.p, H.part.p, H.ctl.p);

@@ -106,6 +106,7 @@ void build_hierarchy(Hier &H, cudaStream_t st)
     H.max_blocks = std::max(1, std::min(RED_MAX_BLOCKS, nsm * 8));
     H.A.clear();
     H.A.emplace_back();  // placeholder for level 0 (the matrix handle's CSR)
+    std::vector<DCSR> R;
     auto Al = [&](int l) -> const DCSR & { return l == 0 ? *H.A0 : H.A[(size_t)l]; };
     double th = o.theta;
     int l = 0;
@@ -137,6 +138,7 @@ void build_hierarchy(Hier &H, cudaStream_t st)
         H.info[(size_t)l].omega_p = omega;
         H.info[(size_t)l].nnz_p = P.nnz;
         H.P.push_back(std::move(P));
+        R.push_back(std::move(Rl));
         H.A.push_back(std::move(Ac));
         ++l;
         th = th * 0.5;
@@ -148,19 +150,8 @@ void build_hierarchy(Hier &H, cudaStream_t st)
     const bool f64 = o.prec == GW_PREC_FP64;
     if (f64) H.cd.resize((size_t)L);
     else H.cf.resize((size_t)L);
-    // Cycle numbering: levels 1..L-2 renumbered by window_order; level 0
-    // (the caller's grid) and the coarsest level (the dense inverse) keep theirs.
-    std::vector<DBuf<int>> n2o((size_t)L), o2n((size_t)L);
-    for (int k = 1; k < L - 1; ++k) window_order(Al(k), n2o[(size_t)k], o2n[(size_t)k], st);
-    std::vector<DCSR> Ac((size_t)L), Pc((size_t)L), Rc((size_t)L);
-    for (int k = 1; k < L - 1; ++k) permute_csr(Al(k), n2o[(size_t)k].p, o2n[(size_t)k].p, Ac[(size_t)k], st);
-    for (int k = 0; k < L - 1; ++k) {
-        permute_csr(H.P[(size_t)k], n2o[(size_t)k].p, o2n[(size_t)k + 1].p, Pc[(size_t)k], st);
-        setup_transpose(Pc[(size_t)k], Rc[(size_t)k], st);
-    }
-    auto Acyc = [&](int k) -> const DCSR & { return (k == 0 || k == L - 1) ? Al(k) : Ac[(size_t)k]; };
     for (int k = 0; k < L; ++k) {
-        const DCSR &A = Acyc(k);
+        const DCSR &A = Al(k);
         const int n = A.nr;
         long long bytes = 0;
         if (k < L - 1) {
@@ -180,8 +171,8 @@ void build_hierarchy(Hier &H, cudaStream_t st)
             if (f64) {
                 CycLevel<double> &c = H.cd[(size_t)k];
                 to_store<double>(A, c.A, k == 0 ? FMT_STEN : choose_fmt(A), H.gnx, H.gny, H.gnz, st);
-                to_store<double>(Pc[(size_t)k], c.P, choose_fmt(Pc[(size_t)k]), 0, 0, 0, st);
-                to_store<double>(Rc[(size_t)k], c.R, choose_fmt(Rc[(size_t)k]), 0, 0, 0, st);
+                to_store<double>(H.P[(size_t)k], c.P, choose_fmt(H.P[(size_t)k]), 0, 0, 0, st);
+                to_store<double>(R[(size_t)k], c.R, choose_fmt(R[(size_t)k]), 0, 0, 0, st);
                 c.dw.alloc((size_t)n);
                 k_make_dw<<<std::max(g, 1), 256, 0, st>>>(n, diag.p, scale, nullptr, c.dw.p);
                 c.c0 = c0;
@@ -193,8 +184,8 @@ void build_hierarchy(Hier &H, cudaStream_t st)
                 const bool h16 = o.half_storage != 0;
                 auto f32 = [h16](int f) { return h16 && f == FMT_SELL ? FMT_SELL16 : f; };
                 to_store<float>(A, c.A, k == 0 ? FMT_STEN : f32(choose_fmt(A)), H.gnx, H.gny, H.gnz, st);
-                to_store<float>(Pc[(size_t)k], c.P, f32(choose_fmt(Pc[(size_t)k])), 0, 0, 0, st);
-                to_store<float>(Rc[(size_t)k], c.R, f32(choose_fmt(Rc[(size_t)k])), 0, 0, 0, st);
+                to_store<float>(H.P[(size_t)k], c.P, f32(choose_fmt(H.P[(size_t)k])), 0, 0, 0, st);
+                to_store<float>(R[(size_t)k], c.R, f32(choose_fmt(R[(size_t)k])), 0, 0, 0, st);
                 c.dw.alloc((size_t)n);
                 k_make_dw<<<std::max(g, 1), 256, 0, st>>>(n, diag.p, scale, c.dw.p, nullptr);
                 c.c0 = c0;

@@ -208,8 +208,6 @@ double setup_power_lambda(const DCSR &A, const double *diag, uint64_t seed, int 
 
 template <class T>
 void to_sell(const DCSR &A, Sell<T> &S, cudaStream_t st);
-void window_order(const DCSR &A, DBuf<int> &new2old, DBuf<int> &old2new, cudaStream_t st);
-void permute_csr(const DCSR &A, const int *new2old, const int *colmap, DCSR &B, cudaStream_t st);
 
 // ---------------------------------------------------------------- cycle --
 // Storage of one level of the V-cycle in the cycle's precision T.

@@ -986,83 +986,6 @@ void to_sell(const DCSR &A, Sell<T> &S, cudaStream_t st)
 template void to_sell<float>(const DCSR &, Sell<float> &, cudaStream_t);
 template void to_sell<double>(const DCSR &, Sell<double> &, cudaStream_t);
 
-// ---------------------------------------------- cycle numbering of levels --
-// Within windows of W consecutive rows, rows are ordered by descending length
-// (ties by index), so every 32-row slice of sliced ELL holds rows of nearly
-// equal length and pads little, while rows stay near their neighbours.
-__global__ void k_window_rank(int n, int W, const int *__restrict__ rp, int *__restrict__ new2old,
-                              int *__restrict__ old2new)
-{
-    extern __shared__ int len_s[];
-    const long long w0 = (long long)blockIdx.x * W;
-    if (w0 >= n) return;
-    const int m = (int)((long long)W < n - w0 ? (long long)W : n - w0);
-    for (int t = threadIdx.x; t < m; t += blockDim.x) len_s[t] = rp[w0 + t + 1] - rp[w0 + t];
-    __syncthreads();
-    for (int t = threadIdx.x; t < m; t += blockDim.x) {
-        const int li = len_s[t];
-        int rank = 0;
-        for (int u = 0; u < m; ++u) {
-            const int lu = len_s[u];
-            rank += (lu > li) || (lu == li && u < t);
-        }
-        new2old[w0 + rank] = (int)(w0 + t);
-        old2new[w0 + t] = (int)(w0 + rank);
-    }
-}
-
-void window_order(const DCSR &A, DBuf<int> &new2old, DBuf<int> &old2new, cudaStream_t st)
-{
-    const int W = 2048;
-    new2old.alloc((size_t)A.nr);
-    old2new.alloc((size_t)A.nr);
-    const int nb = (A.nr + W - 1) / W;
-    k_window_rank<<<std::max(nb, 1), 1024, W * sizeof(int), st>>>(A.nr, W, A.rp.p, new2old.p, old2new.p);
-    GW_LAUNCH_CHECK();
-}
-
-__global__ void k_perm_len(int nr, const int *__restrict__ rp, const int *__restrict__ new2old, int *__restrict__ len)
-{
-    GRID_STRIDE(i, nr)
-    {
-        const int o = new2old ? new2old[i] : (int)i;
-        len[i] = rp[o + 1] - rp[o];
-    }
-}
-
-__global__ void k_perm_fill(int nr, const int *__restrict__ rp, const int *__restrict__ ci,
-                            const double *__restrict__ v, const int *__restrict__ new2old,
-                            const int *__restrict__ colmap, const int *__restrict__ nrp, int *__restrict__ nci,
-                            double *__restrict__ nv)
-{
-    GRID_STRIDE(i, nr)
-    {
-        const int o = new2old ? new2old[i] : (int)i;
-        int e2 = nrp[i];
-        for (int e = rp[o]; e < rp[o + 1]; ++e, ++e2) {
-            nci[e2] = colmap ? colmap[ci[e]] : ci[e];
-            nv[e2] = v[e];
-        }
-    }
-}
-
-// B = rows of A taken in the order new2old (identity if null), columns renamed
-// by colmap (unchanged if null); entries keep their order within a row
-void permute_csr(const DCSR &A, const int *new2old, const int *colmap, DCSR &B, cudaStream_t st)
-{
-    B.nr = A.nr;
-    B.nc = A.nc;
-    B.nnz = A.nnz;
-    B.rp.alloc((size_t)A.nr + 1);
-    B.ci.alloc((size_t)std::max(A.nnz, 1));
-    B.v.alloc((size_t)std::max(A.nnz, 1));
-    k_perm_len<<<nblk(A.nr, 256), 256, 0, st>>>(A.nr, A.rp.p, new2old, B.rp.p);
-    GW_LAUNCH_CHECK();
-    exclusive_scan(B.rp.p, B.rp.p, A.nr, st);
-    k_perm_fill<<<nblk(A.nr, 256), 256, 0, st>>>(A.nr, A.rp.p, A.ci.p, A.v.p, new2old, colmap, B.rp.p, B.ci.p, B.v.p);
-    GW_LAUNCH_CHECK();
-}
-
 // ----------------------------------------------- CSR and stencil formats --
 template <class T>
 __global__ void k_convert_vals(long long nnz, const double *__restrict__ v, T *__restrict__ o)

@@ -108,6 +108,23 @@ def make_problem():
     return wl.heterogeneous_3d(side=SIDE, var=VAR, corr=CORR, seed=SEED)
 
 
+def max_over_ranks(values, device=None):
+    """Element-wise maximum of a list of floats over all ranks (identity on one
+    rank).  Replicas exchange only these timing scalars; no data-path collective."""
+    import torch
+
+    if not (torch.distributed.is_available() and torch.distributed.is_initialized()):
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return t.tolist()
+
+
+def replica_throughput(world_size, p50_ms):
+    """Whole-job solves per second of N replicas each solving one problem per step."""
+    return world_size * 1e3 / p50_ms
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -251,12 +268,7 @@ def run_ours(args):
         Hm.solve(b_host, h_host, tol=TOL, stream=stream)
         te.append((time.perf_counter() - t0) * 1e3)
     p50m, p50d = float(np.median(tm)), float(np.median(td))
-    if ws > 1:
-        t = torch.tensor([p50m, p50d, float(np.mean(tm)), float(np.median(te))], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        p50m, p50d, mean_m, p50e = t.tolist()
-    else:
-        mean_m, p50e = float(np.mean(tm)), float(np.median(te))
+    p50m, p50d, mean_m, p50e = max_over_ranks([p50m, p50d, float(np.mean(tm)), float(np.median(te))], device=dev)
     if rank != 0:
         torch.distributed.destroy_process_group()
         return
@@ -289,7 +301,7 @@ def run_ours(args):
                       "l2": "flushed before every timed solve (256 MiB write)",
                       "parallelism": "replicas" if ws > 1 else "single GPU"},
            "p50_ms": p50m, "p99_ms": float(np.percentile(tm, 99)), "iters": it_m, "relres": rel_m,
-           "status": st_m, "solves_per_s": ws * 1e3 / p50m, "profiled_p50_ms": float(np.median(tp)),
+           "status": st_m, "solves_per_s": replica_throughput(ws, p50m), "profiled_p50_ms": float(np.median(tp)),
            "fp64": {"p50_ms": p50d, "p99_ms": float(np.percentile(td, 99)), "iters": it_d, "relres": rel_d,
                     "status": st_d},
            "mixed_speedup_vs_fp64": p50d / p50m,

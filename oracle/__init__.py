@@ -79,6 +79,9 @@ def _load():
         "or_h_smooth": (None, [_vp, ctypes.c_int, _f64p, _f64p, ctypes.c_int]),
         "or_pcg": (ctypes.c_int, [_vp, _f64p, _f64p, ctypes.c_double, ctypes.c_int,
                                   ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
+        "or_adjoint_grad": (None, [ctypes.c_int] * 3 + [ctypes.c_double] * 3 + [_f64p] * 3 +
+                            [_i32p, _f64p, _f64p, _f64p, _f64p]),
+        "or_misfit": (ctypes.c_double, [ctypes.c_int, _f64p, ctypes.c_int, _i32p, _f64p, _vp]),
         "or_cg_plain": (ctypes.c_int, [_vp, _f64p, _f64p, ctypes.c_double, ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
     }
@@ -286,6 +289,28 @@ class Hierarchy:
         if getattr(self, "h", None) and _lib is not None:
             _lib.or_h_free(self.h)
             self.h = None
+
+
+def adjoint_grad(nx, ny, nz, Kx, h, lam, Ky=None, Kz=None, bct=(1, 1, 0, 0, 0, 0), bcv=(1.0, 0.0, 0, 0, 0, 0),
+                 spacing=(1.0, 1.0, 1.0)):
+    """dJ/dlnK per cell from the heads h and the adjoint state lam (C lam = dJ/dh)."""
+    Kx = np.ascontiguousarray(Kx, dtype=np.float64).ravel()
+    Ky = Kx if Ky is None else np.ascontiguousarray(Ky, dtype=np.float64).ravel()
+    Kz = Kx if Kz is None else np.ascontiguousarray(Kz, dtype=np.float64).ravel()
+    g = np.empty(nx * ny * nz)
+    _load().or_adjoint_grad(nx, ny, nz, float(spacing[0]), float(spacing[1]), float(spacing[2]), Kx, Ky, Kz,
+                            np.asarray(bct, np.int32), np.asarray(bcv, np.float64),
+                            np.ascontiguousarray(h, np.float64), np.ascontiguousarray(lam, np.float64), g)
+    return g
+
+
+def misfit(h, obs, hobs):
+    """J = sum (h[obs] - hobs)^2 and dJ/dh."""
+    h = np.ascontiguousarray(h, np.float64)
+    d = np.empty_like(h)
+    J = _load().or_misfit(h.size, h, len(obs), np.ascontiguousarray(obs, np.int32),
+                          np.ascontiguousarray(hobs, np.float64), d.ctypes.data_as(ctypes.c_void_p))
+    return J, d
 
 
 def complexities(ns, nnzs):

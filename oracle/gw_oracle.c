@@ -898,3 +898,64 @@ int or_cg_plain(const ocsr *A, const double *b, double *x, double tol, int maxit
     free(r); free(p); free(q);
     return st;
 }
+
+/* ------------------------------------------------------------- adjoint -- */
+/*
+ * Gradient of an objective J(h) with respect to ln K (K scaling Kx, Ky, Kz of
+ * a cell together), given the heads h of C h = Q and the adjoint state
+ * lambda of C lambda = dJ/dh (C is symmetric, so the same operator serves).
+ * Differentiating C(K) h = Q(K):
+ *   dJ/dlnK_i = lambda^T (dQ/dlnK_i - dC/dlnK_i h).
+ * An interior face between i and j with T = 2 K_i K_j/(K_i + K_j) g has
+ * dT/dlnK_i = T K_j/(K_i + K_j) and enters rows i and j as T (h_i - h_j) and
+ * T (h_j - h_i), giving -dT/dlnK_i (h_i - h_j)(lambda_i - lambda_j); a
+ * Dirichlet face with T_b = 2 K_i g enters row i as T_b (h_i - h_b), giving
+ * -T_b (h_i - h_b) lambda_i.  Faces are visited in the order -x,+x,-y,+y,-z,+z.
+ */
+void or_adjoint_grad(int nx, int ny, int nz, double dx, double dy, double dz, const double *Kx, const double *Ky,
+                     const double *Kz, const int *bct, const double *bcv, const double *h, const double *lam,
+                     double *grad)
+{
+    const double g[3] = {(dy * dz) / dx, (dx * dz) / dy, (dx * dy) / dz};
+    const double *K[3] = {Kx, Ky, Kz};
+    const int dim[3] = {nx, ny, nz};
+    const int stride[3] = {1, nx, nx * ny};
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                int i = x + nx * (y + ny * z);
+                int crd[3] = {x, y, z};
+                double s = 0.0;
+                for (int d = 0; d < 3; ++d)
+                    for (int side = 0; side < 2; ++side) {
+                        int f = 2 * d + side;
+                        int interior = side == 0 ? crd[d] > 0 : crd[d] < dim[d] - 1;
+                        if (interior) {
+                            int j = side == 0 ? i - stride[d] : i + stride[d];
+                            int lo = i < j ? i : j, hi = i < j ? j : i;
+                            double T = harm(K[d][lo], K[d][hi]) * g[d];
+                            double c = T * (K[d][j] / (K[d][i] + K[d][j]));
+                            s += c * (h[i] - h[j]) * (lam[i] - lam[j]);
+                        } else if (bct[f] == OR_DIRICHLET) {
+                            double Tb = (2.0 * K[d][i]) * g[d];
+                            s += Tb * (h[i] - bcv[f]) * lam[i];
+                        }
+                    }
+                grad[i] = -s;
+            }
+}
+
+/* J = sum_k (h[obs_k] - hobs_k)^2 and its gradient dJ/dh (zero off the
+ * observation cells) */
+double or_misfit(int n, const double *h, int nobs, const int *obs, const double *hobs, double *dJdh)
+{
+    double J = 0.0;
+    if (dJdh)
+        for (int i = 0; i < n; ++i) dJdh[i] = 0.0;
+    for (int k = 0; k < nobs; ++k) {
+        double r = h[obs[k]] - hobs[k];
+        J += r * r;
+        if (dJdh) dJdh[obs[k]] += 2.0 * r;
+    }
+    return J;
+}

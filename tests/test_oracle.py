@@ -519,3 +519,46 @@ def test_lnk_field_statistics():
     # covariance at a lag of one correlation length along x is about var / e
     c = np.mean((f1[:, :, :-4] - f1.mean()) * (f1[:, :, 4:] - f1.mean()))
     assert 0.8 < c / (4.0 / np.e) < 1.25
+
+
+# ----------------------------------------------------------------- adjoint --
+def _adjoint_case(nx, ny, nz, seed, kz_ratio=1.0, bct=(1, 1, 0, 0, 0, 0), bcv=(1.0, 0.0, 0, 0, 0, 0)):
+    p = wl.problem(nx, ny, nz, var=2.0, corr=2.0, seed=seed, kz_ratio=kz_ratio, bct=bct, bcv=bcv,
+                   wells_count=2, wells_seed=seed + 1)
+    lnk = np.log(p["Kx"])
+    obs = wl.cells(nx * ny * nz, 6, seed + 2)
+    hobs = np.random.default_rng(seed + 3).normal(0.5, 0.1, len(obs))
+    return p, lnk, obs, hobs
+
+
+def _J_of(lnk, p, obs, hobs, kz_ratio):
+    K = np.exp(lnk)
+    A, b = oracle.assemble(p["nx"], p["ny"], p["nz"], K, K, K / kz_ratio, p["bct"], p["bcv"], p["q"])
+    h = np.linalg.solve(A.dense(), b)
+    return oracle.misfit(h, obs, hobs)[0], h, A
+
+
+@pytest.mark.parametrize("kz_ratio,bct,bcv", [(1.0, (1, 1, 0, 0, 0, 0), (1.0, 0.0, 0, 0, 0, 0)),
+                                              (10.0, (0, 0, 0, 0, 0, 1), (0, 0, 0, 0, 0, 0.3))])
+def test_adjoint_gradient_matches_central_differences(kz_ratio, bct, bcv):
+    nx, ny, nz = 7, 6, 5
+    p, lnk, obs, hobs = _adjoint_case(nx, ny, nz, 3, kz_ratio, bct, bcv)
+    J, h, A = _J_of(lnk, p, obs, hobs, kz_ratio)
+    _, dJdh = oracle.misfit(h, obs, hobs)
+    lam = np.linalg.solve(A.dense(), dJdh)
+    K = np.exp(lnk)
+    g = oracle.adjoint_grad(nx, ny, nz, K, h, lam, K, K / kz_ratio, p["bct"], p["bcv"])
+    eps = 1e-5
+    for i in np.random.default_rng(1).choice(nx * ny * nz, 25, replace=False):
+        lp, lm = lnk.copy(), lnk.copy()
+        lp[i] += eps
+        lm[i] -= eps
+        fd = (_J_of(lp, p, obs, hobs, kz_ratio)[0] - _J_of(lm, p, obs, hobs, kz_ratio)[0]) / (2 * eps)
+        assert fd == pytest.approx(g[i], rel=1e-5, abs=1e-9 * max(1.0, abs(J)))
+
+
+def test_misfit_definition():
+    h = np.array([1.0, 2.0, 3.0, 4.0])
+    J, d = oracle.misfit(h, [1, 3], [1.5, 3.0])
+    assert J == pytest.approx(0.25 + 1.0)
+    assert list(d) == [0.0, 1.0, 0.0, 2.0]

@@ -166,6 +166,35 @@ int gw_assemble(const gw_grid *grid, const double *Kx, const double *Ky, const d
 int gw_assemble_noalloc(const gw_grid *grid, const double *Kx, const double *Ky, const double *Kz, const gw_bc *bc,
                         const double *q, int *rowptr, int *col, double *val, double *b, void *stream);
 
+/*
+ * gw_adjoint_gradient -- the face-flux product of the adjoint method: the
+ * gradient of an objective J(h) with respect to ln K per cell (ln K scaling
+ * Kx, Ky, Kz of the cell together), given the heads h of C h = Q and the
+ * adjoint state lambda solving C lambda = dJ/dh (C is symmetric, so
+ * gw_pcg_solve on the same hierarchy gives lambda).  Differentiating the
+ * assembly of gw_assemble: an interior face with T = 2 K_i K_j/(K_i+K_j) g
+ * contributes -T K_j/(K_i+K_j) (h_i - h_j)(lambda_i - lambda_j) to cell i, a
+ * Dirichlet face with T_b = 2 K_i g contributes -T_b (h_i - h_b) lambda_i.
+ * The paper's method does not need gradients; this serves sensitivity
+ * analysis, which the paper names as the use of fast flow solves (Abstract).
+ *   grid, Kx, Ky, Kz, bc  as passed to gw_assemble (arrays in device memory).
+ *   h, lambda             n doubles, device.
+ *   grad                  n doubles, device: receives dJ/dlnK.
+ * Asynchronous on stream.  Errors: GW_ERR_ARG.
+ */
+int gw_adjoint_gradient(const gw_grid *grid, const double *Kx, const double *Ky, const double *Kz, const gw_bc *bc,
+                        const double *h, const double *lambda, double *grad, void *stream);
+
+/*
+ * gw_misfit -- the head-misfit objective J = sum_k (h[obs_k] - hobs_k)^2 over
+ * observation cells and, if dJdh is not NULL, its gradient dJ/dh (n doubles,
+ * device; zero off the observation cells, repeated cells add up).  h, obs
+ * (nobs ints), hobs (nobs doubles) in device memory; J is one double, host or
+ * device.  Synchronises the stream.
+ */
+int gw_misfit(int n, const double *h, int nobs, const int *obs, const double *hobs, double *J, double *dJdh,
+              void *stream);
+
 /* Size of the matrix behind a handle. */
 int gw_matrix_size(gw_matrix A, int *n, long long *nnz);
 

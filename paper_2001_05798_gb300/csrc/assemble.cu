@@ -140,6 +140,76 @@ void assemble_csr(int nx, int ny, int nz, double dx, double dy, double dz, const
     GW_LAUNCH_CHECK();
 }
 
+// ---------------------------------------------------------------- adjoint --
+// dJ/dlnK_i = lambda^T (dQ/dlnK_i - dC/dlnK_i h), with lnK scaling Kx, Ky, Kz of
+// cell i together: an interior face with T = 2 K_i K_j/(K_i+K_j) g has
+// dT/dlnK_i = T K_j/(K_i + K_j) and contributes -dT/dlnK_i (h_i - h_j)
+// (lambda_i - lambda_j); a Dirichlet face (T_b = 2 K_i g, dT_b/dlnK_i = T_b)
+// contributes -T_b (h_i - h_b) lambda_i.
+__global__ void k_adj_grad(AsmGeom G, const double *__restrict__ Kx, const double *__restrict__ Ky,
+                           const double *__restrict__ Kz, const double *__restrict__ h,
+                           const double *__restrict__ lam, double *__restrict__ grad)
+{
+    const long long n = (long long)G.nx * G.ny * G.nz;
+    const int sxy = G.nx * G.ny;
+    for (long long ii = blockIdx.x * (long long)blockDim.x + threadIdx.x; ii < n; ii += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)ii;
+        const int crd[3] = {i % G.nx, (i / G.nx) % G.ny, i / sxy}, dim[3] = {G.nx, G.ny, G.nz},
+                  stride[3] = {1, G.nx, sxy};
+        const double *K[3] = {Kx, Ky, Kz};
+        const double hi = h[i], li = lam[i];
+        double s = 0.0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const double Ki = K[d][i];
+#pragma unroll
+            for (int side = 0; side < 2; ++side) {
+                const int f = 2 * d + side;
+                const bool interior = side == 0 ? crd[d] > 0 : crd[d] < dim[d] - 1;
+                if (interior) {
+                    const int j = side == 0 ? i - stride[d] : i + stride[d];
+                    const double Kj = K[d][j];
+                    const double T = harm_T(K[d][min(i, j)], K[d][max(i, j)], G.g[d]);
+                    s += T * (Kj / (Ki + Kj)) * (hi - h[j]) * (li - lam[j]);
+                } else if (G.bct[f] == GW_DIRICHLET) {
+                    s += (2.0 * Ki) * G.g[d] * (hi - G.bcv[f]) * li;
+                }
+            }
+        }
+        grad[i] = -s;
+    }
+}
+
+__global__ void k_zero(long long n, double *__restrict__ a)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        a[i] = 0.0;
+}
+
+// J = sum_k (h[obs_k] - hobs_k)^2 summed in k order by one block; dJ/dh
+// scattered in k order by one thread (repeated cells add up)
+__global__ void k_misfit(int nobs, const double *__restrict__ h, const int *__restrict__ obs,
+                         const double *__restrict__ hobs, double *__restrict__ J, double *__restrict__ dJdh)
+{
+    __shared__ double sh[1024];
+    double loc = 0.0;
+    for (int k = threadIdx.x; k < nobs; k += blockDim.x) {
+        const double r = h[obs[k]] - hobs[k];
+        loc += r * r;
+    }
+    sh[threadIdx.x] = loc;
+    __syncthreads();
+    for (int off = blockDim.x >> 1; off > 0; off >>= 1) {
+        if ((int)threadIdx.x < off) sh[threadIdx.x] += sh[threadIdx.x + off];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        *J = sh[0];
+        if (dJdh)
+            for (int k = 0; k < nobs; ++k) dJdh[obs[k]] += 2.0 * (h[obs[k]] - hobs[k]);
+    }
+}
+
 }  // namespace gw
 
 // ------------------------------------------- assembly without allocations --
@@ -241,6 +311,72 @@ extern "C" int gw_assemble_noalloc(const gw_grid *grid, const double *Kx, const 
             fail(GW_ERR_ARG, "gw_assemble_noalloc: grid too large for the scan workspace");
         k_asm_fill<<<grid_b, bs, 0, st>>>(G, Kx, ky, kz, q, rowptr, col, val, b);
         GW_LAUNCH_CHECK();
+        GW_CUDA(cudaStreamSynchronize(st));
+    } catch (const Error &e) {
+        set_last_error(e.msg.c_str());
+        return e.code;
+    } catch (...) {
+        set_last_error("unexpected failure");
+        return GW_ERR_CUDA;
+    }
+    return GW_OK;
+}
+
+extern "C" int gw_adjoint_gradient(const gw_grid *grid, const double *Kx, const double *Ky, const double *Kz,
+                                   const gw_bc *bc, const double *h, const double *lambda, double *grad, void *stream)
+{
+    using namespace gw;
+    try {
+        if (!grid || !Kx || !bc || !h || !lambda || !grad) fail(GW_ERR_ARG, "gw_adjoint_gradient: null argument");
+        const int nx = grid->nx, ny = grid->ny, nz = grid->nz;
+        if (nx < 1 || ny < 1 || nz < 1) fail(GW_ERR_ARG, "gw_adjoint_gradient: grid sizes must be >= 1");
+        const long long n64 = (long long)nx * ny * nz;
+        if (n64 > 0x7fffffffLL / 8) fail(GW_ERR_ARG, "gw_adjoint_gradient: too many cells");
+        const double *ky = Ky ? Ky : Kx, *kz = Kz ? Kz : Kx;
+        const void *ptrs[7] = {Kx, ky, kz, h, lambda, grad, nullptr};
+        for (int k = 0; k < 6; ++k)
+            if (!is_device_ptr(ptrs[k])) fail(GW_ERR_ARG, "gw_adjoint_gradient: arrays must be device memory");
+        AsmGeom G;
+        G.nx = nx;
+        G.ny = ny;
+        G.nz = nz;
+        G.g[0] = (grid->dy * grid->dz) / grid->dx;
+        G.g[1] = (grid->dx * grid->dz) / grid->dy;
+        G.g[2] = (grid->dx * grid->dy) / grid->dz;
+        for (int f = 0; f < 6; ++f) {
+            G.bct[f] = bc->type[f];
+            G.bcv[f] = bc->value[f];
+        }
+        cudaStream_t st = (cudaStream_t)stream;
+        const int grid_b = (int)std::min<long long>((n64 + 255) / 256, 152LL * 16);
+        k_adj_grad<<<grid_b, 256, 0, st>>>(G, Kx, ky, kz, h, lambda, grad);
+        GW_LAUNCH_CHECK();
+    } catch (const Error &e) {
+        set_last_error(e.msg.c_str());
+        return e.code;
+    } catch (...) {
+        set_last_error("unexpected failure");
+        return GW_ERR_CUDA;
+    }
+    return GW_OK;
+}
+
+extern "C" int gw_misfit(int n, const double *h, int nobs, const int *obs, const double *hobs, double *J,
+                         double *dJdh, void *stream)
+{
+    using namespace gw;
+    try {
+        if (n < 1 || nobs < 0 || nobs > (1 << 24) || !h || !J || (nobs && (!obs || !hobs)))
+            fail(GW_ERR_ARG, "gw_misfit: bad argument");
+        cudaStream_t st = (cudaStream_t)stream;
+        DBuf<double> jd(1);
+        if (dJdh) {
+            k_zero<<<(int)std::min<long long>((n + 255) / 256, 152LL * 16), 256, 0, st>>>(n, dJdh);
+            GW_LAUNCH_CHECK();
+        }
+        k_misfit<<<1, 1024, 0, st>>>(nobs, h, obs, hobs, jd.p, dJdh);
+        GW_LAUNCH_CHECK();
+        GW_CUDA(cudaMemcpyAsync(J, jd.p, sizeof(double), cudaMemcpyDefault, st));
         GW_CUDA(cudaStreamSynchronize(st));
     } catch (const Error &e) {
         set_last_error(e.msg.c_str());

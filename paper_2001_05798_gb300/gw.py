@@ -22,7 +22,7 @@ GW_SMOOTH_JACOBI, GW_SMOOTH_CHEBYSHEV = 0, 1
 EXPORTS = ("gw_amg_opts_default", "gw_assemble", "gw_matrix_size", "gw_matrix_export", "gw_amg_setup",
            "gw_pcg_solve", "gw_vcycle", "gw_hierarchy_info", "gw_hierarchy_export", "gw_matrix_free",
            "gw_hierarchy_free", "gw_status_str", "gw_last_error", "gw_profile_enable", "gw_profile_read",
-           "gw_assemble_noalloc")
+           "gw_assemble_noalloc", "gw_adjoint_gradient", "gw_misfit")
 
 PK_NAMES = ("spmv", "update", "pre1", "pre2", "resid", "restrict", "l1down", "deep", "l1up", "prolong", "post1",
             "post2", "pupdate")
@@ -91,6 +91,8 @@ def load():
         "gw_profile_enable": (i, [vp, i]),
         "gw_profile_read": (i, [vp, P(gw_profile), i]),
         "gw_assemble_noalloc": (i, [P(gw_grid), vp, vp, vp, P(gw_bc), vp, vp, vp, vp, vp, vp]),
+        "gw_adjoint_gradient": (i, [P(gw_grid), vp, vp, vp, P(gw_bc), vp, vp, vp, vp]),
+        "gw_misfit": (i, [i, vp, i, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -200,6 +202,32 @@ def gw_assemble_noalloc(nx, ny, nz, Kx, rowptr, col, val, b, Ky=None, Kz=None, b
         bc.value[f] = float(bcv[f])
     _check(load().gw_assemble_noalloc(ctypes.byref(g), _ptr(Kx), _ptr(Ky), _ptr(Kz), ctypes.byref(bc), _ptr(q),
                                       _ptr(rowptr), _ptr(col), _ptr(val), _ptr(b), _stream(stream)))
+
+
+def _grid_bc(nx, ny, nz, bct, bcv, spacing):
+    g = gw_grid(nx, ny, nz, float(spacing[0]), float(spacing[1]), float(spacing[2]))
+    bc = gw_bc()
+    for f in range(6):
+        bc.type[f] = int(bct[f])
+        bc.value[f] = float(bcv[f])
+    return g, bc
+
+
+def gw_adjoint_gradient(nx, ny, nz, Kx, h, lam, grad, Ky=None, Kz=None, bct=(1, 1, 0, 0, 0, 0),
+                        bcv=(1.0, 0.0, 0, 0, 0, 0), spacing=(1.0, 1.0, 1.0), stream=None):
+    """dJ/dlnK from heads and adjoint state (include/gw.h: gw_adjoint_gradient); device arrays."""
+    g, bc = _grid_bc(nx, ny, nz, bct, bcv, spacing)
+    _check(load().gw_adjoint_gradient(ctypes.byref(g), _ptr(Kx), _ptr(Ky), _ptr(Kz), ctypes.byref(bc), _ptr(h),
+                                      _ptr(lam), _ptr(grad), _stream(stream)))
+    return grad
+
+
+def gw_misfit(h, obs, hobs, dJdh=None, stream=None):
+    """J = sum (h[obs] - hobs)^2 and optionally dJ/dh (include/gw.h: gw_misfit)."""
+    J = ctypes.c_double()
+    _check(load().gw_misfit(int(h.numel() if hasattr(h, "numel") else h.size), _ptr(h), len(obs), _ptr(obs),
+                            _ptr(hobs), ctypes.byref(J), _ptr(dJdh), _stream(stream)))
+    return J.value
 
 
 class Hierarchy:

@@ -320,6 +320,56 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_adjoint(args):
+    """Secondary workload: adjoint sensitivity at 96^3 (lnK variance 2, correlation
+    6 cells, seeds 5/6/7): one step = forward solve (setup included) + backward
+    (adjoint solve on the same hierarchy + face-flux gradient kernel)."""
+    import torch
+
+    from paper_2001_05798_gb300 import build, gw, workload as wl
+    from paper_2001_05798_gb300.adjoint import heads
+
+    torch.cuda.set_device(0)
+    build.build()
+    gw.load()
+    side = 96
+    p = wl.heterogeneous_3d(side=side, var=2.0, corr=6.0, seed=5)
+    t = wl.heterogeneous_3d(side=side, var=2.0, corr=6.0, seed=6)
+    obs = torch.from_numpy(wl.cells(side ** 3, 64, 7).astype(np.int64)).cuda()
+    tK = torch.from_numpy(t["Kx"]).cuda()
+    bt = torch.empty(side ** 3, dtype=torch.float64, device="cuda")
+    At, _ = gw.gw_assemble(side, side, side, tK, tK, tK, t["bct"], t["bcv"], None, b_out=bt)
+    ht, _, _, _ = gw.Hierarchy(At).solve(bt, tol=1e-10)
+    hobs = ht[obs].contiguous()
+    lnK0 = torch.from_numpy(np.log(p["Kx"])).cuda()
+
+    def step():
+        lnK = lnK0.clone().requires_grad_(True)
+        h = heads(lnK, side, side, side, tol=1e-8)
+        J = ((h[obs] - hobs) ** 2).sum()
+        J.backward()
+        return J, lnK.grad
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    times = []
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        J, g = step()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    out = {"metric": "adjoint d(head misfit)/d(lnK) per cell, forward + backward ms", "value": float(np.median(times)),
+           "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": float(np.mean(times)), "higher_is_better": False, "dtype": "f32 V-cycle + f64 CG",
+           "data": "synthetic", "config": {"workload": "adjoint sensitivity 96^3, lnK var 2 corr 6 seed 5, truth seed 6, "
+                                                       "64 observation cells seed 7, tol 1e-8, setup included"},
+           "J": float(J.detach()), "grad_norm": float(g.norm())}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -332,6 +382,8 @@ def main():
     ap.add_argument("--delta", type=float, default=0.1, help="reliable-update factor of the mixed form")
     ap.add_argument("--half-storage", type=int, default=0, help="FP16 storage of P, R and coarse operators (mixed)")
     ap.add_argument("--side", type=int, default=SIDE, help="grid side for profiling captures (default 128)")
+    ap.add_argument("--workload", choices=("solve", "adjoint"), default="solve",
+                    help="solve: the 128^3 benchmark (default); adjoint: the 96^3 sensitivity case")
     args = ap.parse_args()
     if args.side != SIDE:
         globals()["SIDE"] = args.side
@@ -340,6 +392,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "adjoint":
+        run_adjoint(args)
     else:
         run_ours(args)
 

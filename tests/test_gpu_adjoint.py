@@ -80,7 +80,7 @@ def test_autograd_gradient_small_against_oracle(gw, prec):
     Jref, dJdh = oracle.misfit(href, obs, hobs)
     lam = np.linalg.solve(A.dense(), dJdh)
     gref = oracle.adjoint_grad(side, side, side, p["Kx"], href, lam)
-    assert float(J) == pytest.approx(Jref, rel=1e-8)
+    assert float(J.detach()) == pytest.approx(Jref, rel=1e-8)
     g = lnK.grad.cpu().numpy()
     assert np.linalg.norm(g - gref) <= 1e-7 * np.linalg.norm(gref)
 

@@ -82,6 +82,9 @@ def _load():
         "or_adjoint_grad": (None, [ctypes.c_int] * 3 + [ctypes.c_double] * 3 + [_f64p] * 3 +
                             [_i32p, _f64p, _f64p, _f64p, _f64p]),
         "or_misfit": (ctypes.c_double, [ctypes.c_int, _f64p, ctypes.c_int, _i32p, _f64p, _vp]),
+        "or_shift_csr": (_vp, [_vp, _f64p]),
+        "or_reuse_ok": (ctypes.c_int, [_vp, _f64p, _vp, ctypes.c_double]),
+        "or_h_refresh_level0": (None, [_vp, _vp]),
         "or_cg_plain": (ctypes.c_int, [_vp, _f64p, _f64p, ctypes.c_double, ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
     }
@@ -260,6 +263,11 @@ class Hierarchy:
         _load().or_h_scalars(self.h, l, out)
         return dict(theta2=out[0], omegaP=out[1], rhoP=out[2], jacobi_w=out[3], rhoJ=out[4], lam=out[5])
 
+    def refresh_level0(self, A):
+        """Keep the coarse levels; level 0 becomes A (with its smoother data redone)."""
+        _load().or_h_refresh_level0(self.h, A.h)
+        self._A0 = A
+
     def smooth(self, l, b, x, x0zero=False):
         """One application of the level-l smoother to A_l x = b; returns the new x."""
         x = np.array(x, dtype=np.float64, copy=True)
@@ -311,6 +319,17 @@ def misfit(h, obs, hobs):
     J = _load().or_misfit(h.size, h, len(obs), np.ascontiguousarray(obs, np.int32),
                           np.ascontiguousarray(hobs, np.float64), d.ctypes.data_as(ctypes.c_void_p))
     return J, d
+
+
+def shift(C, s):
+    """C + diag(s) (Eq. 2: the transient operator with s_i = S_i V_i / dt)."""
+    return CSR(_load().or_shift_csr(C.h, np.ascontiguousarray(s, np.float64)))
+
+
+def reuse_ok(C, s, s_built=None, delta=0.01):
+    """|s_i - s_built_i| < delta C_ii for every row (Discussion section criterion)."""
+    sb = None if s_built is None else np.ascontiguousarray(s_built, np.float64)
+    return bool(_load().or_reuse_ok(C.h, np.ascontiguousarray(s, np.float64), _ptr(sb), float(delta)))
 
 
 def complexities(ns, nnzs):

@@ -959,3 +959,37 @@ double or_misfit(int n, const double *h, int nobs, const int *obs, const double 
     }
     return J;
 }
+
+/* ---------------------------------------------------- transient shift -- */
+/* C + diag(s): the implicit transient operator of Eq. 2, s_i = S_i V_i / dt */
+ocsr *or_shift_csr(const ocsr *C, const double *s)
+{
+    ocsr *A = or_csr_from(C->nr, C->nc, C->rp, C->ci, C->v);
+    for (int i = 0; i < A->nr; ++i)
+        for (int e = A->rp[i]; e < A->rp[i + 1]; ++e)
+            if (A->ci[e] == i) A->v[e] = A->v[e] + s[i];
+    return A;
+}
+
+/* The cached hierarchy stays valid while the diagonal moved by less than
+ * delta C_ii in every row: |s_i - s_built_i| < delta * C_ii (s_built = 0 gives
+ * the criterion S_i V_i / dt < delta C_ii of the Discussion section). */
+int or_reuse_ok(const ocsr *C, const double *s, const double *s_built, double delta)
+{
+    for (int i = 0; i < C->nr; ++i) {
+        double cii = csr_diag_of(C, i);
+        double ds = s[i] - (s_built ? s_built[i] : 0.0);
+        if (!(fabs(ds) < delta * cii)) return 0;
+    }
+    return 1;
+}
+
+/* keep the coarse levels, replace the level-0 operator and redo its smoother data */
+void or_h_refresh_level0(ohier *H, const ocsr *A)
+{
+    or_csr_free(H->A[0]);
+    H->A[0] = or_csr_from(A->nr, A->nc, A->rp, A->ci, A->v);
+    free(H->dinv[0]);
+    H->dinv[0] = NULL;
+    if (H->L > 1) smoother_setup(H, 0);
+}

@@ -562,3 +562,36 @@ def test_misfit_definition():
     J, d = oracle.misfit(h, [1, 3], [1.5, 3.0])
     assert J == pytest.approx(0.25 + 1.0)
     assert list(d) == [0.0, 1.0, 0.0, 2.0]
+
+
+# --------------------------------------------------------- transient shift --
+def test_shift_and_reuse_criterion():
+    p = wl.problem(6, 5, 4, var=2.0, corr=2.0, seed=3)
+    C, b = asm(p)
+    s = np.linspace(0.0, 0.3, C.nr)
+    np.testing.assert_array_equal(oracle.shift(C, s).dense(), C.dense() + np.diag(s))
+    d = np.diag(C.dense())
+    assert oracle.reuse_ok(C, 0.009 * d, delta=0.01)
+    assert not oracle.reuse_ok(C, 0.011 * d, delta=0.01)
+    bad = 0.005 * d
+    bad[7] = 0.02 * d[7]
+    assert not oracle.reuse_ok(C, bad, delta=0.01)
+    assert oracle.reuse_ok(C, bad, s_built=bad - 0.001 * d, delta=0.01)
+
+
+@pytest.mark.parametrize("frac", [0.005, 0.5])
+def test_transient_step_with_reused_hierarchy_solves_the_shifted_system(frac):
+    # implicit step (C + S/dt) h1 = Q + (S/dt) h0 on a cached hierarchy of C
+    p = wl.problem(12, 11, 10, var=3.0, corr=3.0, seed=8)
+    C, b = asm(p)
+    d = np.diag(C.dense())
+    s = frac * d * np.random.default_rng(4).random(C.nr)
+    h0 = np.random.default_rng(5).normal(size=C.nr)
+    A = oracle.shift(C, s)
+    rhs = b + s * h0
+    H = oracle.Hierarchy(C, n_coarse=60)
+    H.refresh_level0(A)
+    x, it, rel, st = H.pcg(rhs, tol=1e-12)
+    assert st == 0 and rel <= 1e-12
+    ref = np.linalg.solve(A.dense(), rhs)
+    assert np.linalg.norm(x - ref) <= 1e-10 * np.linalg.norm(ref)

@@ -239,6 +239,22 @@ int gw_amg_setup(gw_matrix A, const gw_amg_opts *opts, gw_hierarchy *H_out, void
 int gw_pcg_solve(gw_hierarchy H, const double *b, double *h, double tol, int maxit, int *iters,
                  double *relres, void *stream);
 
+/*
+ * gw_hierarchy_shift -- the implicit transient form (Eq. 2): the hierarchy
+ * set up from C now solves (C + diag(s)) h = b, s_i = S_i V_i / dt (s NULL:
+ * back to C).  The cached hierarchy is reused while the diagonal moved by less
+ * than delta C_ii in every row since the coarse levels were built,
+ * |s_i - s_built_i| < delta C_ii, the criterion of the Discussion section
+ * with delta about 0.01: then only level 0 (its operator and smoother data) is
+ * refreshed and *rebuilt = 0.  Otherwise the whole hierarchy is set up again
+ * for C + diag(s) and *rebuilt = 1.
+ *   s       n doubles (host or device), s_i >= 0, or NULL.
+ *   delta   in (0, 1).
+ * Synchronises the stream.  Errors: GW_ERR_ARG, GW_ERR_OOM, GW_ERR_SETUP,
+ * GW_ERR_CUDA (the hierarchy keeps its previous state on an error).
+ */
+int gw_hierarchy_shift(gw_hierarchy H, const double *s, double delta, int *rebuilt, void *stream);
+
 /* Applies one V-cycle z = M^-1 r (from a zero initial guess) with the
  * hierarchy's precision; r and z are n doubles on the device. */
 int gw_vcycle(gw_hierarchy H, const double *r, double *z, void *stream);

@@ -2,6 +2,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <memory>
 #include <new>
 
 #include "gw_internal.cuh"
@@ -13,7 +14,11 @@ struct gw_matrix_s {
 };
 
 struct gw_hierarchy_s {
-    gw::Hier H;
+    std::unique_ptr<gw::Hier> h;
+    gw_matrix base = nullptr;   // the matrix the caller set the hierarchy up from (C)
+    gw::DCSR shifted;           // C + diag(s) while a transient shift is applied
+    gw::DBuf<double> s_built;   // shift the coarse levels were built with (empty: none)
+    gw::DBuf<double> s_now;     // shift now applied (empty: none)
 };
 
 namespace gw {
@@ -94,6 +99,69 @@ static void cheb_coeffs(double lam, int degree, double &c0, double *c1, double *
     }
 }
 
+// Cycle storage of level k in the cycle precision: A_k (the 7-point stencil on
+// level 0), P_k and R_k when given, the smoother's diagonal weights and the
+// Chebyshev coefficients.  Returns the device bytes it holds.
+static long long store_level(Hier &H, int k, const DCSR &A, const DCSR *P, const DCSR *R, cudaStream_t st)
+{
+    const gw_amg_opts &o = H.o;
+    const bool f64 = o.prec == GW_PREC_FP64;
+    const int n = A.nr;
+    long long bytes = 0;
+    DBuf<double> diag;
+    const double rhoJ = setup_gershgorin(A, diag, st);
+    H.info[(size_t)k].jacobi_w = (4.0 / 3.0) / rhoJ;
+    double scale = 1.0;
+    double c0 = 0.0, c1[8] = {0}, c2[8] = {0};
+    if (o.smoother == GW_SMOOTH_JACOBI) {
+        scale = H.info[(size_t)k].jacobi_w;
+    } else {
+        const double lam = setup_power_lambda(A, diag.p, o.seed, k, st);
+        H.info[(size_t)k].lambda_max = lam;
+        cheb_coeffs(lam, o.degree, c0, c1, c2);
+    }
+    const int g = (int)std::min<long long>(((long long)n + 255) / 256, 152LL * 16);
+    if (f64) {
+        CycLevel<double> &c = H.cd[(size_t)k];
+        to_store<double>(A, c.A, k == 0 ? FMT_STEN : choose_fmt(A), H.gnx, H.gny, H.gnz, st);
+        if (P) to_store<double>(*P, c.P, choose_fmt(*P), 0, 0, 0, st);
+        if (R) to_store<double>(*R, c.R, choose_fmt(*R), 0, 0, 0, st);
+        c.dw.alloc((size_t)n);
+        k_make_dw<<<std::max(g, 1), 256, 0, st>>>(n, diag.p, scale, nullptr, c.dw.p);
+        c.c0 = c0;
+        memcpy(c.c1, c1, sizeof c1);
+        memcpy(c.c2, c2, sizeof c2);
+        bytes += (long long)(c.A.bytes() + c.P.bytes() + c.R.bytes() + c.dw.bytes());
+    } else {
+        CycLevel<float> &c = H.cf[(size_t)k];
+        const bool h16 = o.half_storage != 0;
+        auto f32 = [h16](int f) { return h16 && f == FMT_SELL ? FMT_SELL16 : f; };
+        to_store<float>(A, c.A, k == 0 ? FMT_STEN : f32(choose_fmt(A)), H.gnx, H.gny, H.gnz, st);
+        if (P) to_store<float>(*P, c.P, f32(choose_fmt(*P)), 0, 0, 0, st);
+        if (R) to_store<float>(*R, c.R, f32(choose_fmt(*R)), 0, 0, 0, st);
+        c.dw.alloc((size_t)n);
+        k_make_dw<<<std::max(g, 1), 256, 0, st>>>(n, diag.p, scale, c.dw.p, nullptr);
+        c.c0 = c0;
+        memcpy(c.c1, c1, sizeof c1);
+        memcpy(c.c2, c2, sizeof c2);
+        bytes += (long long)(c.A.bytes() + c.P.bytes() + c.R.bytes() + c.dw.bytes());
+    }
+    GW_LAUNCH_CHECK();
+    GW_CUDA(cudaStreamSynchronize(st));
+    return bytes;
+}
+
+// Level 0 becomes A (same grid and pattern); the coarse levels stay.  Used
+// for the transient shift while the cached hierarchy remains valid.
+void refresh_level0(Hier &H, const DCSR &A, cudaStream_t st)
+{
+    H.A0 = &A;
+    store_level(H, 0, A, nullptr, nullptr, st);
+    if (H.o.prec != GW_PREC_FP64) to_store<double>(A, H.A64, FMT_STEN, H.gnx, H.gny, H.gnz, st);
+    drop_graphs(H);
+    GW_CUDA(cudaStreamSynchronize(st));
+}
+
 // Smoothed-aggregation setup (see setup.cu for the stages).  Levels are added
 // while the level has more than n_coarse unknowns and fewer than max_levels
 // levels exist; a level whose aggregation keeps more than 0.9 of its unknowns
@@ -154,48 +222,7 @@ void build_hierarchy(Hier &H, cudaStream_t st)
         const DCSR &A = Al(k);
         const int n = A.nr;
         long long bytes = 0;
-        if (k < L - 1) {
-            DBuf<double> diag;
-            const double rhoJ = setup_gershgorin(A, diag, st);
-            H.info[(size_t)k].jacobi_w = (4.0 / 3.0) / rhoJ;
-            double scale = 1.0;
-            double c0 = 0.0, c1[8] = {0}, c2[8] = {0};
-            if (o.smoother == GW_SMOOTH_JACOBI) {
-                scale = H.info[(size_t)k].jacobi_w;
-            } else {
-                const double lam = setup_power_lambda(A, diag.p, o.seed, k, st);
-                H.info[(size_t)k].lambda_max = lam;
-                cheb_coeffs(lam, o.degree, c0, c1, c2);
-            }
-            const int g = (int)std::min<long long>(((long long)n + 255) / 256, 152LL * 16);
-            if (f64) {
-                CycLevel<double> &c = H.cd[(size_t)k];
-                to_store<double>(A, c.A, k == 0 ? FMT_STEN : choose_fmt(A), H.gnx, H.gny, H.gnz, st);
-                to_store<double>(H.P[(size_t)k], c.P, choose_fmt(H.P[(size_t)k]), 0, 0, 0, st);
-                to_store<double>(R[(size_t)k], c.R, choose_fmt(R[(size_t)k]), 0, 0, 0, st);
-                c.dw.alloc((size_t)n);
-                k_make_dw<<<std::max(g, 1), 256, 0, st>>>(n, diag.p, scale, nullptr, c.dw.p);
-                c.c0 = c0;
-                memcpy(c.c1, c1, sizeof c1);
-                memcpy(c.c2, c2, sizeof c2);
-                bytes += (long long)(c.A.bytes() + c.P.bytes() + c.R.bytes() + c.dw.bytes());
-            } else {
-                CycLevel<float> &c = H.cf[(size_t)k];
-                const bool h16 = o.half_storage != 0;
-                auto f32 = [h16](int f) { return h16 && f == FMT_SELL ? FMT_SELL16 : f; };
-                to_store<float>(A, c.A, k == 0 ? FMT_STEN : f32(choose_fmt(A)), H.gnx, H.gny, H.gnz, st);
-                to_store<float>(H.P[(size_t)k], c.P, f32(choose_fmt(H.P[(size_t)k])), 0, 0, 0, st);
-                to_store<float>(R[(size_t)k], c.R, f32(choose_fmt(R[(size_t)k])), 0, 0, 0, st);
-                c.dw.alloc((size_t)n);
-                k_make_dw<<<std::max(g, 1), 256, 0, st>>>(n, diag.p, scale, c.dw.p, nullptr);
-                c.c0 = c0;
-                memcpy(c.c1, c1, sizeof c1);
-                memcpy(c.c2, c2, sizeof c2);
-                bytes += (long long)(c.A.bytes() + c.P.bytes() + c.R.bytes() + c.dw.bytes());
-            }
-            GW_LAUNCH_CHECK();
-            GW_CUDA(cudaStreamSynchronize(st));
-        }
+        if (k < L - 1) bytes += store_level(H, k, A, &H.P[(size_t)k], &R[(size_t)k], st);
         if (f64) {
             alloc_vectors(H.cd[(size_t)k], n);
             bytes += 6LL * n * 8;
@@ -243,6 +270,46 @@ void build_hierarchy(Hier &H, cudaStream_t st)
 }  // namespace gw
 
 using namespace gw;
+
+static std::unique_ptr<Hier> new_hier(gw_matrix A, const gw_amg_opts &o, const DCSR *A0, cudaStream_t st)
+{
+    std::unique_ptr<Hier> h(new Hier);
+    h->dev = A->dev;
+    h->o = o;
+    h->A0 = A0;
+    h->gnx = A->nx;
+    h->gny = A->ny;
+    h->gnz = A->nz;
+    build_hierarchy(*h, st);
+    if (h->L < 2) fail(GW_ERR_SETUP, "gw_amg_setup: the matrix is small enough for one level (n <= n_coarse)");
+    return h;
+}
+
+// |s_i - s_built_i| >= delta * C_ii counts a row that breaks the reuse criterion
+__global__ void k_reuse_check(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                              const double *__restrict__ v, const double *__restrict__ s,
+                              const double *__restrict__ sb, double delta, int *__restrict__ bad)
+{
+    for (long long ii = blockIdx.x * (long long)blockDim.x + threadIdx.x; ii < n; ii += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)ii;
+        double cii = 0.0;
+        for (int e = rp[i]; e < rp[i + 1]; ++e)
+            if (ci[e] == i) cii = v[e];
+        const double ds = (s ? s[i] : 0.0) - (sb ? sb[i] : 0.0);
+        if (!(fabs(ds) < delta * cii)) atomicAdd(bad, 1);
+    }
+}
+
+// A = C + diag(s) on a copy of C's pattern
+__global__ void k_shift_diag(int n, const int *__restrict__ rp, const int *__restrict__ ci, double *__restrict__ v,
+                             const double *__restrict__ s)
+{
+    for (long long ii = blockIdx.x * (long long)blockDim.x + threadIdx.x; ii < n; ii += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)ii;
+        for (int e = rp[i]; e < rp[i + 1]; ++e)
+            if (ci[e] == i) v[e] = v[e] + s[i];
+    }
+}
 
 #define GW_API_BEGIN try {
 #define GW_API_END                                    \
@@ -390,14 +457,8 @@ int gw_amg_setup(gw_matrix A, const gw_amg_opts *opts, gw_hierarchy *H_out, void
     cudaStream_t st = (cudaStream_t)stream;
     gw_hierarchy h = new gw_hierarchy_s;
     try {
-        h->H.dev = A->dev;
-        h->H.o = o;
-        h->H.A0 = &A->A;
-        h->H.gnx = A->nx;
-        h->H.gny = A->ny;
-        h->H.gnz = A->nz;
-        build_hierarchy(h->H, st);
-        if (h->H.L < 2) fail(GW_ERR_SETUP, "gw_amg_setup: the matrix is small enough for one level (n <= n_coarse)");
+        h->base = A;
+        h->h = new_hier(A, o, &A->A, st);
     } catch (...) {
         delete h;
         throw;
@@ -413,7 +474,7 @@ int gw_pcg_solve(gw_hierarchy H, const double *b, double *h, double tol, int max
     GW_API_BEGIN
     if (!H || !b || !h) fail(GW_ERR_ARG, "gw_pcg_solve: null argument");
     if (!(tol > 0.0) || !isfinite(tol) || maxit < 1) fail(GW_ERR_ARG, "gw_pcg_solve: need tol > 0 and maxit >= 1");
-    Hier &hh = H->H;
+    Hier &hh = *H->h;
     DeviceGuard g(hh.dev);
     cudaStream_t st = (cudaStream_t)stream;
     const size_t bytes = (size_t)hh.n * sizeof(double);
@@ -428,14 +489,80 @@ int gw_pcg_solve(gw_hierarchy H, const double *b, double *h, double tol, int max
     GW_API_END
 }
 
+int gw_hierarchy_shift(gw_hierarchy H, const double *s, double delta, int *rebuilt, void *stream)
+{
+    GW_API_BEGIN
+    if (!H || !H->base) fail(GW_ERR_ARG, "gw_hierarchy_shift: null hierarchy");
+    if (!(delta > 0.0 && delta < 1.0)) fail(GW_ERR_ARG, "gw_hierarchy_shift: delta must be in (0, 1)");
+    gw_matrix C = H->base;
+    DeviceGuard g(C->dev);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = C->A.nr;
+    const int gb = (int)std::min<long long>(((long long)n + 255) / 256, 152LL * 16);
+    DBuf<double> snew;
+    if (s) {
+        snew.alloc((size_t)n);
+        GW_CUDA(cudaMemcpyAsync(snew.p, s, (size_t)n * sizeof(double), cudaMemcpyDefault, st));
+    }
+    DBuf<int> bad(1);
+    GW_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
+    k_reuse_check<<<gb, 256, 0, st>>>(n, C->A.rp.p, C->A.ci.p, C->A.v.p, snew.p, H->s_built.p, delta, bad.p);
+    GW_LAUNCH_CHECK();
+    const bool reuse = read_int(bad.p, st) == 0;
+    DCSR A;
+    const DCSR *target = &C->A;
+    if (s) {
+        A.nr = A.nc = n;
+        A.nnz = C->A.nnz;
+        A.rp.alloc((size_t)n + 1);
+        A.ci.alloc((size_t)A.nnz);
+        A.v.alloc((size_t)A.nnz);
+        GW_CUDA(cudaMemcpyAsync(A.rp.p, C->A.rp.p, A.rp.bytes(), cudaMemcpyDeviceToDevice, st));
+        GW_CUDA(cudaMemcpyAsync(A.ci.p, C->A.ci.p, A.ci.bytes(), cudaMemcpyDeviceToDevice, st));
+        GW_CUDA(cudaMemcpyAsync(A.v.p, C->A.v.p, A.v.bytes(), cudaMemcpyDeviceToDevice, st));
+        k_shift_diag<<<gb, 256, 0, st>>>(n, A.rp.p, A.ci.p, A.v.p, snew.p);
+        GW_LAUNCH_CHECK();
+    }
+    if (reuse) {
+        if (s) {
+            H->shifted = std::move(A);
+            target = &H->shifted;
+        }
+        refresh_level0(*H->h, *target, st);
+        if (s) H->s_now = std::move(snew);
+        else H->s_now.release();
+        if (rebuilt) *rebuilt = 0;
+    } else {
+        const gw_amg_opts o = H->h->o;
+        if (s) target = &A;
+        std::unique_ptr<Hier> nh = new_hier(C, o, target, st);
+        nh->prof_on = H->h->prof_on;
+        H->h = std::move(nh);
+        if (s) {
+            H->shifted = std::move(A);
+            H->h->A0 = &H->shifted;
+            H->s_built.alloc((size_t)n);
+            GW_CUDA(cudaMemcpyAsync(H->s_built.p, snew.p, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+            H->s_now = std::move(snew);
+        } else {
+            H->shifted = DCSR();
+            H->s_built.release();
+            H->s_now.release();
+        }
+        GW_CUDA(cudaStreamSynchronize(st));
+        if (rebuilt) *rebuilt = 1;
+    }
+    GW_API_END
+}
+
 int gw_vcycle(gw_hierarchy H, const double *r, double *z, void *stream)
 {
     GW_API_BEGIN
     if (!H || !r || !z) fail(GW_ERR_ARG, "gw_vcycle: null argument");
     if (!is_device_ptr(r) || !is_device_ptr(z)) fail(GW_ERR_ARG, "gw_vcycle: r and z must be device pointers");
-    DeviceGuard g(H->H.dev);
+    DeviceGuard g(H->h->dev);
     cudaStream_t st = (cudaStream_t)stream;
-    vcycle_enqueue(H->H, r, z, nullptr, false, st);
+    vcycle_enqueue(*H->h, r, z, nullptr, false, st);
     GW_CUDA(cudaStreamSynchronize(st));
     GW_API_END
 }
@@ -444,8 +571,8 @@ int gw_hierarchy_info(gw_hierarchy H, gw_level_info *out, int cap, int *nlevels)
 {
     GW_API_BEGIN
     if (!H) fail(GW_ERR_ARG, "gw_hierarchy_info: null hierarchy");
-    if (nlevels) *nlevels = H->H.L;
-    for (int l = 0; out && l < cap && l < H->H.L; ++l) out[l] = H->H.info[(size_t)l];
+    if (nlevels) *nlevels = H->h->L;
+    for (int l = 0; out && l < cap && l < H->h->L; ++l) out[l] = H->h->info[(size_t)l];
     GW_API_END
 }
 
@@ -454,7 +581,7 @@ int gw_hierarchy_export(gw_hierarchy H, int level, int *agg, unsigned char *root
 {
     GW_API_BEGIN
     if (!H) fail(GW_ERR_ARG, "gw_hierarchy_export: null hierarchy");
-    Hier &hh = H->H;
+    Hier &hh = *H->h;
     if (level < 0 || level >= hh.L) fail(GW_ERR_ARG, "gw_hierarchy_export: level out of range");
     DeviceGuard g(hh.dev);
     cudaStream_t st = (cudaStream_t)stream;
@@ -479,10 +606,10 @@ int gw_profile_enable(gw_hierarchy H, int on)
 {
     GW_API_BEGIN
     if (!H) fail(GW_ERR_ARG, "gw_profile_enable: null hierarchy");
-    DeviceGuard g(H->H.dev);
-    if ((bool)on != H->H.prof_on) {
-        H->H.prof_on = on != 0;
-        drop_graphs(H->H);
+    DeviceGuard g(H->h->dev);
+    if ((bool)on != H->h->prof_on) {
+        H->h->prof_on = on != 0;
+        drop_graphs(*H->h);
     }
     GW_API_END
 }
@@ -491,7 +618,7 @@ int gw_profile_read(gw_hierarchy H, gw_profile *out, int reset)
 {
     GW_API_BEGIN
     if (!H || !out) fail(GW_ERR_ARG, "gw_profile_read: null argument");
-    Hier &h = H->H;
+    Hier &h = *H->h;
     memset(out, 0, sizeof *out);
     for (int k = 0; k < GW_PK_COUNT; ++k) {
         out->ms[k] = h.prof_ms[k];
@@ -525,7 +652,7 @@ void gw_hierarchy_free(gw_hierarchy H)
 {
     if (!H) return;
     try {
-        DeviceGuard g(H->H.dev);
+        DeviceGuard g(H->h->dev);
         delete H;
     } catch (...) {
     }

@@ -265,6 +265,7 @@ struct Hier {
 void drop_graphs(Hier &H);
 
 void build_hierarchy(Hier &H, cudaStream_t st);
+void refresh_level0(Hier &H, const DCSR &A, cudaStream_t st);
 void vcycle_enqueue(Hier &H, const double *r, double *z, Ctl *ctl, bool dot, cudaStream_t st);
 int pcg_run(Hier &H, double tol, int maxit, int *iters, double *relres, cudaStream_t st);
 

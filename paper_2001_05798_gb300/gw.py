@@ -22,7 +22,7 @@ GW_SMOOTH_JACOBI, GW_SMOOTH_CHEBYSHEV = 0, 1
 EXPORTS = ("gw_amg_opts_default", "gw_assemble", "gw_matrix_size", "gw_matrix_export", "gw_amg_setup",
            "gw_pcg_solve", "gw_vcycle", "gw_hierarchy_info", "gw_hierarchy_export", "gw_matrix_free",
            "gw_hierarchy_free", "gw_status_str", "gw_last_error", "gw_profile_enable", "gw_profile_read",
-           "gw_assemble_noalloc", "gw_adjoint_gradient", "gw_misfit")
+           "gw_assemble_noalloc", "gw_adjoint_gradient", "gw_misfit", "gw_hierarchy_shift")
 
 PK_NAMES = ("spmv", "update", "pre1", "pre2", "resid", "restrict", "l1down", "deep", "l1up", "prolong", "post1",
             "post2", "pupdate")
@@ -93,6 +93,7 @@ def load():
         "gw_assemble_noalloc": (i, [P(gw_grid), vp, vp, vp, P(gw_bc), vp, vp, vp, vp, vp, vp]),
         "gw_adjoint_gradient": (i, [P(gw_grid), vp, vp, vp, P(gw_bc), vp, vp, vp, vp]),
         "gw_misfit": (i, [i, vp, i, vp, vp, vp, vp, vp]),
+        "gw_hierarchy_shift": (i, [vp, vp, d, P(i), vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -276,6 +277,12 @@ class Hierarchy:
         if check and st not in (GW_OK, GW_ERR_NOT_CONVERGED):
             _check(st)
         return h, it.value, rel.value, st
+
+    def shift(self, s, delta=0.01, stream=None):
+        """Solve (C + diag(s)) from now on; returns True if the hierarchy was rebuilt."""
+        rb = ctypes.c_int()
+        _check(load().gw_hierarchy_shift(self.h, _ptr(s), float(delta), ctypes.byref(rb), _stream(stream)))
+        return bool(rb.value)
 
     def profile(self, on=True):
         _check(load().gw_profile_enable(self.h, int(bool(on))))

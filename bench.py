@@ -370,6 +370,52 @@ def run_adjoint(args):
     print(json.dumps(out), flush=True)
 
 
+def run_transient(args):
+    """Secondary workload: implicit transient steps (Eq. 2) on the 128^3 field.
+    One step = gw_hierarchy_shift + solve.  Small storage terms
+    (s = 0.005 C_ii) keep the cached hierarchy (level 0 refreshed); large ones
+    (s = 0.5 C_ii) trigger a rebuild.  Reports both step times."""
+    import torch
+
+    from paper_2001_05798_gb300 import build, gw
+
+    torch.cuda.set_device(0)
+    build.build()
+    gw.load()
+    p = make_problem()
+    n = SIDE ** 3
+    K = torch.from_numpy(p["Kx"]).cuda()
+    b = torch.empty(n, dtype=torch.float64, device="cuda")
+    A, _ = gw.gw_assemble(SIDE, SIDE, SIDE, K, K, K, p["bct"], p["bcv"], None, b_out=b)
+    rp, ci, v = A.export()
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    diag = torch.from_numpy(v[rows == ci].copy()).cuda()
+    H = gw.Hierarchy(A)
+    h = torch.zeros_like(b)
+    res = {}
+    for name, frac in (("reuse", 0.005), ("rebuild", 0.5)):
+        times, rebuilt = [], []
+        for k in range(max(args.warmup, 3) + args.steps):
+            s = diag * (frac * (1.0 + 0.1 * (k % 2)))
+            rhs = b + s * h
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rb = H.shift(s, delta=0.01)
+            h, it, rel, st = H.solve(rhs, tol=TOL)
+            torch.cuda.synchronize()
+            if k >= max(args.warmup, 3):
+                times.append((time.perf_counter() - t0) * 1e3)
+                rebuilt.append(rb)
+        res[name] = {"p50_ms": float(np.median(times)), "rebuilt": int(sum(rebuilt)), "steps": len(times),
+                     "iters": it}
+    out = {"metric": "implicit transient step (shift + solve) ms, cached vs rebuilt hierarchy",
+           "value": res["reuse"]["p50_ms"], "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "higher_is_better": False, "dtype": "f32 V-cycle + f64 CG", "data": "synthetic",
+           "config": {"workload": "128^3 lnK var 4 corr 8 seed 1; s = 0.005 C_ii (reuse, delta 0.01) or 0.5 C_ii "
+                                  "(rebuild), alternating +-10%, tol 1e-8"}, "transient": res}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -382,8 +428,9 @@ def main():
     ap.add_argument("--delta", type=float, default=0.1, help="reliable-update factor of the mixed form")
     ap.add_argument("--half-storage", type=int, default=0, help="FP16 storage of P, R and coarse operators (mixed)")
     ap.add_argument("--side", type=int, default=SIDE, help="grid side for profiling captures (default 128)")
-    ap.add_argument("--workload", choices=("solve", "adjoint"), default="solve",
-                    help="solve: the 128^3 benchmark (default); adjoint: the 96^3 sensitivity case")
+    ap.add_argument("--workload", choices=("solve", "adjoint", "transient"), default="solve",
+                    help="solve: the 128^3 benchmark (default); adjoint: the 96^3 sensitivity case; "
+                         "transient: implicit steps with a cached hierarchy")
     args = ap.parse_args()
     if args.side != SIDE:
         globals()["SIDE"] = args.side
@@ -394,6 +441,8 @@ def main():
         run_reference(args)
     elif args.workload == "adjoint":
         run_adjoint(args)
+    elif args.workload == "transient":
+        run_transient(args)
     else:
         run_ours(args)
 

@@ -416,6 +416,56 @@ def run_transient(args):
     print(json.dumps(out), flush=True)
 
 
+def run_serve(args):
+    """Secondary workload: the serving stream.  Requests with cubic grids of side
+    round(exp(U[ln 32, ln 160])), lnK variance U[0.5, 4], correlation length
+    U[4, 16] cells, field seed 1000 + r, tol 1e-8, admitted by a 120 GB HBM
+    budget.  A closed-loop pass measures the saturated throughput; requests
+    then arrive as a Poisson process at 0.7 of it.  Latency = arrival to result."""
+    import torch
+
+    from paper_2001_05798_gb300 import build, gw, serve, workload as wl
+
+    torch.cuda.set_device(0)
+    build.build()
+    gw.load()
+    reqs = wl.serving_requests(count=args.requests, seed=4)
+    warm = wl.serving_requests(count=8, seed=99)
+    srv = serve.Server(slots=args.slots, hbm_budget=120e9)
+    for f in [srv.submit(r) for r in warm]:
+        f.result()
+    # closed loop: everything queued at once
+    nclosed = min(len(reqs), max(16, args.requests // 10))
+    t0 = time.perf_counter()
+    for f in [srv.submit(r) for r in reqs[:nclosed]]:
+        f.result()
+    sat = nclosed / (time.perf_counter() - t0)
+    rate = 0.7 * sat
+    arrivals = wl.poisson_arrivals(len(reqs), rate, seed=4)
+    start = time.perf_counter()
+    futs = []
+    for r, a in zip(reqs, arrivals):
+        delay = start + a - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        futs.append(srv.submit(r, arrival=start + a))
+    outs = [f.result() for f in futs]
+    wall = max(o["done"] for o in outs) - start
+    srv.close()
+    lat = np.array([o["latency_s"] for o in outs]) * 1e3
+    out = {"metric": "serving stream of flow solves: solves/s and p50/p99 latency", "value": len(outs) / wall,
+           "unit": "solves/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32 V-cycle + f64 CG",
+           "data": "synthetic", "requests": len(outs), "slots": args.slots,
+           "config": {"workload": "cubic grids side log-uniform [32,160], lnK var U[0.5,4], corr U[4,16], seed 4, "
+                                  "field seed 1000+r, tol 1e-8, Poisson arrivals at 0.7 x closed-loop throughput, "
+                                  "HBM budget 120 GB"},
+           "p50_latency_ms": float(np.percentile(lat, 50)), "p99_latency_ms": float(np.percentile(lat, 99)),
+           "closed_loop_solves_per_s": sat, "arrival_rate": rate, "peak_inflight": srv.peak_inflight,
+           "peak_budget_in_use_gb": srv.peak_in_use / 1e9, "mean_iters": float(np.mean([o["iters"] for o in outs])),
+           "max_relres": float(max(o["relres"] for o in outs))}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -428,9 +478,11 @@ def main():
     ap.add_argument("--delta", type=float, default=0.1, help="reliable-update factor of the mixed form")
     ap.add_argument("--half-storage", type=int, default=0, help="FP16 storage of P, R and coarse operators (mixed)")
     ap.add_argument("--side", type=int, default=SIDE, help="grid side for profiling captures (default 128)")
-    ap.add_argument("--workload", choices=("solve", "adjoint", "transient"), default="solve",
+    ap.add_argument("--requests", type=int, default=2000, help="serving workload: number of requests")
+    ap.add_argument("--slots", type=int, default=6, help="serving workload: solves in flight")
+    ap.add_argument("--workload", choices=("solve", "adjoint", "transient", "serve"), default="solve",
                     help="solve: the 128^3 benchmark (default); adjoint: the 96^3 sensitivity case; "
-                         "transient: implicit steps with a cached hierarchy")
+                         "transient: implicit steps with a cached hierarchy; serve: the request stream")
     args = ap.parse_args()
     if args.side != SIDE:
         globals()["SIDE"] = args.side
@@ -443,6 +495,8 @@ def main():
         run_adjoint(args)
     elif args.workload == "transient":
         run_transient(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

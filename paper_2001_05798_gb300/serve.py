@@ -1,0 +1,130 @@
+"""Continuous batching of flow solves on one GPU.
+
+Requests (a grid and a conductivity field) arrive at any time.  The server
+keeps `slots` solves in flight, each on its own CUDA stream and host thread
+(the C ABI releases the Python lock, so their kernels overlap on the
+device), and admits the oldest waiting request as soon as a slot is free and
+its estimated device memory fits the HBM budget; a request that does not fit
+waits, and nothing behind it overtakes it.  Each request assembles its
+system, sets up its own hierarchy (resident for the request's lifetime),
+solves with the captured iteration graphs, and releases its memory.  All of
+it runs in libgw's kernels; results do not depend on what else is running,
+because solves share no device state and every reduction has a fixed order.
+"""
+import collections
+import concurrent.futures
+import threading
+import time
+
+import torch
+
+from . import gw
+from . import workload as wl
+
+
+class Server:
+    def __init__(self, slots=4, hbm_budget=120e9, device=0, tol=1e-8, maxit=500, bytes_per_cell=1500.0, **opts):
+        self.slots = slots
+        self.budget = float(hbm_budget)
+        self.device = device
+        self.tol, self.maxit, self.opts = tol, maxit, opts
+        self.bytes_per_cell = float(bytes_per_cell)
+        self.in_use = 0.0
+        self.pending = collections.deque()
+        self.cv = threading.Condition()
+        self.closed = False
+        self.peak_in_use = 0.0
+        self.peak_inflight = 0
+        self.inflight = 0
+        self.threads = [threading.Thread(target=self._worker, daemon=True) for _ in range(slots)]
+        for t in self.threads:
+            t.start()
+
+    def estimate(self, req):
+        return self.bytes_per_cell * req["side"] ** 3
+
+    def submit(self, req, arrival=None):
+        fut = concurrent.futures.Future()
+        with self.cv:
+            if self.estimate(req) > self.budget:
+                fut.set_exception(MemoryError("request %s needs more than the HBM budget" % req.get("id")))
+                return fut
+            self.pending.append((req, fut, time.perf_counter() if arrival is None else arrival))
+            self.cv.notify_all()
+        return fut
+
+    def close(self):
+        with self.cv:
+            self.closed = True
+            self.cv.notify_all()
+        for t in self.threads:
+            t.join()
+
+    def _admit(self):
+        # called with the lock held: the oldest request, if it fits
+        while True:
+            if self.pending:
+                req, fut, arr = self.pending[0]
+                need = self.estimate(req)
+                if need > self.budget:  # the estimate grew past the budget: fail it, do not wait forever
+                    self.pending.popleft()
+                    fut.set_exception(MemoryError("request %s needs more than the HBM budget" % req.get("id")))
+                    continue
+                if self.in_use + need <= self.budget:
+                    self.pending.popleft()
+                    self.in_use += need
+                    self.inflight += 1
+                    self.peak_in_use = max(self.peak_in_use, self.in_use)
+                    self.peak_inflight = max(self.peak_inflight, self.inflight)
+                    return req, fut, arr, need
+            elif self.closed:
+                return None
+            self.cv.wait()
+
+    def _worker(self):
+        torch.cuda.set_device(self.device)
+        stream = torch.cuda.Stream()
+        while True:
+            with self.cv:
+                item = self._admit()
+            if item is None:
+                return
+            req, fut, arrival, need = item
+            try:
+                with torch.cuda.stream(stream):
+                    out = self._solve(req, stream)
+                out["arrival"] = arrival
+                out["done"] = time.perf_counter()
+                out["latency_s"] = out["done"] - arrival
+                fut.set_result(out)
+            except Exception as e:  # the request fails alone; the server keeps going
+                fut.set_exception(e)
+            finally:
+                with self.cv:
+                    self.in_use -= need
+                    self.inflight -= 1
+                    self.cv.notify_all()
+
+    def _solve(self, req, stream):
+        s = req["side"]
+        n = s ** 3
+        t0 = time.perf_counter()
+        if "K" in req:
+            K = req["K"]
+        else:
+            K = torch.exp(wl.lnk_field_device(s, s, s, req["var"], req["corr"], req["seed"]))
+        b = torch.empty(n, dtype=torch.float64, device=K.device)
+        A, _ = gw.gw_assemble(s, s, s, K, K, K, (1, 1, 0, 0, 0, 0), (1.0, 0.0, 0, 0, 0, 0), None, b_out=b,
+                              stream=stream)
+        H = gw.Hierarchy(A, stream=stream, **self.opts)
+        used = sum(l["bytes"] for l in H.info()) + 16 * n
+        with self.cv:
+            self.bytes_per_cell = max(self.bytes_per_cell, 1.25 * used / n)
+        h = torch.empty_like(b)
+        t1 = time.perf_counter()
+        _, it, rel, st = H.solve(b, h, tol=self.tol, maxit=self.maxit, stream=stream)
+        t2 = time.perf_counter()
+        if st != gw.GW_OK:
+            raise gw.GwError(st, "request %s: relres %.3e after %d iterations" % (req.get("id"), rel, it))
+        del H, A
+        return dict(id=req.get("id"), n=n, h=h, iters=it, relres=rel, setup_s=t1 - t0, solve_s=t2 - t1)

@@ -119,3 +119,47 @@ def layered_wells_3d(nx=256, ny=256, nz=128, var=1.0, corr=(32.0, 32.0, 4.0), se
     return problem(nx, ny, nz, var=var, corr=corr, seed=seed, kz_ratio=kz_ratio,
                    bct=(0, 0, 0, 0, 0, DIRICHLET), bcv=(0, 0, 0, 0, 0, 0.0),
                    wells_count=wells_count, wells_seed=wells_seed, wells_rate=wells_rate)
+
+
+def lnk_field_device(nx, ny, nz, var, corr, seed, device="cuda"):
+    """The same circulant-embedding recipe as lnk_field, drawn on a torch
+    device (white noise from torch.Generator(device).manual_seed(seed)), for
+    request streams where thousands of fields are needed.  Returns a float64
+    tensor of nx*ny*nz values (C order (nz, ny, nx))."""
+    import torch
+
+    if np.isscalar(corr):
+        corr = (corr, corr, corr)
+    dims = (nz, ny, nx)
+    lam = (float(corr[2]), float(corr[1]), float(corr[0]))
+    m = tuple(1 if d == 1 else 2 * d for d in dims)
+    axes = []
+    for mi, li in zip(m, lam):
+        k = torch.arange(mi, dtype=torch.float64, device=device)
+        axes.append(torch.minimum(k, mi - k) / li)
+    r2 = axes[0][:, None, None] ** 2 + axes[1][None, :, None] ** 2 + axes[2][None, None, :] ** 2
+    eig = torch.fft.rfftn(var * torch.exp(-torch.sqrt(r2))).real.clamp_min_(0.0).sqrt_()
+    del r2
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    W = torch.randn(m, generator=gen, dtype=torch.float64, device=device)
+    f = torch.fft.irfftn(torch.fft.rfftn(W) * eig, s=m, dim=(0, 1, 2))
+    return f[:nz, :ny, :nx].contiguous().reshape(-1)
+
+
+def serving_requests(count=2000, seed=4, side_range=(32, 160), var_range=(0.5, 4.0), corr_range=(4.0, 16.0),
+                     field_seed0=1000):
+    """The request mix of the serving stream: side = round(exp(U[ln a, ln b])),
+    lnK variance ~ U[var_range], correlation length ~ U[corr_range], request r
+    drawing its field with seed field_seed0 + r."""
+    rng = np.random.default_rng(seed)
+    sides = np.rint(np.exp(rng.uniform(np.log(side_range[0]), np.log(side_range[1]), count))).astype(int)
+    var = rng.uniform(var_range[0], var_range[1], count)
+    corr = rng.uniform(corr_range[0], corr_range[1], count)
+    return [dict(id=r, side=int(sides[r]), var=float(var[r]), corr=float(corr[r]), seed=field_seed0 + r)
+            for r in range(count)]
+
+
+def poisson_arrivals(count, rate, seed=4):
+    """Arrival times (s) of a Poisson process of the given rate."""
+    return np.cumsum(np.random.default_rng(seed + 1).exponential(1.0 / rate, count))

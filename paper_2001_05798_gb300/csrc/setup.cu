@@ -547,6 +547,7 @@ void setup_transpose(const DCSR &P, DCSR &R, cudaStream_t st)
 // take the entries of Rm's row k, which have distinct columns, so every
 // output entry receives its terms in ascending k.
 constexpr int SG_HMAX = 8192;
+constexpr int SG_SMEM_MAX = 96 << 10;  // per block: W warps x 12 bytes x H <= 96 KB
 
 __global__ void k_sg_bound(int nr, int ncol, const int *__restrict__ lrp, const int *__restrict__ lci,
                            const int *__restrict__ rrp, int *__restrict__ maxub)
@@ -680,8 +681,12 @@ void setup_spgemm(const DCSR &L, const DCSR &Rm, DCSR &C, cudaStream_t st)
     const size_t per_warp_num = (size_t)H * 12;
     int W = (int)std::max<size_t>(1, std::min<size_t>(8, (96u << 10) / per_warp_num));
     const size_t smem_sym = (size_t)W * H * sizeof(int), smem_num = (size_t)W * per_warp_num;
-    GW_CUDA(cudaFuncSetAttribute(k_sg_symbolic, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_sym));
-    GW_CUDA(cudaFuncSetAttribute(k_sg_numeric, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_num));
+    // The attribute is global to the kernel, and setups may run concurrently on
+    // several threads: always set the same value, the largest any launch uses.
+    GW_CUDA(cudaFuncSetAttribute(k_sg_symbolic, cudaFuncAttributeMaxDynamicSharedMemorySize, SG_SMEM_MAX));
+    GW_CUDA(cudaFuncSetAttribute(k_sg_numeric, cudaFuncAttributeMaxDynamicSharedMemorySize, SG_SMEM_MAX));
+    if (smem_sym > (size_t)SG_SMEM_MAX || smem_num > (size_t)SG_SMEM_MAX)
+        fail(GW_ERR_SETUP, "SpGEMM shared memory %zu exceeds %d", std::max(smem_sym, smem_num), SG_SMEM_MAX);
     C.nr = L.nr;
     C.nc = Rm.nc;
     C.rp.alloc((size_t)C.nr + 1);

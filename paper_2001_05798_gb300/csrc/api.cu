@@ -60,7 +60,7 @@ Hier::~Hier()
 {
     drop_graphs(*this);
     if (cap) cudaStreamDestroy(cap);
-    if (ctl_host) cudaFreeHost(ctl_host);
+    if (ctl_host) host_free(ctl_host);
 }
 
 __global__ void k_make_dw(int n, const double *__restrict__ d, double scale, float *__restrict__ of,
@@ -261,7 +261,7 @@ void build_hierarchy(Hier &H, cudaStream_t st)
     H.part.alloc(2 * (size_t)RED_MAX_BLOCKS);
     H.ctl.alloc(1);
     GW_CUDA(cudaMemsetAsync(H.ctl.p, 0, sizeof(Ctl), st));
-    GW_CUDA(cudaMallocHost((void **)&H.ctl_host, sizeof(Ctl)));
+    GW_CUDA(host_malloc((void **)&H.ctl_host, sizeof(Ctl)));
     memset(H.ctl_host, 0, sizeof(Ctl));
     H.info[0].bytes += f64 ? 7LL * n * 8 : 2LL * n * 8 + 6LL * n * 4;
     GW_CUDA(cudaStreamSynchronize(st));

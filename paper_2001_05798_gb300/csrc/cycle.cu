@@ -1529,6 +1529,7 @@ static cudaGraphExec_t capture(Hier &H, F body, long long *nkernels)
 {
     if (!H.cap) GW_CUDA(cudaStreamCreateWithFlags(&H.cap, cudaStreamNonBlocking));
     cudaGraph_t g = nullptr;
+    CaptureScope scope;  // no allocation or free of this library runs meanwhile
     GW_CUDA(cudaStreamBeginCapture(H.cap, cudaStreamCaptureModeThreadLocal));
     try {
         body(H.cap);

@@ -35,6 +35,22 @@ const char *last_error_cstr();
 
 #define GW_LAUNCH_CHECK() GW_CUDA(cudaGetLastError())
 
+// ------------------------------------------------- allocation vs capture --
+// cudaFree (and cudaFreeHost) synchronise the device, which invalidates a
+// graph capture that another thread has in progress.  Every allocation and
+// free of the library therefore waits while a capture is in progress, and a
+// capture waits for allocations in flight.
+cudaError_t dev_malloc(void **p, size_t bytes);
+void dev_free(void *p);
+cudaError_t host_malloc(void **p, size_t bytes);
+void host_free(void *p);
+struct CaptureScope {
+    CaptureScope();
+    ~CaptureScope();
+    CaptureScope(const CaptureScope &) = delete;
+    CaptureScope &operator=(const CaptureScope &) = delete;
+};
+
 // ---------------------------------------------------------- device buffers --
 template <class T>
 struct DBuf {
@@ -46,11 +62,11 @@ struct DBuf {
     {
         release();
         n = n_;
-        if (n) GW_CUDA(cudaMalloc((void **)&p, n * sizeof(T)));
+        if (n) GW_CUDA(dev_malloc((void **)&p, n * sizeof(T)));
     }
     void release()
     {
-        if (p) cudaFree(p);
+        if (p) dev_free(p);
         p = nullptr;
         n = 0;
     }

@@ -1,6 +1,9 @@
 // util.cu -- error plumbing, device scan and small host helpers of libgw.
 #include <stdarg.h>
 
+#include <condition_variable>
+#include <mutex>
+
 #include "gw_internal.cuh"
 
 namespace gw {
@@ -19,6 +22,54 @@ const char *last_error_cstr() { return g_last_error.c_str(); }
     vsnprintf(buf, sizeof buf, fmt, ap);
     va_end(ap);
     throw Error{code, std::string(buf)};
+}
+
+// ------------------------------------------------- allocation vs capture --
+static std::mutex g_alloc_mu;
+static std::condition_variable g_alloc_cv;
+static int g_captures = 0;
+
+cudaError_t dev_malloc(void **p, size_t bytes)
+{
+    std::unique_lock<std::mutex> lk(g_alloc_mu);
+    g_alloc_cv.wait(lk, [] { return g_captures == 0; });
+    return cudaMalloc(p, bytes);
+}
+
+void dev_free(void *p)
+{
+    std::unique_lock<std::mutex> lk(g_alloc_mu);
+    g_alloc_cv.wait(lk, [] { return g_captures == 0; });
+    cudaFree(p);
+}
+
+cudaError_t host_malloc(void **p, size_t bytes)
+{
+    std::unique_lock<std::mutex> lk(g_alloc_mu);
+    g_alloc_cv.wait(lk, [] { return g_captures == 0; });
+    return cudaMallocHost(p, bytes);
+}
+
+void host_free(void *p)
+{
+    std::unique_lock<std::mutex> lk(g_alloc_mu);
+    g_alloc_cv.wait(lk, [] { return g_captures == 0; });
+    cudaFreeHost(p);
+}
+
+CaptureScope::CaptureScope()
+{
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    ++g_captures;
+}
+
+CaptureScope::~CaptureScope()
+{
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        --g_captures;
+    }
+    g_alloc_cv.notify_all();
 }
 
 // ------------------------------------------------------------------ scan --

@@ -85,6 +85,8 @@ def _load():
         "or_shift_csr": (_vp, [_vp, _f64p]),
         "or_reuse_ok": (ctypes.c_int, [_vp, _f64p, _vp, ctypes.c_double]),
         "or_h_refresh_level0": (None, [_vp, _vp]),
+        "or_darcy_flux": (None, [ctypes.c_int] * 3 + [ctypes.c_double] * 3 + [_f64p] * 3 +
+                          [_i32p, _f64p, _f64p, _f64p, _f64p, _f64p]),
         "or_cg_plain": (ctypes.c_int, [_vp, _f64p, _f64p, ctypes.c_double, ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
     }
@@ -319,6 +321,21 @@ def misfit(h, obs, hobs):
     J = _load().or_misfit(h.size, h, len(obs), np.ascontiguousarray(obs, np.int32),
                           np.ascontiguousarray(hobs, np.float64), d.ctypes.data_as(ctypes.c_void_p))
     return J, d
+
+
+def darcy_flux(nx, ny, nz, Kx, h, Ky=None, Kz=None, bct=(1, 1, 0, 0, 0, 0), bcv=(1.0, 0.0, 0, 0, 0, 0),
+               spacing=(1.0, 1.0, 1.0)):
+    """Darcy velocities on the x, y, z faces (staggered: (nx+1)*ny*nz, ...)."""
+    Kx = np.ascontiguousarray(Kx, dtype=np.float64).ravel()
+    Ky = Kx if Ky is None else np.ascontiguousarray(Ky, dtype=np.float64).ravel()
+    Kz = Kx if Kz is None else np.ascontiguousarray(Kz, dtype=np.float64).ravel()
+    vx = np.empty((nx + 1) * ny * nz)
+    vy = np.empty(nx * (ny + 1) * nz)
+    vz = np.empty(nx * ny * (nz + 1))
+    _load().or_darcy_flux(nx, ny, nz, float(spacing[0]), float(spacing[1]), float(spacing[2]), Kx, Ky, Kz,
+                          np.asarray(bct, np.int32), np.asarray(bcv, np.float64),
+                          np.ascontiguousarray(h, np.float64), vx, vy, vz)
+    return vx, vy, vz
 
 
 def shift(C, s):

@@ -595,3 +595,30 @@ def test_transient_step_with_reused_hierarchy_solves_the_shifted_system(frac):
     assert st == 0 and rel <= 1e-12
     ref = np.linalg.solve(A.dense(), rhs)
     assert np.linalg.norm(x - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+# ------------------------------------------------------------ face fluxes --
+def test_darcy_flux_uniform_for_linear_head():
+    nx, ny, nz = 8, 5, 3
+    K = 2.5
+    A, b = oracle.assemble(nx, ny, nz, np.full(nx * ny * nz, K), spacing=(2.0, 1.0, 0.5))
+    h = np.linalg.solve(A.dense(), b)
+    vx, vy, vz = oracle.darcy_flux(nx, ny, nz, np.full(nx * ny * nz, K), h, spacing=(2.0, 1.0, 0.5))
+    # Darcy: v = -K dh/dx with h falling from 1 to 0 over nx * dx
+    np.testing.assert_allclose(vx, K / (nx * 2.0), rtol=1e-12)
+    np.testing.assert_allclose(vy, 0.0, atol=1e-14)
+    np.testing.assert_allclose(vz, 0.0, atol=1e-14)
+
+
+def test_darcy_flux_balances_sources_per_cell():
+    p = wl.problem(9, 7, 6, var=3.0, corr=2.0, seed=6, bct=(1, 0, 0, 1, 0, 1), bcv=(1.0, 0, 0, 0.2, 0, -0.4),
+                   wells_count=3, wells_seed=4)
+    nx, ny, nz = 9, 7, 6
+    A, b = asm(p)
+    h = np.linalg.solve(A.dense(), b)
+    vx, vy, vz = oracle.darcy_flux(nx, ny, nz, p["Kx"], h, p["Ky"], p["Kz"], p["bct"], p["bcv"])
+    vx = vx.reshape(nz, ny, nx + 1)
+    vy = vy.reshape(nz, ny + 1, nx)
+    vz = vz.reshape(nz + 1, ny, nx)
+    out = (vx[:, :, 1:] - vx[:, :, :-1]) + (vy[:, 1:, :] - vy[:, :-1, :]) + (vz[1:] - vz[:-1])
+    np.testing.assert_allclose(out.ravel(), p["q"], atol=1e-10)

@@ -416,6 +416,65 @@ def run_transient(args):
     print(json.dumps(out), flush=True)
 
 
+def run_many(args):
+    """Secondary workload: k = 8 right-hand sides (the benchmark's b and seven
+    well scenarios of 6 random wells each, rate U[-1e-3, 1e-3]) on one 128^3
+    hierarchy with gw_pcg_solve_many, from device and from pinned host
+    buffers; plus gw_darcy_flux on the solved heads.  Setup excluded."""
+    import torch
+
+    from paper_2001_05798_gb300 import build, gw, workload as wl
+
+    torch.cuda.set_device(0)
+    build.build()
+    gw.load()
+    p = make_problem()
+    n, k = SIDE ** 3, 8
+    K = torch.from_numpy(p["Kx"]).cuda()
+    b = torch.empty(n, dtype=torch.float64, device="cuda")
+    A, _ = gw.gw_assemble(SIDE, SIDE, SIDE, K, K, K, p["bct"], p["bcv"], None, b_out=b)
+    H = gw.Hierarchy(A)
+    rng = np.random.default_rng(11)
+    B = b.repeat(k, 1)
+    for c in range(1, k):
+        B[c, torch.from_numpy(wl.cells(n, 6, 20 + c)).cuda()] += torch.from_numpy(rng.uniform(-1e-3, 1e-3, 6)).cuda()
+    X = torch.empty_like(B)
+    Bh, Xh = B.cpu().pin_memory(), torch.empty(B.shape, dtype=torch.float64).pin_memory()
+    v = [torch.empty(m, dtype=torch.float64, device="cuda") for m in
+         ((SIDE + 1) * SIDE * SIDE, SIDE * (SIDE + 1) * SIDE, SIDE * SIDE * (SIDE + 1))]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    res = {}
+    for name, (src, dst) in (("device", (B, X)), ("host", (Bh, Xh))):
+        times = []
+        for s in range(args.warmup + args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, its, rels, st = H.solve_many(src, dst, tol=TOL)
+            torch.cuda.synchronize()
+            if s >= args.warmup:
+                times.append((time.perf_counter() - t0) * 1e3)
+        assert st == gw.GW_OK and max(rels) <= TOL
+        res[name] = {"p50_ms": float(np.median(times)), "iters": its, "max_relres": max(rels)}
+    ftimes = []
+    for s in range(args.warmup + args.steps):
+        ev[0].record()
+        gw.gw_darcy_flux(SIDE, SIDE, SIDE, K, X[0], *v, bct=p["bct"], bcv=p["bcv"])
+        ev[1].record()
+        torch.cuda.synchronize()
+        if s >= args.warmup:
+            ftimes.append(ev[0].elapsed_time(ev[1]))
+    fms = float(np.median(ftimes))
+    fbytes = 8.0 * (2 * n + sum(x.numel() for x in v))  # K and h read once, three face arrays written
+    out = {"metric": "right-hand sides per second on one resident hierarchy (gw_pcg_solve_many)",
+           "value": k / (res["device"]["p50_ms"] * 1e-3), "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "higher_is_better": True, "dtype": "f32 V-cycle + f64 CG", "data": "synthetic",
+           "config": {"workload": "128^3 lnK var 4 corr 8 seed 1; k = 8 right-hand sides (b and 7 six-well "
+                                  "scenarios), tol 1e-8, setup excluded"},
+           "many": res, "host_solves_per_s": k / (res["host"]["p50_ms"] * 1e-3),
+           "darcy_flux": {"ms": fms, "algorithmic_GBps": fbytes / (fms * 1e-3) / 1e9}}
+    print(json.dumps(out), flush=True)
+
+
 def run_serve(args):
     """Secondary workload: the serving stream.  Requests with cubic grids of side
     round(exp(U[ln 32, ln 160])), lnK variance U[0.5, 4], correlation length
@@ -480,9 +539,10 @@ def main():
     ap.add_argument("--side", type=int, default=SIDE, help="grid side for profiling captures (default 128)")
     ap.add_argument("--requests", type=int, default=2000, help="serving workload: number of requests")
     ap.add_argument("--slots", type=int, default=6, help="serving workload: solves in flight")
-    ap.add_argument("--workload", choices=("solve", "adjoint", "transient", "serve"), default="solve",
+    ap.add_argument("--workload", choices=("solve", "adjoint", "transient", "serve", "many"), default="solve",
                     help="solve: the 128^3 benchmark (default); adjoint: the 96^3 sensitivity case; "
-                         "transient: implicit steps with a cached hierarchy; serve: the request stream")
+                         "transient: implicit steps with a cached hierarchy; serve: the request stream; "
+                         "many: several right-hand sides on one hierarchy, and face fluxes")
     args = ap.parse_args()
     if args.side != SIDE:
         globals()["SIDE"] = args.side
@@ -497,6 +557,8 @@ def main():
         run_transient(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "many":
+        run_many(args)
     else:
         run_ours(args)
 

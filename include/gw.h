@@ -255,6 +255,34 @@ int gw_pcg_solve(gw_hierarchy H, const double *b, double *h, double tol, int max
  */
 int gw_hierarchy_shift(gw_hierarchy H, const double *s, double delta, int *rebuilt, void *stream);
 
+/*
+ * gw_pcg_solve_many -- k right-hand sides on one hierarchy.  Systems that
+ * share a matrix reuse its factorisation or preconditioner (Introduction,
+ * on the dual delineation approach); here the shared matrix is the flow
+ * operator C, e.g. well or boundary scenarios, or forward and adjoint
+ * solves.  B and X are n x k, column-major
+ * (column c at B + c*n), host or device; iters and relres receive k values
+ * (host, may be NULL).  The columns are solved one after another on the
+ * resident hierarchy and its captured iteration graphs, each to the true
+ * relative residual tol.  Returns GW_OK, or the first failing status with
+ * every column still solved as far as it went.
+ */
+int gw_pcg_solve_many(gw_hierarchy H, int k, const double *B, double *X, double tol, int maxit, int *iters,
+                      double *relres, void *stream);
+
+/*
+ * gw_darcy_flux -- Darcy velocities on every face, from the heads: the
+ * velocity field of the advective transport problem (Eq. 1).  Staggered
+ * layout: vx has (nx+1)*ny*nz entries (face xf = 0..nx of row (y,z) at
+ * xf + (nx+1)(y + ny z)), vy nx*(ny+1)*nz, vz nx*ny*(nz+1); positive along
+ * +x, +y, +z.  An interior face carries T (h_a - h_b)/A_f (T as in
+ * gw_assemble, a the lower cell, A_f the face area), a Dirichlet face uses
+ * T_b and its head, a no-flow face 0.  All arrays device memory.
+ * Asynchronous on stream.  Errors: GW_ERR_ARG.
+ */
+int gw_darcy_flux(const gw_grid *grid, const double *Kx, const double *Ky, const double *Kz, const gw_bc *bc,
+                  const double *h, double *vx, double *vy, double *vz, void *stream);
+
 /* Applies one V-cycle z = M^-1 r (from a zero initial guess) with the
  * hierarchy's precision; r and z are n doubles on the device. */
 int gw_vcycle(gw_hierarchy H, const double *r, double *z, void *stream);

@@ -489,6 +489,35 @@ int gw_pcg_solve(gw_hierarchy H, const double *b, double *h, double tol, int max
     GW_API_END
 }
 
+int gw_pcg_solve_many(gw_hierarchy H, int k, const double *B, double *X, double tol, int maxit, int *iters,
+                      double *relres, void *stream)
+{
+    int worst = GW_OK;
+    GW_API_BEGIN
+    if (!H || !B || !X || k < 1) fail(GW_ERR_ARG, "gw_pcg_solve_many: bad argument");
+    if (!(tol > 0.0) || !isfinite(tol) || maxit < 1) fail(GW_ERR_ARG, "gw_pcg_solve_many: need tol > 0 and maxit >= 1");
+    Hier &hh = *H->h;
+    DeviceGuard g(hh.dev);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t n = (size_t)hh.n, bytes = n * sizeof(double);
+    for (int c = 0; c < k; ++c) {
+        int it = 0;
+        double rel = 0.0;
+        GW_CUDA(cudaMemcpyAsync(hh.b.p, B + (size_t)c * n, bytes, cudaMemcpyDefault, st));
+        const int status = pcg_run(hh, tol, maxit, &it, &rel, st);
+        GW_CUDA(cudaMemcpyAsync(X + (size_t)c * n, hh.x.p, bytes, cudaMemcpyDefault, st));
+        if (iters) iters[c] = it;
+        if (relres) relres[c] = rel;
+        if (status != GW_OK && worst == GW_OK) worst = status;
+    }
+    GW_CUDA(cudaStreamSynchronize(st));
+    if (worst != GW_OK) {
+        gw::set_last_error("gw_pcg_solve_many: a right-hand side did not converge");
+        return worst;
+    }
+    GW_API_END
+}
+
 int gw_hierarchy_shift(gw_hierarchy H, const double *s, double delta, int *rebuilt, void *stream)
 {
     GW_API_BEGIN

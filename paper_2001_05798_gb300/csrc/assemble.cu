@@ -210,6 +210,57 @@ __global__ void k_misfit(int nobs, const double *__restrict__ h, const int *__re
     }
 }
 
+// ------------------------------------------------------ Darcy face fluxes --
+// Velocity on every face (staggered layout: face f = 0..n_d along axis d),
+// positive along the axis: K_harm (h_a - h_b) / spacing between cells a < b
+// (T / A_f with T of the assembly), 2 K (h_face - h) / spacing on Dirichlet
+// faces, 0 on no-flow faces.  One thread per cell writes the lower face of
+// each axis, and the upper one where the cell is last along that axis, so K
+// and h are read once and every face array is written in row order.  One
+// division per face: 2 K_a K_b (h_a - h_b) inv / (K_a + K_b), inv = 1/spacing.
+struct FluxGeom {
+    int n[3];
+    double inv[3];    // 1 / spacing per axis
+    int bct[6];
+    double bcv[6];
+};
+
+__global__ void k_darcy(FluxGeom G, const double *__restrict__ Kx, const double *__restrict__ Ky,
+                        const double *__restrict__ Kz, const double *__restrict__ h, double *__restrict__ vx,
+                        double *__restrict__ vy, double *__restrict__ vz)
+{
+    const int nx = G.n[0], ny = G.n[1], nz = G.n[2];
+    const int ncell = nx * ny * nz;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncell; i += gridDim.x * blockDim.x) {
+        const int x = i % nx, yz = i / nx, y = yz % ny, z = yz / ny;
+        const int c[3] = {x, y, z};
+        const int stride[3] = {1, nx, nx * ny};
+        const double *K[3] = {Kx, Ky, Kz};
+        double *v[3] = {vx, vy, vz};
+        const double hi = h[i];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const double Ki = K[d][i];
+            // face index of this cell's lower face along d
+            const long long lo = d == 0 ? x + (long long)(nx + 1) * yz
+                               : d == 1 ? x + (long long)nx * (y + (long long)(ny + 1) * z)
+                                        : (long long)i;
+            double out = 0.0;
+            if (c[d] > 0) {
+                const double Ka = K[d][i - stride[d]];
+                out = (2.0 * Ka * Ki * (h[i - stride[d]] - hi) * G.inv[d]) / (Ka + Ki);
+            } else if (G.bct[2 * d] == GW_DIRICHLET) {
+                out = 2.0 * Ki * (G.bcv[2 * d] - hi) * G.inv[d];
+            }
+            v[d][lo] = out;
+            if (c[d] == G.n[d] - 1) {
+                const long long up = lo + (d == 0 ? 1 : d == 1 ? nx : (long long)nx * ny);
+                v[d][up] = G.bct[2 * d + 1] == GW_DIRICHLET ? 2.0 * Ki * (hi - G.bcv[2 * d + 1]) * G.inv[d] : 0.0;
+            }
+        }
+    }
+}
+
 }  // namespace gw
 
 // ------------------------------------------- assembly without allocations --
@@ -378,6 +429,48 @@ extern "C" int gw_misfit(int n, const double *h, int nobs, const int *obs, const
         GW_LAUNCH_CHECK();
         GW_CUDA(cudaMemcpyAsync(J, jd.p, sizeof(double), cudaMemcpyDefault, st));
         GW_CUDA(cudaStreamSynchronize(st));
+    } catch (const Error &e) {
+        set_last_error(e.msg.c_str());
+        return e.code;
+    } catch (...) {
+        set_last_error("unexpected failure");
+        return GW_ERR_CUDA;
+    }
+    return GW_OK;
+}
+
+extern "C" int gw_darcy_flux(const gw_grid *grid, const double *Kx, const double *Ky, const double *Kz,
+                             const gw_bc *bc, const double *h, double *vx, double *vy, double *vz, void *stream)
+{
+    using namespace gw;
+    try {
+        if (!grid || !Kx || !bc || !h || !vx || !vy || !vz) fail(GW_ERR_ARG, "gw_darcy_flux: null argument");
+        const int nx = grid->nx, ny = grid->ny, nz = grid->nz;
+        if (nx < 1 || ny < 1 || nz < 1) fail(GW_ERR_ARG, "gw_darcy_flux: grid sizes must be >= 1");
+        const double *K[3] = {Kx, Ky ? Ky : Kx, Kz ? Kz : Kx};
+        double *v[3] = {vx, vy, vz};
+        const void *ptrs[7] = {K[0], K[1], K[2], h, vx, vy, vz};
+        for (int k = 0; k < 7; ++k)
+            if (!is_device_ptr(ptrs[k])) fail(GW_ERR_ARG, "gw_darcy_flux: arrays must be device memory");
+        const double sp[3] = {grid->dx, grid->dy, grid->dz};
+        FluxGeom G;
+        for (int d = 0; d < 3; ++d) {
+            if (!(sp[d] > 0.0) || !isfinite(sp[d])) fail(GW_ERR_ARG, "gw_darcy_flux: spacings must be finite and > 0");
+            G.inv[d] = 1.0 / sp[d];
+        }
+        G.n[0] = nx;
+        G.n[1] = ny;
+        G.n[2] = nz;
+        for (int f = 0; f < 6; ++f) {
+            G.bct[f] = bc->type[f];
+            G.bcv[f] = bc->value[f];
+        }
+        if ((long long)nx * ny * nz > 0x7fffffffLL) fail(GW_ERR_ARG, "gw_darcy_flux: more than 2^31 - 1 cells");
+        cudaStream_t st = (cudaStream_t)stream;
+        const long long n = (long long)nx * ny * nz;
+        const int gb = (int)std::min<long long>((n + 255) / 256, 152LL * 8);
+        k_darcy<<<gb, 256, 0, st>>>(G, K[0], K[1], K[2], h, v[0], v[1], v[2]);
+        GW_LAUNCH_CHECK();
     } catch (const Error &e) {
         set_last_error(e.msg.c_str());
         return e.code;

@@ -22,7 +22,8 @@ GW_SMOOTH_JACOBI, GW_SMOOTH_CHEBYSHEV = 0, 1
 EXPORTS = ("gw_amg_opts_default", "gw_assemble", "gw_matrix_size", "gw_matrix_export", "gw_amg_setup",
            "gw_pcg_solve", "gw_vcycle", "gw_hierarchy_info", "gw_hierarchy_export", "gw_matrix_free",
            "gw_hierarchy_free", "gw_status_str", "gw_last_error", "gw_profile_enable", "gw_profile_read",
-           "gw_assemble_noalloc", "gw_adjoint_gradient", "gw_misfit", "gw_hierarchy_shift")
+           "gw_assemble_noalloc", "gw_adjoint_gradient", "gw_misfit", "gw_hierarchy_shift",
+           "gw_pcg_solve_many", "gw_darcy_flux")
 
 PK_NAMES = ("spmv", "update", "pre1", "pre2", "resid", "restrict", "l1down", "deep", "l1up", "prolong", "post1",
             "post2", "pupdate")
@@ -94,6 +95,8 @@ def load():
         "gw_adjoint_gradient": (i, [P(gw_grid), vp, vp, vp, P(gw_bc), vp, vp, vp, vp]),
         "gw_misfit": (i, [i, vp, i, vp, vp, vp, vp, vp]),
         "gw_hierarchy_shift": (i, [vp, vp, d, P(i), vp]),
+        "gw_pcg_solve_many": (i, [vp, i, vp, vp, d, i, vp, vp, vp]),
+        "gw_darcy_flux": (i, [P(gw_grid), vp, vp, vp, P(gw_bc), vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -231,6 +234,15 @@ def gw_misfit(h, obs, hobs, dJdh=None, stream=None):
     return J.value
 
 
+def gw_darcy_flux(nx, ny, nz, Kx, h, vx, vy, vz, Ky=None, Kz=None, bct=(1, 1, 0, 0, 0, 0),
+                  bcv=(1.0, 0.0, 0, 0, 0, 0), spacing=(1.0, 1.0, 1.0), stream=None):
+    """Darcy velocities on the staggered faces (include/gw.h: gw_darcy_flux); device arrays."""
+    g, bc = _grid_bc(nx, ny, nz, bct, bcv, spacing)
+    _check(load().gw_darcy_flux(ctypes.byref(g), _ptr(Kx), _ptr(Ky), _ptr(Kz), ctypes.byref(bc), _ptr(h), _ptr(vx),
+                                _ptr(vy), _ptr(vz), _stream(stream)))
+    return vx, vy, vz
+
+
 class Hierarchy:
     """AMG hierarchy handle (include/gw.h: gw_amg_setup); keeps its matrix alive."""
 
@@ -277,6 +289,19 @@ class Hierarchy:
         if check and st not in (GW_OK, GW_ERR_NOT_CONVERGED):
             _check(st)
         return h, it.value, rel.value, st
+
+    def solve_many(self, B, X=None, tol=1e-8, maxit=500, stream=None):
+        """k right-hand sides (columns of the n x k column-major B, i.e. rows of a (k, n) array)."""
+        k = B.shape[0]
+        if X is None:
+            X = np.empty_like(B) if isinstance(B, np.ndarray) else B.new_empty(B.shape)
+        its = (ctypes.c_int * k)()
+        rels = (ctypes.c_double * k)()
+        st = load().gw_pcg_solve_many(self.h, k, _ptr(B), _ptr(X), float(tol), int(maxit), its, rels,
+                                      _stream(stream))
+        if st not in (GW_OK, GW_ERR_NOT_CONVERGED):
+            _check(st)
+        return X, list(its), list(rels), st
 
     def shift(self, s, delta=0.01, stream=None):
         """Solve (C + diag(s)) from now on; returns True if the hierarchy was rebuilt."""

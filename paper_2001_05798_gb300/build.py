@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libgw.so")
 OBJ = os.path.join(HERE, "_build")
-SOURCES = ["util.cu", "assemble.cu", "setup.cu", "cycle.cu", "api.cu"]
+SOURCES = ["util.cu", "assemble.cu", "setup.cu", "cycle.cu", "block.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off", "-I" + os.path.join(ROOT, "include"),
          "-I" + CSRC]

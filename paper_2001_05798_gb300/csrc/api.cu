@@ -59,6 +59,7 @@ struct DevIn {
 Hier::~Hier()
 {
     drop_graphs(*this);
+    block_free(blk);
     if (cap) cudaStreamDestroy(cap);
     if (ctl_host) host_free(ctl_host);
 }
@@ -500,6 +501,14 @@ int gw_pcg_solve_many(gw_hierarchy H, int k, const double *B, double *X, double 
     DeviceGuard g(hh.dev);
     cudaStream_t st = (cudaStream_t)stream;
     const size_t n = (size_t)hh.n, bytes = n * sizeof(double);
+    if (k > 1 && block_supported(hh)) {
+        worst = block_solve(hh, k, B, X, tol, maxit, iters, relres, st);
+        if (worst != GW_OK) {
+            gw::set_last_error("gw_pcg_solve_many: a right-hand side did not converge");
+            return worst;
+        }
+        return GW_OK;
+    }
     for (int c = 0; c < k; ++c) {
         int it = 0;
         double rel = 0.0;

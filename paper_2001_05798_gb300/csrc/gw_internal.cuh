@@ -236,6 +236,8 @@ struct CycLevel {
     double c0 = 0.0, c1[8] = {0}, c2[8] = {0};  // Chebyshev coefficients
 };
 
+struct BlockState;  // interleaved multi-right-hand-side solver state (block.cu)
+
 struct Hier {
     int dev = 0;
     gw_amg_opts o{};
@@ -275,6 +277,7 @@ struct Hier {
     double prof_ms[GW_PK_COUNT] = {0}, prof_b[GW_PK_COUNT] = {0};
     long long prof_cnt[GW_PK_COUNT] = {0};
     long long launches = 0, solves = 0;
+    BlockState *blk = nullptr;  // created by the first interleaved solve
     ~Hier();
 };
 
@@ -284,5 +287,13 @@ void build_hierarchy(Hier &H, cudaStream_t st);
 void refresh_level0(Hier &H, const DCSR &A, cudaStream_t st);
 void vcycle_enqueue(Hier &H, const double *r, double *z, Ctl *ctl, bool dot, cudaStream_t st);
 int pcg_run(Hier &H, double tol, int maxit, int *iters, double *relres, cudaStream_t st);
+
+// k right-hand sides (column-major, leading dimension n, host or device)
+// solved in interleaved blocks of up to 8 columns; mixed form only.
+bool block_supported(const Hier &H);
+int block_solve(Hier &H, int k, const double *B, double *X, double tol, int maxit, int *iters, double *relres,
+                cudaStream_t st);
+void block_drop_graphs(BlockState *s);
+void block_free(BlockState *s);
 
 }  // namespace gw

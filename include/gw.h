@@ -82,6 +82,9 @@ typedef enum {
 
 enum { GW_SMOOTH_JACOBI = 0, GW_SMOOTH_CHEBYSHEV = 1 };
 
+/* Bits of gw_amg_opts.half_storage. */
+enum { GW_HALF_TRANSFER = 1, GW_HALF_FINE = 2 };
+
 /* Setup and cycle options (gw_amg_opts_default fills the defaults). */
 typedef struct {
     double theta;        /* strength threshold on level 0, halved per level (0.04) */
@@ -93,8 +96,12 @@ typedef struct {
     uint64_t seed;       /* seed of the MIS-2 priorities (0x5EED) */
     int prec;            /* gw_prec (GW_PREC_MIXED32) */
     double delta;        /* mixed form: reliable update when the FP32 residual fell by this factor (0.1) */
-    int half_storage;    /* mixed form: keep P, R and the coarse operators as FP16 values with 16-bit
-                            column offsets, coarse operators scaled to D^-1/2 A D^-1/2 (0) */
+    int half_storage;    /* mixed form, bit mask (0):
+                            GW_HALF_TRANSFER: P, R and the coarse operators as FP16 values with
+                              16-bit column offsets, coarse operators scaled to D^-1/2 A D^-1/2;
+                            GW_HALF_FINE: the V-cycle's level-0 stencil with BF16 couplings and an
+                              FP32 diagonal corrected so that rows keep their sums (CG's own
+                              products stay FP32) */
 } gw_amg_opts;
 
 /* Per-level statistics in the columns of the paper's Table 1 (unknowns,

@@ -135,9 +135,18 @@ static long long store_level(Hier &H, int k, const DCSR &A, const DCSR *P, const
         bytes += (long long)(c.A.bytes() + c.P.bytes() + c.R.bytes() + c.dw.bytes());
     } else {
         CycLevel<float> &c = H.cf[(size_t)k];
-        const bool h16 = o.half_storage != 0;
+        const bool h16 = (o.half_storage & GW_HALF_TRANSFER) != 0;
+        const bool fine16 = k == 0 && (o.half_storage & GW_HALF_FINE) != 0;
         auto f32 = [h16](int f) { return h16 && f == FMT_SELL ? FMT_SELL16 : f; };
-        to_store<float>(A, c.A, k == 0 ? FMT_STEN : f32(choose_fmt(A)), H.gnx, H.gny, H.gnz, st);
+        to_store<float>(A, c.A, k == 0 ? (fine16 ? FMT_STENB : FMT_STEN) : f32(choose_fmt(A)), H.gnx, H.gny, H.gnz,
+                        st);
+        if (k == 0) {
+            H.A32 = MatStore<float>();
+            if (c.A.fmt == FMT_STENB) {
+                to_store<float>(A, H.A32, FMT_STEN, H.gnx, H.gny, H.gnz, st);
+                bytes += (long long)H.A32.bytes();
+            }
+        }
         if (P) to_store<float>(*P, c.P, f32(choose_fmt(*P)), 0, 0, 0, st);
         if (R) to_store<float>(*R, c.R, f32(choose_fmt(*R)), 0, 0, 0, st);
         c.dw.alloc((size_t)n);

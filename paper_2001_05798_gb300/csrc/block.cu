@@ -169,6 +169,29 @@ struct BCsr {
     }
 };
 
+struct BStenB {
+    const float *__restrict__ d;
+    const __nv_bfloat16 *__restrict__ ox;
+    const __nv_bfloat16 *__restrict__ oy;
+    const __nv_bfloat16 *__restrict__ oz;
+    int n, nx, sxy;
+    template <int CW, class F>
+    __device__ __forceinline__ CV<float, CW> dot(int i, F f) const
+    {
+        CV<float, CW> acc;
+#pragma unroll
+        for (int u = 0; u < CW; ++u) acc.v[u] = 0.f;
+        if (i >= sxy) cacc(acc, __bfloat162float(oz[i - sxy]), f(i - sxy));
+        if (i >= nx) cacc(acc, __bfloat162float(oy[i - nx]), f(i - nx));
+        if (i >= 1) cacc(acc, __bfloat162float(ox[i - 1]), f(i - 1));
+        cacc(acc, __ldg(d + i), f(i));
+        if (i + 1 < n) cacc(acc, __bfloat162float(ox[i]), f(i + 1));
+        if (i + nx < n) cacc(acc, __bfloat162float(oy[i]), f(i + nx));
+        if (i + sxy < n) cacc(acc, __bfloat162float(oz[i]), f(i + sxy));
+        return acc;
+    }
+};
+
 template <class T, class F>
 static void with_bmat(const MatStore<T> &M, F f)
 {
@@ -182,7 +205,14 @@ static void with_bmat(const MatStore<T> &M, F f)
         f(BSten<T>{S.d.p, S.ox.p, S.oy.p, S.oz.p, S.n, S.nx, S.nx * S.ny});
         break;
     }
-    default: fail(GW_ERR_ARG, "interleaved solves need an uncompressed hierarchy (half_storage = 0)");
+    case FMT_STENB:
+        if constexpr (sizeof(T) == 4) {
+            const StenB &S = M.stenb;
+            f(BStenB{S.d.p, S.ox.p, S.oy.p, S.oz.p, S.n, S.nx, S.nx * S.ny});
+            break;
+        }
+        [[fallthrough]];
+    default: fail(GW_ERR_ARG, "interleaved solves need P, R and the coarse operators uncompressed");
     }
 }
 
@@ -963,7 +993,7 @@ struct BCyc {
     {
         const int n = H.n;
         float *pold = parity ? S.pb.p : S.p.p, *pnew = parity ? S.p.p : S.pb.p;
-        with_bmat(H.cf[0].A, [&](auto A) {
+        with_bmat(cg_op32(H), [&](auto A) {
             using M = decltype(A);
             launch_pdl(kb_dir_spmv<KB, CW, M>, g(n), st, A, n, (const float *)S.z.p, (const float *)pold, pnew, S.q.p,
                        part, c);

@@ -330,6 +330,87 @@ struct MSten {
     }
 };
 
+// R BF16 values (R = 4: one 8-byte load) widened to FP32
+template <int R>
+__device__ __forceinline__ VecN<float, R> ld_bf(const __nv_bfloat16 *p)
+{
+    VecN<float, R> o;
+    if constexpr (R == 4) {
+        const uint2 w = __ldg(reinterpret_cast<const uint2 *>(p));
+        o.v[0] = __uint_as_float(w.x << 16);
+        o.v[1] = __uint_as_float(w.x & 0xffff0000u);
+        o.v[2] = __uint_as_float(w.y << 16);
+        o.v[3] = __uint_as_float(w.y & 0xffff0000u);
+    } else if constexpr (R == 2) {
+        const unsigned w = __ldg(reinterpret_cast<const unsigned *>(p));
+        o.v[0] = __uint_as_float(w << 16);
+        o.v[1] = __uint_as_float(w & 0xffff0000u);
+    } else {
+#pragma unroll
+        for (int k = 0; k < R; ++k) o.v[k] = __bfloat162float(p[k]);
+    }
+    return o;
+}
+
+// The level-0 stencil with BF16 couplings and an FP32 diagonal (10 bytes a
+// row instead of 16); same row blocking and term order as MSten.
+template <int R_>
+struct MStenB {
+    using value_type = float;
+    static constexpr int G = 1, R = R_;
+    const float *__restrict__ d;
+    const __nv_bfloat16 *__restrict__ ox;
+    const __nv_bfloat16 *__restrict__ oy;
+    const __nv_bfloat16 *__restrict__ oz;
+    int n, nx, sxy;
+    template <class F>
+    __device__ __forceinline__ VecN<float, R> dot(int i0, int, F f) const
+    {
+        VecN<float, R> acc;
+#pragma unroll
+        for (int k = 0; k < R; ++k) acc.v[k] = 0.f;
+        if (i0 >= sxy) {
+            const VecN<float, R> c = ld_bf<R>(oz + i0 - sxy);
+            const VecN<float, R> x = f.template vec<R>(i0 - sxy);
+#pragma unroll
+            for (int k = 0; k < R; ++k) acc.v[k] += c.v[k] * x.v[k];
+        }
+        if (i0 >= nx) {
+            const VecN<float, R> c = ld_bf<R>(oy + i0 - nx);
+            const VecN<float, R> x = f.template vec<R>(i0 - nx);
+#pragma unroll
+            for (int k = 0; k < R; ++k) acc.v[k] += c.v[k] * x.v[k];
+        }
+        const VecN<float, R> cx = ld_bf<R>(ox + i0);
+        const VecN<float, R> xc = f.template vec<R>(i0);
+        const float cxm = i0 >= 1 ? __bfloat162float(ox[i0 - 1]) : 0.f;
+        const float xm = i0 >= 1 ? f(i0 - 1) : 0.f;
+        const float xp = i0 + R < n ? f(i0 + R) : 0.f;
+        acc.v[0] += cxm * xm;
+#pragma unroll
+        for (int k = 1; k < R; ++k) acc.v[k] += cx.v[k - 1] * xc.v[k - 1];
+        const VecN<float, R> dg = ld_ro<R>(d + i0);
+#pragma unroll
+        for (int k = 0; k < R; ++k) acc.v[k] += dg.v[k] * xc.v[k];
+#pragma unroll
+        for (int k = 0; k < R - 1; ++k) acc.v[k] += cx.v[k] * xc.v[k + 1];
+        acc.v[R - 1] += cx.v[R - 1] * xp;
+        if (i0 + nx < n) {
+            const VecN<float, R> c = ld_bf<R>(oy + i0);
+            const VecN<float, R> x = f.template vec<R>(i0 + nx);
+#pragma unroll
+            for (int k = 0; k < R; ++k) acc.v[k] += c.v[k] * x.v[k];
+        }
+        if (i0 + sxy < n) {
+            const VecN<float, R> c = ld_bf<R>(oz + i0);
+            const VecN<float, R> x = f.template vec<R>(i0 + sxy);
+#pragma unroll
+            for (int k = 0; k < R; ++k) acc.v[k] += c.v[k] * x.v[k];
+        }
+        return acc;
+    }
+};
+
 // Compressed sliced ELL: 8 FP16 values and 8 16-bit column offsets per
 // 16-byte load; scaled square matrices multiply by sd on both sides.
 template <class T>
@@ -395,6 +476,17 @@ static void with_mat(const MatStore<T> &M, F f)
     case FMT_CSR32: f(MCsr<T, 32>{M.csr.rp.p, M.csr.ci.p, M.csr.v.p, M.csr.nr}); break;
     case FMT_SELL16:
         f(MSell16<T>{M.sell16.sp.p, M.sell16.base.p, M.sell16.v.p, M.sell16.ci.p, M.sell16.sd.p});
+        break;
+    case FMT_STENB:
+        if constexpr (sizeof(T) == 4) {
+            const StenB &S = M.stenb;
+            const int sxy = S.nx * S.ny;
+            if (S.n % 4 == 0 && S.nx % 4 == 0) f(MStenB<4>{S.d.p, S.ox.p, S.oy.p, S.oz.p, S.n, S.nx, sxy});
+            else if (S.n % 2 == 0 && S.nx % 2 == 0) f(MStenB<2>{S.d.p, S.ox.p, S.oy.p, S.oz.p, S.n, S.nx, sxy});
+            else f(MStenB<1>{S.d.p, S.ox.p, S.oy.p, S.oz.p, S.n, S.nx, sxy});
+        } else {
+            fail(GW_ERR_SETUP, "a BF16 stencil in an FP64 hierarchy");
+        }
         break;
     default: {
         constexpr int RV = sten_r<T>(), RH = RV / 2;
@@ -818,6 +910,7 @@ template <class T>
 static double mat_bytes(const MatStore<T> &M)
 {
     if (M.fmt == FMT_STEN) return 4.0 * M.nr * sizeof(T);
+    if (M.fmt == FMT_STENB) return 10.0 * M.nr;
     if (M.fmt == FMT_SELL16) return (double)M.nnz * 4.0 + (M.sell16.sd.p ? 4.0 * M.nr : 0.0);
     return (double)M.nnz * (sizeof(T) + 4.0);
 }
@@ -1407,7 +1500,7 @@ static void cg_iteration(Hier &H, int parity, cudaStream_t st)
         GW_LAUNCH_CHECK();
         return;
     }
-    const MatStore<float> &A32 = H.cf[0].A;
+    const MatStore<float> &A32 = cg_op32(H);
     float *pold = parity ? H.p32b.p : H.p32.p, *pnew = parity ? H.p32.p : H.p32b.p;
     timed(H, GW_PK_SPMV, st, [&] {
         H.prof_bytes += vbytes(H, mat_bytes(A32) + 20.0 * dn);

@@ -1,6 +1,7 @@
 // gw_internal.cuh -- internal types and helpers of libgw (CUDA, sm_103a).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -145,6 +146,17 @@ struct StenT {
     size_t bytes() const { return d.bytes() + ox.bytes() + oy.bytes() + oz.bytes(); }
 };
 
+// The level-0 stencil with BF16 couplings (FP32 cycle only).  The diagonal
+// is FP32 and absorbs the rounding of the couplings of its row,
+// d_i = a_ii + sum_j (|bf16(a_ij)| - |a_ij|), so the stored operator keeps
+// the row sums, the symmetry and the M-matrix signs of A.
+struct StenB {
+    int n = 0, nx = 0, ny = 0, nz = 0;
+    DBuf<float> d;
+    DBuf<__nv_bfloat16> ox, oy, oz;
+    size_t bytes() const { return d.bytes() + ox.bytes() + oy.bytes() + oz.bytes(); }
+};
+
 // Compressed sliced ELL (FP32 cycle only): FP16 values and 16-bit column
 // offsets from a per-slice base column, 8 slots per 16-byte load.  A square
 // level matrix is stored symmetrically scaled, D^-1/2 A D^-1/2 (entries in
@@ -160,7 +172,7 @@ struct Sell16 {
     size_t bytes() const { return sp.bytes() + base.bytes() + v.bytes() + ci.bytes() + sd.bytes(); }
 };
 
-enum { FMT_SELL = 0, FMT_CSR4 = 1, FMT_CSR8 = 2, FMT_CSR32 = 3, FMT_STEN = 4, FMT_SELL16 = 5 };
+enum { FMT_SELL = 0, FMT_CSR4 = 1, FMT_CSR8 = 2, FMT_CSR32 = 3, FMT_STEN = 4, FMT_SELL16 = 5, FMT_STENB = 6 };
 
 template <class T>
 struct MatStore {
@@ -171,7 +183,8 @@ struct MatStore {
     CsrT<T> csr;
     StenT<T> sten;
     Sell16 sell16;
-    size_t bytes() const { return sell.bytes() + csr.bytes() + sten.bytes() + sell16.bytes(); }
+    StenB stenb;
+    size_t bytes() const { return sell.bytes() + csr.bytes() + sten.bytes() + sell16.bytes() + stenb.bytes(); }
 };
 
 int choose_fmt(const DCSR &A);
@@ -251,6 +264,7 @@ struct Hier {
     std::vector<CycLevel<float>> cf;
     std::vector<CycLevel<double>> cd;
     MatStore<double> A64;      // level-0 FP64 matrix of the outer CG (mixed precision)
+    MatStore<float> A32;       // level-0 FP32 operator of the CG recurrence when the cycle's is BF16
     int gnx = 0, gny = 0, gnz = 0;  // grid of the level-0 operator
     int max_blocks = 1216;     // one wave of 256-thread blocks (SMs x 8)
     DBuf<double> Ainv;         // dense inverse of the coarsest level, row-major
@@ -282,6 +296,9 @@ struct Hier {
 };
 
 void drop_graphs(Hier &H);
+
+// the FP32 level-0 operator of the mixed CG recurrence
+inline const MatStore<float> &cg_op32(const Hier &H) { return H.A32.nr ? H.A32 : H.cf[0].A; }
 
 void build_hierarchy(Hier &H, cudaStream_t st);
 void refresh_level0(Hier &H, const DCSR &A, cudaStream_t st);

@@ -1024,6 +1024,37 @@ __global__ void k_to_stencil(int n, int nx, int sxy, const int *__restrict__ rp,
     }
 }
 
+// BF16 couplings and the corrected FP32 diagonal (see StenB)
+__global__ void k_to_stencil_bf16(int n, int nx, int sxy, const int *__restrict__ rp, const int *__restrict__ ci,
+                                  const double *__restrict__ v, float *__restrict__ d, __nv_bfloat16 *__restrict__ ox,
+                                  __nv_bfloat16 *__restrict__ oy, __nv_bfloat16 *__restrict__ oz,
+                                  int *__restrict__ bad)
+{
+    GRID_STRIDE(ii, n)
+    {
+        const int i = (int)ii;
+        double dd = 0.0, a = 0.0, b = 0.0, c = 0.0, corr = 0.0;
+        for (int e = rp[i]; e < rp[i + 1]; ++e) {
+            const long long j = ci[e];
+            const double x = v[e];
+            if (j == i) {
+                dd = x;
+                continue;
+            }
+            if (j == (long long)i + sxy) c = x;
+            else if (j == (long long)i + nx) b = x;
+            else if (j == (long long)i + 1) a = x;
+            else if (!(j == (long long)i - sxy || j == (long long)i - nx || j == (long long)i - 1)) atomicAdd(bad, 1);
+            const double xr = (double)__bfloat162float(__double2bfloat16(x));
+            corr += fabs(xr) - fabs(x);
+        }
+        d[i] = (float)(dd + corr);
+        ox[i] = __double2bfloat16(a);
+        oy[i] = __double2bfloat16(b);
+        oz[i] = __double2bfloat16(c);
+    }
+}
+
 // Short rows (the prolongator) and rows of medium length on big levels as
 // sliced ELL, one thread per row; long rows on small levels as CSR read by a
 // whole warp, so the level still covers the GPU.
@@ -1041,6 +1072,32 @@ bool to_store(const DCSR &A, MatStore<T> &M, int fmt, int nx, int ny, int nz, cu
     M.nc = A.nc;
     M.nnz = A.nnz;
     M.fmt = fmt;
+    if (fmt == FMT_STENB) {
+        StenB &S = M.stenb;
+        const int n = A.nr;
+        if (sizeof(T) == 4) {
+            S.n = n;
+            S.nx = nx;
+            S.ny = ny;
+            S.nz = nz;
+            S.d.alloc((size_t)n);
+            S.ox.alloc((size_t)n);
+            S.oy.alloc((size_t)n);
+            S.oz.alloc((size_t)n);
+            DBuf<int> bad(1);
+            GW_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
+            k_to_stencil_bf16<<<nblk(n, 256), 256, 0, st>>>(n, nx, nx * ny, A.rp.p, A.ci.p, A.v.p, S.d.p, S.ox.p,
+                                                            S.oy.p, S.oz.p, bad.p);
+            GW_LAUNCH_CHECK();
+            if (read_int(bad.p, st) == 0) return true;
+            S.d.release();
+            S.ox.release();
+            S.oy.release();
+            S.oz.release();
+        }
+        fmt = FMT_STEN;
+        M.fmt = fmt;
+    }
     if (fmt == FMT_STEN) {
         StenT<T> &S = M.sten;
         const int n = A.nr;

@@ -259,3 +259,70 @@ def test_full_size_128_cubed_sigma4(gw, prec):
     assert np.array_equal(arp1, orp1) and np.array_equal(aci1, oci1) and np.array_equal(av1, ov1)
     href, _, _, _ = Ho.pcg(bo, tol=1e-12)
     assert np.linalg.norm(h.cpu().numpy() - href) / np.linalg.norm(href) <= REL_ERR
+
+
+@pytest.mark.parametrize("name", ["3d_het_33_sigma4", "3d_layered_24", "2d_homog_128"])
+def test_bf16_fine_stencil_solves_to_parity(gw, name):
+    """GW_HALF_FINE: the V-cycle's level-0 stencil with BF16 couplings.  The
+    solve still stops on the FP64 residual, agrees with the oracle, and the
+    preconditioner stays close to the FP32 one (a few iterations more at most)."""
+    p = PROBLEMS[name]()
+    A, b = gpu_assemble(gw, p)
+    H32 = gw.Hierarchy(A, n_coarse=64)
+    Hb = gw.Hierarchy(A, n_coarse=64, half_storage=gw.GW_HALF_FINE)
+    h32, it32, _, _ = H32.solve(b, tol=TOL)
+    hb, itb, relb, st = Hb.solve(b, tol=TOL)
+    assert st == gw.GW_OK and relb <= TOL
+    assert itb <= it32 + 3
+    Ao, bo = ora_assemble(p)
+    href, _, _, _ = oracle.Hierarchy(Ao, n_coarse=64).pcg(bo, tol=1e-12)
+    assert np.linalg.norm(hb.cpu().numpy() - href) / np.linalg.norm(href) <= REL_ERR
+    # the interleaved block path runs the same stored operator
+    B = torch.stack([b, 2.0 * b])
+    X, its, rels, st = Hb.solve_many(B, tol=TOL)
+    assert st == gw.GW_OK and max(rels) <= TOL
+    assert np.linalg.norm(X[1].cpu().numpy() - 2 * href) / np.linalg.norm(2 * href) <= REL_ERR
+
+
+@pytest.mark.parametrize("half", [0, 2])
+@pytest.mark.parametrize("prec", [1, 0])
+def test_full_size_layered_256x256x128(gw, prec, half):
+    """The 256x256x128 layered case (lnK variance 1, correlation 32/32/4 cells,
+    Kh/Kv = 10, 16 wells, fixed head on top) at full size: level-0 aggregates,
+    roots and the level-1 operator bit-exact, the solution within 1e-6 of the
+    oracle's, in the FP64 form, the mixed form and the mixed form with the
+    BF16-stored fine stencil."""
+    if prec == 0 and half:
+        pytest.skip("BF16 storage belongs to the mixed form")
+    p = wl.layered_wells_3d()
+    assert (p["nx"], p["ny"], p["nz"]) == (256, 256, 128)
+    A, b = gpu_assemble(gw, p)
+    H = gw.Hierarchy(A, prec=prec, half_storage=half)
+    h, it, rel, st = H.solve(b, tol=TOL)
+    assert st == gw.GW_OK and rel <= TOL
+    ref = _layered_reference()
+    info = H.info()
+    assert [l["n"] for l in info] == ref["n"]
+    agg, root, _, _ = H.export_level(0)
+    assert np.array_equal(agg, ref["agg"]) and np.array_equal(root, ref["root"])
+    _, _, (arp1, aci1, av1), _ = H.export_level(1)
+    assert np.array_equal(arp1, ref["A1"][0]) and np.array_equal(aci1, ref["A1"][1])
+    assert np.array_equal(av1.view(np.uint64), ref["A1"][2].view(np.uint64))
+    err = np.linalg.norm(h.cpu().numpy() - ref["h"]) / np.linalg.norm(ref["h"])
+    assert err <= REL_ERR, err
+
+
+_LAYERED = {}
+
+
+def _layered_reference():
+    """The oracle's hierarchy statistics, level-0/1 data and solve to 1e-12 of the layered case (computed once)."""
+    if not _LAYERED:
+        p = wl.layered_wells_3d()
+        Ao, bo = ora_assemble(p)
+        Ho = oracle.Hierarchy(Ao)
+        agg, root, _ = Ho.level(0)
+        _LAYERED.update(n=Ho.stats()["n"], agg=agg.copy(), root=root.copy(),
+                        A1=[a.copy() for a in Ho.A(1).arrays()])
+        _LAYERED["h"] = Ho.pcg(bo, tol=1e-12)[0]
+    return _LAYERED

@@ -147,7 +147,8 @@ static long long store_level(Hier &H, int k, const DCSR &A, const DCSR *P, const
                 bytes += (long long)H.A32.bytes();
             }
         }
-        if (P) to_store<float>(*P, c.P, f32(choose_fmt(*P)), 0, 0, 0, st);
+        if (P && !(k == 0 && H.p0.n)) to_store<float>(*P, c.P, f32(choose_fmt(*P)), 0, 0, 0, st);
+        if (k == 0 && H.p0.n) bytes += (long long)H.p0.bytes();
         if (R) to_store<float>(*R, c.R, f32(choose_fmt(*R)), 0, 0, 0, st);
         c.dw.alloc((size_t)n);
         k_make_dw<<<std::max(g, 1), 256, 0, st>>>(n, diag.p, scale, c.dw.p, nullptr);
@@ -210,6 +211,7 @@ void build_hierarchy(Hier &H, cudaStream_t st)
         DCSR P, Rl, AP, Ac;
         double omega = 0.0, rho = 0.0;
         setup_smooth_p(A, S.p, H.agg[(size_t)l].p, m, P, &omega, &rho, st);
+        if (l == 0 && o.prec != GW_PREC_FP64) setup_implicit_p(A, S.p, omega, H.gnx, H.gny, H.gnz, H.p0, st);
         setup_transpose(P, Rl, st);
         setup_spgemm(A, P, AP, st);
         setup_spgemm(Rl, AP, Ac, st);
@@ -223,6 +225,7 @@ void build_hierarchy(Hier &H, cudaStream_t st)
     }
     H.L = l + 1;
     const int L = H.L;
+    if (H.p0.n) H.p0.agg = H.agg[0].p;
     setup_dense_inverse(Al(L - 1), H.Ainv, st);
     H.info[(size_t)L - 1].bytes += (long long)H.Ainv.bytes();
     const bool f64 = o.prec == GW_PREC_FP64;

@@ -546,6 +546,38 @@ __global__ void __launch_bounds__(BS) kb_prolong(M P, int n, const float *__rest
     }
 }
 
+// x += P e on level 0 with the implicit prolongator (ImplP)
+template <int KB, int CW>
+__global__ void __launch_bounds__(BS) kb_prolong_imp(const int *__restrict__ agg, const float *__restrict__ s,
+                                                     const float *__restrict__ fx, const float *__restrict__ fy,
+                                                     const float *__restrict__ fz, int n, int nx, int sxy, float w0,
+                                                     const float *__restrict__ ec, float *__restrict__ x,
+                                                     const BlkCtl *c)
+{
+    pdl_enter();
+    if (bfinished(c)) return;
+    BLOCK_ROWS(n, KB, CW)
+    {
+        const float *eo = ec + off;
+        CV<float, CW> acc;
+#pragma unroll
+        for (int u = 0; u < CW; ++u) acc.v[u] = 0.f;
+        if (i >= sxy) cacc(acc, __ldg(fz + i - sxy), cld<CW>(eo + __ldg(agg + i - sxy) * KB));
+        if (i >= nx) cacc(acc, __ldg(fy + i - nx), cld<CW>(eo + __ldg(agg + i - nx) * KB));
+        if (i >= 1) cacc(acc, __ldg(fx + i - 1), cld<CW>(eo + __ldg(agg + i - 1) * KB));
+        if (i + 1 < n) cacc(acc, __ldg(fx + i), cld<CW>(eo + __ldg(agg + i + 1) * KB));
+        if (i + nx < n) cacc(acc, __ldg(fy + i), cld<CW>(eo + __ldg(agg + i + nx) * KB));
+        if (i + sxy < n) cacc(acc, __ldg(fz + i), cld<CW>(eo + __ldg(agg + i + sxy) * KB));
+        const float si = __ldg(s + i), w = si != 0.f ? w0 : 1.f;
+        const CV<float, CW> ev = cld<CW>(eo + __ldg(agg + i) * KB);
+        const size_t e = (size_t)i * KB + off;
+        CV<float, CW> xv = cld<CW>(x + e);
+#pragma unroll
+        for (int u = 0; u < CW; ++u) xv.v[u] += w * ev.v[u] - si * acc.v[u];
+        cst<CW>(x + e, xv);
+    }
+}
+
 // x = Ainv b on the coarsest level (dense FP64 inverse), one warp per row,
 // KB columns at once
 template <int KB>
@@ -960,6 +992,14 @@ struct BCyc {
             CycLevel<float> &lv = H.cf[l];
             BlockLevel &bl = S.lv[l];
             const int n = lv.n;
+            if (l == 0 && H.p0.n) {
+                const ImplP &I = H.p0;
+                launch_pdl(kb_prolong_imp<KB, CW>, g(n), st, I.agg, (const float *)I.s.p, (const float *)I.fx.p,
+                           (const float *)I.fy.p, (const float *)I.fz.p, I.n, I.nx, I.sxy, I.w0,
+                           (const float *)S.lv[1].x.p, bl.x.p, (const BlkCtl *)c);
+                smooth(l, r, false, true, z, q, mode);
+                continue;
+            }
             with_bmat(lv.P, [&](auto P) {
                 using M = decltype(P);
                 launch_pdl(kb_prolong<KB, CW, M>, g(n), st, P, n, (const float *)S.lv[l + 1].x.p, bl.x.p,
@@ -1140,7 +1180,7 @@ bool block_supported(const Hier &H)
     if ((long long)H.n * KB_MAX > 0x7fffffffLL) return false;
     for (int l = 0; l < H.L; ++l) {
         const CycLevel<float> &lv = H.cf[l];
-        if (lv.A.fmt == FMT_SELL16 || (l < H.L - 1 && (lv.P.fmt == FMT_SELL16 || lv.R.fmt == FMT_SELL16)))
+        if (lv.A.fmt == FMT_SELL16 || (l < H.L - 1 && ((lv.P.nr && lv.P.fmt == FMT_SELL16) || lv.R.fmt == FMT_SELL16)))
             return false;
     }
     return H.A64.fmt != FMT_SELL16;

@@ -690,6 +690,101 @@ __global__ void __launch_bounds__(BS) k_prolong(M P, int n, const typename M::va
     }
 }
 
+// x += P e on level 0 with the implicit prolongator (ImplP), R rows a thread:
+// x_i += w_i e[agg_i] - s_i sum_j f_ij e[agg_j], neighbours in the order
+// -z, -y, -x, +x, +y, +z
+template <int R>
+__device__ __forceinline__ VecN<int, R> ld_int(const int *__restrict__ p)
+{
+    VecN<int, R> o;
+    if constexpr (R == 4) {
+        const int4 t = __ldg(reinterpret_cast<const int4 *>(p));
+        o.v[0] = t.x, o.v[1] = t.y, o.v[2] = t.z, o.v[3] = t.w;
+    } else if constexpr (R == 2) {
+        const int2 t = __ldg(reinterpret_cast<const int2 *>(p));
+        o.v[0] = t.x, o.v[1] = t.y;
+    } else {
+#pragma unroll
+        for (int k = 0; k < R; ++k) o.v[k] = __ldg(p + k);
+    }
+    return o;
+}
+
+struct PImpl {
+    const int *__restrict__ agg;
+    const float *__restrict__ s;
+    const float *__restrict__ fx;
+    const float *__restrict__ fy;
+    const float *__restrict__ fz;
+    int n, nx, sxy;
+    float w0;
+};
+
+template <int R>
+__global__ void __launch_bounds__(BS) k_prolong_imp(PImpl P, const float *__restrict__ e, float *__restrict__ x,
+                                                    const Ctl *ctl)
+{
+    pdl_enter();
+    if (finished(ctl)) return;
+    const int n = P.n, nx = P.nx, sxy = P.sxy;
+    for (int i0 = R * (blockIdx.x * BS + threadIdx.x); i0 < n; i0 += R * gridDim.x * BS) {
+        float acc[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) acc[k] = 0.f;
+        if (i0 >= sxy) {
+            const VecN<float, R> c = ld_ro<R>(P.fz + i0 - sxy);
+            const VecN<int, R> a = ld_int<R>(P.agg + i0 - sxy);
+#pragma unroll
+            for (int k = 0; k < R; ++k) acc[k] += c.v[k] * __ldg(e + a.v[k]);
+        }
+        if (i0 >= nx) {
+            const VecN<float, R> c = ld_ro<R>(P.fy + i0 - nx);
+            const VecN<int, R> a = ld_int<R>(P.agg + i0 - nx);
+#pragma unroll
+            for (int k = 0; k < R; ++k) acc[k] += c.v[k] * __ldg(e + a.v[k]);
+        }
+        const VecN<int, R> ai = ld_int<R>(P.agg + i0);
+        VecN<float, R> ev;
+#pragma unroll
+        for (int k = 0; k < R; ++k) ev.v[k] = __ldg(e + ai.v[k]);
+        const VecN<float, R> cx = ld_ro<R>(P.fx + i0);
+        if (i0 >= 1) acc[0] += __ldg(P.fx + i0 - 1) * __ldg(e + __ldg(P.agg + i0 - 1));
+#pragma unroll
+        for (int k = 1; k < R; ++k) acc[k] += cx.v[k - 1] * ev.v[k - 1];
+#pragma unroll
+        for (int k = 0; k < R - 1; ++k) acc[k] += cx.v[k] * ev.v[k + 1];
+        if (i0 + R < n) acc[R - 1] += cx.v[R - 1] * __ldg(e + __ldg(P.agg + i0 + R));
+        if (i0 + nx < n) {
+            const VecN<float, R> c = ld_ro<R>(P.fy + i0);
+            const VecN<int, R> a = ld_int<R>(P.agg + i0 + nx);
+#pragma unroll
+            for (int k = 0; k < R; ++k) acc[k] += c.v[k] * __ldg(e + a.v[k]);
+        }
+        if (i0 + sxy < n) {
+            const VecN<float, R> c = ld_ro<R>(P.fz + i0);
+            const VecN<int, R> a = ld_int<R>(P.agg + i0 + sxy);
+#pragma unroll
+            for (int k = 0; k < R; ++k) acc[k] += c.v[k] * __ldg(e + a.v[k]);
+        }
+        const VecN<float, R> sv = ld_ro<R>(P.s + i0);
+        VecN<float, R> xv = ld_rw<R>(x + i0);
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const float w = sv.v[k] != 0.f ? P.w0 : 1.f;
+            xv.v[k] += w * ev.v[k] - sv.v[k] * acc[k];
+        }
+        st<R>(x + i0, xv);
+    }
+}
+
+static void prolong_imp(Hier &H, const float *e, float *x, const Ctl *ctl, cudaStream_t st)
+{
+    const ImplP &I = H.p0;
+    const PImpl P{I.agg, I.s.p, I.fx.p, I.fy.p, I.fz.p, I.n, I.nx, I.sxy, I.w0};
+    if (I.n % 4 == 0 && I.nx % 4 == 0) launch_pdl(k_prolong_imp<4>, vgrid(H, I.n / 4), st, P, e, x, ctl);
+    else launch_pdl(k_prolong_imp<1>, vgrid(H, I.n), st, P, e, x, ctl);
+}
+
 // x = Ainv b on the coarsest level (dense FP64 inverse), one warp per row
 template <class T>
 __global__ void __launch_bounds__(BS) k_coarse(int n, const double *__restrict__ Ainv, const T *__restrict__ b,
@@ -1105,6 +1200,14 @@ static void vcycle_t(Hier &H, std::vector<CycLevel<T>> &C, const T *r, T *z, Ctl
         }
         if (l == 0) mark_end(H, st);
         timed(H, l0 ? GW_PK_PROLONG : -1, st, [&] {
+            if constexpr (sizeof(T) == 4) {
+                if (l0 && H.p0.n) {
+                    // s, fx, fy, fz, agg once, the coarse vector once, x read and written
+                    H.prof_bytes += vbytes(H, 20.0 * dn + (double)C[1].n * sx + 2.0 * dn * sx);
+                    prolong_imp(H, C[1].x.p, lv.x.p, ctl, st);
+                    return;
+                }
+            }
             H.prof_bytes += vbytes(H, mat_bytes(lv.P) + (double)lv.P.nc * sx + 2.0 * dn * sx);
             with_mat(lv.P, [&](auto P) {
                 using M = decltype(P);

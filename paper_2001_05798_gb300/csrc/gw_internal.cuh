@@ -217,6 +217,22 @@ void assemble_csr(int nx, int ny, int nz, double dx, double dy, double dz, const
                   const double *Kz, const int *bct, const double *bcv, const double *q, DCSR &A, double *b,
                   int *dflag, cudaStream_t st);
 
+// The level-0 prolongator of the FP32 cycle applied from its definition,
+// P = (I - omega D_F^-1 A_F) P_tent, instead of stored entries: on the 7-point
+// grid (P e)_i = w_i e[agg_i] - s_i sum_j f_ij e[agg_j] over the six
+// neighbours, with s_i = omega / (A_F)_ii, f_ij = a_ij for a strong coupling
+// and 0 otherwise, and w_i = 1 - omega (w_i = 1, s_i = 0 for a row without
+// strong couplings, whose row is the tentative one).  f is symmetric, so
+// only the +x, +y, +z couplings are stored: 16 bytes a row plus agg, against
+// about 63 bytes a row of padded sliced ELL at 128^3.
+struct ImplP {
+    int n = 0, nx = 0, sxy = 0;
+    float w0 = 0.f;  // 1 - omega
+    const int *agg = nullptr;
+    DBuf<float> s, fx, fy, fz;
+    size_t bytes() const { return s.bytes() + fx.bytes() + fy.bytes() + fz.bytes(); }
+};
+
 // ----------------------------------------------------------------- setup --
 struct LevelSetupOut {
     int nagg = 0, rounds = 0;
@@ -230,6 +246,9 @@ int setup_aggregate(const DCSR &A, const unsigned char *S, const unsigned char *
 void setup_smooth_p(const DCSR &A, const unsigned char *S, const int *agg, int nagg, DCSR &P, double *omega,
                     double *rho, cudaStream_t st);
 void setup_transpose(const DCSR &P, DCSR &R, cudaStream_t st);
+// false (out.n = 0) when A is not a 7-point operator on the nx*ny*nz grid
+bool setup_implicit_p(const DCSR &A, const unsigned char *S, double omega, int nx, int ny, int nz, ImplP &out,
+                      cudaStream_t st);
 void setup_spgemm(const DCSR &L, const DCSR &Rm, DCSR &C, cudaStream_t st);
 void setup_dense_inverse(const DCSR &A, DBuf<double> &Ainv, cudaStream_t st);
 double setup_gershgorin(const DCSR &A, DBuf<double> &diag, cudaStream_t st);  // max_i sum|a_ij|/a_ii
@@ -265,6 +284,7 @@ struct Hier {
     std::vector<CycLevel<double>> cd;
     MatStore<double> A64;      // level-0 FP64 matrix of the outer CG (mixed precision)
     MatStore<float> A32;       // level-0 FP32 operator of the CG recurrence when the cycle's is BF16
+    ImplP p0;                  // level-0 prolongator of the FP32 cycle (n = 0: stored P)
     int gnx = 0, gny = 0, gnz = 0;  // grid of the level-0 operator
     int max_blocks = 1216;     // one wave of 256-thread blocks (SMs x 8)
     DBuf<double> Ainv;         // dense inverse of the coarsest level, row-major

@@ -476,6 +476,66 @@ void setup_smooth_p(const DCSR &A, const unsigned char *S, const int *agg, int n
     GW_LAUNCH_CHECK();
 }
 
+// s_i and the strong +x, +y, +z couplings of the implicit level-0 prolongator
+__global__ void k_p_implicit(int n, int nx, int sxy, const int *__restrict__ rp, const int *__restrict__ ci,
+                             const double *__restrict__ v, const unsigned char *__restrict__ S,
+                             const double *__restrict__ aF, const unsigned char *__restrict__ hs, double omega,
+                             float *__restrict__ s, float *__restrict__ fx, float *__restrict__ fy,
+                             float *__restrict__ fz, int *__restrict__ bad)
+{
+    GRID_STRIDE(ii, n)
+    {
+        const int i = (int)ii;
+        double a = 0.0, b = 0.0, c = 0.0;
+        for (int e = rp[i]; e < rp[i + 1]; ++e) {
+            const long long j = ci[e];
+            if (j == i) continue;
+            const double x = S[e] ? v[e] : 0.0;
+            if (j == (long long)i + sxy) c = x;
+            else if (j == (long long)i + nx) b = x;
+            else if (j == (long long)i + 1) a = x;
+            else if (!(j == (long long)i - sxy || j == (long long)i - nx || j == (long long)i - 1)) atomicAdd(bad, 1);
+        }
+        s[i] = hs[i] ? (float)__ddiv_rn(omega, aF[i]) : 0.f;
+        fx[i] = (float)a;
+        fy[i] = (float)b;
+        fz[i] = (float)c;
+    }
+}
+
+bool setup_implicit_p(const DCSR &A, const unsigned char *S, double omega, int nx, int ny, int nz, ImplP &out,
+                      cudaStream_t st)
+{
+    out = ImplP();
+    const int n = A.nr;
+    if (nx < 1 || (long long)nx * ny * nz != n || !(omega > 0.0)) return false;
+    DBuf<double> d((size_t)n), aF((size_t)n);
+    DBuf<unsigned char> hs((size_t)n);
+    DBuf<unsigned long long> rb(1);
+    DBuf<int> bad(1);
+    const int g = nblk(n, 256);
+    k_diag<<<g, 256, 0, st>>>(n, A.rp.p, A.ci.p, A.v.p, d.p);
+    GW_CUDA(cudaMemsetAsync(rb.p, 0, sizeof(unsigned long long), st));
+    GW_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
+    k_filter<<<g, 256, 0, st>>>(n, A.rp.p, A.ci.p, A.v.p, S, d.p, aF.p, hs.p, rb.p);
+    out.s.alloc((size_t)n);
+    out.fx.alloc((size_t)n);
+    out.fy.alloc((size_t)n);
+    out.fz.alloc((size_t)n);
+    k_p_implicit<<<g, 256, 0, st>>>(n, nx, nx * ny, A.rp.p, A.ci.p, A.v.p, S, aF.p, hs.p, omega, out.s.p, out.fx.p,
+                                    out.fy.p, out.fz.p, bad.p);
+    GW_LAUNCH_CHECK();
+    if (read_int(bad.p, st) != 0) {
+        out = ImplP();
+        return false;
+    }
+    out.n = n;
+    out.nx = nx;
+    out.sxy = nx * ny;
+    out.w0 = (float)(1.0 - omega);
+    return true;
+}
+
 // ---------------------------------------------------------------- transpose --
 __global__ void k_tr_count(int nnz, const int *__restrict__ ci, int *__restrict__ cnt)
 {

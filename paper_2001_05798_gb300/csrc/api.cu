@@ -182,7 +182,7 @@ void build_hierarchy(Hier &H, cudaStream_t st)
     const gw_amg_opts &o = H.o;
     int nsm = 0;
     GW_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, H.dev));
-    H.max_blocks = std::max(1, std::min(RED_MAX_BLOCKS, nsm * 8));
+    H.max_blocks = std::max(1, std::min(RED_MAX_BLOCKS, nsm * GW_BLOCKS_PER_SM));
     H.A.clear();
     H.A.emplace_back();  // placeholder for level 0 (the matrix handle's CSR)
     std::vector<DCSR> R;

@@ -867,11 +867,7 @@ void block_drop_graphs(BlockState *s)
 
 static constexpr int BGRAPH_ITERS = 4;  // even: the direction buffers alternate
 
-static int bgrid(const Hier &H, long long threads)
-{
-    long long b = (threads + BS - 1) / BS;
-    return (int)std::max(1LL, std::min<long long>(b, H.max_blocks));
-}
+static int bgrid(const Hier &, long long threads) { return blocks_for(threads); }
 
 template <int KB>
 struct BCyc {
@@ -1128,7 +1124,7 @@ static void block_run(Hier &H, int kk, const double *B, double *X, double tol, i
     BlockState &S = *H.blk;
     const int n = H.n;
     const size_t cols = (size_t)n * kk * sizeof(double);
-    const int gg = bgrid(H, (long long)n * KB);
+    const int gg = std::min(bgrid(H, (long long)n * KB), H.max_blocks);
     const double *Bd = B;
     if (!is_device_ptr(B)) {
         GW_CUDA(cudaMemcpyAsync(S.stage.p, B, cols, cudaMemcpyHostToDevice, st));

@@ -211,36 +211,44 @@ struct VecT<double> {
     using I = int2;
 };
 
-// Sliced ELL, one thread per row; V slots per 16-byte load.
-template <class T>
+// Sliced ELL, G lanes per row (lane g of a row takes chunks g, g + G, ...,
+// so a warp still reads whole 16-byte vectors of consecutive rows); V slots
+// per 16-byte load; every lane of the group gets the sum.
+template <class T, int G_ = 1>
 struct MSell {
     using value_type = T;
-    static constexpr int G = 1, R = 1;
+    static constexpr int G = G_, R = 1;
     SV<T> a;
     template <class F>
-    __device__ __forceinline__ VecN<T, 1> dot(int r, int, F f) const
+    __device__ __forceinline__ VecN<T, 1> dot(int r, int lane, F f) const
     {
         using VV = typename VecT<T>::V;
         using VI = typename VecT<T>::I;
         constexpr int V = SellV<T>::V;
-        const int s = r >> 5, lane = r & 31;
-        const int base = a.sp[s];
-        const int nch = (a.sp[s + 1] - base) / (SELL_C * V);
-        const VV *vv = reinterpret_cast<const VV *>(a.v + base) + lane;
-        const VI *cc = reinterpret_cast<const VI *>(a.ci + base) + lane;
         T acc = 0;
-        for (int c = 0; c < nch; ++c) {
-            const VV x = __ldg(vv + c * SELL_C);
-            const VI j = __ldg(cc + c * SELL_C);
-            if constexpr (V == 4) {
-                acc += x.x * f(j.x);
-                acc += x.y * f(j.y);
-                acc += x.z * f(j.z);
-                acc += x.w * f(j.w);
-            } else {
-                acc += x.x * f(j.x);
-                acc += x.y * f(j.y);
+        if (G == 1 || r < a.nr) {
+            const int s = r >> 5, rl = r & 31;
+            const int base = a.sp[s];
+            const int nch = (a.sp[s + 1] - base) / (SELL_C * V);
+            const VV *vv = reinterpret_cast<const VV *>(a.v + base) + rl;
+            const VI *cc = reinterpret_cast<const VI *>(a.ci + base) + rl;
+            for (int c = (G == 1 ? 0 : lane); c < nch; c += G) {
+                const VV x = __ldg(vv + c * SELL_C);
+                const VI j = __ldg(cc + c * SELL_C);
+                if constexpr (V == 4) {
+                    acc += x.x * f(j.x);
+                    acc += x.y * f(j.y);
+                    acc += x.z * f(j.z);
+                    acc += x.w * f(j.w);
+                } else {
+                    acc += x.x * f(j.x);
+                    acc += x.y * f(j.y);
+                }
             }
+        }
+        if constexpr (G > 1) {
+#pragma unroll
+            for (int off = G / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off, G);
         }
         return VecN<T, 1>{{acc}};
     }
@@ -466,11 +474,22 @@ constexpr int sten_r()
     return 4;
 }
 
+// rows longer than this on average are read by GW_SELL_LANES lanes each
+constexpr int SELL_LONG_ROW = 12;
+#ifndef GW_SELL_LANES
+#define GW_SELL_LANES 1
+#endif
+
 template <class T, class F>
 static void with_mat(const MatStore<T> &M, F f)
 {
     switch (M.fmt) {
-    case FMT_SELL: f(MSell<T>{SV<T>{M.sell.sp.p, M.sell.ci.p, M.sell.v.p, M.sell.nr}}); break;
+    case FMT_SELL: {
+        const SV<T> sv{M.sell.sp.p, M.sell.ci.p, M.sell.v.p, M.sell.nr};
+        if (M.nnz > (long long)SELL_LONG_ROW * M.nr) f(MSell<T, GW_SELL_LANES>{sv});
+        else f(MSell<T, 1>{sv});
+        break;
+    }
     case FMT_CSR4: f(MCsr<T, 4>{M.csr.rp.p, M.csr.ci.p, M.csr.v.p, M.csr.nr}); break;
     case FMT_CSR8: f(MCsr<T, 8>{M.csr.rp.p, M.csr.ci.p, M.csr.v.p, M.csr.nr}); break;
     case FMT_CSR32: f(MCsr<T, 32>{M.csr.rp.p, M.csr.ci.p, M.csr.v.p, M.csr.nr}); break;
@@ -511,19 +530,15 @@ static void with_mat(const MatStore<T> &M, F f)
              stride_ = gridDim.x * (BS / M::G) * M::R;                                                     \
          M::G == 1 ? (i < (n)) : __any_sync(0xffffffffu, i < (n)); i += stride_)
 
+// blocks asked for by a pass over n rows (launch_pdl fits them to one wave)
 template <class M>
-static inline int grid_for(const Hier &H, long long n)
+static inline int grid_for(const Hier &, long long n)
 {
     long long groups = (n + M::R - 1) / M::R;
-    long long b = (groups * M::G + BS - 1) / BS;
-    return (int)std::max(1LL, std::min<long long>(b, H.max_blocks));
+    return blocks_for(groups * M::G);
 }
 
-static inline int vgrid(const Hier &H, long long n)
-{
-    long long b = (n + BS - 1) / BS;
-    return (int)std::max(1LL, std::min<long long>(b, H.max_blocks));
-}
+static inline int vgrid(const Hier &, long long n) { return blocks_for(n); }
 
 
 // ------------------------------------------------------- V-cycle kernels --

@@ -203,7 +203,10 @@ struct Ctl {
     unsigned int cnt[8];  // arrival counters of the last-block reductions
 };
 
-constexpr int RED_MAX_BLOCKS = 2048;
+constexpr int RED_MAX_BLOCKS = 4096;
+#ifndef GW_BLOCKS_PER_SM
+#define GW_BLOCKS_PER_SM 8  // grid cap of the cycle and CG kernels, per SM
+#endif
 
 // ------------------------------------------------------------ scan / misc --
 void exclusive_scan(const int *in, int *out, int n, cudaStream_t st);  // out[n] = total
@@ -211,6 +214,9 @@ bool exclusive_scan_in(const int *in, int *out, int n, int *scratch, size_t cap,
 int read_int(const int *dptr, cudaStream_t st);
 void to_device(void *dst, const void *src, size_t bytes, cudaStream_t st);
 bool is_device_ptr(const void *p);
+// one wave of a kernel on the current device: resident blocks per SM (at
+// block_size threads) times the SMs; cached per device and kernel
+int kernel_wave(const void *fn, int block_size);
 
 // -------------------------------------------------------------- assembly --
 void assemble_csr(int nx, int ny, int nz, double dx, double dy, double dz, const double *Kx, const double *Ky,

@@ -3,6 +3,7 @@
 // sides (block.cu).
 #pragma once
 
+#include <algorithm>
 #include <utility>
 
 #include "gw_internal.cuh"
@@ -10,6 +11,30 @@
 namespace gw {
 
 constexpr int BS = 256;  // threads per block of every cycle and CG kernel
+
+// Blocks a grid-stride loop over `threads` work items asks for.
+static inline int blocks_for(long long threads)
+{
+    const long long b = (threads + BS - 1) / BS;
+    return (int)std::max(1LL, std::min<long long>(b, 1LL << 30));
+}
+
+#ifndef GW_GRID_BALANCE
+#define GW_GRID_BALANCE 0
+#endif
+
+// The grid actually launched for `blocks`: at most one wave of the kernel
+// (its resident blocks per SM times the SMs, from the occupancy calculator),
+// and within that as few blocks as give every thread the same number of
+// grid-stride iterations.
+static inline int wave_grid(const void *fn, int blocks)
+{
+    const int cap = kernel_wave(fn, BS);
+    if (blocks <= cap) return std::max(1, blocks);
+    if (!GW_GRID_BALANCE) return cap;
+    const int iters = (blocks + cap - 1) / cap;
+    return (blocks + iters - 1) / iters;
+}
 
 #define ROWS(i, n) for (int i = blockIdx.x * BS + threadIdx.x; i < (n); i += gridDim.x * BS)
 
@@ -29,7 +54,7 @@ template <class... KArgs, class... Args>
 static void launch_pdl(void (*kernel)(KArgs...), int grid, cudaStream_t st, Args &&...args)
 {
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)grid);
+    cfg.gridDim = dim3((unsigned)wave_grid((const void *)kernel, grid));
     cfg.blockDim = dim3(BS);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = st;
@@ -70,24 +95,41 @@ __device__ __forceinline__ double block_sum(double v, double *sh)
 template <int K>
 __device__ __forceinline__ bool reduce_last(const double (&loc)[K], double *part, unsigned *cnt, double (&tot)[K])
 {
-    __shared__ double sh[32];
+    constexpr int W = BS / 32;
+    __shared__ double sh[K][W];
     __shared__ unsigned ticket;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // warps (shuffle tree), then one thread per value adds the warps in order
+#pragma unroll
     for (int k = 0; k < K; ++k) {
-        double s = block_sum(loc[k], sh);
-        if (threadIdx.x == 0) part[(size_t)k * gridDim.x + blockIdx.x] = s;
+        const double v = warp_sum(loc[k]);
+        if (lane == 0) sh[k][w] = v;
     }
-    __threadfence();
+    __syncthreads();
+    if (threadIdx.x < K) {
+        double s = 0.0;
+#pragma unroll
+        for (int q = 0; q < W; ++q) s += sh[threadIdx.x][q];
+        part[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = s;
+        __threadfence();
+    }
     __syncthreads();
     if (threadIdx.x == 0) ticket = atomicAdd(cnt, 1u);
     __syncthreads();
     if (ticket != gridDim.x - 1) return false;
     __threadfence();
-    for (int k = 0; k < K; ++k) {
+    // last block: warp k adds the partials of value k, lanes strided, in a fixed order
+    __shared__ double fin[K];
+    for (int k = w; k < K; k += W) {
         double s = 0.0;
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += BS) s += __ldcg(part + (size_t)k * gridDim.x + b);
-        tot[k] = block_sum(s, sh);
+        for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(part + (size_t)k * gridDim.x + b);
+        s = warp_sum(s);
+        if (lane == 0) fin[k] = s;
     }
     if (threadIdx.x == 0) *cnt = 0u;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) tot[k] = fin[k];
     return true;
 }
 

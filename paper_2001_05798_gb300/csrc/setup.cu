@@ -1118,10 +1118,15 @@ __global__ void k_to_stencil_bf16(int n, int nx, int sxy, const int *__restrict_
 // Short rows (the prolongator) and rows of medium length on big levels as
 // sliced ELL, one thread per row; long rows on small levels as CSR read by a
 // whole warp, so the level still covers the GPU.
+#ifndef GW_LONG_BIG_FMT
+#define GW_LONG_BIG_FMT FMT_SELL  // long rows on levels of 65536 rows or more
+#endif
+
 int choose_fmt(const DCSR &A)
 {
     const double avg = A.nr > 0 ? (double)A.nnz / A.nr : 0.0;
-    if (avg <= 12.0 || A.nr >= 65536) return FMT_SELL;
+    if (avg <= 12.0) return FMT_SELL;
+    if (A.nr >= 65536) return GW_LONG_BIG_FMT;
     return FMT_CSR32;
 }
 

@@ -4,6 +4,9 @@
 #include <condition_variable>
 #include <mutex>
 
+#include <map>
+#include <mutex>
+
 #include "gw_internal.cuh"
 
 namespace gw {
@@ -186,6 +189,24 @@ bool is_device_ptr(const void *p)
 void to_device(void *dst, const void *src, size_t bytes, cudaStream_t st)
 {
     GW_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, st));
+}
+
+int kernel_wave(const void *fn, int block_size)
+{
+    static std::mutex mu;
+    static std::map<std::pair<int, const void *>, int> cache;
+    int dev = 0;
+    GW_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    const auto key = std::make_pair(dev, fn);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int nb = 0, sms = 0;
+    GW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, block_size, 0));
+    GW_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int w = std::max(1, nb) * std::max(1, sms);
+    cache[key] = w;
+    return w;
 }
 
 }  // namespace gw

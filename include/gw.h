@@ -77,7 +77,8 @@ typedef struct {
  * residual. */
 typedef enum {
     GW_PREC_FP64 = 0,
-    GW_PREC_MIXED32 = 1
+    GW_PREC_MIXED32 = 1,
+    GW_PREC_MIXEDBF16 = 3  /* GW_PREC_MIXED32 with GW_HALF_FINE: BF16-stored fine stencil */
 } gw_prec;
 
 enum { GW_SMOOTH_JACOBI = 0, GW_SMOOTH_CHEBYSHEV = 1 };

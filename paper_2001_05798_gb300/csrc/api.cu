@@ -464,7 +464,14 @@ int gw_amg_setup(gw_matrix A, const gw_amg_opts *opts, gw_hierarchy *H_out, void
     if (o.degree < 1 || o.degree > 8 || o.nu < 1 || o.nu > 8) fail(GW_ERR_ARG, "gw_amg_setup: degree and nu must be in 1..8");
     if (o.n_coarse < 1 || o.n_coarse > 4096) fail(GW_ERR_ARG, "gw_amg_setup: n_coarse must be in 1..4096");
     if (o.max_levels < 2 || o.max_levels > 16) fail(GW_ERR_ARG, "gw_amg_setup: max_levels must be in 2..16");
+    if (o.prec == GW_PREC_MIXEDBF16) {
+        o.prec = GW_PREC_MIXED32;
+        o.half_storage |= GW_HALF_FINE;
+    }
     if (o.prec != GW_PREC_FP64 && o.prec != GW_PREC_MIXED32) fail(GW_ERR_ARG, "gw_amg_setup: bad precision");
+    if (o.half_storage & ~(GW_HALF_TRANSFER | GW_HALF_FINE)) fail(GW_ERR_ARG, "gw_amg_setup: bad half_storage bits");
+    if (o.prec == GW_PREC_FP64 && o.half_storage)
+        fail(GW_ERR_ARG, "gw_amg_setup: half_storage belongs to the mixed form");
     if (!(o.delta > 0.0 && o.delta < 1.0)) fail(GW_ERR_ARG, "gw_amg_setup: delta must be in (0, 1)");
     DeviceGuard g(A->dev);
     cudaStream_t st = (cudaStream_t)stream;

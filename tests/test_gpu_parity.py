@@ -277,6 +277,11 @@ def test_bf16_fine_stencil_solves_to_parity(gw, name):
     Ao, bo = ora_assemble(p)
     href, _, _, _ = oracle.Hierarchy(Ao, n_coarse=64).pcg(bo, tol=1e-12)
     assert np.linalg.norm(hb.cpu().numpy() - href) / np.linalg.norm(href) <= REL_ERR
+    # GW_PREC_MIXEDBF16 names the same configuration
+    hp, itp, _, _ = gw.Hierarchy(A, n_coarse=64, prec=gw.GW_PREC_MIXEDBF16).solve(b, tol=TOL)
+    assert itp == itb and torch.equal(hp, hb)
+    with pytest.raises(gw.GwError):
+        gw.Hierarchy(A, prec=gw.GW_PREC_FP64, half_storage=gw.GW_HALF_FINE)
     # the interleaved block path runs the same stored operator
     B = torch.stack([b, 2.0 * b])
     X, its, rels, st = Hb.solve_many(B, tol=TOL)

@@ -103,6 +103,14 @@ static void cheb_coeffs(double lam, int degree, double &c0, double *c1, double *
 // Cycle storage of level k in the cycle precision: A_k (the 7-point stencil on
 // level 0), P_k and R_k when given, the smoother's diagonal weights and the
 // Chebyshev coefficients.  Returns the device bytes it holds.
+// restrictions in sliced ELL are stored over length-sorted rows (padding of
+// the 32-row slices 1.51 -> 1.11 at 128^3); their kernel writes through the
+// row permutation
+#ifndef GW_SORT_RESTRICTION
+#define GW_SORT_RESTRICTION 1
+#endif
+static int sorted_sell(int fmt) { return GW_SORT_RESTRICTION && fmt == FMT_SELL ? FMT_SELL_SORTED : fmt; }
+
 static long long store_level(Hier &H, int k, const DCSR &A, const DCSR *P, const DCSR *R, cudaStream_t st)
 {
     const gw_amg_opts &o = H.o;
@@ -126,9 +134,9 @@ static long long store_level(Hier &H, int k, const DCSR &A, const DCSR *P, const
         CycLevel<double> &c = H.cd[(size_t)k];
         to_store<double>(A, c.A, k == 0 ? FMT_STEN : choose_fmt(A), H.gnx, H.gny, H.gnz, st);
         if (P) to_store<double>(*P, c.P, choose_fmt(*P), 0, 0, 0, st);
-        if (R) to_store<double>(*R, c.R, choose_fmt(*R), 0, 0, 0, st);
+        if (R) to_store<double>(*R, c.R, sorted_sell(choose_fmt(*R)), 0, 0, 0, st);
         c.dw.alloc((size_t)n);
-        k_make_dw<<<std::max(g, 1), 256, 0, st>>>(n, diag.p, scale, nullptr, c.dw.p);
+        gw_launch(k_make_dw, std::max(g, 1), 256, 0, st, n, diag.p, scale, nullptr, c.dw.p);
         c.c0 = c0;
         memcpy(c.c1, c1, sizeof c1);
         memcpy(c.c2, c2, sizeof c2);
@@ -149,9 +157,9 @@ static long long store_level(Hier &H, int k, const DCSR &A, const DCSR *P, const
         }
         if (P && !(k == 0 && H.p0.n)) to_store<float>(*P, c.P, f32(choose_fmt(*P)), 0, 0, 0, st);
         if (k == 0 && H.p0.n) bytes += (long long)H.p0.bytes();
-        if (R) to_store<float>(*R, c.R, f32(choose_fmt(*R)), 0, 0, 0, st);
+        if (R) to_store<float>(*R, c.R, sorted_sell(f32(choose_fmt(*R))), 0, 0, 0, st);
         c.dw.alloc((size_t)n);
-        k_make_dw<<<std::max(g, 1), 256, 0, st>>>(n, diag.p, scale, c.dw.p, nullptr);
+        gw_launch(k_make_dw, std::max(g, 1), 256, 0, st, n, diag.p, scale, c.dw.p, nullptr);
         c.c0 = c0;
         memcpy(c.c1, c1, sizeof c1);
         memcpy(c.c2, c2, sizeof c2);
@@ -563,7 +571,7 @@ int gw_hierarchy_shift(gw_hierarchy H, const double *s, double delta, int *rebui
     }
     DBuf<int> bad(1);
     GW_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
-    k_reuse_check<<<gb, 256, 0, st>>>(n, C->A.rp.p, C->A.ci.p, C->A.v.p, snew.p, H->s_built.p, delta, bad.p);
+    gw_launch(k_reuse_check, gb, 256, 0, st, n, C->A.rp.p, C->A.ci.p, C->A.v.p, snew.p, H->s_built.p, delta, bad.p);
     GW_LAUNCH_CHECK();
     const bool reuse = read_int(bad.p, st) == 0;
     DCSR A;
@@ -577,7 +585,7 @@ int gw_hierarchy_shift(gw_hierarchy H, const double *s, double delta, int *rebui
         GW_CUDA(cudaMemcpyAsync(A.rp.p, C->A.rp.p, A.rp.bytes(), cudaMemcpyDeviceToDevice, st));
         GW_CUDA(cudaMemcpyAsync(A.ci.p, C->A.ci.p, A.ci.bytes(), cudaMemcpyDeviceToDevice, st));
         GW_CUDA(cudaMemcpyAsync(A.v.p, C->A.v.p, A.v.bytes(), cudaMemcpyDeviceToDevice, st));
-        k_shift_diag<<<gb, 256, 0, st>>>(n, A.rp.p, A.ci.p, A.v.p, snew.p);
+        gw_launch(k_shift_diag, gb, 256, 0, st, n, A.rp.p, A.ci.p, A.v.p, snew.p);
         GW_LAUNCH_CHECK();
     }
     if (reuse) {

@@ -125,18 +125,18 @@ void assemble_csr(int nx, int ny, int nz, double dx, double dy, double dz, const
     const int bs = 256;
     const int grid = (int)std::min<long long>((n + bs - 1) / bs, 152LL * 16);
     GW_CUDA(cudaMemsetAsync(dflag, 0, sizeof(int), st));
-    k_asm_validate<<<grid, bs, 0, st>>>(n, Kx, Ky, Kz, q, dflag);
+    gw_launch(k_asm_validate, grid, bs, 0, st, n, Kx, Ky, Kz, q, dflag);
     GW_LAUNCH_CHECK();
     if (read_int(dflag, st)) fail(GW_ERR_ARG, "gw_assemble: a conductivity is <= 0 or not finite, or q is not finite");
     A.nr = A.nc = n;
     A.rp.alloc((size_t)n + 1);
-    k_asm_rowcount<<<grid, bs, 0, st>>>(G, A.rp.p);
+    gw_launch(k_asm_rowcount, grid, bs, 0, st, G, A.rp.p);
     GW_LAUNCH_CHECK();
     exclusive_scan(A.rp.p, A.rp.p, n, st);
     A.nnz = read_int(A.rp.p + n, st);
     A.ci.alloc((size_t)A.nnz);
     A.v.alloc((size_t)A.nnz);
-    k_asm_fill<<<grid, bs, 0, st>>>(G, Kx, Ky, Kz, q, A.rp.p, A.ci.p, A.v.p, b);
+    gw_launch(k_asm_fill, grid, bs, 0, st, G, Kx, Ky, Kz, q, A.rp.p, A.ci.p, A.v.p, b);
     GW_LAUNCH_CHECK();
 }
 
@@ -352,15 +352,15 @@ extern "C" int gw_assemble_noalloc(const gw_grid *grid, const double *Kx, const 
         const int grid_b = (int)std::min<long long>((n + bs - 1) / bs, 152LL * 16);
         int *flag = scratch;
         GW_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), st));
-        k_asm_validate<<<grid_b, bs, 0, st>>>(n, Kx, ky, kz, q, flag);
+        gw_launch(k_asm_validate, grid_b, bs, 0, st, n, Kx, ky, kz, q, flag);
         GW_LAUNCH_CHECK();
         if (read_int(flag, st))
             fail(GW_ERR_ARG, "gw_assemble_noalloc: a conductivity is <= 0 or not finite, or q is not finite");
-        k_asm_rowcount<<<grid_b, bs, 0, st>>>(G, rowptr);
+        gw_launch(k_asm_rowcount, grid_b, bs, 0, st, G, rowptr);
         GW_LAUNCH_CHECK();
         if (!exclusive_scan_in(rowptr, rowptr, n, scratch + 1, NOALLOC_SCRATCH_INTS - 1, st))
             fail(GW_ERR_ARG, "gw_assemble_noalloc: grid too large for the scan workspace");
-        k_asm_fill<<<grid_b, bs, 0, st>>>(G, Kx, ky, kz, q, rowptr, col, val, b);
+        gw_launch(k_asm_fill, grid_b, bs, 0, st, G, Kx, ky, kz, q, rowptr, col, val, b);
         GW_LAUNCH_CHECK();
         GW_CUDA(cudaStreamSynchronize(st));
     } catch (const Error &e) {
@@ -400,7 +400,7 @@ extern "C" int gw_adjoint_gradient(const gw_grid *grid, const double *Kx, const 
         }
         cudaStream_t st = (cudaStream_t)stream;
         const int grid_b = (int)std::min<long long>((n64 + 255) / 256, 152LL * 16);
-        k_adj_grad<<<grid_b, 256, 0, st>>>(G, Kx, ky, kz, h, lambda, grad);
+        gw_launch(k_adj_grad, grid_b, 256, 0, st, G, Kx, ky, kz, h, lambda, grad);
         GW_LAUNCH_CHECK();
     } catch (const Error &e) {
         set_last_error(e.msg.c_str());
@@ -422,10 +422,10 @@ extern "C" int gw_misfit(int n, const double *h, int nobs, const int *obs, const
         cudaStream_t st = (cudaStream_t)stream;
         DBuf<double> jd(1);
         if (dJdh) {
-            k_zero<<<(int)std::min<long long>((n + 255) / 256, 152LL * 16), 256, 0, st>>>(n, dJdh);
+            gw_launch(k_zero, (int)std::min<long long>((n + 255) / 256, 152LL * 16), 256, 0, st, n, dJdh);
             GW_LAUNCH_CHECK();
         }
-        k_misfit<<<1, 1024, 0, st>>>(nobs, h, obs, hobs, jd.p, dJdh);
+        gw_launch(k_misfit, 1, 1024, 0, st, nobs, h, obs, hobs, jd.p, dJdh);
         GW_LAUNCH_CHECK();
         GW_CUDA(cudaMemcpyAsync(J, jd.p, sizeof(double), cudaMemcpyDefault, st));
         GW_CUDA(cudaStreamSynchronize(st));
@@ -469,7 +469,7 @@ extern "C" int gw_darcy_flux(const gw_grid *grid, const double *Kx, const double
         cudaStream_t st = (cudaStream_t)stream;
         const long long n = (long long)nx * ny * nz;
         const int gb = (int)std::min<long long>((n + 255) / 256, 152LL * 8);
-        k_darcy<<<gb, 256, 0, st>>>(G, K[0], K[1], K[2], h, v[0], v[1], v[2]);
+        gw_launch(k_darcy, gb, 256, 0, st, G, K[0], K[1], K[2], h, v[0], v[1], v[2]);
         GW_LAUNCH_CHECK();
     } catch (const Error &e) {
         set_last_error(e.msg.c_str());

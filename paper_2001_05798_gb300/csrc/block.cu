@@ -19,6 +19,7 @@
 #include <string.h>
 
 #include <memory>
+#include <type_traits>
 #include <vector>
 
 #include "gw_internal.cuh"
@@ -133,6 +134,8 @@ struct BSell {
     const int *__restrict__ sp;
     const int *__restrict__ ci;
     const T *__restrict__ v;
+    const int *__restrict__ perm;  // row of slot row r (null: r); restriction matrices only
+    __device__ __forceinline__ int out_row(int r) const { return perm ? __ldg(perm + r) : r; }
     template <int CW, class F>
     __device__ __forceinline__ CV<T, CW> dot(int r, F f) const
     {
@@ -196,7 +199,7 @@ template <class T, class F>
 static void with_bmat(const MatStore<T> &M, F f)
 {
     switch (M.fmt) {
-    case FMT_SELL: f(BSell<T>{M.sell.sp.p, M.sell.ci.p, M.sell.v.p}); break;
+    case FMT_SELL: f(BSell<T>{M.sell.sp.p, M.sell.ci.p, M.sell.v.p, M.sell.perm.p}); break;
     case FMT_CSR4:
     case FMT_CSR8:
     case FMT_CSR32: f(BCsr<T>{M.csr.rp.p, M.csr.ci.p, M.csr.v.p}); break;
@@ -525,7 +528,13 @@ __global__ void __launch_bounds__(BS) kb_spmv(M Rm, int n, const float *__restri
 {
     pdl_enter();
     if (bfinished(c)) return;
-    BLOCK_ROWS(n, KB, CW) cst<CW>(y + (size_t)i * KB + off, Rm.template dot<CW>(i, BVec<float, CW, KB>{x + off}));
+    BLOCK_ROWS(n, KB, CW)
+    {
+        const CV<float, CW> s = Rm.template dot<CW>(i, BVec<float, CW, KB>{x + off});
+        int o = i;
+        if constexpr (std::is_same<M, BSell<float>>::value) o = Rm.out_row(i);
+        cst<CW>(y + (size_t)o * KB + off, s);
+    }
 }
 
 // x += P e (interpolate and correct)
@@ -1130,7 +1139,7 @@ static void block_run(Hier &H, int kk, const double *B, double *X, double tol, i
         GW_CUDA(cudaMemcpyAsync(S.stage.p, B, cols, cudaMemcpyHostToDevice, st));
         Bd = S.stage.p;
     }
-    kb_gather<KB><<<gg, BS, 0, st>>>(n, kk, Bd, S.b64.p);
+    gw_launch(kb_gather<KB>, gg, BS, 0, st, n, kk, Bd, S.b64.p);
     BlkCtl init;
     memset(&init, 0, sizeof init);
     for (int j = 0; j < KB; ++j) {
@@ -1155,7 +1164,7 @@ static void block_run(Hier &H, int kk, const double *B, double *X, double tol, i
     BCyc<KB>{H, S, S.ctl.p, S.part.p, st}.rel_update(1);
     H.launches += 2;
     double *Xd = is_device_ptr(X) ? X : S.stage.p;
-    kb_scatter<KB><<<gg, BS, 0, st>>>(n, kk, S.x64.p, Xd);
+    gw_launch(kb_scatter<KB>, gg, BS, 0, st, n, kk, S.x64.p, Xd);
     H.launches += 2;
     GW_LAUNCH_CHECK();
     if (Xd != X) GW_CUDA(cudaMemcpyAsync(X, Xd, cols, cudaMemcpyDeviceToHost, st));

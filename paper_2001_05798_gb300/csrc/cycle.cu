@@ -27,6 +27,12 @@
 namespace gw {
 
 
+// chunks of a sliced-ELL row whose loads the compiler may issue together
+#ifndef GW_SELL_UNROLL
+#define GW_SELL_UNROLL 1
+#endif
+constexpr int SELL_UNROLL = GW_SELL_UNROLL;
+
 // ------------------------------------------------------------ matrix views --
 // R consecutive values handled by one thread (R = 4 floats or 2 doubles is
 // one 16-byte load or store).
@@ -196,6 +202,7 @@ struct SV {
     const int *__restrict__ ci;
     const T *__restrict__ v;
     int nr;
+    const int *__restrict__ perm;  // row of slot row r (null: r); restriction matrices only
 };
 
 template <class T>
@@ -232,6 +239,7 @@ struct MSell {
             const int nch = (a.sp[s + 1] - base) / (SELL_C * V);
             const VV *vv = reinterpret_cast<const VV *>(a.v + base) + rl;
             const VI *cc = reinterpret_cast<const VI *>(a.ci + base) + rl;
+#pragma unroll SELL_UNROLL
             for (int c = (G == 1 ? 0 : lane); c < nch; c += G) {
                 const VV x = __ldg(vv + c * SELL_C);
                 const VI j = __ldg(cc + c * SELL_C);
@@ -253,6 +261,19 @@ struct MSell {
         return VecN<T, 1>{{acc}};
     }
 };
+
+// output row of a row product: the slot row's row for a length-sorted sliced
+// ELL, the row itself otherwise
+template <class M>
+__device__ __forceinline__ int out_row(const M &, int i)
+{
+    return i;
+}
+template <class T, int G>
+__device__ __forceinline__ int out_row(const MSell<T, G> &m, int i)
+{
+    return m.a.perm ? __ldg(m.a.perm + i) : i;
+}
 
 // CSR read by a group of G lanes per row; every lane of the group gets the sum.
 template <class T, int G_>
@@ -485,7 +506,7 @@ static void with_mat(const MatStore<T> &M, F f)
 {
     switch (M.fmt) {
     case FMT_SELL: {
-        const SV<T> sv{M.sell.sp.p, M.sell.ci.p, M.sell.v.p, M.sell.nr};
+        const SV<T> sv{M.sell.sp.p, M.sell.ci.p, M.sell.v.p, M.sell.nr, M.sell.perm.p};
         if (M.nnz > (long long)SELL_LONG_ROW * M.nr) f(MSell<T, GW_SELL_LANES>{sv});
         else f(MSell<T, 1>{sv});
         break;
@@ -680,7 +701,10 @@ __global__ void __launch_bounds__(BS) k_spmv(M Rm, int n, const typename M::valu
     GROUP_ROWS(M, n)
     {
         const VecN<T, M::R> s = Rm.dot(i, lane, GVec<T, T>{x});
-        if (i < n && lane == 0) st<M::R>(y + i, s);
+        if (i < n && lane == 0) {
+            if constexpr (M::R == 1) y[out_row(Rm, i)] = s.v[0];
+            else st<M::R>(y + i, s);
+        }
     }
 }
 

@@ -122,7 +122,8 @@ struct Sell {
     DBuf<int> sp;  // nslices + 1 slice offsets (elements)
     DBuf<int> ci;
     DBuf<T> v;
-    size_t bytes() const { return sp.bytes() + ci.bytes() + v.bytes(); }
+    DBuf<int> perm;  // rows sorted by length within windows: slot row r is row perm[r] (empty: r)
+    size_t bytes() const { return sp.bytes() + ci.bytes() + v.bytes() + perm.bytes(); }
 };
 
 // CSR in the cycle's precision T (read by groups of 8 or 32 lanes per row).
@@ -173,6 +174,11 @@ struct Sell16 {
 };
 
 enum { FMT_SELL = 0, FMT_CSR4 = 1, FMT_CSR8 = 2, FMT_CSR32 = 3, FMT_STEN = 4, FMT_SELL16 = 5, FMT_STENB = 6 };
+// to_store request: sliced ELL over rows sorted by length within windows of
+// SELL_SORT_WINDOW rows (stored as FMT_SELL with a row permutation); only
+// for matrices read by the restriction, which writes its output row through it
+constexpr int FMT_SELL_SORTED = 7;
+constexpr int SELL_SORT_WINDOW = 256;
 
 template <class T>
 struct MatStore {
@@ -214,6 +220,18 @@ bool exclusive_scan_in(const int *in, int *out, int n, int *scratch, size_t cap,
 int read_int(const int *dptr, cudaStream_t st);
 void to_device(void *dst, const void *src, size_t bytes, cudaStream_t st);
 bool is_device_ptr(const void *p);
+// Loads a kernel's code before its first launch outside a graph capture,
+// waiting while another thread captures (with lazy module loading, a kernel
+// loaded during a capture on another thread invalidates that capture).
+void prime_kernel(const void *fn);
+
+template <class... KArgs, class... Args>
+inline void gw_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args &&...args)
+{
+    prime_kernel((const void *)kernel);
+    kernel<<<grid, block, smem, st>>>(std::forward<Args>(args)...);
+}
+
 // one wave of a kernel on the current device: resident blocks per SM (at
 // block_size threads) times the SMs; cached per device and kernel
 int kernel_wave(const void *fn, int block_size);
@@ -261,7 +279,7 @@ double setup_gershgorin(const DCSR &A, DBuf<double> &diag, cudaStream_t st);  //
 double setup_power_lambda(const DCSR &A, const double *diag, uint64_t seed, int level, cudaStream_t st);
 
 template <class T>
-void to_sell(const DCSR &A, Sell<T> &S, cudaStream_t st);
+void to_sell(const DCSR &A, Sell<T> &S, cudaStream_t st, bool sorted = false);
 
 // ---------------------------------------------------------------- cycle --
 // Storage of one level of the V-cycle in the cycle's precision T.

@@ -124,9 +124,9 @@ void setup_strength(const DCSR &A, double theta2, DBuf<unsigned char> &S, cudaSt
     DBuf<double> d((size_t)A.nr);
     DBuf<unsigned char> raw((size_t)A.nnz + 1);
     S.alloc((size_t)A.nnz + 1);
-    k_diag<<<nblk(A.nr, 256), 256, 0, st>>>(A.nr, A.rp.p, A.ci.p, A.v.p, d.p);
-    k_strength_raw<<<nblk(A.nr, 256), 256, 0, st>>>(A.nr, A.rp.p, A.ci.p, A.v.p, d.p, theta2, raw.p);
-    k_strength_sym<<<nblk(A.nr, 256), 256, 0, st>>>(A.nr, A.rp.p, A.ci.p, raw.p, S.p);
+    gw_launch(k_diag, nblk(A.nr, 256), 256, 0, st, A.nr, A.rp.p, A.ci.p, A.v.p, d.p);
+    gw_launch(k_strength_raw, nblk(A.nr, 256), 256, 0, st, A.nr, A.rp.p, A.ci.p, A.v.p, d.p, theta2, raw.p);
+    gw_launch(k_strength_sym, nblk(A.nr, 256), 256, 0, st, A.nr, A.rp.p, A.ci.p, raw.p, S.p);
     GW_LAUNCH_CHECK();
     GW_CUDA(cudaStreamSynchronize(st));
 }
@@ -243,14 +243,14 @@ int setup_mis2(const DCSR &A, const unsigned char *S, uint64_t seed, int level, 
         if (rounds >= max_rounds) fail(GW_ERR_SETUP, "MIS-2 did not finish in %d rounds on level %d", max_rounds, level);
         ++rounds;
         GW_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int), st));
-        k_mis_max1<<<g, 256, 0, st>>>(n, A.rp.p, A.ci.p, S, state.p, seed, level, mk.p, mi.p);
-        k_mis_select<<<g, 256, 0, st>>>(n, A.rp.p, A.ci.p, S, state.p, mk.p, mi.p);
-        k_mis_near1<<<g, 256, 0, st>>>(n, A.rp.p, A.ci.p, S, state.p, near1.p);
-        k_mis_remove<<<g, 256, 0, st>>>(n, A.rp.p, A.ci.p, S, state.p, near1.p, cnt.p);
+        gw_launch(k_mis_max1, g, 256, 0, st, n, A.rp.p, A.ci.p, S, state.p, seed, level, mk.p, mi.p);
+        gw_launch(k_mis_select, g, 256, 0, st, n, A.rp.p, A.ci.p, S, state.p, mk.p, mi.p);
+        gw_launch(k_mis_near1, g, 256, 0, st, n, A.rp.p, A.ci.p, S, state.p, near1.p);
+        gw_launch(k_mis_remove, g, 256, 0, st, n, A.rp.p, A.ci.p, S, state.p, near1.p, cnt.p);
         GW_LAUNCH_CHECK();
         if (read_int(cnt.p, st) == 0) break;
     }
-    k_mis_roots<<<g, 256, 0, st>>>(n, state.p, root.p);
+    gw_launch(k_mis_roots, g, 256, 0, st, n, state.p, root.p);
     GW_LAUNCH_CHECK();
     return rounds;
 }
@@ -329,12 +329,12 @@ int setup_aggregate(const DCSR &A, const unsigned char *S, const unsigned char *
     DBuf<int> id((size_t)n + 1), agg1((size_t)n), rootof((size_t)n), bad(1);
     agg.alloc((size_t)n);
     const int g = nblk(n, 256);
-    k_root_flag<<<g, 256, 0, st>>>(n, root, id.p);
+    gw_launch(k_root_flag, g, 256, 0, st, n, root, id.p);
     GW_LAUNCH_CHECK();
     exclusive_scan(id.p, id.p, n, st);
-    k_join1<<<g, 256, 0, st>>>(n, A.rp.p, A.ci.p, S, root, id.p, agg1.p, rootof.p);
+    gw_launch(k_join1, g, 256, 0, st, n, A.rp.p, A.ci.p, S, root, id.p, agg1.p, rootof.p);
     GW_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
-    k_join2<<<g, 256, 0, st>>>(n, A.rp.p, A.ci.p, S, agg1.p, rootof.p, seed, level, agg.p, bad.p);
+    gw_launch(k_join2, g, 256, 0, st, n, A.rp.p, A.ci.p, S, agg1.p, rootof.p, seed, level, agg.p, bad.p);
     GW_LAUNCH_CHECK();
     if (read_int(bad.p, st)) fail(GW_ERR_SETUP, "aggregation left nodes unassigned on level %d", level);
     return read_int(id.p + n, st);
@@ -452,9 +452,9 @@ void setup_smooth_p(const DCSR &A, const unsigned char *S, const int *agg, int n
     DBuf<unsigned char> hs((size_t)n);
     DBuf<unsigned long long> rb(1);
     const int g = nblk(n, 256);
-    k_diag<<<g, 256, 0, st>>>(n, A.rp.p, A.ci.p, A.v.p, d.p);
+    gw_launch(k_diag, g, 256, 0, st, n, A.rp.p, A.ci.p, A.v.p, d.p);
     GW_CUDA(cudaMemsetAsync(rb.p, 0, sizeof(unsigned long long), st));
-    k_filter<<<g, 256, 0, st>>>(n, A.rp.p, A.ci.p, A.v.p, S, d.p, aF.p, hs.p, rb.p);
+    gw_launch(k_filter, g, 256, 0, st, n, A.rp.p, A.ci.p, A.v.p, S, d.p, aF.p, hs.p, rb.p);
     GW_LAUNCH_CHECK();
     unsigned long long bits = 0;
     GW_CUDA(cudaMemcpyAsync(&bits, rb.p, sizeof bits, cudaMemcpyDeviceToHost, st));
@@ -466,13 +466,13 @@ void setup_smooth_p(const DCSR &A, const unsigned char *S, const int *agg, int n
     P.nr = n;
     P.nc = nagg;
     P.rp.alloc((size_t)n + 1);
-    k_p_count<<<g, 256, 0, st>>>(n, A.rp.p, A.ci.p, S, agg, hs.p, P.rp.p);
+    gw_launch(k_p_count, g, 256, 0, st, n, A.rp.p, A.ci.p, S, agg, hs.p, P.rp.p);
     GW_LAUNCH_CHECK();
     exclusive_scan(P.rp.p, P.rp.p, n, st);
     P.nnz = read_int(P.rp.p + n, st);
     P.ci.alloc((size_t)P.nnz);
     P.v.alloc((size_t)P.nnz);
-    k_p_fill<<<g, 256, 0, st>>>(n, A.rp.p, A.ci.p, A.v.p, S, agg, hs.p, aF.p, *omega, P.rp.p, P.ci.p, P.v.p);
+    gw_launch(k_p_fill, g, 256, 0, st, n, A.rp.p, A.ci.p, A.v.p, S, agg, hs.p, aF.p, *omega, P.rp.p, P.ci.p, P.v.p);
     GW_LAUNCH_CHECK();
 }
 
@@ -514,15 +514,15 @@ bool setup_implicit_p(const DCSR &A, const unsigned char *S, double omega, int n
     DBuf<unsigned long long> rb(1);
     DBuf<int> bad(1);
     const int g = nblk(n, 256);
-    k_diag<<<g, 256, 0, st>>>(n, A.rp.p, A.ci.p, A.v.p, d.p);
+    gw_launch(k_diag, g, 256, 0, st, n, A.rp.p, A.ci.p, A.v.p, d.p);
     GW_CUDA(cudaMemsetAsync(rb.p, 0, sizeof(unsigned long long), st));
     GW_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
-    k_filter<<<g, 256, 0, st>>>(n, A.rp.p, A.ci.p, A.v.p, S, d.p, aF.p, hs.p, rb.p);
+    gw_launch(k_filter, g, 256, 0, st, n, A.rp.p, A.ci.p, A.v.p, S, d.p, aF.p, hs.p, rb.p);
     out.s.alloc((size_t)n);
     out.fx.alloc((size_t)n);
     out.fy.alloc((size_t)n);
     out.fz.alloc((size_t)n);
-    k_p_implicit<<<g, 256, 0, st>>>(n, nx, nx * ny, A.rp.p, A.ci.p, A.v.p, S, aF.p, hs.p, omega, out.s.p, out.fx.p,
+    gw_launch(k_p_implicit, g, 256, 0, st, n, nx, nx * ny, A.rp.p, A.ci.p, A.v.p, S, aF.p, hs.p, omega, out.s.p, out.fx.p,
                                     out.fy.p, out.fz.p, bad.p);
     GW_LAUNCH_CHECK();
     if (read_int(bad.p, st) != 0) {
@@ -589,11 +589,11 @@ void setup_transpose(const DCSR &P, DCSR &R, cudaStream_t st)
     DBuf<double> tv((size_t)R.nnz);
     GW_CUDA(cudaMemsetAsync(R.rp.p, 0, ((size_t)R.nr + 1) * sizeof(int), st));
     GW_CUDA(cudaMemsetAsync(fill.p, 0, (size_t)R.nr * sizeof(int), st));
-    k_tr_count<<<nblk(P.nnz, 256), 256, 0, st>>>(P.nnz, P.ci.p, R.rp.p);
+    gw_launch(k_tr_count, nblk(P.nnz, 256), 256, 0, st, P.nnz, P.ci.p, R.rp.p);
     GW_LAUNCH_CHECK();
     exclusive_scan(R.rp.p, R.rp.p, R.nr, st);
-    k_tr_scatter<<<nblk(P.nr, 256), 256, 0, st>>>(P.nr, P.rp.p, P.ci.p, P.v.p, R.rp.p, fill.p, tci.p, tv.p);
-    k_rank_sort_rows<<<nblk((long long)R.nr * 32, 256), 256, 0, st>>>(R.nr, R.rp.p, tci.p, tv.p, R.ci.p, R.v.p);
+    gw_launch(k_tr_scatter, nblk(P.nr, 256), 256, 0, st, P.nr, P.rp.p, P.ci.p, P.v.p, R.rp.p, fill.p, tci.p, tv.p);
+    gw_launch(k_rank_sort_rows, nblk((long long)R.nr * 32, 256), 256, 0, st, R.nr, R.rp.p, tci.p, tv.p, R.ci.p, R.v.p);
     GW_LAUNCH_CHECK();
     GW_CUDA(cudaStreamSynchronize(st));
 }
@@ -732,7 +732,7 @@ void setup_spgemm(const DCSR &L, const DCSR &Rm, DCSR &C, cudaStream_t st)
     DBuf<int> maxub(1), ovf(1);
     GW_CUDA(cudaMemsetAsync(maxub.p, 0, sizeof(int), st));
     GW_CUDA(cudaMemsetAsync(ovf.p, 0, sizeof(int), st));
-    k_sg_bound<<<nblk(L.nr, 256), 256, 0, st>>>(L.nr, Rm.nc, L.rp.p, L.ci.p, Rm.rp.p, maxub.p);
+    gw_launch(k_sg_bound, nblk(L.nr, 256), 256, 0, st, L.nr, Rm.nc, L.rp.p, L.ci.p, Rm.rp.p, maxub.p);
     GW_LAUNCH_CHECK();
     const int ub = read_int(maxub.p, st);
     int H = 32;
@@ -751,110 +751,112 @@ void setup_spgemm(const DCSR &L, const DCSR &Rm, DCSR &C, cudaStream_t st)
     C.nc = Rm.nc;
     C.rp.alloc((size_t)C.nr + 1);
     const int grid = (int)std::max(1LL, std::min<long long>(((long long)L.nr + W - 1) / W, 152LL * 64));
-    k_sg_symbolic<<<grid, 32 * W, smem_sym, st>>>(L.nr, L.rp.p, L.ci.p, Rm.rp.p, Rm.ci.p, H, C.rp.p, ovf.p);
+    gw_launch(k_sg_symbolic, grid, 32 * W, smem_sym, st, L.nr, L.rp.p, L.ci.p, Rm.rp.p, Rm.ci.p, H, C.rp.p, ovf.p);
     GW_LAUNCH_CHECK();
     if (read_int(ovf.p, st)) fail(GW_ERR_SETUP, "SpGEMM row has more than %d distinct columns", H / 2);
     exclusive_scan(C.rp.p, C.rp.p, C.nr, st);
     C.nnz = read_int(C.rp.p + C.nr, st);
     C.ci.alloc((size_t)C.nnz);
     C.v.alloc((size_t)C.nnz);
-    k_sg_numeric<<<grid, 32 * W, smem_num, st>>>(L.nr, L.rp.p, L.ci.p, L.v.p, Rm.rp.p, Rm.ci.p, Rm.v.p, H, C.rp.p,
+    gw_launch(k_sg_numeric, grid, 32 * W, smem_num, st, L.nr, L.rp.p, L.ci.p, L.v.p, Rm.rp.p, Rm.ci.p, Rm.v.p, H, C.rp.p,
                                                   C.ci.p, C.v.p);
     GW_LAUNCH_CHECK();
     GW_CUDA(cudaStreamSynchronize(st));
 }
 
 // ---------------------------------------------------------- coarsest level --
-__global__ void k_dense_fill(int n, const int *__restrict__ rp, const int *__restrict__ ci,
-                             const double *__restrict__ v, double *__restrict__ a)
+// Dense inverse of the coarsest level by Gauss-Jordan elimination with
+// partial pivoting on the augmented matrix W = [A | I] (n x 2n, row-major):
+// after step k column k of the left half is e_k, and after n steps the right
+// half is the inverse.  Each step is two launches: one block picks the pivot
+// (largest |W_ik|, i >= k, lowest index on ties), swaps it into row k, scales
+// that row and copies it and the multipliers W_ik aside; then the whole GPU
+// subtracts m_i times the pivot row from every other row.  The O(n^3)
+// FP64 work so runs on every SM instead of one.
+__global__ void __launch_bounds__(1024) k_gj_pivot(int n, int k, double *__restrict__ W, double *__restrict__ prow,
+                                                   double *__restrict__ m, int *__restrict__ singular)
+{
+    __shared__ double sv[1024];
+    __shared__ int si[1024];
+    const int tid = threadIdx.x, bs = blockDim.x, w2 = 2 * n;
+    if (*singular) return;
+    double best = -1.0;
+    int bi = n;
+    for (int i = k + tid; i < n; i += bs) {
+        const double t = fabs(W[(size_t)i * w2 + k]);
+        if (t > best) {
+            best = t;
+            bi = i;
+        }
+    }
+    sv[tid] = best;
+    si[tid] = bi;
+    __syncthreads();
+    for (int off = bs >> 1; off > 0; off >>= 1) {
+        if (tid < off) {
+            const double o = sv[tid + off];
+            const int oi = si[tid + off];
+            if (o > sv[tid] || (o == sv[tid] && oi < si[tid])) {
+                sv[tid] = o;
+                si[tid] = oi;
+            }
+        }
+        __syncthreads();
+    }
+    const int p = si[0];
+    if (!(sv[0] > 0.0) || !isfinite(sv[0])) {
+        if (tid == 0) *singular = 1;
+        return;
+    }
+    if (p != k)
+        for (int j = tid; j < w2; j += bs) {
+            const double t = W[(size_t)k * w2 + j];
+            W[(size_t)k * w2 + j] = W[(size_t)p * w2 + j];
+            W[(size_t)p * w2 + j] = t;
+        }
+    __syncthreads();
+    const double pv = W[(size_t)k * w2 + k];
+    __syncthreads();
+    for (int j = tid; j < w2; j += bs) {
+        const double t = j < k ? 0.0 : W[(size_t)k * w2 + j] / pv;
+        prow[j] = t;
+        W[(size_t)k * w2 + j] = t;
+    }
+    for (int i = tid; i < n; i += bs) m[i] = i == k ? 0.0 : W[(size_t)i * w2 + k];
+}
+
+__global__ void k_gj_elim(int n, int k, double *__restrict__ W, const double *__restrict__ prow,
+                          const double *__restrict__ m, const int *__restrict__ singular)
+{
+    if (*singular) return;
+    const int w2 = 2 * n, cols = w2 - k;
+    const long long total = (long long)n * cols;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(t / cols), j = k + (int)(t % cols);
+        const double mi = m[i];
+        if (i == k || mi == 0.0) continue;
+        W[(size_t)i * w2 + j] -= mi * prow[j];
+    }
+}
+
+__global__ void k_gj_copy(int n, const double *__restrict__ W, double *__restrict__ X)
+{
+    GRID_STRIDE(t, (long long)n * n)
+    {
+        const int i = (int)(t / n), j = (int)(t % n);
+        X[t] = W[(size_t)i * 2 * n + n + j];
+    }
+}
+
+__global__ void k_gj_fill(int n, const int *__restrict__ rp, const int *__restrict__ ci, const double *__restrict__ v,
+                          double *__restrict__ W)
 {
     GRID_STRIDE(ii, n)
     {
         const int i = (int)ii;
-        for (int e = rp[i]; e < rp[i + 1]; ++e) a[(size_t)i * n + ci[e]] = v[e];
-    }
-}
-
-// Doolittle LU with partial pivoting (first row of largest |a_ik|), one block.
-__global__ void k_lu_factor(int n, double *__restrict__ a, int *__restrict__ piv, int *__restrict__ singular)
-{
-    __shared__ double sv[1024];
-    __shared__ int si[1024];
-    const int tid = threadIdx.x, bs = blockDim.x;
-    for (int k = 0; k < n; ++k) {
-        double best = -1.0;
-        int bi = n;
-        for (int i = k + tid; i < n; i += bs) {
-            const double t = fabs(a[(size_t)i * n + k]);
-            if (t > best) {
-                best = t;
-                bi = i;
-            }
-        }
-        sv[tid] = best;
-        si[tid] = bi;
-        __syncthreads();
-        for (int off = bs >> 1; off > 0; off >>= 1) {
-            if (tid < off) {
-                const double o = sv[tid + off];
-                const int oi = si[tid + off];
-                if (o > sv[tid] || (o == sv[tid] && oi < si[tid])) {
-                    sv[tid] = o;
-                    si[tid] = oi;
-                }
-            }
-            __syncthreads();
-        }
-        const int p = si[0];
-        const double pmax = sv[0];
-        __syncthreads();
-        if (tid == 0) {
-            piv[k] = p;
-            if (!(pmax > 0.0)) *singular = 1;
-        }
-        if (!(pmax > 0.0)) return;
-        if (p != k)
-            for (int j = tid; j < n; j += bs) {
-                const double t = a[(size_t)k * n + j];
-                a[(size_t)k * n + j] = a[(size_t)p * n + j];
-                a[(size_t)p * n + j] = t;
-            }
-        __syncthreads();
-        const double pv = a[(size_t)k * n + k];
-        for (int i = k + 1 + tid; i < n; i += bs) a[(size_t)i * n + k] /= pv;
-        __syncthreads();
-        const int m = n - k - 1;
-        for (long long idx = tid; idx < (long long)m * m; idx += bs) {
-            const int i = k + 1 + (int)(idx / m), j = k + 1 + (int)(idx % m);
-            a[(size_t)i * n + j] -= a[(size_t)i * n + k] * a[(size_t)k * n + j];
-        }
-        __syncthreads();
-    }
-}
-
-// Column j of the inverse: solve L U x = P e_j; thread j owns column j of X.
-__global__ void k_lu_inverse(int n, const double *__restrict__ lu, const int *__restrict__ piv, double *__restrict__ X)
-{
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
-    for (int i = 0; i < n; ++i) X[(size_t)i * n + j] = i == j ? 1.0 : 0.0;
-    for (int k = 0; k < n; ++k) {
-        const int p = piv[k];
-        if (p != k) {
-            const double t = X[(size_t)k * n + j];
-            X[(size_t)k * n + j] = X[(size_t)p * n + j];
-            X[(size_t)p * n + j] = t;
-        }
-    }
-    for (int i = 0; i < n; ++i) {
-        double s = X[(size_t)i * n + j];
-        for (int m = 0; m < i; ++m) s -= lu[(size_t)i * n + m] * X[(size_t)m * n + j];
-        X[(size_t)i * n + j] = s;
-    }
-    for (int i = n - 1; i >= 0; --i) {
-        double s = X[(size_t)i * n + j];
-        for (int m = i + 1; m < n; ++m) s -= lu[(size_t)i * n + m] * X[(size_t)m * n + j];
-        X[(size_t)i * n + j] = s / lu[(size_t)i * n + i];
+        for (int e = rp[i]; e < rp[i + 1]; ++e) W[(size_t)i * 2 * n + ci[e]] = v[e];
+        W[(size_t)i * 2 * n + n + i] = 1.0;
     }
 }
 
@@ -862,16 +864,24 @@ void setup_dense_inverse(const DCSR &A, DBuf<double> &Ainv, cudaStream_t st)
 {
     const int n = A.nr;
     if (n > 4096) fail(GW_ERR_SETUP, "coarsest level has %d unknowns (more than 4096)", n);
-    DBuf<double> lu((size_t)n * n);
-    DBuf<int> piv((size_t)n), sing(1);
+    DBuf<double> W((size_t)n * 2 * n), prow((size_t)2 * n), m((size_t)n);
+    DBuf<int> sing(1);
     Ainv.alloc((size_t)n * n);
-    GW_CUDA(cudaMemsetAsync(lu.p, 0, lu.bytes(), st));
+    GW_CUDA(cudaMemsetAsync(W.p, 0, W.bytes(), st));
     GW_CUDA(cudaMemsetAsync(sing.p, 0, sizeof(int), st));
-    k_dense_fill<<<nblk(n, 128), 128, 0, st>>>(n, A.rp.p, A.ci.p, A.v.p, lu.p);
-    k_lu_factor<<<1, 1024, 0, st>>>(n, lu.p, piv.p, sing.p);
+    gw_launch(k_gj_fill, nblk(n, 128), 128, 0, st, n, A.rp.p, A.ci.p, A.v.p, W.p);
+    int sms = 0, dev = 0;
+    GW_CUDA(cudaGetDevice(&dev));
+    GW_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    for (int k = 0; k < n; ++k) {
+        gw_launch(k_gj_pivot, 1, 1024, 0, st, n, k, W.p, prow.p, m.p, sing.p);
+        const long long total = (long long)n * (2 * n - k);
+        const int g = (int)std::max(1LL, std::min<long long>((total + 255) / 256, 8LL * std::max(1, sms)));
+        gw_launch(k_gj_elim, g, 256, 0, st, n, k, W.p, prow.p, m.p, sing.p);
+    }
     GW_LAUNCH_CHECK();
     if (read_int(sing.p, st)) fail(GW_ERR_SETUP, "coarsest-level matrix (%d unknowns) is singular", n);
-    k_lu_inverse<<<(n + 31) / 32, 32, 0, st>>>(n, lu.p, piv.p, Ainv.p);
+    gw_launch(k_gj_copy, nblk((long long)n * n, 256), 256, 0, st, n, W.p, Ainv.p);
     GW_LAUNCH_CHECK();
     GW_CUDA(cudaStreamSynchronize(st));
 }
@@ -899,7 +909,7 @@ double setup_gershgorin(const DCSR &A, DBuf<double> &diag, cudaStream_t st)
     diag.alloc((size_t)A.nr);
     DBuf<unsigned long long> rb(1);
     GW_CUDA(cudaMemsetAsync(rb.p, 0, sizeof(unsigned long long), st));
-    k_gersh<<<nblk(A.nr, 256), 256, 0, st>>>(A.nr, A.rp.p, A.ci.p, A.v.p, diag.p, rb.p);
+    gw_launch(k_gersh, nblk(A.nr, 256), 256, 0, st, A.nr, A.rp.p, A.ci.p, A.v.p, diag.p, rb.p);
     GW_LAUNCH_CHECK();
     unsigned long long bits = 0;
     GW_CUDA(cudaMemcpyAsync(&bits, rb.p, sizeof bits, cudaMemcpyDeviceToHost, st));
@@ -973,13 +983,13 @@ double setup_power_lambda(const DCSR &A, const double *diag, uint64_t seed, int 
 {
     const int n = A.nr, g = nblk(n, 256, 1024);
     DBuf<double> v((size_t)n), w((size_t)n), part((size_t)g);
-    k_pow_start<<<g, 256, 0, st>>>(n, seed, level, v.p);
-    k_sumsq<<<g, 256, 0, st>>>(n, v.p, part.p);
+    gw_launch(k_pow_start, g, 256, 0, st, n, seed, level, v.p);
+    gw_launch(k_sumsq, g, 256, 0, st, n, v.p, part.p);
     GW_LAUNCH_CHECK();
     double scale = 1.0 / sqrt(host_sum(part, g, st));
     double lam = 0.0;
     for (int it = 0; it < 10; ++it) {
-        k_pow_step<<<g, 256, 0, st>>>(n, A.rp.p, A.ci.p, A.v.p, diag, v.p, scale, w.p, part.p);
+        gw_launch(k_pow_step, g, 256, 0, st, n, A.rp.p, A.ci.p, A.v.p, diag, v.p, scale, w.p, part.p);
         GW_LAUNCH_CHECK();
         lam = sqrt(host_sum(part, g, st));
         std::swap(v, w);
@@ -989,14 +999,35 @@ double setup_power_lambda(const DCSR &A, const double *diag, uint64_t seed, int 
 }
 
 // ------------------------------------------------------- sliced ELL format --
-__global__ void k_sell_width(int nr, int nslices, int V, const int *__restrict__ rp, int *__restrict__ width)
+// perm for rows sorted by descending length (ties by index) within windows of
+// SELL_SORT_WINDOW rows: one block per window, rank by counting
+__global__ void __launch_bounds__(SELL_SORT_WINDOW) k_sell_sort(int nr, const int *__restrict__ rp,
+                                                                int *__restrict__ perm)
+{
+    __shared__ int len[SELL_SORT_WINDOW];
+    const int w0 = blockIdx.x * SELL_SORT_WINDOW, t = threadIdx.x, r = w0 + t;
+    const int m = min(SELL_SORT_WINDOW, nr - w0);
+    len[t] = t < m ? rp[r + 1] - rp[r] : -1;
+    __syncthreads();
+    if (t < m) {
+        int rank = 0;
+        for (int u = 0; u < m; ++u) rank += (len[u] > len[t] || (len[u] == len[t] && u < t)) ? 1 : 0;
+        perm[w0 + rank] = r;
+    }
+}
+
+__global__ void k_sell_width(int nr, int nslices, int V, const int *__restrict__ rp, const int *__restrict__ perm,
+                             int *__restrict__ width)
 {
     GRID_STRIDE(s, nslices)
     {
         int w = 0;
         for (int l = 0; l < SELL_C; ++l) {
             const long long r = s * SELL_C + l;
-            if (r < nr) w = max(w, rp[r + 1] - rp[r]);
+            if (r < nr) {
+                const int o = perm ? perm[r] : (int)r;
+                w = max(w, rp[o + 1] - rp[o]);
+            }
         }
         w = (w + V - 1) / V * V;
         width[s] = w * SELL_C;
@@ -1005,16 +1036,17 @@ __global__ void k_sell_width(int nr, int nslices, int V, const int *__restrict__
 
 template <class T>
 __global__ void k_sell_fill(int nr, int nc, int nslices, const int *__restrict__ rp, const int *__restrict__ ci,
-                            const double *__restrict__ v, const int *__restrict__ sp, int *__restrict__ sci,
-                            T *__restrict__ sv)
+                            const double *__restrict__ v, const int *__restrict__ perm, const int *__restrict__ sp,
+                            int *__restrict__ sci, T *__restrict__ sv)
 {
     constexpr int V = SellV<T>::V;
     GRID_STRIDE(rr, (long long)nslices * SELL_C)
     {
         const int r = (int)rr, s = r / SELL_C, lane = r % SELL_C;
+        const int o = (perm && r < nr) ? perm[r] : r;
         const int base = sp[s], w = (sp[s + 1] - base) / SELL_C;
-        const int b = r < nr ? rp[r] : 0, len = r < nr ? rp[r + 1] - b : 0;
-        const int pad = r < nc ? r : 0;
+        const int b = r < nr ? rp[o] : 0, len = r < nr ? rp[o + 1] - b : 0;
+        const int pad = o < nc ? o : 0;
         for (int k = 0; k < w; ++k) {
             const size_t o = (size_t)base + (size_t)(k / V) * SELL_C * V + (size_t)lane * V + (k % V);
             if (k < len) {
@@ -1029,27 +1061,34 @@ __global__ void k_sell_fill(int nr, int nc, int nslices, const int *__restrict__
 }
 
 template <class T>
-void to_sell(const DCSR &A, Sell<T> &S, cudaStream_t st)
+void to_sell(const DCSR &A, Sell<T> &S, cudaStream_t st, bool sorted)
 {
     constexpr int V = SellV<T>::V;
     S.nr = A.nr;
     S.nc = A.nc;
     S.nnz = A.nnz;
     S.nslices = (A.nr + SELL_C - 1) / SELL_C;
+    S.perm.release();
+    if (sorted && A.nr > 0) {
+        S.perm.alloc((size_t)A.nr);
+        gw_launch(k_sell_sort, (A.nr + SELL_SORT_WINDOW - 1) / SELL_SORT_WINDOW, SELL_SORT_WINDOW, 0, st, A.nr, A.rp.p,
+                                                                                                  S.perm.p);
+        GW_LAUNCH_CHECK();
+    }
     S.sp.alloc((size_t)S.nslices + 1);
-    k_sell_width<<<nblk(S.nslices, 256), 256, 0, st>>>(A.nr, S.nslices, V, A.rp.p, S.sp.p);
+    gw_launch(k_sell_width, nblk(S.nslices, 256), 256, 0, st, A.nr, S.nslices, V, A.rp.p, S.perm.p, S.sp.p);
     GW_LAUNCH_CHECK();
     exclusive_scan(S.sp.p, S.sp.p, S.nslices, st);
     S.stored = read_int(S.sp.p + S.nslices, st);
     S.ci.alloc((size_t)S.stored);
     S.v.alloc((size_t)S.stored);
-    k_sell_fill<T><<<nblk((long long)S.nslices * SELL_C, 256), 256, 0, st>>>(A.nr, A.nc, S.nslices, A.rp.p, A.ci.p,
-                                                                          A.v.p, S.sp.p, S.ci.p, S.v.p);
+    gw_launch(k_sell_fill<T>, nblk((long long)S.nslices * SELL_C, 256), 256, 0, st, A.nr, A.nc, S.nslices, A.rp.p, A.ci.p,
+                                                                          A.v.p, S.perm.p, S.sp.p, S.ci.p, S.v.p);
     GW_LAUNCH_CHECK();
 }
 
-template void to_sell<float>(const DCSR &, Sell<float> &, cudaStream_t);
-template void to_sell<double>(const DCSR &, Sell<double> &, cudaStream_t);
+template void to_sell<float>(const DCSR &, Sell<float> &, cudaStream_t, bool);
+template void to_sell<double>(const DCSR &, Sell<double> &, cudaStream_t, bool);
 
 // ----------------------------------------------- CSR and stencil formats --
 template <class T>
@@ -1137,6 +1176,11 @@ bool to_store(const DCSR &A, MatStore<T> &M, int fmt, int nx, int ny, int nz, cu
     M.nc = A.nc;
     M.nnz = A.nnz;
     M.fmt = fmt;
+    if (fmt == FMT_SELL_SORTED) {
+        M.fmt = FMT_SELL;
+        to_sell<T>(A, M.sell, st, true);
+        return true;
+    }
     if (fmt == FMT_STENB) {
         StenB &S = M.stenb;
         const int n = A.nr;
@@ -1151,7 +1195,7 @@ bool to_store(const DCSR &A, MatStore<T> &M, int fmt, int nx, int ny, int nz, cu
             S.oz.alloc((size_t)n);
             DBuf<int> bad(1);
             GW_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
-            k_to_stencil_bf16<<<nblk(n, 256), 256, 0, st>>>(n, nx, nx * ny, A.rp.p, A.ci.p, A.v.p, S.d.p, S.ox.p,
+            gw_launch(k_to_stencil_bf16, nblk(n, 256), 256, 0, st, n, nx, nx * ny, A.rp.p, A.ci.p, A.v.p, S.d.p, S.ox.p,
                                                             S.oy.p, S.oz.p, bad.p);
             GW_LAUNCH_CHECK();
             if (read_int(bad.p, st) == 0) return true;
@@ -1176,7 +1220,7 @@ bool to_store(const DCSR &A, MatStore<T> &M, int fmt, int nx, int ny, int nz, cu
         S.oz.alloc((size_t)n);
         DBuf<int> bad(1);
         GW_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
-        k_to_stencil<T><<<nblk(n, 256), 256, 0, st>>>(n, nx, nx * ny, A.rp.p, A.ci.p, A.v.p, S.d.p, S.ox.p, S.oy.p,
+        gw_launch(k_to_stencil<T>, nblk(n, 256), 256, 0, st, n, nx, nx * ny, A.rp.p, A.ci.p, A.v.p, S.d.p, S.ox.p, S.oy.p,
                                                      S.oz.p, bad.p);
         GW_LAUNCH_CHECK();
         if (read_int(bad.p, st) == 0) return true;
@@ -1206,7 +1250,7 @@ bool to_store(const DCSR &A, MatStore<T> &M, int fmt, int nx, int ny, int nz, cu
     GW_CUDA(cudaMemcpyAsync(C.rp.p, A.rp.p, ((size_t)A.nr + 1) * sizeof(int), cudaMemcpyDeviceToDevice, st));
     if (A.nnz) {
         GW_CUDA(cudaMemcpyAsync(C.ci.p, A.ci.p, (size_t)A.nnz * sizeof(int), cudaMemcpyDeviceToDevice, st));
-        k_convert_vals<T><<<nblk(A.nnz, 256), 256, 0, st>>>(A.nnz, A.v.p, C.v.p);
+        gw_launch(k_convert_vals<T>, nblk(A.nnz, 256), 256, 0, st, A.nnz, A.v.p, C.v.p);
         GW_LAUNCH_CHECK();
     }
     return true;
@@ -1293,13 +1337,13 @@ bool to_sell16(const DCSR &A, Sell16 &S, bool scaled, cudaStream_t st)
     S.base.alloc((size_t)S.nslices);
     DBuf<int> bad(1);
     GW_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
-    k_s16_width<<<nblk(S.nslices, 256), 256, 0, st>>>(A.nr, S.nslices, A.rp.p, A.ci.p, S.sp.p, S.base.p, bad.p);
+    gw_launch(k_s16_width, nblk(S.nslices, 256), 256, 0, st, A.nr, S.nslices, A.rp.p, A.ci.p, S.sp.p, S.base.p, bad.p);
     GW_LAUNCH_CHECK();
     DBuf<double> sd;
     if (scaled) {
         sd.alloc((size_t)A.nr);
         S.sd.alloc((size_t)A.nr);
-        k_sqrt_diag<<<nblk(A.nr, 256), 256, 0, st>>>(A.nr, A.rp.p, A.ci.p, A.v.p, sd.p, S.sd.p, bad.p);
+        gw_launch(k_sqrt_diag, nblk(A.nr, 256), 256, 0, st, A.nr, A.rp.p, A.ci.p, A.v.p, sd.p, S.sd.p, bad.p);
         GW_LAUNCH_CHECK();
     }
     if (read_int(bad.p, st)) {
@@ -1310,7 +1354,7 @@ bool to_sell16(const DCSR &A, Sell16 &S, bool scaled, cudaStream_t st)
     S.stored = read_int(S.sp.p + S.nslices, st);
     S.v.alloc((size_t)std::max<long long>(S.stored, 1));
     S.ci.alloc((size_t)std::max<long long>(S.stored, 1));
-    k_s16_fill<<<nblk((long long)S.nslices * SELL_C, 256), 256, 0, st>>>(A.nr, S.nslices, A.rp.p, A.ci.p, A.v.p,
+    gw_launch(k_s16_fill, nblk((long long)S.nslices * SELL_C, 256), 256, 0, st, A.nr, S.nslices, A.rp.p, A.ci.p, A.v.p,
                                                                       scaled ? sd.p : nullptr, S.sp.p, S.base.p,
                                                                       S.v.p, S.ci.p);
     GW_LAUNCH_CHECK();

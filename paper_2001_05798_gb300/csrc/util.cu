@@ -5,6 +5,7 @@
 #include <mutex>
 
 #include <map>
+#include <set>
 #include <mutex>
 
 #include "gw_internal.cuh"
@@ -60,19 +61,32 @@ void host_free(void *p)
     cudaFreeHost(p);
 }
 
+// One capture at a time: the first use of a kernel in a capture loads its
+// code (the occupancy query of launch sizing does), which invalidates a
+// capture running on another thread; the capturing thread's own capture is
+// not affected.
+static std::mutex g_capture_mu;
+static thread_local bool t_capturing = false;
+
 CaptureScope::CaptureScope()
 {
-    std::lock_guard<std::mutex> lk(g_alloc_mu);
-    ++g_captures;
+    g_capture_mu.lock();
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        ++g_captures;
+    }
+    t_capturing = true;
 }
 
 CaptureScope::~CaptureScope()
 {
+    t_capturing = false;
     {
         std::lock_guard<std::mutex> lk(g_alloc_mu);
         --g_captures;
     }
     g_alloc_cv.notify_all();
+    g_capture_mu.unlock();
 }
 
 // ------------------------------------------------------------------ scan --
@@ -128,15 +142,15 @@ void exclusive_scan(const int *in, int *out, int n, cudaStream_t st)
     int nb = (n + SCAN_CHUNK - 1) / SCAN_CHUNK;
     int *bsum = nullptr;
     GW_CUDA(cudaMallocAsync((void **)&bsum, (size_t)(nb + 1) * sizeof(int), st));
-    k_scan_block<<<nb, SCAN_BS, 0, st>>>(in, out, bsum, n);
+    gw_launch(k_scan_block, nb, SCAN_BS, 0, st, in, out, bsum, n);
     GW_LAUNCH_CHECK();
     if (nb > 1) {
         exclusive_scan(bsum, bsum, nb, st);
-        k_scan_add<<<(n + 255) / 256, 256, 0, st>>>(out, bsum, n);
+        gw_launch(k_scan_add, (n + 255) / 256, 256, 0, st, out, bsum, n);
         GW_LAUNCH_CHECK();
-        k_set_at<<<1, 1, 0, st>>>(out + n, bsum + nb);
+        gw_launch(k_set_at, 1, 1, 0, st, out + n, bsum + nb);
     } else {
-        k_set_at<<<1, 1, 0, st>>>(out + n, bsum);
+        gw_launch(k_set_at, 1, 1, 0, st, out + n, bsum);
     }
     GW_LAUNCH_CHECK();
     GW_CUDA(cudaFreeAsync(bsum, st));
@@ -153,15 +167,15 @@ bool exclusive_scan_in(const int *in, int *out, int n, int *scratch, size_t cap,
     const int nb = (n + SCAN_CHUNK - 1) / SCAN_CHUNK;
     if ((size_t)nb + 1 > cap) return false;
     int *bsum = scratch;
-    k_scan_block<<<nb, SCAN_BS, 0, st>>>(in, out, bsum, n);
+    gw_launch(k_scan_block, nb, SCAN_BS, 0, st, in, out, bsum, n);
     GW_LAUNCH_CHECK();
     if (nb > 1) {
         if (!exclusive_scan_in(bsum, bsum, nb, scratch + nb + 1, cap - (size_t)nb - 1, st)) return false;
-        k_scan_add<<<(n + 255) / 256, 256, 0, st>>>(out, bsum, n);
+        gw_launch(k_scan_add, (n + 255) / 256, 256, 0, st, out, bsum, n);
         GW_LAUNCH_CHECK();
-        k_set_at<<<1, 1, 0, st>>>(out + n, bsum + nb);
+        gw_launch(k_set_at, 1, 1, 0, st, out + n, bsum + nb);
     } else {
-        k_set_at<<<1, 1, 0, st>>>(out + n, bsum);
+        gw_launch(k_set_at, 1, 1, 0, st, out + n, bsum);
     }
     GW_LAUNCH_CHECK();
     return true;
@@ -191,20 +205,52 @@ void to_device(void *dst, const void *src, size_t bytes, cudaStream_t st)
     GW_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, st));
 }
 
+void prime_kernel(const void *fn)
+{
+    static std::mutex mu;
+    static std::set<std::pair<int, const void *>> loaded;
+    int dev = 0;
+    GW_CUDA(cudaGetDevice(&dev));
+    const auto key = std::make_pair(dev, fn);
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (loaded.count(key)) return;
+    }
+    std::unique_lock<std::mutex> alloc_lk(g_alloc_mu, std::defer_lock);
+    if (!t_capturing) {
+        alloc_lk.lock();
+        g_alloc_cv.wait(alloc_lk, [] { return g_captures == 0; });
+    }
+    cudaFuncAttributes a;
+    GW_CUDA(cudaFuncGetAttributes(&a, fn));
+    std::lock_guard<std::mutex> lock(mu);
+    loaded.insert(key);
+}
+
 int kernel_wave(const void *fn, int block_size)
 {
     static std::mutex mu;
     static std::map<std::pair<int, const void *>, int> cache;
     int dev = 0;
     GW_CUDA(cudaGetDevice(&dev));
-    std::lock_guard<std::mutex> lock(mu);
     const auto key = std::make_pair(dev, fn);
-    auto it = cache.find(key);
-    if (it != cache.end()) return it->second;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) return it->second;
+    }
+    // the query may load the kernel's code: outside a capture of this thread,
+    // wait until no other thread captures (and keep captures from starting)
+    std::unique_lock<std::mutex> alloc_lk(g_alloc_mu, std::defer_lock);
+    if (!t_capturing) {
+        alloc_lk.lock();
+        g_alloc_cv.wait(alloc_lk, [] { return g_captures == 0; });
+    }
     int nb = 0, sms = 0;
     GW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, block_size, 0));
     GW_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int w = std::max(1, nb) * std::max(1, sms);
+    std::lock_guard<std::mutex> lock(mu);
     cache[key] = w;
     return w;
 }

@@ -13,10 +13,19 @@ because solves share no device state and every reduction has a fixed order.
 """
 import collections
 import concurrent.futures
+import os
 import threading
 import time
 
 import torch
+
+# Slots capture their CUDA graphs while other slots launch torch and libgw
+# kernels.  Under lazy module loading a kernel whose code is loaded during a
+# capture on another thread invalidates that capture (libgw loads its own
+# kernels outside captures, but torch and cuFFT load theirs on first use), so
+# a process that starts serving before it touches CUDA loads modules eagerly.
+if not torch.cuda.is_initialized():
+    os.environ.setdefault("CUDA_MODULE_LOADING", "EAGER")
 
 from . import gw
 from . import workload as wl

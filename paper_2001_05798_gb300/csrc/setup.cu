@@ -46,6 +46,26 @@ __device__ __forceinline__ bool prio_gt(uint64_t k1, int i1, uint64_t k2, int i2
     return k1 > k2 || (k1 == k2 && i1 > i2);
 }
 
+// Block-wide maximum of non-negative doubles given as their bit patterns
+// (ordered like the values), then one atomicMax per block.  Every thread of
+// the block must call it.
+__device__ __forceinline__ void block_atomic_max(unsigned long long v, unsigned long long *dst)
+{
+    __shared__ unsigned long long sm[32];
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long t = __shfl_xor_sync(0xffffffffu, v, o);
+        v = t > v ? t : v;
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) sm[w] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long m = 0;
+        for (int k = 0; k < (int)((blockDim.x + 31) >> 5); ++k) m = sm[k] > m ? sm[k] : m;
+        if (m) atomicMax(dst, m);
+    }
+}
+
 // ----------------------------------------------------------------- strength --
 __global__ void k_diag(int n, const int *__restrict__ rp, const int *__restrict__ ci, const double *__restrict__ v,
                        double *__restrict__ d)
@@ -349,6 +369,7 @@ __global__ void k_filter(int n, const int *__restrict__ rp, const int *__restric
                          const double *__restrict__ d, double *__restrict__ aF, unsigned char *__restrict__ hs,
                          unsigned long long *__restrict__ rho_bits)
 {
+    unsigned long long best = 0;
     GRID_STRIDE(ii, n)
     {
         const int i = (int)ii;
@@ -370,8 +391,12 @@ __global__ void k_filter(int n, const int *__restrict__ rp, const int *__restric
             else if (S[e]) s = __dadd_rn(s, fabs(v[e]));
         }
         const double ratio = __ddiv_rn(s, di);
-        if (ratio > 0.0 && isfinite(ratio)) atomicMax(rho_bits, (unsigned long long)__double_as_longlong(ratio));
+        if (ratio > 0.0 && isfinite(ratio)) {
+            const unsigned long long b = (unsigned long long)__double_as_longlong(ratio);
+            best = b > best ? b : best;
+        }
     }
+    block_atomic_max(best, rho_bits);
 }
 
 __device__ __forceinline__ bool p_member(int i, int j, unsigned char s) { return j == i || s; }
@@ -640,6 +665,19 @@ __device__ __forceinline__ int sg_insert(int *keys, int H, int c)
     return -1000000;  // table full: flagged by the caller through the count
 }
 
+// Table size for one row: the smallest power of two (at least 32, at most H)
+// of at least twice the row's bound on distinct columns.
+__device__ __forceinline__ int sg_row_table(const int *__restrict__ lrp, const int *__restrict__ lci,
+                                            const int *__restrict__ rrp, int row, int H, int lane)
+{
+    int ub = 0;
+    for (int e = lrp[row] + lane; e < lrp[row + 1]; e += 32) ub += rrp[lci[e] + 1] - rrp[lci[e]];
+    for (int off = 16; off > 0; off >>= 1) ub += __shfl_xor_sync(0xffffffffu, ub, off);
+    int h = 32;
+    while (h < 2 * ub && h < H) h <<= 1;
+    return h;
+}
+
 __device__ int sg_build_set(const int *__restrict__ lrp, const int *__restrict__ lci, const int *__restrict__ rrp,
                             const int *__restrict__ rci, int row, int *keys, int H, int lane)
 {
@@ -655,21 +693,27 @@ __device__ int sg_build_set(const int *__restrict__ lrp, const int *__restrict__
     return mine;
 }
 
+// Distinct columns of every row (table per row sized by its own bound), and
+// their maximum, which sizes the numeric pass's tables.
 __global__ void k_sg_symbolic(int nr, const int *__restrict__ lrp, const int *__restrict__ lci,
                               const int *__restrict__ rrp, const int *__restrict__ rci, int H, int *__restrict__ cnt,
-                              int *__restrict__ overflow)
+                              int *__restrict__ overflow, int *__restrict__ maxu)
 {
     extern __shared__ int sg_smem[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, W = blockDim.x >> 5;
     int *keys = sg_smem + (size_t)w * H;
+    int best = 0;
     for (long long row = (long long)blockIdx.x * W + w; row < nr; row += (long long)gridDim.x * W) {
-        int u = sg_build_set(lrp, lci, rrp, rci, (int)row, keys, H, lane);
+        const int Hr = sg_row_table(lrp, lci, rrp, (int)row, H, lane);
+        int u = sg_build_set(lrp, lci, rrp, rci, (int)row, keys, Hr, lane);
         if (lane == 0) {
-            if (u < 0 || u > H / 2) atomicOr(overflow, 1);
+            if (u < 0 || u > Hr / 2) atomicOr(overflow, 1);
             cnt[row] = u < 0 ? 0 : u;
         }
+        best = max(best, u);
         __syncwarp();
     }
+    if (lane == 0 && best > 0) atomicMax(maxu, best);
 }
 
 __global__ void k_sg_numeric(int nr, const int *__restrict__ lrp, const int *__restrict__ lci,
@@ -729,36 +773,46 @@ __global__ void k_sg_numeric(int nr, const int *__restrict__ lrp, const int *__r
 
 void setup_spgemm(const DCSR &L, const DCSR &Rm, DCSR &C, cudaStream_t st)
 {
-    DBuf<int> maxub(1), ovf(1);
+    DBuf<int> maxub(1), ovf(1), maxu(1);
     GW_CUDA(cudaMemsetAsync(maxub.p, 0, sizeof(int), st));
     GW_CUDA(cudaMemsetAsync(ovf.p, 0, sizeof(int), st));
+    GW_CUDA(cudaMemsetAsync(maxu.p, 0, sizeof(int), st));
     gw_launch(k_sg_bound, nblk(L.nr, 256), 256, 0, st, L.nr, Rm.nc, L.rp.p, L.ci.p, Rm.rp.p, maxub.p);
     GW_LAUNCH_CHECK();
     const int ub = read_int(maxub.p, st);
     int H = 32;
     while (H < 2 * ub && H < SG_HMAX) H <<= 1;
     // warps per block so that a block's tables stay within 96 KB
-    const size_t per_warp_num = (size_t)H * 12;
-    int W = (int)std::max<size_t>(1, std::min<size_t>(8, (96u << 10) / per_warp_num));
-    const size_t smem_sym = (size_t)W * H * sizeof(int), smem_num = (size_t)W * per_warp_num;
+    const int W = (int)std::max<size_t>(1, std::min<size_t>(8, (96u << 10) / ((size_t)H * sizeof(int))));
+    const size_t smem_sym = (size_t)W * H * sizeof(int);
     // The attribute is global to the kernel, and setups may run concurrently on
     // several threads: always set the same value, the largest any launch uses.
     GW_CUDA(cudaFuncSetAttribute(k_sg_symbolic, cudaFuncAttributeMaxDynamicSharedMemorySize, SG_SMEM_MAX));
     GW_CUDA(cudaFuncSetAttribute(k_sg_numeric, cudaFuncAttributeMaxDynamicSharedMemorySize, SG_SMEM_MAX));
-    if (smem_sym > (size_t)SG_SMEM_MAX || smem_num > (size_t)SG_SMEM_MAX)
-        fail(GW_ERR_SETUP, "SpGEMM shared memory %zu exceeds %d", std::max(smem_sym, smem_num), SG_SMEM_MAX);
+    if (smem_sym > (size_t)SG_SMEM_MAX)
+        fail(GW_ERR_SETUP, "SpGEMM shared memory %zu exceeds %d", smem_sym, SG_SMEM_MAX);
     C.nr = L.nr;
     C.nc = Rm.nc;
     C.rp.alloc((size_t)C.nr + 1);
     const int grid = (int)std::max(1LL, std::min<long long>(((long long)L.nr + W - 1) / W, 152LL * 64));
-    gw_launch(k_sg_symbolic, grid, 32 * W, smem_sym, st, L.nr, L.rp.p, L.ci.p, Rm.rp.p, Rm.ci.p, H, C.rp.p, ovf.p);
+    gw_launch(k_sg_symbolic, grid, 32 * W, smem_sym, st, L.nr, L.rp.p, L.ci.p, Rm.rp.p, Rm.ci.p, H, C.rp.p, ovf.p,
+              maxu.p);
     GW_LAUNCH_CHECK();
     if (read_int(ovf.p, st)) fail(GW_ERR_SETUP, "SpGEMM row has more than %d distinct columns", H / 2);
+    // the numeric pass knows every row's distinct count: tables of twice the largest
+    const int mu = read_int(maxu.p, st);
+    int Hn = 32;
+    while (Hn < 2 * mu) Hn <<= 1;
+    const size_t per_warp_num = (size_t)Hn * 12;
+    const int Wn = (int)std::max<size_t>(1, std::min<size_t>(8, (96u << 10) / per_warp_num));
+    const size_t smem_num = (size_t)Wn * per_warp_num;
+    if (smem_num > (size_t)SG_SMEM_MAX) fail(GW_ERR_SETUP, "SpGEMM shared memory %zu exceeds %d", smem_num, SG_SMEM_MAX);
+    const int grid_n = (int)std::max(1LL, std::min<long long>(((long long)L.nr + Wn - 1) / Wn, 152LL * 64));
     exclusive_scan(C.rp.p, C.rp.p, C.nr, st);
     C.nnz = read_int(C.rp.p + C.nr, st);
     C.ci.alloc((size_t)C.nnz);
     C.v.alloc((size_t)C.nnz);
-    gw_launch(k_sg_numeric, grid, 32 * W, smem_num, st, L.nr, L.rp.p, L.ci.p, L.v.p, Rm.rp.p, Rm.ci.p, Rm.v.p, H, C.rp.p,
+    gw_launch(k_sg_numeric, grid_n, 32 * Wn, smem_num, st, L.nr, L.rp.p, L.ci.p, L.v.p, Rm.rp.p, Rm.ci.p, Rm.v.p, Hn, C.rp.p,
                                                   C.ci.p, C.v.p);
     GW_LAUNCH_CHECK();
     GW_CUDA(cudaStreamSynchronize(st));
@@ -890,6 +944,7 @@ void setup_dense_inverse(const DCSR &A, DBuf<double> &Ainv, cudaStream_t st)
 __global__ void k_gersh(int n, const int *__restrict__ rp, const int *__restrict__ ci, const double *__restrict__ v,
                         double *__restrict__ d, unsigned long long *__restrict__ rho_bits)
 {
+    unsigned long long best = 0;
     GRID_STRIDE(ii, n)
     {
         const int i = (int)ii;
@@ -900,8 +955,12 @@ __global__ void k_gersh(int n, const int *__restrict__ rp, const int *__restrict
         }
         d[i] = dd;
         const double ratio = s / dd;
-        if (ratio > 0.0 && isfinite(ratio)) atomicMax(rho_bits, (unsigned long long)__double_as_longlong(ratio));
+        if (ratio > 0.0 && isfinite(ratio)) {
+            const unsigned long long b = (unsigned long long)__double_as_longlong(ratio);
+            best = b > best ? b : best;
+        }
     }
+    block_atomic_max(best, rho_bits);
 }
 
 double setup_gershgorin(const DCSR &A, DBuf<double> &diag, cudaStream_t st)

@@ -219,7 +219,7 @@ void build_hierarchy(Hier &H, cudaStream_t st)
         DCSR P, Rl, AP, Ac;
         double omega = 0.0, rho = 0.0;
         setup_smooth_p(A, S.p, H.agg[(size_t)l].p, m, P, &omega, &rho, st);
-        if (l == 0 && o.prec != GW_PREC_FP64) setup_implicit_p(A, S.p, omega, H.gnx, H.gny, H.gnz, H.p0, st);
+        if (l == 0 && o.prec != GW_PREC_FP64) setup_implicit_p(A, S.p, H.agg[0].p, m, omega, H.gnx, H.gny, H.gnz, H.p0, st);
         setup_transpose(P, Rl, st);
         setup_spgemm(A, P, AP, st);
         setup_spgemm(Rl, AP, Ac, st);

@@ -816,6 +816,90 @@ __global__ void __launch_bounds__(BS) k_prolong_imp(PImpl P, const float *__rest
     }
 }
 
+// u_j = w_j r_j - sum_i f_ij s_i r_i over the six neighbours (the first half
+// of r_c = (P^T r)_c on level 0), R rows a thread, neighbours in the order
+// -z, -y, -x, +x, +y, +z
+template <int R>
+__global__ void __launch_bounds__(BS) k_restrict_u(PImpl P, const float *__restrict__ r, float *__restrict__ u,
+                                                   const Ctl *ctl)
+{
+    pdl_enter();
+    if (finished(ctl)) return;
+    const int n = P.n, nx = P.nx, sxy = P.sxy;
+    for (int i0 = R * (blockIdx.x * BS + threadIdx.x); i0 < n; i0 += R * gridDim.x * BS) {
+        float acc[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) acc[k] = 0.f;
+        if (i0 >= sxy) {
+            const VecN<float, R> c = ld_ro<R>(P.fz + i0 - sxy), sv = ld_ro<R>(P.s + i0 - sxy),
+                                 rv = ld_ro<R>(r + i0 - sxy);
+#pragma unroll
+            for (int k = 0; k < R; ++k) acc[k] += c.v[k] * (sv.v[k] * rv.v[k]);
+        }
+        if (i0 >= nx) {
+            const VecN<float, R> c = ld_ro<R>(P.fy + i0 - nx), sv = ld_ro<R>(P.s + i0 - nx),
+                                 rv = ld_ro<R>(r + i0 - nx);
+#pragma unroll
+            for (int k = 0; k < R; ++k) acc[k] += c.v[k] * (sv.v[k] * rv.v[k]);
+        }
+        const VecN<float, R> s0 = ld_ro<R>(P.s + i0), r0 = ld_ro<R>(r + i0), cx = ld_ro<R>(P.fx + i0);
+        if (i0 >= 1) acc[0] += __ldg(P.fx + i0 - 1) * (__ldg(P.s + i0 - 1) * __ldg(r + i0 - 1));
+#pragma unroll
+        for (int k = 1; k < R; ++k) acc[k] += cx.v[k - 1] * (s0.v[k - 1] * r0.v[k - 1]);
+#pragma unroll
+        for (int k = 0; k < R - 1; ++k) acc[k] += cx.v[k] * (s0.v[k + 1] * r0.v[k + 1]);
+        if (i0 + R < n) acc[R - 1] += cx.v[R - 1] * (__ldg(P.s + i0 + R) * __ldg(r + i0 + R));
+        if (i0 + nx < n) {
+            const VecN<float, R> c = ld_ro<R>(P.fy + i0), sv = ld_ro<R>(P.s + i0 + nx), rv = ld_ro<R>(r + i0 + nx);
+#pragma unroll
+            for (int k = 0; k < R; ++k) acc[k] += c.v[k] * (sv.v[k] * rv.v[k]);
+        }
+        if (i0 + sxy < n) {
+            const VecN<float, R> c = ld_ro<R>(P.fz + i0), sv = ld_ro<R>(P.s + i0 + sxy),
+                                 rv = ld_ro<R>(r + i0 + sxy);
+#pragma unroll
+            for (int k = 0; k < R; ++k) acc[k] += c.v[k] * (sv.v[k] * rv.v[k]);
+        }
+        VecN<float, R> uo;
+#pragma unroll
+        for (int k = 0; k < R; ++k) uo.v[k] = (s0.v[k] != 0.f ? P.w0 : 1.f) * r0.v[k] - acc[k];
+        st<R>(u + i0, uo);
+    }
+}
+
+// r_c = sum of u over the members of aggregate c: four lanes per aggregate,
+// lane g adding members g, g + 4, ... in order, then a fixed shuffle tree
+constexpr int RS_LANES = 4;
+__global__ void __launch_bounds__(BS) k_restrict_sum(int nc, const int *__restrict__ mptr, const int *__restrict__ mem,
+                                                     const float *__restrict__ u, float *__restrict__ rc,
+                                                     const Ctl *ctl)
+{
+    pdl_enter();
+    if (finished(ctl)) return;
+    const int g = threadIdx.x & (RS_LANES - 1);
+    for (int c = (int)((blockIdx.x * (long long)BS + threadIdx.x) / RS_LANES), stride = gridDim.x * (BS / RS_LANES);
+         __any_sync(0xffffffffu, c < nc); c += stride) {
+        float acc = 0.f;
+        if (c < nc) {
+            const int e1 = __ldg(mptr + c + 1);
+            for (int e = __ldg(mptr + c) + g; e < e1; e += RS_LANES) acc += __ldg(u + __ldg(mem + e));
+        }
+#pragma unroll
+        for (int off = RS_LANES / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off, RS_LANES);
+        if (c < nc && g == 0) rc[c] = acc;
+    }
+}
+
+static void restrict_imp(Hier &H, const float *r, float *u, float *rc, const Ctl *ctl, cudaStream_t st)
+{
+    const ImplP &I = H.p0;
+    const PImpl P{I.agg, I.s.p, I.fx.p, I.fy.p, I.fz.p, I.n, I.nx, I.sxy, I.w0};
+    if (I.n % 4 == 0 && I.nx % 4 == 0) launch_pdl(k_restrict_u<4>, vgrid(H, I.n / 4), st, P, r, u, ctl);
+    else launch_pdl(k_restrict_u<1>, vgrid(H, I.n), st, P, r, u, ctl);
+    launch_pdl(k_restrict_sum, vgrid(H, (long long)I.nc * RS_LANES), st, I.nc, (const int *)I.mptr.p, (const int *)I.mem.p, (const float *)u,
+               rc, ctl);
+}
+
 static void prolong_imp(Hier &H, const float *e, float *x, const Ctl *ctl, cudaStream_t st)
 {
     const ImplP &I = H.p0;
@@ -1208,6 +1292,15 @@ static void vcycle_t(Hier &H, std::vector<CycLevel<T>> &C, const T *r, T *z, Ctl
             });
         }
         timed(H, l0 ? GW_PK_RESTRICT : -1, st, [&] {
+            if constexpr (sizeof(T) == 4) {
+                if (l0 && H.p0.n) {
+                    // u pass: r, s, fx, fy, fz read, u written; sum pass: mem and u read,
+                    // mptr read and r_c written per aggregate
+                    H.prof_bytes += vbytes(H, 24.0 * dn + 8.0 * dn + 8.0 * (double)H.p0.nc);
+                    restrict_imp(H, lv.r.p, lv.t.p, C[1].b.p, ctl, st);
+                    return;
+                }
+            }
             H.prof_bytes += vbytes(H, mat_bytes(lv.R) + dn * sx + (double)lv.R.nr * sx);
             with_mat(lv.R, [&](auto Rm) {
                 using M = decltype(Rm);

@@ -249,12 +249,21 @@ void assemble_csr(int nx, int ny, int nz, double dx, double dy, double dz, const
 // strong couplings, whose row is the tentative one).  f is symmetric, so
 // only the +x, +y, +z couplings are stored: 16 bytes a row plus agg, against
 // about 63 bytes a row of padded sliced ELL at 128^3.
+// Its transpose, the restriction, is applied the same way:
+// (P^T r)_c = sum over the members j of aggregate c of u_j, with
+// u_j = w_j r_j - sum_i f_ij s_i r_i over the six neighbours i of j; the
+// member lists (ascending) are the rows of the tentative prolongator's
+// transpose.
 struct ImplP {
-    int n = 0, nx = 0, sxy = 0;
+    int n = 0, nx = 0, sxy = 0, nc = 0;
     float w0 = 0.f;  // 1 - omega
     const int *agg = nullptr;
     DBuf<float> s, fx, fy, fz;
-    size_t bytes() const { return s.bytes() + fx.bytes() + fy.bytes() + fz.bytes(); }
+    DBuf<int> mptr, mem;  // members of aggregate c: mem[mptr[c] .. mptr[c+1])
+    size_t bytes() const
+    {
+        return s.bytes() + fx.bytes() + fy.bytes() + fz.bytes() + mptr.bytes() + mem.bytes();
+    }
 };
 
 // ----------------------------------------------------------------- setup --
@@ -271,8 +280,8 @@ void setup_smooth_p(const DCSR &A, const unsigned char *S, const int *agg, int n
                     double *rho, cudaStream_t st);
 void setup_transpose(const DCSR &P, DCSR &R, cudaStream_t st);
 // false (out.n = 0) when A is not a 7-point operator on the nx*ny*nz grid
-bool setup_implicit_p(const DCSR &A, const unsigned char *S, double omega, int nx, int ny, int nz, ImplP &out,
-                      cudaStream_t st);
+bool setup_implicit_p(const DCSR &A, const unsigned char *S, const int *agg, int nagg, double omega, int nx, int ny,
+                      int nz, ImplP &out, cudaStream_t st);
 void setup_spgemm(const DCSR &L, const DCSR &Rm, DCSR &C, cudaStream_t st);
 void setup_dense_inverse(const DCSR &A, DBuf<double> &Ainv, cudaStream_t st);
 double setup_gershgorin(const DCSR &A, DBuf<double> &diag, cudaStream_t st);  // max_i sum|a_ij|/a_ii

@@ -528,8 +528,23 @@ __global__ void k_p_implicit(int n, int nx, int sxy, const int *__restrict__ rp,
     }
 }
 
-bool setup_implicit_p(const DCSR &A, const unsigned char *S, double omega, int nx, int ny, int nz, ImplP &out,
-                      cudaStream_t st)
+__global__ void k_tent(int n, const int *__restrict__ agg, int *__restrict__ rp, int *__restrict__ ci,
+                       double *__restrict__ v)
+{
+    GRID_STRIDE(i, (long long)n + 1)
+    {
+        rp[i] = (int)i;
+        if (i < n) {
+            ci[i] = agg[i];
+            v[i] = 1.0;
+        }
+    }
+}
+
+void setup_transpose(const DCSR &P, DCSR &R, cudaStream_t st);
+
+bool setup_implicit_p(const DCSR &A, const unsigned char *S, const int *agg, int nagg, double omega, int nx, int ny,
+                      int nz, ImplP &out, cudaStream_t st)
 {
     out = ImplP();
     const int n = A.nr;
@@ -554,6 +569,20 @@ bool setup_implicit_p(const DCSR &A, const unsigned char *S, double omega, int n
         out = ImplP();
         return false;
     }
+    // member lists: rows of the tentative prolongator's transpose
+    DCSR Pt, Rt;
+    Pt.nr = n;
+    Pt.nc = nagg;
+    Pt.nnz = n;
+    Pt.rp.alloc((size_t)n + 1);
+    Pt.ci.alloc((size_t)n);
+    Pt.v.alloc((size_t)n);
+    gw_launch(k_tent, nblk((long long)n + 1, 256), 256, 0, st, n, agg, Pt.rp.p, Pt.ci.p, Pt.v.p);
+    GW_LAUNCH_CHECK();
+    setup_transpose(Pt, Rt, st);
+    out.mptr = std::move(Rt.rp);
+    out.mem = std::move(Rt.ci);
+    out.nc = nagg;
     out.n = n;
     out.nx = nx;
     out.sxy = nx * ny;

@@ -199,6 +199,24 @@ def timed_solves(torch, H, b, h, steps, flush, stream):
     return times, it, rel, st
 
 
+TRAFFIC_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles", "ncu_traffic_bench_128cubed.json")
+
+
+def traffic_of(roof, n):
+    """DRAM bytes per launch of the roofline kernel from the committed ncu capture
+    of the same workload (read + write, caches flushed by ncu), when it covers
+    this kernel at this size."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            t = json.load(f)
+    except (OSError, ValueError):
+        return
+    k = t.get("kinds", {}).get(roof.get("kernel"))
+    if k and t.get("n") == n:
+        roof["traffic"] = k["dram_bytes_per_launch"]
+        roof["traffic_source"] = "profiles/ncu_traffic_bench_128cubed.json (%s)" % ", ".join(k["kernels"])
+
+
 def run_ours(args):
     import torch
 
@@ -313,6 +331,7 @@ def run_ours(args):
            "e2e": {"value": p50e, "unit": "ms", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},
            "roofline": roof, "gpu_launches": int(launches), "timed_wall_s": t_wall,
            "clocks": clk.summary()}
+    traffic_of(roof, n)
     if ws == 1 and not args.no_cpu_baseline:
         cb, x_or = cpu_baseline_sample()
         out["cpu_baseline"] = cb

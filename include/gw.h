@@ -264,6 +264,18 @@ int gw_pcg_solve(gw_hierarchy H, const double *b, double *h, double tol, int max
 int gw_hierarchy_shift(gw_hierarchy H, const double *s, double delta, int *rebuilt, void *stream);
 
 /*
+ * gw_hierarchy_prepare -- capture the CUDA graphs of gw_pcg_solve now; the
+ * first solve does it otherwise.  Later solves only replay them.  A capture
+ * is invalidated when another thread meanwhile starts work that synchronises
+ * the device (cudaMalloc or cudaFree by other libraries, a kernel module
+ * loaded on first use); a multi-threaded caller that runs such work
+ * concurrently calls this while it holds that work off.  The library's own
+ * allocations already wait for its captures.  Errors: GW_ERR_ARG,
+ * GW_ERR_CUDA.
+ */
+int gw_hierarchy_prepare(gw_hierarchy H);
+
+/*
  * gw_pcg_solve_many -- k right-hand sides on one hierarchy.  Systems that
  * share a matrix reuse its factorisation or preconditioner (Introduction,
  * on the dual delineation approach); here the shared matrix is the flow

@@ -517,6 +517,16 @@ int gw_pcg_solve(gw_hierarchy H, const double *b, double *h, double tol, int max
     GW_API_END
 }
 
+int gw_hierarchy_prepare(gw_hierarchy H)
+{
+    GW_API_BEGIN
+    if (!H) fail(GW_ERR_ARG, "gw_hierarchy_prepare: null hierarchy");
+    Hier &hh = *H->h;
+    DeviceGuard g(hh.dev);
+    pcg_prepare(hh);
+    GW_API_END
+}
+
 int gw_pcg_solve_many(gw_hierarchy H, int k, const double *B, double *X, double tol, int maxit, int *iters,
                       double *relres, void *stream)
 {

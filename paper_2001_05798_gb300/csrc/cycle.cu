@@ -1856,6 +1856,8 @@ static void collect_marks(Hier &H, int first_iter, int it_now, bool done)
     }
 }
 
+void pcg_prepare(Hier &H) { ensure_graphs(H); }
+
 int pcg_run(Hier &H, double tol, int maxit, int *iters, double *relres, cudaStream_t st)
 {
     Ctl *c = H.ctl.p;

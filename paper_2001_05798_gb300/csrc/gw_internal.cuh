@@ -357,6 +357,7 @@ void build_hierarchy(Hier &H, cudaStream_t st);
 void refresh_level0(Hier &H, const DCSR &A, cudaStream_t st);
 void vcycle_enqueue(Hier &H, const double *r, double *z, Ctl *ctl, bool dot, cudaStream_t st);
 int pcg_run(Hier &H, double tol, int maxit, int *iters, double *relres, cudaStream_t st);
+void pcg_prepare(Hier &H);  // capture the solver's graphs now
 
 // k right-hand sides (column-major, leading dimension n, host or device)
 // solved in interleaved blocks of up to 8 columns; mixed form only.

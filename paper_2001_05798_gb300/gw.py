@@ -24,7 +24,7 @@ EXPORTS = ("gw_amg_opts_default", "gw_assemble", "gw_matrix_size", "gw_matrix_ex
            "gw_pcg_solve", "gw_vcycle", "gw_hierarchy_info", "gw_hierarchy_export", "gw_matrix_free",
            "gw_hierarchy_free", "gw_status_str", "gw_last_error", "gw_profile_enable", "gw_profile_read",
            "gw_assemble_noalloc", "gw_adjoint_gradient", "gw_misfit", "gw_hierarchy_shift",
-           "gw_pcg_solve_many", "gw_darcy_flux")
+           "gw_pcg_solve_many", "gw_darcy_flux", "gw_hierarchy_prepare")
 
 PK_NAMES = ("spmv", "update", "pre1", "pre2", "resid", "restrict", "l1down", "deep", "l1up", "prolong", "post1",
             "post2", "pupdate")
@@ -97,6 +97,7 @@ def load():
         "gw_misfit": (i, [i, vp, i, vp, vp, vp, vp, vp]),
         "gw_hierarchy_shift": (i, [vp, vp, d, P(i), vp]),
         "gw_pcg_solve_many": (i, [vp, i, vp, vp, d, i, vp, vp, vp]),
+        "gw_hierarchy_prepare": (i, [vp]),
         "gw_darcy_flux": (i, [P(gw_grid), vp, vp, vp, P(gw_bc), vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
@@ -290,6 +291,10 @@ class Hierarchy:
         if check and st not in (GW_OK, GW_ERR_NOT_CONVERGED):
             _check(st)
         return h, it.value, rel.value, st
+
+    def prepare(self):
+        """Capture the solver's CUDA graphs now (include/gw.h: gw_hierarchy_prepare)."""
+        _check(load().gw_hierarchy_prepare(self.h))
 
     def solve_many(self, B, X=None, tol=1e-8, maxit=500, stream=None):
         """k right-hand sides (columns of the n x k column-major B, i.e. rows of a (k, n) array)."""

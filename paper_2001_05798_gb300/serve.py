@@ -7,7 +7,10 @@ device), and admits the oldest waiting request as soon as a slot is free and
 its estimated device memory fits the HBM budget; a request that does not fit
 waits, and nothing behind it overtakes it.  Each request assembles its
 system, sets up its own hierarchy (resident for the request's lifetime),
-solves with the captured iteration graphs, and releases its memory.  All of
+solves with the captured iteration graphs, and releases its memory.  The
+graph capture of a request runs while no other slot is inside its torch,
+cuFFT or set-up work (a shared/exclusive gate): their allocations and first
+kernel launches would invalidate it.  Solves themselves only replay graphs.  All of
 it runs in libgw's kernels; results do not depend on what else is running,
 because solves share no device state and every reduction has a fixed order.
 """
@@ -31,6 +34,39 @@ from . import gw
 from . import workload as wl
 
 
+class _SharedExclusive:
+    """Many holders of the shared side or one of the exclusive side; a waiting
+    exclusive holder keeps new shared holders out."""
+
+    def __init__(self):
+        self._cv = threading.Condition()
+        self._shared = 0
+        self._exclusive = False
+        self._waiting = 0
+
+    def acquire_shared(self):
+        with self._cv:
+            self._cv.wait_for(lambda: not self._exclusive and self._waiting == 0)
+            self._shared += 1
+
+    def release_shared(self):
+        with self._cv:
+            self._shared -= 1
+            self._cv.notify_all()
+
+    def acquire_exclusive(self):
+        with self._cv:
+            self._waiting += 1
+            self._cv.wait_for(lambda: not self._exclusive and self._shared == 0)
+            self._waiting -= 1
+            self._exclusive = True
+
+    def release_exclusive(self):
+        with self._cv:
+            self._exclusive = False
+            self._cv.notify_all()
+
+
 class Server:
     def __init__(self, slots=4, hbm_budget=120e9, device=0, tol=1e-8, maxit=500, bytes_per_cell=1500.0, **opts):
         self.slots = slots
@@ -45,6 +81,10 @@ class Server:
         self.peak_in_use = 0.0
         self.peak_inflight = 0
         self.inflight = 0
+        # graph captures (exclusive) never overlap the slots' torch, cuFFT and
+        # set-up work (shared), whose allocations and first kernel launches
+        # would invalidate them
+        self.capture_gate = _SharedExclusive()
         self.threads = [threading.Thread(target=self._worker, daemon=True) for _ in range(slots)]
         for t in self.threads:
             t.start()
@@ -118,22 +158,37 @@ class Server:
         s = req["side"]
         n = s ** 3
         t0 = time.perf_counter()
-        if "K" in req:
-            K = req["K"]
-        else:
-            K = torch.exp(wl.lnk_field_device(s, s, s, req["var"], req["corr"], req["seed"]))
-        b = torch.empty(n, dtype=torch.float64, device=K.device)
-        A, _ = gw.gw_assemble(s, s, s, K, K, K, (1, 1, 0, 0, 0, 0), (1.0, 0.0, 0, 0, 0, 0), None, b_out=b,
-                              stream=stream)
-        H = gw.Hierarchy(A, stream=stream, **self.opts)
+        gate = self.capture_gate
+        gate.acquire_shared()
+        try:
+            if "K" in req:
+                K = req["K"]
+            else:
+                K = torch.exp(wl.lnk_field_device(s, s, s, req["var"], req["corr"], req["seed"]))
+            b = torch.empty(n, dtype=torch.float64, device=K.device)
+            A, _ = gw.gw_assemble(s, s, s, K, K, K, (1, 1, 0, 0, 0, 0), (1.0, 0.0, 0, 0, 0, 0), None, b_out=b,
+                                  stream=stream)
+            H = gw.Hierarchy(A, stream=stream, **self.opts)
+            h = torch.empty_like(b)
+            stream.synchronize()
+        finally:
+            gate.release_shared()
         used = sum(l["bytes"] for l in H.info()) + 16 * n
         with self.cv:
             self.bytes_per_cell = max(self.bytes_per_cell, 1.25 * used / n)
-        h = torch.empty_like(b)
+        gate.acquire_exclusive()
+        try:
+            H.prepare()
+        finally:
+            gate.release_exclusive()
         t1 = time.perf_counter()
         _, it, rel, st = H.solve(b, h, tol=self.tol, maxit=self.maxit, stream=stream)
         t2 = time.perf_counter()
         if st != gw.GW_OK:
             raise gw.GwError(st, "request %s: relres %.3e after %d iterations" % (req.get("id"), rel, it))
-        del H, A
+        gate.acquire_shared()
+        try:
+            del H, A
+        finally:
+            gate.release_shared()
         return dict(id=req.get("id"), n=n, h=h, iters=it, relres=rel, setup_s=t1 - t0, solve_s=t2 - t1)

@@ -1,0 +1,115 @@
+"""Host logic of the serving loop's capture gate, on the CPU.
+
+A graph capture must not overlap another slot's torch, cuFFT or set-up work:
+the server holds a shared side for that work and an exclusive side for the
+capture.  These tests drive the gate with plain threads: shared holders run
+together, an exclusive holder runs alone, and a waiting exclusive holder is
+not starved by a stream of new shared holders.
+"""
+import threading
+import time
+
+import pytest
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def gate_cls():
+    from paper_2001_05798_gb300 import serve
+
+    return serve._SharedExclusive
+
+
+def test_shared_holders_overlap(gate_cls):
+    g = gate_cls()
+    inside, peak, lock = [0], [0], threading.Lock()
+
+    def work():
+        g.acquire_shared()
+        with lock:
+            inside[0] += 1
+            peak[0] = max(peak[0], inside[0])
+        time.sleep(0.05)
+        with lock:
+            inside[0] -= 1
+        g.release_shared()
+
+    ts = [threading.Thread(target=work) for _ in range(4)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    assert peak[0] >= 2
+
+
+def test_exclusive_holder_runs_alone(gate_cls):
+    g = gate_cls()
+    log, lock = [], threading.Lock()
+
+    def shared(i):
+        g.acquire_shared()
+        with lock:
+            log.append(("s+", i))
+        time.sleep(0.02)
+        with lock:
+            log.append(("s-", i))
+        g.release_shared()
+
+    def exclusive(i):
+        g.acquire_exclusive()
+        with lock:
+            log.append(("x+", i))
+        time.sleep(0.02)
+        with lock:
+            log.append(("x-", i))
+        g.release_exclusive()
+
+    ts = [threading.Thread(target=shared if k % 3 else exclusive, args=(k,)) for k in range(12)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    active_shared, active_x = 0, 0
+    for kind, _ in log:
+        if kind == "s+":
+            assert active_x == 0
+            active_shared += 1
+        elif kind == "s-":
+            active_shared -= 1
+        elif kind == "x+":
+            assert active_x == 0 and active_shared == 0
+            active_x += 1
+        else:
+            active_x -= 1
+    assert active_shared == 0 and active_x == 0
+
+
+def test_waiting_exclusive_is_not_starved(gate_cls):
+    g = gate_cls()
+    stop = threading.Event()
+    got = threading.Event()
+
+    def churn():
+        while not stop.is_set():
+            g.acquire_shared()
+            time.sleep(0.005)
+            g.release_shared()
+
+    ts = [threading.Thread(target=churn) for _ in range(4)]
+    for t in ts:
+        t.start()
+    time.sleep(0.02)
+
+    def capture():
+        g.acquire_exclusive()
+        got.set()
+        g.release_exclusive()
+
+    c = threading.Thread(target=capture)
+    c.start()
+    ok = got.wait(timeout=5.0)
+    stop.set()
+    for t in ts + [c]:
+        t.join()
+    assert ok

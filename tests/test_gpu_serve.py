@@ -80,3 +80,22 @@ def test_budget_admission_and_rejection(serve):
             big.submit(dict(id=0, side=64, var=1.0, corr=4.0, seed=1)).result(timeout=60)
     finally:
         big.close()
+
+
+def test_prepare_then_solve_equals_plain_solve(serve):
+    """gw_hierarchy_prepare captures the solver's graphs up front; the solves
+    that follow replay them and give the same heads, bit for bit, as a
+    hierarchy whose first solve captures them itself."""
+    from paper_2001_05798_gb300 import gw, workload as wl
+
+    p = wl.heterogeneous_3d(side=24, var=2.0, corr=4.0, seed=8)
+    A, b = gw.gw_assemble(24, 24, 24, p["Kx"])
+    H1 = gw.Hierarchy(A, n_coarse=200)
+    H1.prepare()
+    H1.prepare()  # a second call keeps the captured graphs
+    H2 = gw.Hierarchy(A, n_coarse=200)
+    bd = torch.from_numpy(b).cuda()
+    h1, it1, rel1, st1 = H1.solve(bd, tol=1e-9)
+    h2, it2, rel2, st2 = H2.solve(bd, tol=1e-9)
+    assert st1 == st2 == gw.GW_OK and it1 == it2 and rel1 == rel2
+    assert torch.equal(h1, h2)

@@ -159,3 +159,22 @@ def test_solve_many_reports_non_convergence(gw):
     B = np.stack([b, 2 * b])
     X, its, rels, st = H.solve_many(B, tol=1e-14, maxit=2)
     assert st == gw.GW_ERR_NOT_CONVERGED and its == [2, 2]
+
+
+@pytest.mark.parametrize("degree,nu", [(3, 1), (2, 2)])
+def test_interleaved_block_other_cycles(gw, degree, nu):
+    """Interleaved blocks with Chebyshev(3) and with V(2,2): every column meets the
+    FP64 residual test and agrees with the oracle's solve."""
+    side = 20
+    p = wl.heterogeneous_3d(side=side, var=3.0, corr=4.0, seed=6)
+    A, b = gw.gw_assemble(side, side, side, p["Kx"])
+    H = gw.Hierarchy(A, n_coarse=200, degree=degree, nu=nu)
+    B = np.random.default_rng(3).normal(size=(3, side ** 3))
+    X, its, rels, st = H.solve_many(dev(B), tol=1e-9)
+    assert st == gw.GW_OK and max(rels) <= 1e-9
+    Ao, _ = oracle.assemble(side, side, side, p["Kx"])
+    Ho = oracle.Hierarchy(Ao, n_coarse=200, degree=degree, nu=nu)
+    X = X.cpu().numpy()
+    for c in range(3):
+        ref, _, _, _ = Ho.pcg(B[c], tol=1e-12)
+        assert np.linalg.norm(X[c] - ref) <= 1e-7 * np.linalg.norm(ref)

@@ -136,7 +136,7 @@ def test_setup_bit_exact_other_seed(gw):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("smoother,nu", [(0, 1), (0, 2), (1, 1)])
+@pytest.mark.parametrize("smoother,nu", [(0, 1), (0, 2), (1, 1), (1, 2)])
 def test_solve_parity(gw, prec, smoother, nu):
     p = PROBLEMS["3d_het_33_sigma4"]()
     A, b = gpu_assemble(gw, p)
@@ -331,3 +331,16 @@ def _layered_reference():
                         A1=[a.copy() for a in Ho.A(1).arrays()])
         _LAYERED["h"] = Ho.pcg(bo, tol=1e-12)[0]
     return _LAYERED
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_chebyshev_degree3_solve_parity(gw, prec):
+    """Chebyshev of degree 3 (the steps after the first two keep r and d)."""
+    p = PROBLEMS["3d_het_33_sigma4"]()
+    A, b = gpu_assemble(gw, p)
+    H = gw.Hierarchy(A, n_coarse=200, prec=prec, degree=3)
+    h, it, rel, st = H.solve(b, tol=TOL)
+    assert st == gw.GW_OK and rel <= TOL
+    Ao, bo = ora_assemble(p)
+    href, _, _, _ = oracle.Hierarchy(Ao, n_coarse=200, degree=3).pcg(bo, tol=1e-12)
+    assert np.linalg.norm(h.cpu().numpy() - href) / np.linalg.norm(href) <= REL_ERR

@@ -527,7 +527,8 @@ def run_layered(args):
     """Secondary workload: the 256x256x128 layered case (lnK variance 1,
     correlation 32/32/4 cells, Kh/Kv = 10, 16 wells of -1e-3, fixed head on
     top): solve time of the mixed form with the FP32 fine stencil, the mixed
-    form with the BF16-stored fine stencil, and the FP64 form, each with its
+    form with the BF16- and with the FP16-stored fine stencil, and the FP64
+    form, each with its
     error against the FP64 form solved to 1e-12 (the oracle comparison of the
     same case is a GPU test).  L2 flushed before every timed solve."""
     import torch
@@ -548,6 +549,7 @@ def run_layered(args):
     h = torch.empty_like(b)
     forms = {"mixed_fp32_fine": dict(prec=gw.GW_PREC_MIXED32),
              "mixed_bf16_fine": dict(prec=gw.GW_PREC_MIXED32, half_storage=gw.GW_HALF_FINE),
+             "mixed_fp16_fine": dict(prec=gw.GW_PREC_MIXED32, half_storage=gw.GW_HALF_FINE16),
              "fp64": dict(prec=gw.GW_PREC_FP64)}
     Href = gw.Hierarchy(A, prec=gw.GW_PREC_FP64)
     href, _, _, _ = Href.solve(b, tol=1e-12)

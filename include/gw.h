@@ -78,13 +78,14 @@ typedef struct {
 typedef enum {
     GW_PREC_FP64 = 0,
     GW_PREC_MIXED32 = 1,
+    GW_PREC_MIXED16 = 2,   /* GW_PREC_MIXED32 with GW_HALF_FINE16: FP16-stored scaled fine stencil */
     GW_PREC_MIXEDBF16 = 3  /* GW_PREC_MIXED32 with GW_HALF_FINE: BF16-stored fine stencil */
 } gw_prec;
 
 enum { GW_SMOOTH_JACOBI = 0, GW_SMOOTH_CHEBYSHEV = 1 };
 
 /* Bits of gw_amg_opts.half_storage. */
-enum { GW_HALF_TRANSFER = 1, GW_HALF_FINE = 2 };
+enum { GW_HALF_TRANSFER = 1, GW_HALF_FINE = 2, GW_HALF_FINE16 = 4 };
 
 /* Setup and cycle options (gw_amg_opts_default fills the defaults). */
 typedef struct {
@@ -102,7 +103,10 @@ typedef struct {
                               16-bit column offsets, coarse operators scaled to D^-1/2 A D^-1/2;
                             GW_HALF_FINE: the V-cycle's level-0 stencil with BF16 couplings and an
                               FP32 diagonal corrected so that rows keep their sums (CG's own
-                              products stay FP32) */
+                              products stay FP32);
+                            GW_HALF_FINE16: the level-0 stencil scaled to D^-1/2 A D^-1/2, its
+                              couplings in FP16, sqrt(a_ii) in FP32 and the unit diagonal's
+                              row-sum correction in FP16 (not together with GW_HALF_FINE) */
 } gw_amg_opts;
 
 /* Per-level statistics in the columns of the paper's Table 1 (unknowns,

@@ -145,12 +145,14 @@ static long long store_level(Hier &H, int k, const DCSR &A, const DCSR *P, const
         CycLevel<float> &c = H.cf[(size_t)k];
         const bool h16 = (o.half_storage & GW_HALF_TRANSFER) != 0;
         const bool fine16 = k == 0 && (o.half_storage & GW_HALF_FINE) != 0;
+        const bool fineh = k == 0 && (o.half_storage & GW_HALF_FINE16) != 0;
         auto f32 = [h16](int f) { return h16 && f == FMT_SELL ? FMT_SELL16 : f; };
-        to_store<float>(A, c.A, k == 0 ? (fine16 ? FMT_STENB : FMT_STEN) : f32(choose_fmt(A)), H.gnx, H.gny, H.gnz,
+        to_store<float>(A, c.A, k == 0 ? (fine16 ? FMT_STENB : fineh ? FMT_STENH : FMT_STEN) : f32(choose_fmt(A)),
+                        H.gnx, H.gny, H.gnz,
                         st);
         if (k == 0) {
             H.A32 = MatStore<float>();
-            if (c.A.fmt == FMT_STENB) {
+            if (c.A.fmt == FMT_STENB || c.A.fmt == FMT_STENH) {
                 to_store<float>(A, H.A32, FMT_STEN, H.gnx, H.gny, H.gnz, st);
                 bytes += (long long)H.A32.bytes();
             }
@@ -476,8 +478,15 @@ int gw_amg_setup(gw_matrix A, const gw_amg_opts *opts, gw_hierarchy *H_out, void
         o.prec = GW_PREC_MIXED32;
         o.half_storage |= GW_HALF_FINE;
     }
+    if (o.prec == GW_PREC_MIXED16) {
+        o.prec = GW_PREC_MIXED32;
+        o.half_storage |= GW_HALF_FINE16;
+    }
     if (o.prec != GW_PREC_FP64 && o.prec != GW_PREC_MIXED32) fail(GW_ERR_ARG, "gw_amg_setup: bad precision");
-    if (o.half_storage & ~(GW_HALF_TRANSFER | GW_HALF_FINE)) fail(GW_ERR_ARG, "gw_amg_setup: bad half_storage bits");
+    if (o.half_storage & ~(GW_HALF_TRANSFER | GW_HALF_FINE | GW_HALF_FINE16))
+        fail(GW_ERR_ARG, "gw_amg_setup: bad half_storage bits");
+    if ((o.half_storage & GW_HALF_FINE) && (o.half_storage & GW_HALF_FINE16))
+        fail(GW_ERR_ARG, "gw_amg_setup: the fine stencil is stored either in BF16 or in FP16");
     if (o.prec == GW_PREC_FP64 && o.half_storage)
         fail(GW_ERR_ARG, "gw_amg_setup: half_storage belongs to the mixed form");
     if (!(o.delta > 0.0 && o.delta < 1.0)) fail(GW_ERR_ARG, "gw_amg_setup: delta must be in (0, 1)");

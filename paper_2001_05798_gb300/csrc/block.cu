@@ -195,6 +195,39 @@ struct BStenB {
     }
 };
 
+struct BStenH {
+    const float *__restrict__ sd;
+    const __half *__restrict__ dd;
+    const __half *__restrict__ ox;
+    const __half *__restrict__ oy;
+    const __half *__restrict__ oz;
+    int n, nx, sxy;
+    template <int CW>
+    __device__ __forceinline__ CV<float, CW> scaled(float s, const CV<float, CW> &x) const
+    {
+        CV<float, CW> o;
+#pragma unroll
+        for (int u = 0; u < CW; ++u) o.v[u] = s * x.v[u];
+        return o;
+    }
+    template <int CW, class F>
+    __device__ __forceinline__ CV<float, CW> dot(int i, F f) const
+    {
+        CV<float, CW> acc;
+#pragma unroll
+        for (int u = 0; u < CW; ++u) acc.v[u] = 0.f;
+        const float si = __ldg(sd + i);
+        if (i >= sxy) cacc(acc, __half2float(oz[i - sxy]), scaled<CW>(__ldg(sd + i - sxy), f(i - sxy)));
+        if (i >= nx) cacc(acc, __half2float(oy[i - nx]), scaled<CW>(__ldg(sd + i - nx), f(i - nx)));
+        if (i >= 1) cacc(acc, __half2float(ox[i - 1]), scaled<CW>(__ldg(sd + i - 1), f(i - 1)));
+        cacc(acc, 1.f + __half2float(dd[i]), scaled<CW>(si, f(i)));
+        if (i + 1 < n) cacc(acc, __half2float(ox[i]), scaled<CW>(__ldg(sd + i + 1), f(i + 1)));
+        if (i + nx < n) cacc(acc, __half2float(oy[i]), scaled<CW>(__ldg(sd + i + nx), f(i + nx)));
+        if (i + sxy < n) cacc(acc, __half2float(oz[i]), scaled<CW>(__ldg(sd + i + sxy), f(i + sxy)));
+        return scaled<CW>(si, acc);
+    }
+};
+
 template <class T, class F>
 static void with_bmat(const MatStore<T> &M, F f)
 {
@@ -212,6 +245,13 @@ static void with_bmat(const MatStore<T> &M, F f)
         if constexpr (sizeof(T) == 4) {
             const StenB &S = M.stenb;
             f(BStenB{S.d.p, S.ox.p, S.oy.p, S.oz.p, S.n, S.nx, S.nx * S.ny});
+            break;
+        }
+        [[fallthrough]];
+    case FMT_STENH:
+        if constexpr (sizeof(T) == 4) {
+            const StenH &S = M.stenh;
+            f(BStenH{S.sd.p, S.dd.p, S.ox.p, S.oy.p, S.oz.p, S.n, S.nx, S.nx * S.ny});
             break;
         }
         [[fallthrough]];

@@ -440,6 +440,93 @@ struct MStenB {
     }
 };
 
+// R FP16 values (R = 4: one 8-byte load) widened to FP32
+template <int R>
+__device__ __forceinline__ VecN<float, R> ld_h(const __half *p)
+{
+    VecN<float, R> o;
+    if constexpr (R == 4) {
+        const uint2 w = __ldg(reinterpret_cast<const uint2 *>(p));
+        __half2 a, b;
+        memcpy(&a, &w.x, sizeof a);
+        memcpy(&b, &w.y, sizeof b);
+        const float2 fa = __half22float2(a), fb = __half22float2(b);
+        o.v[0] = fa.x, o.v[1] = fa.y, o.v[2] = fb.x, o.v[3] = fb.y;
+    } else if constexpr (R == 2) {
+        const unsigned w = __ldg(reinterpret_cast<const unsigned *>(p));
+        __half2 a;
+        memcpy(&a, &w, sizeof a);
+        const float2 fa = __half22float2(a);
+        o.v[0] = fa.x, o.v[1] = fa.y;
+    } else {
+#pragma unroll
+        for (int k = 0; k < R; ++k) o.v[k] = __half2float(p[k]);
+    }
+    return o;
+}
+
+// The scaled FP16 stencil (StenH): (A x)_i = sd_i ((1 + dd_i) sd_i x_i +
+// sum_j c_ij sd_j x_j), 12 bytes a row; sd is gathered at the neighbours.
+// Same row blocking and term order as MSten.
+template <int R_>
+struct MStenH {
+    using value_type = float;
+    static constexpr int G = 1, R = R_;
+    const float *__restrict__ sd;
+    const __half *__restrict__ dd;
+    const __half *__restrict__ ox;
+    const __half *__restrict__ oy;
+    const __half *__restrict__ oz;
+    int n, nx, sxy;
+    template <class F>
+    __device__ __forceinline__ VecN<float, R> dot(int i0, int, F f) const
+    {
+        VecN<float, R> acc;
+#pragma unroll
+        for (int k = 0; k < R; ++k) acc.v[k] = 0.f;
+        if (i0 >= sxy) {
+            const VecN<float, R> c = ld_h<R>(oz + i0 - sxy), s = ld_ro<R>(sd + i0 - sxy);
+            const VecN<float, R> x = f.template vec<R>(i0 - sxy);
+#pragma unroll
+            for (int k = 0; k < R; ++k) acc.v[k] += c.v[k] * (s.v[k] * x.v[k]);
+        }
+        if (i0 >= nx) {
+            const VecN<float, R> c = ld_h<R>(oy + i0 - nx), s = ld_ro<R>(sd + i0 - nx);
+            const VecN<float, R> x = f.template vec<R>(i0 - nx);
+#pragma unroll
+            for (int k = 0; k < R; ++k) acc.v[k] += c.v[k] * (s.v[k] * x.v[k]);
+        }
+        const VecN<float, R> cx = ld_h<R>(ox + i0), sc = ld_ro<R>(sd + i0), dg = ld_h<R>(dd + i0);
+        const VecN<float, R> xc = f.template vec<R>(i0);
+        const float cxm = i0 >= 1 ? __half2float(ox[i0 - 1]) : 0.f;
+        const float sxm = i0 >= 1 ? __ldg(sd + i0 - 1) * f(i0 - 1) : 0.f;
+        const float sxp = i0 + R < n ? __ldg(sd + i0 + R) * f(i0 + R) : 0.f;
+        acc.v[0] += cxm * sxm;
+#pragma unroll
+        for (int k = 1; k < R; ++k) acc.v[k] += cx.v[k - 1] * (sc.v[k - 1] * xc.v[k - 1]);
+#pragma unroll
+        for (int k = 0; k < R; ++k) acc.v[k] += (1.f + dg.v[k]) * (sc.v[k] * xc.v[k]);
+#pragma unroll
+        for (int k = 0; k < R - 1; ++k) acc.v[k] += cx.v[k] * (sc.v[k + 1] * xc.v[k + 1]);
+        acc.v[R - 1] += cx.v[R - 1] * sxp;
+        if (i0 + nx < n) {
+            const VecN<float, R> c = ld_h<R>(oy + i0), s = ld_ro<R>(sd + i0 + nx);
+            const VecN<float, R> x = f.template vec<R>(i0 + nx);
+#pragma unroll
+            for (int k = 0; k < R; ++k) acc.v[k] += c.v[k] * (s.v[k] * x.v[k]);
+        }
+        if (i0 + sxy < n) {
+            const VecN<float, R> c = ld_h<R>(oz + i0), s = ld_ro<R>(sd + i0 + sxy);
+            const VecN<float, R> x = f.template vec<R>(i0 + sxy);
+#pragma unroll
+            for (int k = 0; k < R; ++k) acc.v[k] += c.v[k] * (s.v[k] * x.v[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k) acc.v[k] *= sc.v[k];
+        return acc;
+    }
+};
+
 // Compressed sliced ELL: 8 FP16 values and 8 16-bit column offsets per
 // 16-byte load; scaled square matrices multiply by sd on both sides.
 template <class T>
@@ -516,6 +603,20 @@ static void with_mat(const MatStore<T> &M, F f)
     case FMT_CSR32: f(MCsr<T, 32>{M.csr.rp.p, M.csr.ci.p, M.csr.v.p, M.csr.nr}); break;
     case FMT_SELL16:
         f(MSell16<T>{M.sell16.sp.p, M.sell16.base.p, M.sell16.v.p, M.sell16.ci.p, M.sell16.sd.p});
+        break;
+    case FMT_STENH:
+        if constexpr (sizeof(T) == 4) {
+            const StenH &S = M.stenh;
+            const int sxy = S.nx * S.ny;
+            if (S.n % 4 == 0 && S.nx % 4 == 0)
+                f(MStenH<4>{S.sd.p, S.dd.p, S.ox.p, S.oy.p, S.oz.p, S.n, S.nx, sxy});
+            else if (S.n % 2 == 0 && S.nx % 2 == 0)
+                f(MStenH<2>{S.sd.p, S.dd.p, S.ox.p, S.oy.p, S.oz.p, S.n, S.nx, sxy});
+            else
+                f(MStenH<1>{S.sd.p, S.dd.p, S.ox.p, S.oy.p, S.oz.p, S.n, S.nx, sxy});
+        } else {
+            fail(GW_ERR_SETUP, "an FP16 stencil in an FP64 hierarchy");
+        }
         break;
     case FMT_STENB:
         if constexpr (sizeof(T) == 4) {
@@ -1129,6 +1230,7 @@ static double mat_bytes(const MatStore<T> &M)
 {
     if (M.fmt == FMT_STEN) return 4.0 * M.nr * sizeof(T);
     if (M.fmt == FMT_STENB) return 10.0 * M.nr;
+    if (M.fmt == FMT_STENH) return 12.0 * M.nr;
     if (M.fmt == FMT_SELL16) return (double)M.nnz * 4.0 + (M.sell16.sd.p ? 4.0 * M.nr : 0.0);
     return (double)M.nnz * (sizeof(T) + 4.0);
 }

@@ -158,6 +158,18 @@ struct StenB {
     size_t bytes() const { return d.bytes() + ox.bytes() + oy.bytes() + oz.bytes(); }
 };
 
+// The level-0 stencil scaled to D^-1/2 A D^-1/2 (FP32 cycle only): sd_i =
+// sqrt(a_ii) in FP32, the scaled +x/+y/+z couplings in FP16 (all in
+// [-1, 0]), and the diagonal 1 + dd_i with dd_i in FP16 chosen so that the
+// stored operator sd (C + diag(1 + dd)) sd keeps the row sums of A:
+// dd_i = sum_j (|fp16(c_ij)| - |c_ij|) sd_j / sd_i.
+struct StenH {
+    int n = 0, nx = 0, ny = 0, nz = 0;
+    DBuf<float> sd;
+    DBuf<__half> dd, ox, oy, oz;
+    size_t bytes() const { return sd.bytes() + dd.bytes() + ox.bytes() + oy.bytes() + oz.bytes(); }
+};
+
 // Compressed sliced ELL (FP32 cycle only): FP16 values and 16-bit column
 // offsets from a per-slice base column, 8 slots per 16-byte load.  A square
 // level matrix is stored symmetrically scaled, D^-1/2 A D^-1/2 (entries in
@@ -173,7 +185,8 @@ struct Sell16 {
     size_t bytes() const { return sp.bytes() + base.bytes() + v.bytes() + ci.bytes() + sd.bytes(); }
 };
 
-enum { FMT_SELL = 0, FMT_CSR4 = 1, FMT_CSR8 = 2, FMT_CSR32 = 3, FMT_STEN = 4, FMT_SELL16 = 5, FMT_STENB = 6 };
+enum { FMT_SELL = 0, FMT_CSR4 = 1, FMT_CSR8 = 2, FMT_CSR32 = 3, FMT_STEN = 4, FMT_SELL16 = 5, FMT_STENB = 6,
+       FMT_STENH = 8 };
 // to_store request: sliced ELL over rows sorted by length within windows of
 // SELL_SORT_WINDOW rows (stored as FMT_SELL with a row permutation); only
 // for matrices read by the restriction, which writes its output row through it
@@ -190,7 +203,11 @@ struct MatStore {
     StenT<T> sten;
     Sell16 sell16;
     StenB stenb;
-    size_t bytes() const { return sell.bytes() + csr.bytes() + sten.bytes() + sell16.bytes() + stenb.bytes(); }
+    StenH stenh;
+    size_t bytes() const
+    {
+        return sell.bytes() + csr.bytes() + sten.bytes() + sell16.bytes() + stenb.bytes() + stenh.bytes();
+    }
 };
 
 int choose_fmt(const DCSR &A);

@@ -1242,6 +1242,51 @@ __global__ void k_to_stencil_bf16(int n, int nx, int sxy, const int *__restrict_
     }
 }
 
+// sqrt of the diagonal (FP32) for the scaled FP16 stencil
+__global__ void k_sten_sd(int n, const int *__restrict__ rp, const int *__restrict__ ci, const double *__restrict__ v,
+                          float *__restrict__ sd)
+{
+    GRID_STRIDE(ii, n)
+    {
+        const int i = (int)ii;
+        double dd = 0.0;
+        for (int e = rp[i]; e < rp[i + 1]; ++e)
+            if (ci[e] == i) dd = v[e];
+        sd[i] = (float)sqrt(dd);
+    }
+}
+
+// scaled couplings in FP16 and the FP16 correction of the unit diagonal (see StenH)
+__global__ void k_to_stencil_fp16(int n, int nx, int sxy, const int *__restrict__ rp, const int *__restrict__ ci,
+                                  const double *__restrict__ v, const float *__restrict__ sd,
+                                  __half *__restrict__ dd, __half *__restrict__ ox, __half *__restrict__ oy,
+                                  __half *__restrict__ oz, int *__restrict__ bad)
+{
+    GRID_STRIDE(ii, n)
+    {
+        const int i = (int)ii;
+        const double si = (double)sd[i];
+        double a = 0.0, b = 0.0, c = 0.0, corr = 0.0;
+        if (!(si > 0.0)) atomicAdd(bad, 1);
+        for (int e = rp[i]; e < rp[i + 1]; ++e) {
+            const long long j = ci[e];
+            if (j == i) continue;
+            const double sj = (double)sd[j];
+            const double x = v[e] / (si * sj);
+            if (j == (long long)i + sxy) c = x;
+            else if (j == (long long)i + nx) b = x;
+            else if (j == (long long)i + 1) a = x;
+            else if (!(j == (long long)i - sxy || j == (long long)i - nx || j == (long long)i - 1)) atomicAdd(bad, 1);
+            const double xr = (double)__half2float(__double2half(x));
+            corr += (fabs(xr) - fabs(x)) * sj / si;
+        }
+        dd[i] = __double2half(corr);
+        ox[i] = __double2half(a);
+        oy[i] = __double2half(b);
+        oz[i] = __double2half(c);
+    }
+}
+
 // Short rows (the prolongator) and rows of medium length on big levels as
 // sliced ELL, one thread per row; long rows on small levels as CSR read by a
 // whole warp, so the level still covers the GPU.
@@ -1268,6 +1313,31 @@ bool to_store(const DCSR &A, MatStore<T> &M, int fmt, int nx, int ny, int nz, cu
         M.fmt = FMT_SELL;
         to_sell<T>(A, M.sell, st, true);
         return true;
+    }
+    if (fmt == FMT_STENH) {
+        StenH &S = M.stenh;
+        const int n = A.nr;
+        if (sizeof(T) == 4) {
+            S.n = n;
+            S.nx = nx;
+            S.ny = ny;
+            S.nz = nz;
+            S.sd.alloc((size_t)n);
+            S.dd.alloc((size_t)n);
+            S.ox.alloc((size_t)n);
+            S.oy.alloc((size_t)n);
+            S.oz.alloc((size_t)n);
+            DBuf<int> bad(1);
+            GW_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
+            gw_launch(k_sten_sd, nblk(n, 256), 256, 0, st, n, A.rp.p, A.ci.p, A.v.p, S.sd.p);
+            gw_launch(k_to_stencil_fp16, nblk(n, 256), 256, 0, st, n, nx, nx * ny, A.rp.p, A.ci.p, A.v.p,
+                      (const float *)S.sd.p, S.dd.p, S.ox.p, S.oy.p, S.oz.p, bad.p);
+            GW_LAUNCH_CHECK();
+            if (read_int(bad.p, st) == 0) return true;
+            S = StenH();
+        }
+        fmt = FMT_STEN;
+        M.fmt = fmt;
     }
     if (fmt == FMT_STENB) {
         StenB &S = M.stenb;

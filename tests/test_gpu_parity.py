@@ -261,15 +261,19 @@ def test_full_size_128_cubed_sigma4(gw, prec):
     assert np.linalg.norm(h.cpu().numpy() - href) / np.linalg.norm(href) <= REL_ERR
 
 
+@pytest.mark.parametrize("half", ["bf16", "fp16"])
 @pytest.mark.parametrize("name", ["3d_het_33_sigma4", "3d_layered_24", "2d_homog_128"])
-def test_bf16_fine_stencil_solves_to_parity(gw, name):
-    """GW_HALF_FINE: the V-cycle's level-0 stencil with BF16 couplings.  The
-    solve still stops on the FP64 residual, agrees with the oracle, and the
-    preconditioner stays close to the FP32 one (a few iterations more at most)."""
+def test_half_fine_stencil_solves_to_parity(gw, name, half):
+    """GW_HALF_FINE (BF16 couplings, corrected FP32 diagonal) and GW_HALF_FINE16
+    (FP16 couplings of the diagonally scaled stencil): the solve still stops
+    on the FP64 residual, agrees with the oracle, and the preconditioner stays
+    close to the FP32 one (a few iterations more at most)."""
+    bits, alias = ((gw.GW_HALF_FINE, gw.GW_PREC_MIXEDBF16) if half == "bf16"
+                   else (gw.GW_HALF_FINE16, gw.GW_PREC_MIXED16))
     p = PROBLEMS[name]()
     A, b = gpu_assemble(gw, p)
     H32 = gw.Hierarchy(A, n_coarse=64)
-    Hb = gw.Hierarchy(A, n_coarse=64, half_storage=gw.GW_HALF_FINE)
+    Hb = gw.Hierarchy(A, n_coarse=64, half_storage=bits)
     h32, it32, _, _ = H32.solve(b, tol=TOL)
     hb, itb, relb, st = Hb.solve(b, tol=TOL)
     assert st == gw.GW_OK and relb <= TOL
@@ -277,11 +281,13 @@ def test_bf16_fine_stencil_solves_to_parity(gw, name):
     Ao, bo = ora_assemble(p)
     href, _, _, _ = oracle.Hierarchy(Ao, n_coarse=64).pcg(bo, tol=1e-12)
     assert np.linalg.norm(hb.cpu().numpy() - href) / np.linalg.norm(href) <= REL_ERR
-    # GW_PREC_MIXEDBF16 names the same configuration
-    hp, itp, _, _ = gw.Hierarchy(A, n_coarse=64, prec=gw.GW_PREC_MIXEDBF16).solve(b, tol=TOL)
+    # the precision name of the same configuration
+    hp, itp, _, _ = gw.Hierarchy(A, n_coarse=64, prec=alias).solve(b, tol=TOL)
     assert itp == itb and torch.equal(hp, hb)
     with pytest.raises(gw.GwError):
-        gw.Hierarchy(A, prec=gw.GW_PREC_FP64, half_storage=gw.GW_HALF_FINE)
+        gw.Hierarchy(A, prec=gw.GW_PREC_FP64, half_storage=bits)
+    with pytest.raises(gw.GwError):
+        gw.Hierarchy(A, half_storage=gw.GW_HALF_FINE | gw.GW_HALF_FINE16)
     # the interleaved block path runs the same stored operator
     B = torch.stack([b, 2.0 * b])
     X, its, rels, st = Hb.solve_many(B, tol=TOL)
@@ -289,14 +295,14 @@ def test_bf16_fine_stencil_solves_to_parity(gw, name):
     assert np.linalg.norm(X[1].cpu().numpy() - 2 * href) / np.linalg.norm(2 * href) <= REL_ERR
 
 
-@pytest.mark.parametrize("half", [0, 2])
+@pytest.mark.parametrize("half", [0, 2, 4])
 @pytest.mark.parametrize("prec", [1, 0])
 def test_full_size_layered_256x256x128(gw, prec, half):
     """The 256x256x128 layered case (lnK variance 1, correlation 32/32/4 cells,
     Kh/Kv = 10, 16 wells, fixed head on top) at full size: level-0 aggregates,
     roots and the level-1 operator bit-exact, the solution within 1e-6 of the
     oracle's, in the FP64 form, the mixed form and the mixed form with the
-    BF16-stored fine stencil."""
+    BF16- or FP16-stored fine stencil."""
     if prec == 0 and half:
         pytest.skip("BF16 storage belongs to the mixed form")
     p = wl.layered_wells_3d()

@@ -856,12 +856,38 @@ void setup_spgemm(const DCSR &L, const DCSR &Rm, DCSR &C, cudaStream_t st)
 // that row and copies it and the multipliers W_ik aside; then the whole GPU
 // subtracts m_i times the pivot row from every other row.  The O(n^3)
 // FP64 work so runs on every SM instead of one.
+// The 2n launches of the elimination run back to back with programmatic
+// dependent launch: each kernel may be scheduled while its predecessor runs
+// and waits for it (and its writes) before touching memory.
+__device__ __forceinline__ void gj_enter()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <class... KArgs, class... Args>
+static void gj_launch(void (*kernel)(KArgs...), int grid, int block, cudaStream_t st, Args &&...args)
+{
+    prime_kernel((const void *)kernel);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    GW_CUDA(cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...));
+}
+
 __global__ void __launch_bounds__(1024) k_gj_pivot(int n, int k, double *__restrict__ W, double *__restrict__ prow,
                                                    double *__restrict__ m, int *__restrict__ singular)
 {
     __shared__ double sv[1024];
     __shared__ int si[1024];
     const int tid = threadIdx.x, bs = blockDim.x, w2 = 2 * n;
+    gj_enter();
     if (*singular) return;
     double best = -1.0;
     int bi = n;
@@ -911,6 +937,7 @@ __global__ void __launch_bounds__(1024) k_gj_pivot(int n, int k, double *__restr
 __global__ void k_gj_elim(int n, int k, double *__restrict__ W, const double *__restrict__ prow,
                           const double *__restrict__ m, const int *__restrict__ singular)
 {
+    gj_enter();
     if (*singular) return;
     const int w2 = 2 * n, cols = w2 - k;
     const long long total = (long long)n * cols;
@@ -957,10 +984,10 @@ void setup_dense_inverse(const DCSR &A, DBuf<double> &Ainv, cudaStream_t st)
     GW_CUDA(cudaGetDevice(&dev));
     GW_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     for (int k = 0; k < n; ++k) {
-        gw_launch(k_gj_pivot, 1, 1024, 0, st, n, k, W.p, prow.p, m.p, sing.p);
+        gj_launch(k_gj_pivot, 1, 1024, st, n, k, W.p, prow.p, m.p, (int *)sing.p);
         const long long total = (long long)n * (2 * n - k);
         const int g = (int)std::max(1LL, std::min<long long>((total + 255) / 256, 8LL * std::max(1, sms)));
-        gw_launch(k_gj_elim, g, 256, 0, st, n, k, W.p, prow.p, m.p, sing.p);
+        gj_launch(k_gj_elim, g, 256, st, n, k, W.p, (const double *)prow.p, (const double *)m.p, (const int *)sing.p);
     }
     GW_LAUNCH_CHECK();
     if (read_int(sing.p, st)) fail(GW_ERR_SETUP, "coarsest-level matrix (%d unknowns) is singular", n);

@@ -34,6 +34,12 @@ from . import gw
 from . import workload as wl
 
 
+# the request fields' padded FFT grids are multiples of this many cells per
+# axis, so that a stream of many grid sizes reuses a few cuFFT plans (a new
+# plan costs tens of milliseconds)
+FIELD_PAD = 32
+
+
 class _SharedExclusive:
     """Many holders of the shared side or one of the exclusive side; a waiting
     exclusive holder keeps new shared holders out."""
@@ -164,7 +170,7 @@ class Server:
             if "K" in req:
                 K = req["K"]
             else:
-                K = torch.exp(wl.lnk_field_device(s, s, s, req["var"], req["corr"], req["seed"]))
+                K = torch.exp(wl.lnk_field_device(s, s, s, req["var"], req["corr"], req["seed"], pad=FIELD_PAD))
             b = torch.empty(n, dtype=torch.float64, device=K.device)
             A, _ = gw.gw_assemble(s, s, s, K, K, K, (1, 1, 0, 0, 0, 0), (1.0, 0.0, 0, 0, 0, 0), None, b_out=b,
                                   stream=stream)

@@ -121,18 +121,22 @@ def layered_wells_3d(nx=256, ny=256, nz=128, var=1.0, corr=(32.0, 32.0, 4.0), se
                    wells_count=wells_count, wells_seed=wells_seed, wells_rate=wells_rate)
 
 
-def lnk_field_device(nx, ny, nz, var, corr, seed, device="cuda"):
+def lnk_field_device(nx, ny, nz, var, corr, seed, device="cuda", pad=1):
     """The same circulant-embedding recipe as lnk_field, drawn on a torch
     device (white noise from torch.Generator(device).manual_seed(seed)), for
-    request streams where thousands of fields are needed.  Returns a float64
-    tensor of nx*ny*nz values (C order (nz, ny, nx))."""
+    request streams where thousands of fields are needed.  The padded grid is
+    twice the size on every axis with more than one cell, rounded up to a
+    multiple of ``pad``: any periodic domain of at least twice the size embeds
+    the covariance at every lag of the grid, and a few padded sizes let the
+    FFT plans be reused across requests of different sizes.  Returns a
+    float64 tensor of nx*ny*nz values (C order (nz, ny, nx))."""
     import torch
 
     if np.isscalar(corr):
         corr = (corr, corr, corr)
     dims = (nz, ny, nx)
     lam = (float(corr[2]), float(corr[1]), float(corr[0]))
-    m = tuple(1 if d == 1 else 2 * d for d in dims)
+    m = tuple(1 if d == 1 else -(-2 * d // pad) * pad for d in dims)
     axes = []
     for mi, li in zip(m, lam):
         k = torch.arange(mi, dtype=torch.float64, device=device)

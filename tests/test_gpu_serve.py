@@ -52,7 +52,7 @@ def test_alone_and_in_the_mix_agree(serve):
     # one result against the oracle (the field is regenerated identically)
     r = reqs[0]
     s = r["side"]
-    K = torch.exp(wl.lnk_field_device(s, s, s, r["var"], r["corr"], r["seed"])).cpu().numpy()
+    K = torch.exp(wl.lnk_field_device(s, s, s, r["var"], r["corr"], r["seed"], pad=serve.FIELD_PAD)).cpu().numpy()
     A, b = oracle.assemble(s, s, s, K)
     href, _, _, _ = oracle.Hierarchy(A, n_coarse=200).pcg(b, tol=1e-12)
     h = alone[r["id"]]["h"].cpu().numpy()

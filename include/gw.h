@@ -286,10 +286,15 @@ int gw_hierarchy_prepare(gw_hierarchy H);
  * operator C, e.g. well or boundary scenarios, or forward and adjoint
  * solves.  B and X are n x k, column-major
  * (column c at B + c*n), host or device; iters and relres receive k values
- * (host, may be NULL).  The columns are solved one after another on the
- * resident hierarchy and its captured iteration graphs, each to the true
- * relative residual tol.  Returns GW_OK, or the first failing status with
- * every column still solved as far as it went.
+ * (host, may be NULL).  In the mixed form (without GW_HALF_TRANSFER) k >= 2
+ * columns run in interleaved blocks of up to 8 that share every matrix read
+ * of the V-cycle and of CG, each column with its own CG scalars, reliable
+ * updates and stop; otherwise the columns are solved one after another.
+ * Each column is solved to the true relative residual tol; the first call
+ * of a block width captures its graphs and allocates its working vectors
+ * (about 40 bytes per cell and column at width 8).  Returns GW_OK, or the
+ * first failing status with every column solved as far as it went.
+ * Errors: GW_ERR_ARG, GW_ERR_CUDA, GW_ERR_NOT_CONVERGED, GW_ERR_BREAKDOWN.
  */
 int gw_pcg_solve_many(gw_hierarchy H, int k, const double *B, double *X, double tol, int maxit, int *iters,
                       double *relres, void *stream);

@@ -292,7 +292,7 @@ int gw_hierarchy_prepare(gw_hierarchy H);
  * updates and stop; otherwise the columns are solved one after another.
  * Each column is solved to the true relative residual tol; the first call
  * of a block width captures its graphs and allocates its working vectors
- * (about 40 bytes per cell and column at width 8).  Returns GW_OK, or the
+ * (about 70 bytes per cell and column at width 8).  Returns GW_OK, or the
  * first failing status with every column solved as far as it went.
  * Errors: GW_ERR_ARG, GW_ERR_CUDA, GW_ERR_NOT_CONVERGED, GW_ERR_BREAKDOWN.
  */

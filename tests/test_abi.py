@@ -64,3 +64,27 @@ def test_product_code_never_touches_the_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "gw_oracle" not in text and "liboracle" not in text, f
+
+
+def test_null_arguments_are_rejected_without_a_device(lib):
+    """Every entry point checks its handles and pointers before it touches the
+    GPU: a null argument returns GW_ERR_ARG with a message, and nothing aborts."""
+    from paper_2001_05798_gb300 import gw
+
+    L = gw.load()
+    it, rel, rb = ctypes.c_int(), ctypes.c_double(), ctypes.c_int()
+    calls = {
+        "gw_pcg_solve": lambda: L.gw_pcg_solve(None, None, None, 1e-8, 10, ctypes.byref(it), ctypes.byref(rel), None),
+        "gw_pcg_solve_many": lambda: L.gw_pcg_solve_many(None, 2, None, None, 1e-8, 10, None, None, None),
+        "gw_hierarchy_prepare": lambda: L.gw_hierarchy_prepare(None),
+        "gw_hierarchy_shift": lambda: L.gw_hierarchy_shift(None, None, 0.01, ctypes.byref(rb), None),
+        "gw_vcycle": lambda: L.gw_vcycle(None, None, None, None),
+        "gw_amg_setup": lambda: L.gw_amg_setup(None, None, None, None),
+        "gw_darcy_flux": lambda: L.gw_darcy_flux(None, None, None, None, None, None, None, None, None, None),
+        "gw_adjoint_gradient": lambda: L.gw_adjoint_gradient(None, None, None, None, None, None, None, None, None),
+        "gw_matrix_size": lambda: L.gw_matrix_size(None, None, None),
+        "gw_hierarchy_info": lambda: L.gw_hierarchy_info(None, None, 0, None),
+    }
+    for name, call in calls.items():
+        assert call() == gw.GW_ERR_ARG, name
+        assert L.gw_last_error(), name

@@ -107,6 +107,8 @@ typedef struct {
                             GW_HALF_FINE16: the level-0 stencil scaled to D^-1/2 A D^-1/2, its
                               couplings in FP16, sqrt(a_ii) in FP32 and the unit diagonal's
                               row-sum correction in FP16 (not together with GW_HALF_FINE) */
+    int mis_max_rounds;  /* parallel MIS-2 rounds allowed per level before the setup fails with
+                            GW_ERR_SETUP (200; 0 means the default) */
 } gw_amg_opts;
 
 /* Per-level statistics in the columns of the paper's Table 1 (unknowns,
@@ -168,12 +170,17 @@ int gw_assemble(const gw_grid *grid, const double *Kx, const double *Ky, const d
  * Working memory: a fixed array of about 256 KB in device memory that the
  * library holds on every GPU that loads it, until the process exits; grids
  * of more than 2^27 cells are rejected with GW_ERR_ARG.  The first call on a
- * device looks up that array's device address, so make the first call on
- * each device outside any stream capture.  All calls on a device share the
- * array (the call clears the part that must start at zero): calls that
- * overlap on the GPU race, so serialise them (one stream, or wait for the
- * previous call, which synchronises its stream before returning).
- * Errors: as gw_assemble, plus GW_ERR_ARG for a host pointer.
+ * device looks up that array's device address.  Every call synchronises its
+ * stream (it reads a validation flag back), so no call may be made on a
+ * stream that is being captured: such a call returns GW_ERR_ARG.  With
+ * stream NULL the call runs on the legacy default stream, which
+ * synchronises with other blocking streams; pass a non-default stream when
+ * other threads capture graphs.  All calls on a device share the array (the
+ * call clears the part that must start at zero): calls that overlap on the
+ * GPU race, so serialise them (one stream, or wait for the previous call,
+ * which synchronises its stream before returning).
+ * Errors: as gw_assemble, plus GW_ERR_ARG for a host pointer or a capturing
+ * stream.
  */
 int gw_assemble_noalloc(const gw_grid *grid, const double *Kx, const double *Ky, const double *Kz, const gw_bc *bc,
                         const double *q, int *rowptr, int *col, double *val, double *b, void *stream);
@@ -387,6 +394,14 @@ const char *gw_status_str(int status);
 
 /* One-line description of the last failure on the calling thread. */
 const char *gw_last_error(void);
+
+/*
+ * gw_device_allocations -- the number of device allocations (cudaMalloc and
+ * cudaMallocAsync calls) the library has made in this process so far.  It
+ * lets a caller check that a sequence of calls allocated nothing, for
+ * example gw_assemble_noalloc.  Not part of the paper's method.
+ */
+long long gw_device_allocations(void);
 
 #ifdef __cplusplus
 }

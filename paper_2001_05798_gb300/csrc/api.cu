@@ -211,7 +211,7 @@ void build_hierarchy(Hier &H, cudaStream_t st)
         if (A.nr <= o.n_coarse || l + 1 >= o.max_levels) break;
         DBuf<unsigned char> S;
         setup_strength(A, th * th, S, st);
-        H.info[(size_t)l].mis_rounds = setup_mis2(A, S.p, o.seed, l, H.root[(size_t)l], st);
+        H.info[(size_t)l].mis_rounds = setup_mis2(A, S.p, o.seed, l, H.root[(size_t)l], o.mis_max_rounds, st);
         const int m = setup_aggregate(A, S.p, H.root[(size_t)l].p, o.seed, l, H.agg[(size_t)l], st);
         H.info[(size_t)l].naggregates = m;
         if (m == 0 || (double)m > 0.9 * (double)A.nr) {
@@ -369,6 +369,7 @@ void gw_amg_opts_default(gw_amg_opts *o)
     o->prec = GW_PREC_MIXED32;
     o->delta = 0.1;
     o->half_storage = 0;
+    o->mis_max_rounds = 200;
 }
 
 const char *gw_status_str(int s)
@@ -386,6 +387,8 @@ const char *gw_status_str(int s)
 }
 
 const char *gw_last_error(void) { return gw::last_error_cstr(); }
+
+long long gw_device_allocations(void) { return gw::device_allocations(); }
 
 int gw_assemble(const gw_grid *grid, const double *Kx, const double *Ky, const double *Kz, const gw_bc *bc,
                 const double *q, gw_matrix *A_out, double *b_out, void *stream)
@@ -474,6 +477,8 @@ int gw_amg_setup(gw_matrix A, const gw_amg_opts *opts, gw_hierarchy *H_out, void
     if (o.degree < 1 || o.degree > 8 || o.nu < 1 || o.nu > 8) fail(GW_ERR_ARG, "gw_amg_setup: degree and nu must be in 1..8");
     if (o.n_coarse < 1 || o.n_coarse > 4096) fail(GW_ERR_ARG, "gw_amg_setup: n_coarse must be in 1..4096");
     if (o.max_levels < 2 || o.max_levels > 16) fail(GW_ERR_ARG, "gw_amg_setup: max_levels must be in 2..16");
+    if (o.mis_max_rounds < 0) fail(GW_ERR_ARG, "gw_amg_setup: mis_max_rounds must be >= 0");
+    if (o.mis_max_rounds == 0) o.mis_max_rounds = 200;
     if (o.prec == GW_PREC_MIXEDBF16) {
         o.prec = GW_PREC_MIXED32;
         o.half_storage |= GW_HALF_FINE;
@@ -520,7 +525,9 @@ int gw_pcg_solve(gw_hierarchy H, const double *b, double *h, double tol, int max
     GW_CUDA(cudaMemcpyAsync(h, hh.x.p, bytes, cudaMemcpyDefault, st));
     GW_CUDA(cudaStreamSynchronize(st));
     if (status != GW_OK) {
-        gw::set_last_error(status == GW_ERR_NOT_CONVERGED ? "gw_pcg_solve: maxit reached" : "gw_pcg_solve: CG breakdown");
+        gw::set_last_error(status == GW_ERR_NOT_CONVERGED ? "gw_pcg_solve: maxit reached"
+                           : status == GW_ERR_ARG          ? "gw_pcg_solve: the right-hand side has a non-finite entry"
+                                                           : "gw_pcg_solve: CG breakdown");
         return status;
     }
     GW_API_END

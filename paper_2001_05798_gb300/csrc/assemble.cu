@@ -7,6 +7,9 @@
 // on the boundary face, half a cell from the centre.  Every product and sum
 // is an explicitly rounded intrinsic in a fixed order, so the matrix is the
 // same double for double as any implementation that follows that order.
+#include <atomic>
+#include <mutex>
+
 #include "gw_internal.cuh"
 
 namespace gw {
@@ -283,21 +286,27 @@ constexpr size_t NOALLOC_SCRATCH_INTS = 1 + (size_t)(NOALLOC_MAX_CELLS / 2048) +
 static __device__ __align__(256) int g_noalloc_scratch[NOALLOC_SCRATCH_INTS];
 
 constexpr int NOALLOC_MAX_DEVICES = 64;
-static int *g_noalloc_ptr[NOALLOC_MAX_DEVICES];
+static std::atomic<int *> g_noalloc_ptr[NOALLOC_MAX_DEVICES];
+static std::mutex g_noalloc_mu;
 
 // The device address of the array: its name in host code is only a host-side
-// stand-in, so it is looked up once per device with that device current.
+// stand-in, so it is looked up once per device with that device current.  The
+// lookup can load this file's module, which would invalidate a graph capture
+// running on another thread, so it waits at the library's capture gate.
 static int *noalloc_scratch(int dev)
 {
     if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) fail(GW_ERR_ARG, "gw_assemble_noalloc: device %d out of range", dev);
-    if (!g_noalloc_ptr[dev]) {
-        int *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress((void **)&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p)
-            fail(GW_ERR_CUDA, "gw_assemble_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
-        g_noalloc_ptr[dev] = p;
-    }
-    return g_noalloc_ptr[dev];
+    int *p = g_noalloc_ptr[dev].load(std::memory_order_acquire);
+    if (p) return p;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    p = g_noalloc_ptr[dev].load(std::memory_order_relaxed);
+    if (p) return p;
+    auto gate = capture_gate();
+    cudaError_t e = cudaGetSymbolAddress((void **)&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+        fail(GW_ERR_CUDA, "gw_assemble_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+    g_noalloc_ptr[dev].store(p, std::memory_order_release);
+    return p;
 }
 
 }  // namespace gw
@@ -309,6 +318,12 @@ extern "C" int gw_assemble_noalloc(const gw_grid *grid, const double *Kx, const 
     using namespace gw;
     try {
         if (!grid || !Kx || !bc || !rowptr || !col || !val || !b) fail(GW_ERR_ARG, "gw_assemble_noalloc: null argument");
+        {
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            GW_CUDA(cudaStreamIsCapturing((cudaStream_t)stream, &cs));
+            if (cs != cudaStreamCaptureStatusNone)
+                fail(GW_ERR_ARG, "gw_assemble_noalloc: the stream is being captured (the call synchronises it)");
+        }
         const int nx = grid->nx, ny = grid->ny, nz = grid->nz;
         if (nx < 1 || ny < 1 || nz < 1) fail(GW_ERR_ARG, "gw_assemble_noalloc: grid sizes must be >= 1");
         const double dx = grid->dx, dy = grid->dy, dz = grid->dz;
@@ -332,10 +347,10 @@ extern "C" int gw_assemble_noalloc(const gw_grid *grid, const double *Kx, const 
         for (int k = 0; k < 8; ++k)
             if (ptrs[k] && !is_device_ptr(ptrs[k]))
                 fail(GW_ERR_ARG, "gw_assemble_noalloc: every array must be device memory (argument %d is not)", k);
+        cudaStream_t st = (cudaStream_t)stream;
         int dev = 0;
         GW_CUDA(cudaGetDevice(&dev));
         int *scratch = noalloc_scratch(dev);
-        cudaStream_t st = (cudaStream_t)stream;
         const int n = (int)n64;
         AsmGeom G;
         G.nx = nx;

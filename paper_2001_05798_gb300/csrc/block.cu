@@ -692,10 +692,10 @@ __global__ void __launch_bounds__(BS) kb_init(int n, const double *__restrict__ 
         cj.rmax2 = b2;
         cj.it = 0;
         cj.check = 0;
-        cj.status = GW_OK;
+        cj.status = isfinite(b2) ? GW_OK : GW_ERR_ARG;  // a non-finite right-hand side entry
         cj.rz = cj.pq = cj.alpha = cj.beta = cj.rr = cj.rt2 = cj.qz = 0.0;
-        cj.relres = b2 > 0.0 ? 1.0 : 0.0;
-        cj.done = b2 > 0.0 ? 0 : 1;
+        cj.relres = isfinite(b2) ? (b2 > 0.0 ? 1.0 : 0.0) : b2;
+        cj.done = (b2 > 0.0 && isfinite(b2)) ? 0 : 1;
     }
     __syncthreads();
     if (threadIdx.x == 0) refresh_done<KB>(c);

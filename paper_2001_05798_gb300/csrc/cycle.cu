@@ -1510,10 +1510,11 @@ __global__ void __launch_bounds__(BS) k_cg_init(int n, const double *__restrict_
         c->rmax2 = tot[0];
         c->it = 0;
         c->check = 0;
-        c->status = GW_OK;
+        const bool fin = isfinite(tot[0]);  // false: b has a non-finite entry
+        c->status = fin ? GW_OK : GW_ERR_ARG;
         c->rz = c->pq = c->alpha = c->beta = c->rr = c->rt2 = c->qz = 0.0;
-        c->relres = tot[0] > 0.0 ? 1.0 : 0.0;
-        c->done = tot[0] > 0.0 ? 0 : 1;
+        c->relres = fin ? (tot[0] > 0.0 ? 1.0 : 0.0) : tot[0];
+        c->done = (fin && tot[0] > 0.0) ? 0 : 1;
     }
 }
 

@@ -8,6 +8,7 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string>
 #include <utility>
 #include <vector>
@@ -45,6 +46,15 @@ cudaError_t dev_malloc(void **p, size_t bytes);
 void dev_free(void *p);
 cudaError_t host_malloc(void **p, size_t bytes);
 void host_free(void *p);
+// Device allocations made by the library so far (cudaMalloc and
+// cudaMallocAsync calls), for callers that must check that a call allocates
+// nothing.
+long long device_allocations();
+// Outside this thread's own capture: waits until no other thread of the
+// library captures, and keeps captures from starting while the returned
+// lock is held (with lazy module loading, a module load or symbol lookup
+// during another thread's capture invalidates that capture).
+std::unique_lock<std::mutex> capture_gate();
 struct CaptureScope {
     CaptureScope();
     ~CaptureScope();
@@ -290,7 +300,7 @@ struct LevelSetupOut {
 };
 void setup_strength(const DCSR &A, double theta2, DBuf<unsigned char> &S, cudaStream_t st);
 int setup_mis2(const DCSR &A, const unsigned char *S, uint64_t seed, int level, DBuf<unsigned char> &root,
-               cudaStream_t st);  // returns rounds
+               int max_rounds, cudaStream_t st);  // returns rounds; GW_ERR_SETUP after max_rounds
 int setup_aggregate(const DCSR &A, const unsigned char *S, const unsigned char *root, uint64_t seed, int level,
                     DBuf<int> &agg, cudaStream_t st);  // returns nagg
 void setup_smooth_p(const DCSR &A, const unsigned char *S, const int *agg, int nagg, DCSR &P, double *omega,

@@ -248,7 +248,7 @@ __global__ void k_mis_roots(int n, const unsigned char *__restrict__ state, unsi
 }
 
 int setup_mis2(const DCSR &A, const unsigned char *S, uint64_t seed, int level, DBuf<unsigned char> &root,
-               cudaStream_t st)
+               int max_rounds, cudaStream_t st)
 {
     const int n = A.nr;
     DBuf<unsigned char> state((size_t)n), near1((size_t)n);
@@ -257,7 +257,6 @@ int setup_mis2(const DCSR &A, const unsigned char *S, uint64_t seed, int level, 
     root.alloc((size_t)n);
     GW_CUDA(cudaMemsetAsync(state.p, 0, (size_t)n, st));
     const int g = nblk(n, 256);
-    const int max_rounds = 200;
     int rounds = 0;
     for (;;) {
         if (rounds >= max_rounds) fail(GW_ERR_SETUP, "MIS-2 did not finish in %d rounds on level %d", max_rounds, level);

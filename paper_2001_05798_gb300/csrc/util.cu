@@ -1,12 +1,11 @@
 // util.cu -- error plumbing, device scan and small host helpers of libgw.
 #include <stdarg.h>
 
+#include <atomic>
 #include <condition_variable>
-#include <mutex>
-
 #include <map>
-#include <set>
 #include <mutex>
+#include <set>
 
 #include "gw_internal.cuh"
 
@@ -32,11 +31,15 @@ const char *last_error_cstr() { return g_last_error.c_str(); }
 static std::mutex g_alloc_mu;
 static std::condition_variable g_alloc_cv;
 static int g_captures = 0;
+static std::atomic<long long> g_device_allocs{0};
+
+long long device_allocations() { return g_device_allocs.load(); }
 
 cudaError_t dev_malloc(void **p, size_t bytes)
 {
     std::unique_lock<std::mutex> lk(g_alloc_mu);
     g_alloc_cv.wait(lk, [] { return g_captures == 0; });
+    g_device_allocs.fetch_add(1);
     return cudaMalloc(p, bytes);
 }
 
@@ -76,6 +79,16 @@ CaptureScope::CaptureScope()
         ++g_captures;
     }
     t_capturing = true;
+}
+
+std::unique_lock<std::mutex> capture_gate()
+{
+    std::unique_lock<std::mutex> lk(g_alloc_mu, std::defer_lock);
+    if (!t_capturing) {
+        lk.lock();
+        g_alloc_cv.wait(lk, [] { return g_captures == 0; });
+    }
+    return lk;
 }
 
 CaptureScope::~CaptureScope()
@@ -141,6 +154,7 @@ void exclusive_scan(const int *in, int *out, int n, cudaStream_t st)
     }
     int nb = (n + SCAN_CHUNK - 1) / SCAN_CHUNK;
     int *bsum = nullptr;
+    g_device_allocs.fetch_add(1);
     GW_CUDA(cudaMallocAsync((void **)&bsum, (size_t)(nb + 1) * sizeof(int), st));
     gw_launch(k_scan_block, nb, SCAN_BS, 0, st, in, out, bsum, n);
     GW_LAUNCH_CHECK();
@@ -216,11 +230,7 @@ void prime_kernel(const void *fn)
         std::lock_guard<std::mutex> lock(mu);
         if (loaded.count(key)) return;
     }
-    std::unique_lock<std::mutex> alloc_lk(g_alloc_mu, std::defer_lock);
-    if (!t_capturing) {
-        alloc_lk.lock();
-        g_alloc_cv.wait(alloc_lk, [] { return g_captures == 0; });
-    }
+    auto gate = capture_gate();
     cudaFuncAttributes a;
     GW_CUDA(cudaFuncGetAttributes(&a, fn));
     std::lock_guard<std::mutex> lock(mu);
@@ -241,11 +251,7 @@ int kernel_wave(const void *fn, int block_size)
     }
     // the query may load the kernel's code: outside a capture of this thread,
     // wait until no other thread captures (and keep captures from starting)
-    std::unique_lock<std::mutex> alloc_lk(g_alloc_mu, std::defer_lock);
-    if (!t_capturing) {
-        alloc_lk.lock();
-        g_alloc_cv.wait(alloc_lk, [] { return g_captures == 0; });
-    }
+    auto gate = capture_gate();
     int nb = 0, sms = 0;
     GW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, block_size, 0));
     GW_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));

@@ -24,7 +24,7 @@ EXPORTS = ("gw_amg_opts_default", "gw_assemble", "gw_matrix_size", "gw_matrix_ex
            "gw_pcg_solve", "gw_vcycle", "gw_hierarchy_info", "gw_hierarchy_export", "gw_matrix_free",
            "gw_hierarchy_free", "gw_status_str", "gw_last_error", "gw_profile_enable", "gw_profile_read",
            "gw_assemble_noalloc", "gw_adjoint_gradient", "gw_misfit", "gw_hierarchy_shift",
-           "gw_pcg_solve_many", "gw_darcy_flux", "gw_hierarchy_prepare")
+           "gw_pcg_solve_many", "gw_darcy_flux", "gw_hierarchy_prepare", "gw_device_allocations")
 
 PK_NAMES = ("spmv", "update", "pre1", "pre2", "resid", "restrict", "l1down", "deep", "l1up", "prolong", "post1",
             "post2", "pupdate")
@@ -43,7 +43,7 @@ class gw_amg_opts(ctypes.Structure):
     _fields_ = [("theta", ctypes.c_double), ("smoother", ctypes.c_int), ("degree", ctypes.c_int),
                 ("nu", ctypes.c_int), ("n_coarse", ctypes.c_int), ("max_levels", ctypes.c_int),
                 ("seed", ctypes.c_uint64), ("prec", ctypes.c_int), ("delta", ctypes.c_double),
-                ("half_storage", ctypes.c_int)]
+                ("half_storage", ctypes.c_int), ("mis_max_rounds", ctypes.c_int)]
 
 
 class gw_level_info(ctypes.Structure):
@@ -99,6 +99,7 @@ def load():
         "gw_pcg_solve_many": (i, [vp, i, vp, vp, d, i, vp, vp, vp]),
         "gw_hierarchy_prepare": (i, [vp]),
         "gw_darcy_flux": (i, [P(gw_grid), vp, vp, vp, P(gw_bc), vp, vp, vp, vp, vp]),
+        "gw_device_allocations": (ll, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -148,6 +149,11 @@ def _stream(stream):
     if hasattr(stream, "cuda_stream"):
         return ctypes.c_void_p(stream.cuda_stream)
     return ctypes.c_void_p(int(stream))
+
+
+def gw_device_allocations():
+    """Device allocations the library has made in this process so far."""
+    return int(load().gw_device_allocations())
 
 
 def amg_opts(**kw):

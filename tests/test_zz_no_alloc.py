@@ -33,24 +33,32 @@ def dev(a):
     return None if a is None else torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-def reference(gw, p):
+def reference(gw, p, spacing=(1.0, 1.0, 1.0)):
     n = p["nx"] * p["ny"] * p["nz"]
     b = torch.empty(n, dtype=torch.float64, device="cuda")
     A, _ = gw.gw_assemble(p["nx"], p["ny"], p["nz"], dev(p["Kx"]), dev(p["Ky"]), dev(p["Kz"]), p["bct"], p["bcv"],
-                          dev(p["q"]), b_out=b)
+                          dev(p["q"]), b_out=b, spacing=spacing)
     rp, ci, v = A.export()
     return rp, ci, v, b.cpu().numpy()
 
 
-def no_alloc(gw, p):
+def no_alloc(gw, p, spacing=(1.0, 1.0, 1.0), stream=None):
+    """Calls the allocation-free entry point into fresh output arrays and
+    checks that the library made no device allocation meanwhile."""
     n = p["nx"] * p["ny"] * p["nz"]
     nnz = 7 * n - 2 * (p["ny"] * p["nz"] + p["nx"] * p["nz"] + p["nx"] * p["ny"])
     rp = torch.full((n + 1,), -1, dtype=torch.int32, device="cuda")
     ci = torch.full((nnz,), -1, dtype=torch.int32, device="cuda")
     v = torch.full((nnz,), np.nan, dtype=torch.float64, device="cuda")
     b = torch.full((n,), np.nan, dtype=torch.float64, device="cuda")
-    gw.gw_assemble_noalloc(p["nx"], p["ny"], p["nz"], dev(p["Kx"]), rp, ci, v, b, Ky=dev(p["Ky"]), Kz=dev(p["Kz"]),
-                           bct=p["bct"], bcv=p["bcv"], q=dev(p["q"]))
+    Kx, Ky, Kz, q = dev(p["Kx"]), dev(p["Ky"]), dev(p["Kz"]), dev(p["q"])
+    torch.cuda.synchronize()
+    before = gw.gw_device_allocations()
+    try:
+        gw.gw_assemble_noalloc(p["nx"], p["ny"], p["nz"], Kx, rp, ci, v, b, Ky=Ky, Kz=Kz, bct=p["bct"],
+                               bcv=p["bcv"], q=q, spacing=spacing, stream=stream)
+    finally:
+        assert gw.gw_device_allocations() == before, "the allocation-free assembly allocated device memory"
     torch.cuda.synchronize()
     return rp.cpu().numpy(), ci.cpu().numpy(), v.cpu().numpy(), b.cpu().numpy()
 
@@ -72,6 +80,50 @@ def test_no_alloc_matches_gw_assemble_on_consecutive_calls(gw):
     same(no_alloc(gw, p1), r1)
     same(no_alloc(gw, p2), r2)
     same(no_alloc(gw, p1), r1)
+
+
+def test_no_alloc_degenerate_axis_shared_conductivity_and_spacing(gw):
+    # a 2D grid (nz = 1, where the nonzero count formula is tightest), no
+    # sources, Ky and Kz left to default to Kx, and unequal cell sizes
+    p = wl.problem(31, 17, 1, var=3.0, corr=3.0, seed=11)
+    p = dict(p, q=None, Ky=None, Kz=None, bct=(1, 1, 1, 0, 0, 0), bcv=(1.0, 0.0, 0.5, 0, 0, 0))
+    for spacing in ((1.0, 1.0, 1.0), (1.0, 2.0, 0.5)):
+        r = reference(gw, p, spacing)
+        same(no_alloc(gw, p, spacing), r)
+        same(no_alloc(gw, p, spacing), r)
+
+
+def test_no_alloc_on_a_caller_stream(gw):
+    p = wl.problem(20, 12, 6, var=2.0, corr=2.0, seed=13, wells_count=2, wells_seed=3)
+    r = reference(gw, p)
+    s = torch.cuda.Stream()
+    same(no_alloc(gw, p, stream=s), r)
+    same(no_alloc(gw, p, stream=s), r)
+
+
+def test_no_alloc_refuses_a_capturing_stream(gw):
+    p = wl.problem(8, 8, 4, var=1.0, corr=2.0, seed=3)
+    n = 8 * 8 * 4
+    nnz = 7 * n - 2 * (8 * 4 + 8 * 4 + 8 * 8)
+    K = dev(p["Kx"])
+    rp = torch.zeros(n + 1, dtype=torch.int32, device="cuda")
+    ci = torch.zeros(nnz, dtype=torch.int32, device="cuda")
+    v = torch.zeros(nnz, dtype=torch.float64, device="cuda")
+    b = torch.zeros(n, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    status = None
+    with torch.cuda.stream(s):
+        g.capture_begin(capture_error_mode="thread_local")
+        try:
+            gw.gw_assemble_noalloc(8, 8, 4, K, rp, ci, v, b, stream=s)
+        except gw.GwError as e:
+            status = e.status
+        finally:
+            g.capture_end()
+    assert status == gw.GW_ERR_ARG
+    same(no_alloc(gw, p), reference(gw, p))
 
 
 def test_no_alloc_after_a_rejected_call(gw):

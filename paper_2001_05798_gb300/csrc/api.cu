@@ -61,6 +61,7 @@ Hier::~Hier()
     drop_graphs(*this);
     block_free(blk);
     if (cap) cudaStreamDestroy(cap);
+    if (cap2) cudaStreamDestroy(cap2);
     if (ctl_host) host_free(ctl_host);
 }
 

@@ -676,8 +676,7 @@ __device__ __forceinline__ void cg_rz_epilogue(double lrz, double lqz, double *p
             const double beta = c->flexible ? -c->alpha * tot[1] / c->rz : rz_new / c->rz;
             c->beta = beta;
             if (!isfinite(beta) || !isfinite(rz_new)) {
-                c->status = GW_ERR_BREAKDOWN;
-                c->done = 1;
+                ctl_stop(c, GW_ERR_BREAKDOWN);
             }
         }
         c->rz = rz_new;
@@ -969,8 +968,11 @@ __global__ void __launch_bounds__(BS) k_restrict_u(PImpl P, const float *__restr
 }
 
 // r_c = sum of u over the members of aggregate c: four lanes per aggregate,
-// lane g adding members g, g + 4, ... in order, then a fixed shuffle tree
-constexpr int RS_LANES = 4;
+// lane g adding members g, g + 4, ... in order, then a fixed shuffle tree.
+// A lane takes its members RS_CHUNK at a time: the member indices first, then
+// the gathered u values, then the additions in order, so that the loads of a
+// chunk are in flight together instead of one dependent pair per member.
+constexpr int RS_LANES = 4, RS_CHUNK = 4;
 __global__ void __launch_bounds__(BS) k_restrict_sum(int nc, const int *__restrict__ mptr, const int *__restrict__ mem,
                                                      const float *__restrict__ u, float *__restrict__ rc,
                                                      const Ctl *ctl)
@@ -983,7 +985,17 @@ __global__ void __launch_bounds__(BS) k_restrict_sum(int nc, const int *__restri
         float acc = 0.f;
         if (c < nc) {
             const int e1 = __ldg(mptr + c + 1);
-            for (int e = __ldg(mptr + c) + g; e < e1; e += RS_LANES) acc += __ldg(u + __ldg(mem + e));
+            for (int e = __ldg(mptr + c) + g; e < e1; e += RS_LANES * RS_CHUNK) {
+                int m[RS_CHUNK];
+                float v[RS_CHUNK];
+#pragma unroll
+                for (int k = 0; k < RS_CHUNK; ++k) m[k] = e + k * RS_LANES < e1 ? __ldg(mem + e + k * RS_LANES) : -1;
+#pragma unroll
+                for (int k = 0; k < RS_CHUNK; ++k) v[k] = m[k] >= 0 ? __ldg(u + m[k]) : 0.f;
+#pragma unroll
+                for (int k = 0; k < RS_CHUNK; ++k)
+                    if (m[k] >= 0) acc += v[k];
+            }
         }
 #pragma unroll
         for (int off = RS_LANES / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off, RS_LANES);
@@ -1511,10 +1523,12 @@ __global__ void __launch_bounds__(BS) k_cg_init(int n, const double *__restrict_
         c->it = 0;
         c->check = 0;
         const bool fin = isfinite(tot[0]);  // false: b has a non-finite entry
-        c->status = fin ? GW_OK : GW_ERR_ARG;
+        c->status = GW_OK;
+        c->done = 0;
         c->rz = c->pq = c->alpha = c->beta = c->rr = c->rt2 = c->qz = 0.0;
         c->relres = fin ? (tot[0] > 0.0 ? 1.0 : 0.0) : tot[0];
-        c->done = (fin && tot[0] > 0.0) ? 0 : 1;
+        if (!fin) ctl_stop(c, GW_ERR_ARG);
+        else if (!(tot[0] > 0.0)) ctl_stop(c, GW_OK);
     }
 }
 
@@ -1537,8 +1551,7 @@ __global__ void __launch_bounds__(BS) k_cg_spmv_dot(M A, int n, const typename M
     if (finished(c)) return;
     if (c->it >= c->maxit) {
         if (blockIdx.x == 0 && threadIdx.x == 0) {
-            c->status = GW_ERR_NOT_CONVERGED;
-            c->done = 1;
+            ctl_stop(c, GW_ERR_NOT_CONVERGED);
         }
         return;
     }
@@ -1560,8 +1573,7 @@ __global__ void __launch_bounds__(BS) k_cg_spmv_dot(M A, int n, const typename M
         c->pq = pq;
         c->it += 1;
         if (!(pq > 0.0) || !isfinite(pq)) {
-            c->status = GW_ERR_BREAKDOWN;
-            c->done = 1;
+            ctl_stop(c, GW_ERR_BREAKDOWN);
         } else {
             c->alpha = c->rz / pq;
         }
@@ -1570,21 +1582,24 @@ __global__ void __launch_bounds__(BS) k_cg_spmv_dot(M A, int n, const typename M
 
 // The direction update fused into the product: p_new = z + beta p_old (formed
 // where gathered, stored for the own rows), q = A p_new, pq = (p_new, q),
-// alpha = rz / pq.  p_old and p_new are distinct buffers.
+// alpha = rz / pq.  The direction lives in two buffers that swap roles every
+// iteration: p_old is pa in even iterations (c->it even at the start) and pb
+// in odd ones, p_new the other one.
 template <class M>
 __global__ void __launch_bounds__(BS) k_cg_dir_spmv(M A, int n, const typename M::value_type *__restrict__ z,
-                                                    const typename M::value_type *__restrict__ pold,
-                                                    typename M::value_type *__restrict__ pnew,
+                                                    typename M::value_type *pa, typename M::value_type *pb,
                                                     typename M::value_type *__restrict__ q, double *part, Ctl *c)
 {
     using V = typename M::value_type;
     constexpr int R = M::R;
     pdl_enter();
     if (finished(c)) return;
+    const int odd = c->it & 1;
+    const V *__restrict__ pold = odd ? pb : pa;
+    V *__restrict__ pnew = odd ? pa : pb;
     if (c->it >= c->maxit) {
         if (blockIdx.x == 0 && threadIdx.x == 0) {
-            c->status = GW_ERR_NOT_CONVERGED;
-            c->done = 1;
+            ctl_stop(c, GW_ERR_NOT_CONVERGED);
         }
         return;
     }
@@ -1608,8 +1623,7 @@ __global__ void __launch_bounds__(BS) k_cg_dir_spmv(M A, int n, const typename M
         c->pq = pq;
         c->it += 1;
         if (!(pq > 0.0) || !isfinite(pq)) {
-            c->status = GW_ERR_BREAKDOWN;
-            c->done = 1;
+            ctl_stop(c, GW_ERR_BREAKDOWN);
         } else {
             c->alpha = c->rz / pq;
         }
@@ -1618,14 +1632,16 @@ __global__ void __launch_bounds__(BS) k_cg_dir_spmv(M A, int n, const typename M
 
 // x += alpha p; r -= alpha q; rr = (r, r).  Sets check when r passes the
 // stopping test, or (mixed form) when it fell below delta times the residual
-// of the last reliable update.
+// of the last reliable update.  With pb, p is the new direction of the two
+// alternating buffers (pb after an even iteration, pa after an odd one).
 template <class V, int R>
-__global__ void __launch_bounds__(BS) k_cg_update(int n, V *__restrict__ x, V *__restrict__ r,
-                                                  const V *__restrict__ p, const V *__restrict__ q, double *part,
-                                                  Ctl *c, int reliable)
+__global__ void __launch_bounds__(BS) k_cg_update(int n, V *__restrict__ x, V *__restrict__ r, const V *pa,
+                                                  const V *pb, const V *__restrict__ q, double *part, Ctl *c,
+                                                  int reliable)
 {
     pdl_enter();
     if (finished(c)) return;
+    const V *__restrict__ p = (pb && !((c->it - 1) & 1)) ? pb : pa;
     const V a = (V)c->alpha;
     double loc[1] = {0.0}, tot[1];
     for (int i = R * (blockIdx.x * BS + threadIdx.x); i < n; i += R * gridDim.x * BS) {
@@ -1645,8 +1661,7 @@ __global__ void __launch_bounds__(BS) k_cg_update(int n, V *__restrict__ x, V *_
     if (reduce_last<1>(loc, part, &c->cnt[0], tot) && threadIdx.x == 0) {
         c->rr = tot[0];
         if (!isfinite(tot[0])) {
-            c->status = GW_ERR_BREAKDOWN;
-            c->done = 1;
+            ctl_stop(c, GW_ERR_BREAKDOWN);
         } else if (tot[0] <= c->tol2 * c->bnorm2 || (reliable && tot[0] <= c->delta2 * c->rmax2)) {
             c->check = 1;
         }
@@ -1683,8 +1698,7 @@ __global__ void __launch_bounds__(BS) k_cg_true(M A, int n, const double *__rest
             c->relres = rel;
         } else if (tot[0] <= c->tol2 * c->bnorm2) {
             c->relres = rel;
-            c->status = GW_OK;
-            c->done = 1;
+            ctl_stop(c, GW_OK);
         } else {
             c->check = 0;
         }
@@ -1743,8 +1757,7 @@ __global__ void __launch_bounds__(BS) k_rel_res(M A, int n, const double *__rest
         c->relres = rel;
         if (!force) {
             if (tot[0] <= c->tol2 * c->bnorm2) {
-                c->status = GW_OK;
-                c->done = 1;
+                ctl_stop(c, GW_OK);
             } else {
                 c->rmax2 = tot[0];
                 c->check = 0;
@@ -1772,13 +1785,15 @@ __global__ void __launch_bounds__(BS) k_cg_p(int n, const V *__restrict__ z, V *
 // ------------------------------------------------------------------ CG loop --
 static const MatStore<double> &fine64(Hier &H) { return H.o.prec == GW_PREC_FP64 ? H.cd[0].A : H.A64; }
 
+// pb: p is the new one of the two alternating direction buffers (pa, pb)
 template <class V>
-static void cg_vec_update(Hier &H, V *x, V *r, const V *p, const V *q, int reliable, cudaStream_t st)
+static void cg_vec_update(Hier &H, V *x, V *r, const V *pa, const V *pb, const V *q, int reliable, cudaStream_t st)
 {
     const int n = H.n;
     constexpr int R = 16 / sizeof(V);
-    if (n % R == 0) launch_pdl(k_cg_update<V, R>, vgrid(H, n / R), st, n, x, r, p, q, H.part.p, H.ctl.p, reliable);
-    else launch_pdl(k_cg_update<V, 1>, vgrid(H, n), st, n, x, r, p, q, H.part.p, H.ctl.p, reliable);
+    if (n % R == 0)
+        launch_pdl(k_cg_update<V, R>, vgrid(H, n / R), st, n, x, r, pa, pb, q, H.part.p, H.ctl.p, reliable);
+    else launch_pdl(k_cg_update<V, 1>, vgrid(H, n), st, n, x, r, pa, pb, q, H.part.p, H.ctl.p, reliable);
 }
 
 template <class V>
@@ -1824,7 +1839,7 @@ static void cg_iteration(Hier &H, int parity, cudaStream_t st)
         });
         timed(H, GW_PK_UPDATE, st, [&] {
             H.prof_bytes += vbytes(H, 48.0 * dn);
-            cg_vec_update<double>(H, H.x.p, H.r.p, H.p.p, H.q.p, 0, st);
+            cg_vec_update<double>(H, H.x.p, H.r.p, H.p.p, (const double *)nullptr, H.q.p, 0, st);
         });
         with_mat(A64, [&](auto A) {
             using M = decltype(A);
@@ -1839,25 +1854,27 @@ static void cg_iteration(Hier &H, int parity, cudaStream_t st)
         return;
     }
     const MatStore<float> &A32 = cg_op32(H);
-    float *pold = parity ? H.p32b.p : H.p32.p, *pnew = parity ? H.p32.p : H.p32b.p;
+    (void)parity;
     timed(H, GW_PK_SPMV, st, [&] {
         H.prof_bytes += vbytes(H, mat_bytes(A32) + 20.0 * dn);
         with_mat(A32, [&](auto A) {
             using M = decltype(A);
-            launch_pdl(k_cg_dir_spmv<M>, grid_for<M>(H, n), st, A, n, (const float *)H.z32.p,
-                       (const float *)pold, pnew, H.q32.p, H.part.p, c);
+            launch_pdl(k_cg_dir_spmv<M>, grid_for<M>(H, n), st, A, n, (const float *)H.z32.p, H.p32.p, H.p32b.p,
+                       H.q32.p, H.part.p, c);
         });
     });
     timed(H, GW_PK_UPDATE, st, [&] {
         H.prof_bytes += vbytes(H, 24.0 * dn);
-        cg_vec_update<float>(H, H.xs32.p, H.r32.p, pnew, H.q32.p, 1, st);
+        cg_vec_update<float>(H, H.xs32.p, H.r32.p, H.p32.p, H.p32b.p, H.q32.p, 1, st);
     });
     rel_update(H, 0, st);
     vcycle_t<float>(H, H.cf, H.r32.p, H.z32.p, c, H.q32.p, 1, st);
     GW_LAUNCH_CHECK();
 }
 
-static constexpr int GRAPH_ITERS = 4;  // even: the direction buffers alternate
+// Iterations per replay of the profiled iteration graph (events cannot sit
+// inside a while node's body, so the profiled solve keeps host-polled replays)
+static constexpr int GRAPH_ITERS = 4;
 
 static size_t kernel_nodes(cudaGraph_t g)
 {
@@ -1898,12 +1915,71 @@ static cudaGraphExec_t capture(Hier &H, F body, long long *nkernels)
     return ex;
 }
 
+// The whole solve as one graph: the start (b -> r, the first V-cycle), then a
+// while node whose body is one CG iteration.  The loop's condition starts at
+// 1 on every launch; the kernel that finishes the solve (converged, maxit,
+// breakdown) sets it to 0 through the handle kept in the control block.
+// init_kernels / iter_kernels receive the kernels of the start and of the body.
+template <class FI, class FB>
+static cudaGraphExec_t capture_loop(Hier &H, FI init, FB iteration, unsigned long long *handle)
+{
+    if (!H.cap) GW_CUDA(cudaStreamCreateWithFlags(&H.cap, cudaStreamNonBlocking));
+    if (!H.cap2) GW_CUDA(cudaStreamCreateWithFlags(&H.cap2, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr, body = nullptr;
+    CaptureScope scope;
+    GW_CUDA(cudaStreamBeginCapture(H.cap, cudaStreamCaptureModeThreadLocal));
+    bool body_open = false;
+    try {
+        init(H.cap);
+        cudaStreamCaptureStatus cs;
+        cudaGraph_t cg = nullptr;
+        const cudaGraphNode_t *deps = nullptr;
+        size_t ndeps = 0;
+        GW_CUDA(cudaStreamGetCaptureInfo(H.cap, &cs, nullptr, &cg, &deps, nullptr, &ndeps));
+        cudaGraphConditionalHandle h = 0;
+        GW_CUDA(cudaGraphConditionalHandleCreate(&h, cg, 1u, cudaGraphCondAssignDefault));
+        cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t loop = nullptr;
+        GW_CUDA(cudaGraphAddNode(&loop, cg, deps, nullptr, ndeps, &np));
+        body = np.conditional.phGraph_out[0];
+        GW_CUDA(cudaStreamUpdateCaptureDependencies(H.cap, &loop, nullptr, 1, cudaStreamSetCaptureDependencies));
+        GW_CUDA(cudaStreamBeginCaptureToGraph(H.cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        body_open = true;
+        iteration(H.cap2);
+        body_open = false;
+        cudaGraph_t bout = nullptr;
+        GW_CUDA(cudaStreamEndCapture(H.cap2, &bout));
+        *handle = (unsigned long long)h;
+    } catch (...) {
+        cudaGraph_t t = nullptr;
+        if (body_open) cudaStreamEndCapture(H.cap2, &t);
+        cudaStreamEndCapture(H.cap, &g);
+        if (g) cudaGraphDestroy(g);
+        throw;
+    }
+    GW_CUDA(cudaStreamEndCapture(H.cap, &g));
+    cudaGraphExec_t ex = nullptr;
+    cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+    if (e == cudaSuccess) {
+        H.iter_kernels = (long long)kernel_nodes(body);
+        H.init_kernels = (long long)kernel_nodes(g);  // the while node is not a kernel node
+    }
+    cudaGraphDestroy(g);
+    GW_CUDA(e);
+    return ex;
+}
+
 void drop_graphs(Hier &H)
 {
     block_drop_graphs(H.blk);
     if (H.gexec) cudaGraphExecDestroy(H.gexec);
     if (H.ginit) cudaGraphExecDestroy(H.ginit);
-    H.gexec = H.ginit = nullptr;
+    if (H.gsolve) cudaGraphExecDestroy(H.gsolve);
+    H.gexec = H.ginit = H.gsolve = nullptr;
+    H.cond = 0;
     for (auto &m : H.marks) {
         cudaEventDestroy(m.a);
         cudaEventDestroy(m.b);
@@ -1911,33 +1987,45 @@ void drop_graphs(Hier &H)
     H.marks.clear();
 }
 
+// the start of a solve: x = 0, r = b, the first V-cycle, p = z (FP64 form)
+static void cg_start(Hier &H, cudaStream_t s)
+{
+    const int n = H.n, g = vgrid(H, n);
+    if (H.o.prec == GW_PREC_FP64) {
+        launch_pdl(k_cg_init<double>, g, s, n, (const double *)H.b.p, H.x.p, (double *)nullptr, H.r.p, H.p.p,
+                   H.p2.p, H.part.p, H.ctl.p);
+        vcycle_t<double>(H, H.cd, H.r.p, H.z.p, H.ctl.p, nullptr, 0, s);
+        launch_pdl(k_copy<double>, g, s, n, (const double *)H.z.p, H.p.p, H.ctl.p);
+    } else {
+        launch_pdl(k_cg_init<float>, g, s, n, (const double *)H.b.p, H.x.p, H.xs32.p, H.r32.p, H.p32.p, H.p32b.p,
+                   H.part.p, H.ctl.p);
+        vcycle_t<float>(H, H.cf, H.r32.p, H.z32.p, H.ctl.p, nullptr, 0, s);
+    }
+    GW_LAUNCH_CHECK();
+}
+
 static void ensure_graphs(Hier &H)
 {
-    if (H.gexec && H.ginit) return;
+    if (H.prof_on) {
+        if (H.gexec && H.ginit) return;
+        drop_graphs(H);
+        H.ginit = capture(H, [&](cudaStream_t s) { cg_start(H, s); }, &H.init_kernels);
+        H.prof_capture = true;
+        H.gexec = capture(H, [&](cudaStream_t s) {
+            for (int k = 0; k < GRAPH_ITERS; ++k) {
+                H.cap_iter = k;
+                cg_iteration(H, k & 1, s);
+            }
+        }, &H.iter_kernels);
+        H.prof_capture = false;
+        H.graph_iters = GRAPH_ITERS;
+        return;
+    }
+    if (H.gsolve) return;
     drop_graphs(H);
-    const int n = H.n, g = vgrid(H, n);
-    H.ginit = capture(H, [&](cudaStream_t s) {
-        if (H.o.prec == GW_PREC_FP64) {
-            launch_pdl(k_cg_init<double>, g, s, n, (const double *)H.b.p, H.x.p, (double *)nullptr, H.r.p, H.p.p,
-                       H.p2.p, H.part.p, H.ctl.p);
-            vcycle_t<double>(H, H.cd, H.r.p, H.z.p, H.ctl.p, nullptr, 0, s);
-            launch_pdl(k_copy<double>, g, s, n, (const double *)H.z.p, H.p.p, H.ctl.p);
-        } else {
-            launch_pdl(k_cg_init<float>, g, s, n, (const double *)H.b.p, H.x.p, H.xs32.p, H.r32.p, H.p32.p,
-                       H.p32b.p, H.part.p, H.ctl.p);
-            vcycle_t<float>(H, H.cf, H.r32.p, H.z32.p, H.ctl.p, nullptr, 0, s);
-        }
-        GW_LAUNCH_CHECK();
-    }, &H.init_kernels);
-    H.prof_capture = H.prof_on;
-    H.gexec = capture(H, [&](cudaStream_t s) {
-        for (int k = 0; k < GRAPH_ITERS; ++k) {
-            H.cap_iter = k;
-            cg_iteration(H, k & 1, s);
-        }
-    }, &H.iter_kernels);
-    H.prof_capture = false;
-    H.graph_iters = GRAPH_ITERS;
+    H.gsolve = capture_loop(H, [&](cudaStream_t s) { cg_start(H, s); },
+                            [&](cudaStream_t s) { cg_iteration(H, 0, s); }, &H.cond);
+    H.graph_iters = 1;
 }
 
 // accumulate the profiled level-0 kernel times of one replay of the iteration
@@ -1971,18 +2059,27 @@ int pcg_run(Hier &H, double tol, int maxit, int *iters, double *relres, cudaStre
     init.maxit = maxit;
     init.flexible = H.o.prec == GW_PREC_FP64 ? 0 : 1;
     init.delta2 = H.o.delta * H.o.delta;
+    init.cond = H.gsolve ? H.cond : 0ULL;
     *H.ctl_host = init;
     GW_CUDA(cudaMemcpyAsync(c, H.ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, st));
-    GW_CUDA(cudaGraphLaunch(H.ginit, st));
-    H.launches += H.init_kernels;
-    const int max_launches = (maxit + GRAPH_ITERS - 1) / GRAPH_ITERS + 2;
-    for (int k = 0; k < max_launches; ++k) {
-        GW_CUDA(cudaGraphLaunch(H.gexec, st));
-        H.launches += H.iter_kernels;
+    if (H.gsolve) {
+        // one launch runs the solve to its stop
+        GW_CUDA(cudaGraphLaunch(H.gsolve, st));
         GW_CUDA(cudaMemcpyAsync(H.ctl_host, c, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
         GW_CUDA(cudaStreamSynchronize(st));
-        if (H.prof_on && !H.marks.empty()) collect_marks(H, k * GRAPH_ITERS + 1, H.ctl_host->it, H.ctl_host->done);
-        if (H.ctl_host->done) break;
+        H.launches += H.init_kernels + (long long)std::max(1, H.ctl_host->it) * H.iter_kernels;
+    } else {
+        GW_CUDA(cudaGraphLaunch(H.ginit, st));
+        H.launches += H.init_kernels;
+        const int max_launches = (maxit + GRAPH_ITERS - 1) / GRAPH_ITERS + 2;
+        for (int k = 0; k < max_launches; ++k) {
+            GW_CUDA(cudaGraphLaunch(H.gexec, st));
+            H.launches += H.iter_kernels;
+            GW_CUDA(cudaMemcpyAsync(H.ctl_host, c, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+            GW_CUDA(cudaStreamSynchronize(st));
+            if (!H.marks.empty()) collect_marks(H, k * GRAPH_ITERS + 1, H.ctl_host->it, H.ctl_host->done);
+            if (H.ctl_host->done) break;
+        }
     }
     if (H.ctl_host->status == GW_ERR_NOT_CONVERGED || !H.ctl_host->done) {
         if (H.o.prec == GW_PREC_FP64) {

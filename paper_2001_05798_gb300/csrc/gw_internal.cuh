@@ -234,6 +234,9 @@ struct Ctl {
     double rz, pq, alpha, beta, rr, rt2, relres, qz, rmax2, delta2;
     int it, maxit, done, status, check, flexible;
     unsigned int cnt[8];  // arrival counters of the last-block reductions
+    // handle of the while node of the solve's graph (0 when the solve does
+    // not run under one): the kernel that finishes the solve sets it to 0
+    unsigned long long cond;
 };
 
 constexpr int RED_MAX_BLOCKS = 4096;
@@ -354,8 +357,12 @@ struct Hier {
     DBuf<float> xs32, r32, p32, p32b, q32, z32;  // mixed form: FP32 recurrence (two direction buffers)
     DBuf<Ctl> ctl;
     Ctl *ctl_host = nullptr;   // pinned mirror of the control block
-    cudaStream_t cap = nullptr;
-    cudaGraphExec_t gexec = nullptr, ginit = nullptr;
+    cudaStream_t cap = nullptr, cap2 = nullptr;
+    // gsolve: the whole solve (start + while node over one CG iteration);
+    // ginit + gexec: the profiled form (start, then replays of GRAPH_ITERS
+    // iterations polled by the host)
+    cudaGraphExec_t gexec = nullptr, ginit = nullptr, gsolve = nullptr;
+    unsigned long long cond = 0;  // the while node's conditional handle
     int graph_iters = 0;
     long long init_kernels = 0, iter_kernels = 0;
     // profiling of the level-0 kernels (events captured into the graph)

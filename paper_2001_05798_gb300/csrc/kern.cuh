@@ -135,4 +135,14 @@ __device__ __forceinline__ bool reduce_last(const double (&loc)[K], double *part
 
 __device__ __forceinline__ bool finished(const Ctl *c) { return c && *(volatile const int *)&c->done; }
 
+// Ends the solve with the given status; under a graph while node also ends
+// the loop (one thread of one kernel calls this, so the condition is never
+// set concurrently).
+__device__ __forceinline__ void ctl_stop(Ctl *c, int status)
+{
+    c->status = status;
+    c->done = 1;
+    if (c->cond) cudaGraphSetConditional((cudaGraphConditionalHandle)c->cond, 0u);
+}
+
 }  // namespace gw

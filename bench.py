@@ -639,7 +639,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the all-FP64 arm (profiling runs)")
     ap.add_argument("--delta", type=float, default=0.1, help="reliable-update factor of the mixed form")
-    ap.add_argument("--half-storage", type=int, default=0, help="FP16 storage of P, R and coarse operators (mixed)")
+    ap.add_argument("--half-storage", type=int, default=0,
+                    help="half-precision fine stencil of the mixed form: 2 = BF16 couplings, 4 = scaled FP16")
     ap.add_argument("--side", type=int, default=SIDE, help="grid side for profiling captures (default 128)")
     ap.add_argument("--requests", type=int, default=2000, help="serving workload: number of requests")
     ap.add_argument("--slots", type=int, default=6, help="serving workload: solves in flight")

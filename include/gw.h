@@ -85,7 +85,7 @@ typedef enum {
 enum { GW_SMOOTH_JACOBI = 0, GW_SMOOTH_CHEBYSHEV = 1 };
 
 /* Bits of gw_amg_opts.half_storage. */
-enum { GW_HALF_TRANSFER = 1, GW_HALF_FINE = 2, GW_HALF_FINE16 = 4 };
+enum { GW_HALF_FINE = 2, GW_HALF_FINE16 = 4 };
 
 /* Setup and cycle options (gw_amg_opts_default fills the defaults). */
 typedef struct {
@@ -99,8 +99,6 @@ typedef struct {
     int prec;            /* gw_prec (GW_PREC_MIXED32) */
     double delta;        /* mixed form: reliable update when the FP32 residual fell by this factor (0.1) */
     int half_storage;    /* mixed form, bit mask (0):
-                            GW_HALF_TRANSFER: P, R and the coarse operators as FP16 values with
-                              16-bit column offsets, coarse operators scaled to D^-1/2 A D^-1/2;
                             GW_HALF_FINE: the V-cycle's level-0 stencil with BF16 couplings and an
                               FP32 diagonal corrected so that rows keep their sums (CG's own
                               products stay FP32);
@@ -293,7 +291,7 @@ int gw_hierarchy_prepare(gw_hierarchy H);
  * operator C, e.g. well or boundary scenarios, or forward and adjoint
  * solves.  B and X are n x k, column-major
  * (column c at B + c*n), host or device; iters and relres receive k values
- * (host, may be NULL).  In the mixed form (without GW_HALF_TRANSFER) k >= 2
+ * (host, may be NULL).  In the mixed form k >= 2
  * columns run in interleaved blocks of up to 8 that share every matrix read
  * of the V-cycle and of CG, each column with its own CG scalars, reliable
  * updates and stop; otherwise the columns are solved one after another.

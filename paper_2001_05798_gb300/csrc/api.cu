@@ -144,11 +144,9 @@ static long long store_level(Hier &H, int k, const DCSR &A, const DCSR *P, const
         bytes += (long long)(c.A.bytes() + c.P.bytes() + c.R.bytes() + c.dw.bytes());
     } else {
         CycLevel<float> &c = H.cf[(size_t)k];
-        const bool h16 = (o.half_storage & GW_HALF_TRANSFER) != 0;
         const bool fine16 = k == 0 && (o.half_storage & GW_HALF_FINE) != 0;
         const bool fineh = k == 0 && (o.half_storage & GW_HALF_FINE16) != 0;
-        auto f32 = [h16](int f) { return h16 && f == FMT_SELL ? FMT_SELL16 : f; };
-        to_store<float>(A, c.A, k == 0 ? (fine16 ? FMT_STENB : fineh ? FMT_STENH : FMT_STEN) : f32(choose_fmt(A)),
+        to_store<float>(A, c.A, k == 0 ? (fine16 ? FMT_STENB : fineh ? FMT_STENH : FMT_STEN) : choose_fmt(A),
                         H.gnx, H.gny, H.gnz,
                         st);
         if (k == 0) {
@@ -158,9 +156,9 @@ static long long store_level(Hier &H, int k, const DCSR &A, const DCSR *P, const
                 bytes += (long long)H.A32.bytes();
             }
         }
-        if (P && !(k == 0 && H.p0.n)) to_store<float>(*P, c.P, f32(choose_fmt(*P)), 0, 0, 0, st);
+        if (P && !(k == 0 && H.p0.n)) to_store<float>(*P, c.P, choose_fmt(*P), 0, 0, 0, st);
         if (k == 0 && H.p0.n) bytes += (long long)H.p0.bytes();
-        if (R) to_store<float>(*R, c.R, sorted_sell(f32(choose_fmt(*R))), 0, 0, 0, st);
+        if (R) to_store<float>(*R, c.R, sorted_sell(choose_fmt(*R)), 0, 0, 0, st);
         c.dw.alloc((size_t)n);
         gw_launch(k_make_dw, std::max(g, 1), 256, 0, st, n, diag.p, scale, c.dw.p, nullptr);
         c.c0 = c0;
@@ -489,7 +487,7 @@ int gw_amg_setup(gw_matrix A, const gw_amg_opts *opts, gw_hierarchy *H_out, void
         o.half_storage |= GW_HALF_FINE16;
     }
     if (o.prec != GW_PREC_FP64 && o.prec != GW_PREC_MIXED32) fail(GW_ERR_ARG, "gw_amg_setup: bad precision");
-    if (o.half_storage & ~(GW_HALF_TRANSFER | GW_HALF_FINE | GW_HALF_FINE16))
+    if (o.half_storage & ~(GW_HALF_FINE | GW_HALF_FINE16))
         fail(GW_ERR_ARG, "gw_amg_setup: bad half_storage bits");
     if ((o.half_storage & GW_HALF_FINE) && (o.half_storage & GW_HALF_FINE16))
         fail(GW_ERR_ARG, "gw_amg_setup: the fine stencil is stored either in BF16 or in FP16");

@@ -1222,13 +1222,7 @@ static void block_run(Hier &H, int kk, const double *B, double *X, double tol, i
 bool block_supported(const Hier &H)
 {
     if (H.o.prec != GW_PREC_MIXED32 || H.L < 2) return false;
-    if ((long long)H.n * KB_MAX > 0x7fffffffLL) return false;
-    for (int l = 0; l < H.L; ++l) {
-        const CycLevel<float> &lv = H.cf[l];
-        if (lv.A.fmt == FMT_SELL16 || (l < H.L - 1 && ((lv.P.nr && lv.P.fmt == FMT_SELL16) || lv.R.fmt == FMT_SELL16)))
-            return false;
-    }
-    return H.A64.fmt != FMT_SELL16;
+    return (long long)H.n * KB_MAX <= 0x7fffffffLL;
 }
 
 // k columns in blocks of 8 (a last block of 1-4 columns runs 4 wide)

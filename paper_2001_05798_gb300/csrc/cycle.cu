@@ -527,52 +527,6 @@ struct MStenH {
     }
 };
 
-// Compressed sliced ELL: 8 FP16 values and 8 16-bit column offsets per
-// 16-byte load; scaled square matrices multiply by sd on both sides.
-template <class T>
-struct MSell16 {
-    using value_type = T;
-    static constexpr int G = 1, R = 1;
-    const int *__restrict__ sp;
-    const int *__restrict__ base;
-    const __half *__restrict__ v;
-    const uint16_t *__restrict__ ci;
-    const float *__restrict__ sd;
-    template <class F>
-    __device__ __forceinline__ VecN<T, 1> dot(int r, int, F f) const
-    {
-        const int s = r >> 5, lane = r & 31;
-        const int o0 = sp[s];
-        const int nch = (sp[s + 1] - o0) >> 8;
-        const int b0 = base[s];
-        const int4 *vv = reinterpret_cast<const int4 *>(v + o0) + lane;
-        const int4 *cc = reinterpret_cast<const int4 *>(ci + o0) + lane;
-        T acc = 0;
-        for (int c = 0; c < nch; ++c) {
-            const int4 a = __ldg(vv + c * SELL_C);
-            const int4 j = __ldg(cc + c * SELL_C);
-            const unsigned aw[4] = {(unsigned)a.x, (unsigned)a.y, (unsigned)a.z, (unsigned)a.w};
-            const unsigned jw[4] = {(unsigned)j.x, (unsigned)j.y, (unsigned)j.z, (unsigned)j.w};
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                __half2 h2;
-                memcpy(&h2, &aw[q], sizeof h2);
-                const float2 w = __half22float2(h2);
-                const int c0 = b0 + (int)(jw[q] & 0xffffu), c1 = b0 + (int)(jw[q] >> 16);
-                if (sd) {
-                    acc += (T)w.x * ((T)__ldg(sd + c0) * f(c0));
-                    acc += (T)w.y * ((T)__ldg(sd + c1) * f(c1));
-                } else {
-                    acc += (T)w.x * f(c0);
-                    acc += (T)w.y * f(c1);
-                }
-            }
-        }
-        if (sd) acc *= (T)__ldg(sd + r);
-        return VecN<T, 1>{{acc}};
-    }
-};
-
 // rows per thread of the level-0 stencil: 4 (16 bytes of FP32, 32 bytes of
 // FP64 per array); 8 FP32 rows per thread measured slower (more registers,
 // fewer resident blocks)
@@ -601,9 +555,6 @@ static void with_mat(const MatStore<T> &M, F f)
     case FMT_CSR4: f(MCsr<T, 4>{M.csr.rp.p, M.csr.ci.p, M.csr.v.p, M.csr.nr}); break;
     case FMT_CSR8: f(MCsr<T, 8>{M.csr.rp.p, M.csr.ci.p, M.csr.v.p, M.csr.nr}); break;
     case FMT_CSR32: f(MCsr<T, 32>{M.csr.rp.p, M.csr.ci.p, M.csr.v.p, M.csr.nr}); break;
-    case FMT_SELL16:
-        f(MSell16<T>{M.sell16.sp.p, M.sell16.base.p, M.sell16.v.p, M.sell16.ci.p, M.sell16.sd.p});
-        break;
     case FMT_STENH:
         if constexpr (sizeof(T) == 4) {
             const StenH &S = M.stenh;
@@ -1243,7 +1194,6 @@ static double mat_bytes(const MatStore<T> &M)
     if (M.fmt == FMT_STEN) return 4.0 * M.nr * sizeof(T);
     if (M.fmt == FMT_STENB) return 10.0 * M.nr;
     if (M.fmt == FMT_STENH) return 12.0 * M.nr;
-    if (M.fmt == FMT_SELL16) return (double)M.nnz * 4.0 + (M.sell16.sd.p ? 4.0 * M.nr : 0.0);
     return (double)M.nnz * (sizeof(T) + 4.0);
 }
 

@@ -180,22 +180,7 @@ struct StenH {
     size_t bytes() const { return sd.bytes() + dd.bytes() + ox.bytes() + oy.bytes() + oz.bytes(); }
 };
 
-// Compressed sliced ELL (FP32 cycle only): FP16 values and 16-bit column
-// offsets from a per-slice base column, 8 slots per 16-byte load.  A square
-// level matrix is stored symmetrically scaled, D^-1/2 A D^-1/2 (entries in
-// [-1, 1]), with sd = sqrt(diag) kept in FP32: (A x)_i = sd_i sum_j a^_ij sd_j x_j.
-struct Sell16 {
-    int nr = 0, nc = 0, nslices = 0;
-    long long stored = 0;
-    DBuf<int> sp;        // nslices + 1 slice offsets (slots)
-    DBuf<int> base;      // per-slice base column
-    DBuf<__half> v;
-    DBuf<uint16_t> ci;
-    DBuf<float> sd;      // sqrt of the diagonal (square matrices only)
-    size_t bytes() const { return sp.bytes() + base.bytes() + v.bytes() + ci.bytes() + sd.bytes(); }
-};
-
-enum { FMT_SELL = 0, FMT_CSR4 = 1, FMT_CSR8 = 2, FMT_CSR32 = 3, FMT_STEN = 4, FMT_SELL16 = 5, FMT_STENB = 6,
+enum { FMT_SELL = 0, FMT_CSR4 = 1, FMT_CSR8 = 2, FMT_CSR32 = 3, FMT_STEN = 4, FMT_STENB = 6,
        FMT_STENH = 8 };
 // to_store request: sliced ELL over rows sorted by length within windows of
 // SELL_SORT_WINDOW rows (stored as FMT_SELL with a row permutation); only
@@ -211,17 +196,15 @@ struct MatStore {
     Sell<T> sell;
     CsrT<T> csr;
     StenT<T> sten;
-    Sell16 sell16;
     StenB stenb;
     StenH stenh;
     size_t bytes() const
     {
-        return sell.bytes() + csr.bytes() + sten.bytes() + sell16.bytes() + stenb.bytes() + stenh.bytes();
+        return sell.bytes() + csr.bytes() + sten.bytes() + stenb.bytes() + stenh.bytes();
     }
 };
 
 int choose_fmt(const DCSR &A);
-bool to_sell16(const DCSR &A, Sell16 &S, bool scaled, cudaStream_t st);
 // fmt FMT_STEN needs the grid (nx, ny, nz); returns false if A is not a 7-point grid operator
 template <class T>
 bool to_store(const DCSR &A, MatStore<T> &M, int fmt, int nx, int ny, int nz, cudaStream_t st);

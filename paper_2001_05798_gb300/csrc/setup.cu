@@ -1415,11 +1415,6 @@ bool to_store(const DCSR &A, MatStore<T> &M, int fmt, int nx, int ny, int nz, cu
         fmt = choose_fmt(A);
         M.fmt = fmt;
     }
-    if (fmt == FMT_SELL16) {
-        if (sizeof(T) == 4 && to_sell16(A, M.sell16, A.nr == A.nc, st)) return true;
-        fmt = FMT_SELL;
-        M.fmt = fmt;
-    }
     if (fmt == FMT_SELL) {
         to_sell<T>(A, M.sell, st);
         return true;
@@ -1441,110 +1436,6 @@ bool to_store(const DCSR &A, MatStore<T> &M, int fmt, int nx, int ny, int nz, cu
 }
 
 template bool to_store<float>(const DCSR &, MatStore<float> &, int, int, int, int, cudaStream_t);
-
-// ------------------------------------------------- compressed sliced ELL --
-constexpr int V16 = 8;
-
-__global__ void k_s16_width(int nr, int nslices, const int *__restrict__ rp, const int *__restrict__ ci,
-                            int *__restrict__ width, int *__restrict__ base, int *__restrict__ span_bad)
-{
-    GRID_STRIDE(s, nslices)
-    {
-        int w = 0, lo = 0x7fffffff, hi = -1;
-        for (int l = 0; l < SELL_C; ++l) {
-            const long long r = s * SELL_C + l;
-            if (r >= nr) break;
-            w = max(w, rp[r + 1] - rp[r]);
-            for (int e = rp[r]; e < rp[r + 1]; ++e) {
-                lo = min(lo, ci[e]);
-                hi = max(hi, ci[e]);
-            }
-        }
-        if (hi < 0) lo = hi = 0;
-        if (hi - lo > 65535) atomicOr(span_bad, 1);
-        base[s] = lo;
-        width[s] = (w + V16 - 1) / V16 * V16 * SELL_C;
-    }
-}
-
-// value of entry e of row r: a_rc / (sd_r sd_c) for a scaled square matrix
-__global__ void k_s16_fill(int nr, int nslices, const int *__restrict__ rp, const int *__restrict__ ci,
-                           const double *__restrict__ v, const double *__restrict__ sdiag, const int *__restrict__ sp,
-                           const int *__restrict__ base, __half *__restrict__ sv, uint16_t *__restrict__ sc)
-{
-    GRID_STRIDE(rr, (long long)nslices * SELL_C)
-    {
-        const int r = (int)rr, s = r / SELL_C, lane = r % SELL_C;
-        const int o0 = sp[s], w = (sp[s + 1] - o0) / SELL_C, b0 = base[s];
-        const int b = r < nr ? rp[r] : 0, len = r < nr ? rp[r + 1] - b : 0;
-        for (int k = 0; k < w; ++k) {
-            const size_t o = (size_t)o0 + (size_t)(k / V16) * SELL_C * V16 + (size_t)lane * V16 + (k % V16);
-            if (k < len) {
-                const int c = ci[b + k];
-                double a = v[b + k];
-                if (sdiag) a = a / (sdiag[r] * sdiag[c]);
-                sv[o] = __float2half_rn((float)a);
-                sc[o] = (uint16_t)(c - b0);
-            } else {
-                sv[o] = __float2half_rn(0.0f);
-                sc[o] = 0;
-            }
-        }
-    }
-}
-
-__global__ void k_sqrt_diag(int n, const int *__restrict__ rp, const int *__restrict__ ci,
-                            const double *__restrict__ v, double *__restrict__ sd, float *__restrict__ sdf,
-                            int *__restrict__ bad)
-{
-    GRID_STRIDE(ii, n)
-    {
-        const int i = (int)ii;
-        double d = 0.0;
-        for (int e = rp[i]; e < rp[i + 1]; ++e)
-            if (ci[e] == i) d = v[e];
-        if (!(d > 0.0)) atomicOr(bad, 1);
-        const double s = sqrt(d > 0.0 ? d : 1.0);
-        sd[i] = s;
-        sdf[i] = (float)s;
-    }
-}
-
-// FP16/16-bit-offset sliced ELL; false (nothing kept) if a slice's columns
-// span more than 65535 or a scaled matrix has a non-positive diagonal
-bool to_sell16(const DCSR &A, Sell16 &S, bool scaled, cudaStream_t st)
-{
-    S.nr = A.nr;
-    S.nc = A.nc;
-    S.nslices = (A.nr + SELL_C - 1) / SELL_C;
-    S.sp.alloc((size_t)S.nslices + 1);
-    S.base.alloc((size_t)S.nslices);
-    DBuf<int> bad(1);
-    GW_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
-    gw_launch(k_s16_width, nblk(S.nslices, 256), 256, 0, st, A.nr, S.nslices, A.rp.p, A.ci.p, S.sp.p, S.base.p, bad.p);
-    GW_LAUNCH_CHECK();
-    DBuf<double> sd;
-    if (scaled) {
-        sd.alloc((size_t)A.nr);
-        S.sd.alloc((size_t)A.nr);
-        gw_launch(k_sqrt_diag, nblk(A.nr, 256), 256, 0, st, A.nr, A.rp.p, A.ci.p, A.v.p, sd.p, S.sd.p, bad.p);
-        GW_LAUNCH_CHECK();
-    }
-    if (read_int(bad.p, st)) {
-        S = Sell16();
-        return false;
-    }
-    exclusive_scan(S.sp.p, S.sp.p, S.nslices, st);
-    S.stored = read_int(S.sp.p + S.nslices, st);
-    S.v.alloc((size_t)std::max<long long>(S.stored, 1));
-    S.ci.alloc((size_t)std::max<long long>(S.stored, 1));
-    gw_launch(k_s16_fill, nblk((long long)S.nslices * SELL_C, 256), 256, 0, st, A.nr, S.nslices, A.rp.p, A.ci.p, A.v.p,
-                                                                      scaled ? sd.p : nullptr, S.sp.p, S.base.p,
-                                                                      S.v.p, S.ci.p);
-    GW_LAUNCH_CHECK();
-    GW_CUDA(cudaStreamSynchronize(st));
-    return true;
-}
 template bool to_store<double>(const DCSR &, MatStore<double> &, int, int, int, int, cudaStream_t);
 
 }  // namespace gw

@@ -18,7 +18,7 @@ GW_OK, GW_ERR_ARG, GW_ERR_CUDA, GW_ERR_OOM, GW_ERR_SETUP, GW_ERR_NOT_CONVERGED, 
 GW_NOFLOW, GW_DIRICHLET = 0, 1
 GW_PREC_FP64, GW_PREC_MIXED32, GW_PREC_MIXED16, GW_PREC_MIXEDBF16 = 0, 1, 2, 3
 GW_SMOOTH_JACOBI, GW_SMOOTH_CHEBYSHEV = 0, 1
-GW_HALF_TRANSFER, GW_HALF_FINE, GW_HALF_FINE16 = 1, 2, 4
+GW_HALF_FINE, GW_HALF_FINE16 = 2, 4
 
 EXPORTS = ("gw_amg_opts_default", "gw_assemble", "gw_matrix_size", "gw_matrix_export", "gw_amg_setup",
            "gw_pcg_solve", "gw_vcycle", "gw_hierarchy_info", "gw_hierarchy_export", "gw_matrix_free",

@@ -53,6 +53,9 @@ def test_mis2_round_cap_reports_a_setup_failure(gw, system):
     with pytest.raises(gw.GwError) as e:
         gw.Hierarchy(A, n_coarse=64, mis_max_rounds=-1)
     assert e.value.status == gw.GW_ERR_ARG
+    with pytest.raises(gw.GwError) as e:  # bit 1 (FP16 transfer operators) no longer exists
+        gw.Hierarchy(A, n_coarse=64, half_storage=1)
+    assert e.value.status == gw.GW_ERR_ARG
     # the matrix and the device are still usable: the default cap sets up and solves
     H = gw.Hierarchy(A, n_coarse=64)
     h, it, rel, st = H.solve(b, tol=1e-8)

@@ -170,9 +170,6 @@ def test_vcycle_matches_oracle_fp64(gw):
         H32 = gw.Hierarchy(A, n_coarse=64, prec=1, smoother=smoother)
         H32.vcycle(b, z)
         assert np.linalg.norm(z.cpu().numpy() - zo) <= 1e-5 * np.linalg.norm(zo)
-        H16 = gw.Hierarchy(A, n_coarse=64, prec=1, smoother=smoother, half_storage=1)
-        H16.vcycle(b, z)
-        assert np.linalg.norm(z.cpu().numpy() - zo) <= 5e-3 * np.linalg.norm(zo)
 
 
 def test_config0_closed_form(gw):

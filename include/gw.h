@@ -125,6 +125,7 @@ typedef struct {
 
 typedef struct gw_matrix_s *gw_matrix;
 typedef struct gw_hierarchy_s *gw_hierarchy;
+typedef struct gw_batch_s *gw_batch;
 
 /* Fills *opts with the defaults listed in gw_amg_opts. */
 void gw_amg_opts_default(gw_amg_opts *opts);
@@ -386,6 +387,52 @@ int gw_profile_read(gw_hierarchy H, gw_profile *out, int reset);
 
 void gw_matrix_free(gw_matrix A);
 void gw_hierarchy_free(gw_hierarchy H);
+
+/*
+ * Batched solves -- many flow solves at once, as in the sensitivity-analysis
+ * sweeps the paper names as the use of fast solves (Abstract), each with its
+ * own resident hierarchy (grid size and conductivity field free per solve).
+ * A batch keeps up to max_slots solves in flight.  Every launch of the batched
+ * iteration runs one pass of the AMG-preconditioned CG iteration (the CG
+ * product, the update, the reliable update, or one smoothing, residual,
+ * restriction, coarse-solve or interpolation pass of one level) for every
+ * solve that has it, over a device table of the slots' levels; the iteration
+ * is one captured CUDA graph replayed by gw_batch_run.  A solve gives the same
+ * result bit for bit alone or in any mix (its passes keep their own work
+ * partition and reduction order), and the same iterates as gw_pcg_solve up to
+ * the rounding of its reductions.  Solves join and leave between replays.
+ * Supported hierarchies: the mixed form with FP32 storage (GW_PREC_MIXED32,
+ * half_storage 0), Chebyshev smoothing of degree >= 2 with nu = 1 (the same
+ * degree for every solve of a batch), 2 to 12 levels on a 7-point grid.
+ * Calls on one batch must not overlap (one host thread drives it); the batch
+ * runs on its own CUDA stream.
+ *
+ * gw_batch_create -- an empty batch of max_slots (1..256) slots on the
+ *   current device.  Errors: GW_ERR_ARG, GW_ERR_OOM, GW_ERR_CUDA.
+ * gw_batch_add -- starts the solve of C h = b on hierarchy H (b: n doubles,
+ *   host or device; tol > 0 on the true relative residual, maxit >= 1) in a
+ *   free slot, written to *slot; runs the solve's first V-cycle.  While the
+ *   solve is in the batch, H may not be solved, shifted or prepared
+ *   elsewhere (GW_ERR_ARG); freeing H removes its solve from the batch.
+ *   Errors: GW_ERR_ARG (unsupported hierarchy, no free slot, bad argument),
+ *   GW_ERR_OOM, GW_ERR_CUDA.
+ * gw_batch_run -- replays the batched iteration up to `iterations` times,
+ *   returning after the first replay in which some solve finished; *finished
+ *   receives the number of finished solves waiting to be taken.
+ * gw_batch_state -- *state = 0 (free slot), 1 (solve running) or 2 (finished).
+ * gw_batch_take -- takes the finished solve of a slot: heads into h (n
+ *   doubles, host or device, or NULL), iterations and true relative residual
+ *   (host, may be NULL); frees the slot.  Returns the solve's status (GW_OK,
+ *   GW_ERR_NOT_CONVERGED, GW_ERR_BREAKDOWN, or GW_ERR_ARG for a non-finite
+ *   right-hand side) or GW_ERR_ARG when the slot holds no finished solve.
+ * gw_batch_free -- frees the batch; solves not taken are abandoned.
+ */
+int gw_batch_create(int max_slots, gw_batch *B_out);
+int gw_batch_add(gw_batch B, gw_hierarchy H, const double *b, double tol, int maxit, int *slot);
+int gw_batch_run(gw_batch B, int iterations, int *finished);
+int gw_batch_state(gw_batch B, int slot, int *state);
+int gw_batch_take(gw_batch B, int slot, double *h, int *iters, double *relres);
+void gw_batch_free(gw_batch B);
 
 /* Static string naming a status code. */
 const char *gw_status_str(int status);

@@ -58,6 +58,7 @@ struct DevIn {
 
 Hier::~Hier()
 {
+    if (batch) batch_forget(*static_cast<Batch *>(batch), this);
     drop_graphs(*this);
     block_free(blk);
     if (cap) cudaStreamDestroy(cap);
@@ -514,6 +515,7 @@ int gw_pcg_solve(gw_hierarchy H, const double *b, double *h, double tol, int max
     int status = GW_OK;
     GW_API_BEGIN
     if (!H || !b || !h) fail(GW_ERR_ARG, "gw_pcg_solve: null argument");
+    if (H->h->batch) fail(GW_ERR_ARG, "gw_pcg_solve: the hierarchy's solve is in a batch");
     if (!(tol > 0.0) || !isfinite(tol) || maxit < 1) fail(GW_ERR_ARG, "gw_pcg_solve: need tol > 0 and maxit >= 1");
     Hier &hh = *H->h;
     DeviceGuard g(hh.dev);
@@ -536,6 +538,7 @@ int gw_hierarchy_prepare(gw_hierarchy H)
 {
     GW_API_BEGIN
     if (!H) fail(GW_ERR_ARG, "gw_hierarchy_prepare: null hierarchy");
+    if (H->h->batch) fail(GW_ERR_ARG, "gw_hierarchy_prepare: the hierarchy's solve is in a batch");
     Hier &hh = *H->h;
     DeviceGuard g(hh.dev);
     pcg_prepare(hh);
@@ -548,6 +551,7 @@ int gw_pcg_solve_many(gw_hierarchy H, int k, const double *B, double *X, double 
     int worst = GW_OK;
     GW_API_BEGIN
     if (!H || !B || !X || k < 1) fail(GW_ERR_ARG, "gw_pcg_solve_many: bad argument");
+    if (H->h->batch) fail(GW_ERR_ARG, "gw_pcg_solve_many: the hierarchy's solve is in a batch");
     if (!(tol > 0.0) || !isfinite(tol) || maxit < 1) fail(GW_ERR_ARG, "gw_pcg_solve_many: need tol > 0 and maxit >= 1");
     Hier &hh = *H->h;
     DeviceGuard g(hh.dev);
@@ -583,6 +587,7 @@ int gw_hierarchy_shift(gw_hierarchy H, const double *s, double delta, int *rebui
 {
     GW_API_BEGIN
     if (!H || !H->base) fail(GW_ERR_ARG, "gw_hierarchy_shift: null hierarchy");
+    if (H->h->batch) fail(GW_ERR_ARG, "gw_hierarchy_shift: the hierarchy's solve is in a batch");
     if (!(delta > 0.0 && delta < 1.0)) fail(GW_ERR_ARG, "gw_hierarchy_shift: delta must be in (0, 1)");
     gw_matrix C = H->base;
     DeviceGuard g(C->dev);
@@ -649,6 +654,7 @@ int gw_vcycle(gw_hierarchy H, const double *r, double *z, void *stream)
 {
     GW_API_BEGIN
     if (!H || !r || !z) fail(GW_ERR_ARG, "gw_vcycle: null argument");
+    if (H->h->batch) fail(GW_ERR_ARG, "gw_vcycle: the hierarchy's solve is in a batch");
     if (!is_device_ptr(r) || !is_device_ptr(z)) fail(GW_ERR_ARG, "gw_vcycle: r and z must be device pointers");
     DeviceGuard g(H->h->dev);
     cudaStream_t st = (cudaStream_t)stream;
@@ -746,6 +752,82 @@ void gw_hierarchy_free(gw_hierarchy H)
         delete H;
     } catch (...) {
     }
+}
+
+// ------------------------------------------------------------ batched solves --
+struct gw_batch_s {
+    gw::Batch *b = nullptr;
+    int dev = 0;
+};
+
+int gw_batch_create(int max_slots, gw_batch *B_out)
+{
+    GW_API_BEGIN
+    if (!B_out) fail(GW_ERR_ARG, "gw_batch_create: null argument");
+    *B_out = nullptr;
+    std::unique_ptr<gw_batch_s> B(new gw_batch_s);
+    GW_CUDA(cudaGetDevice(&B->dev));
+    B->b = gw::batch_create(max_slots);
+    *B_out = B.release();
+    GW_API_END
+}
+
+int gw_batch_add(gw_batch B, gw_hierarchy H, const double *b, double tol, int maxit, int *slot)
+{
+    GW_API_BEGIN
+    if (!B || !H || !b) fail(GW_ERR_ARG, "gw_batch_add: null argument");
+    if (!(tol > 0.0) || !isfinite(tol) || maxit < 1) fail(GW_ERR_ARG, "gw_batch_add: need tol > 0 and maxit >= 1");
+    if (H->h->batch) fail(GW_ERR_ARG, "gw_batch_add: the hierarchy's solve is already in a batch");
+    DeviceGuard g(B->dev);
+    const int s = gw::batch_add(*B->b, *H->h, b, tol, maxit);
+    if (slot) *slot = s;
+    GW_API_END
+}
+
+int gw_batch_run(gw_batch B, int iterations, int *finished)
+{
+    GW_API_BEGIN
+    if (!B || iterations < 0) fail(GW_ERR_ARG, "gw_batch_run: bad argument");
+    DeviceGuard g(B->dev);
+    const int f = gw::batch_run(*B->b, iterations);
+    if (finished) *finished = f;
+    GW_API_END
+}
+
+int gw_batch_state(gw_batch B, int slot, int *state)
+{
+    GW_API_BEGIN
+    if (!B || !state) fail(GW_ERR_ARG, "gw_batch_state: null argument");
+    *state = gw::batch_state(*B->b, slot);
+    if (*state < 0) fail(GW_ERR_ARG, "gw_batch_state: no slot %d", slot);
+    GW_API_END
+}
+
+int gw_batch_take(gw_batch B, int slot, double *h, int *iters, double *relres)
+{
+    int status = GW_OK;
+    GW_API_BEGIN
+    if (!B) fail(GW_ERR_ARG, "gw_batch_take: null batch");
+    DeviceGuard g(B->dev);
+    status = gw::batch_take(*B->b, slot, h, iters, relres);
+    if (status != GW_OK) {
+        gw::set_last_error(status == GW_ERR_NOT_CONVERGED ? "gw_batch_take: maxit reached"
+                           : status == GW_ERR_ARG          ? "gw_batch_take: the right-hand side has a non-finite entry"
+                                                           : "gw_batch_take: CG breakdown");
+        return status;
+    }
+    GW_API_END
+}
+
+void gw_batch_free(gw_batch B)
+{
+    if (!B) return;
+    try {
+        DeviceGuard g(B->dev);
+        gw::batch_free(B->b);
+    } catch (...) {
+    }
+    delete B;
 }
 
 }  // extern "C"

@@ -21,6 +21,8 @@
 // trip per iteration.
 #include <string.h>
 
+#include <memory>
+
 #include "gw_internal.cuh"
 #include "kern.cuh"
 
@@ -599,8 +601,8 @@ static void with_mat(const MatStore<T> &M, F f)
 // block starts at or past n does no epilogue.
 #define GROUP_ROWS(M, n)                                                                                  \
     const int lane = M::G == 1 ? 0 : (int)(threadIdx.x & (M::G - 1));                                    \
-    for (int i = (int)((blockIdx.x * (long long)BS + threadIdx.x) / M::G) * M::R,                          \
-             stride_ = gridDim.x * (BS / M::G) * M::R;                                                     \
+    for (int i = (int)((vb.bid * (long long)BS + threadIdx.x) / M::G) * M::R,                             \
+             stride_ = vb.nb * (BS / M::G) * M::R;                                                        \
          M::G == 1 ? (i < (n)) : __any_sync(0xffffffffu, i < (n)); i += stride_)
 
 // blocks asked for by a pass over n rows (launch_pdl fits them to one wave)
@@ -617,11 +619,11 @@ static inline int vgrid(const Hier &, long long n) { return blocks_for(n); }
 // ------------------------------------------------------- V-cycle kernels --
 // Epilogue of the last kernel of a preconditioner application inside CG:
 // rz = (r, z); mode 1 also forms beta (flexible: -alpha (q,z) / rz_old).
-__device__ __forceinline__ void cg_rz_epilogue(double lrz, double lqz, double *part, Ctl *c, int mode)
+__device__ __forceinline__ void cg_rz_epilogue(VB vb, double lrz, double lqz, double *part, Ctl *c, int mode)
 {
     if (!c) return;
     double loc[2] = {lrz, lqz}, tot[2];
-    if (reduce_last<2>(loc, part, &c->cnt[0], tot) && threadIdx.x == 0) {
+    if (reduce_last<2>(vb, loc, part, &c->cnt[0], tot) && threadIdx.x == 0) {
         const double rz_new = tot[0];
         if (mode == 1) {
             const double beta = c->flexible ? -c->alpha * tot[1] / c->rz : rz_new / c->rz;
@@ -655,11 +657,9 @@ __device__ __forceinline__ void dot_rows(int i, const T *b, const OT (&z)[R], co
 
 // x = dw * b ; r = b - A x   (first Jacobi step from zero, fused with the residual)
 template <class M, class BT>
-__global__ void __launch_bounds__(BS) k_jac0_res(M A, int n, const typename M::value_type *__restrict__ dw,
+__device__ __forceinline__ void b_jac0_res(VB vb, M A, int n, const typename M::value_type *__restrict__ dw,
                                                  const BT *__restrict__ b, typename M::value_type *__restrict__ x,
-                                                 typename M::value_type *__restrict__ r, const Ctl *ctl)
-{
-    pdl_enter();
+                                                 typename M::value_type *__restrict__ r, const Ctl *ctl) {
     using T = typename M::value_type;
     constexpr int R = M::R;
     if (finished(ctl)) return;
@@ -681,15 +681,22 @@ __global__ void __launch_bounds__(BS) k_jac0_res(M A, int n, const typename M::v
     }
 }
 
+template <class M, class BT>
+__global__ void __launch_bounds__(BS) k_jac0_res(M A, int n, const typename M::value_type *__restrict__ dw,
+                                                 const BT *__restrict__ b, typename M::value_type *__restrict__ x,
+                                                 typename M::value_type *__restrict__ r, const Ctl *ctl)
+{
+    pdl_enter();
+    b_jac0_res<M, BT>(vb_grid(), A, n, dw, b, x, r, ctl);
+}
+
 // xo = xi + dw * (b - A xi); xi == nullptr means xi = 0.  With DOT, xo is the
 // CG's z (double) and (b, z) [and (q, z)] are reduced.
 template <class M, class BT, class OT, bool DOT>
-__global__ void __launch_bounds__(BS) k_jacobi(M A, int n, const typename M::value_type *__restrict__ dw,
+__device__ __forceinline__ void b_jacobi(VB vb, M A, int n, const typename M::value_type *__restrict__ dw,
                                                const BT *__restrict__ b, const typename M::value_type *__restrict__ xi,
                                                OT *__restrict__ xo, const typename M::value_type *__restrict__ q,
-                                               double *part, Ctl *ctl, int mode)
-{
-    pdl_enter();
+                                               double *part, Ctl *ctl, int mode) {
     using T = typename M::value_type;
     constexpr int R = M::R;
     if (finished(ctl)) return;
@@ -715,16 +722,24 @@ __global__ void __launch_bounds__(BS) k_jacobi(M A, int n, const typename M::val
             if constexpr (DOT) dot_rows<R>(i, b, out, q, lrz, lqz);
         }
     }
-    if constexpr (DOT) cg_rz_epilogue(lrz, lqz, part, ctl, mode);
+    if constexpr (DOT) cg_rz_epilogue(vb, lrz, lqz, part, ctl, mode);
+}
+
+template <class M, class BT, class OT, bool DOT>
+__global__ void __launch_bounds__(BS) k_jacobi(M A, int n, const typename M::value_type *__restrict__ dw,
+                                               const BT *__restrict__ b, const typename M::value_type *__restrict__ xi,
+                                               OT *__restrict__ xo, const typename M::value_type *__restrict__ q,
+                                               double *part, Ctl *ctl, int mode)
+{
+    pdl_enter();
+    b_jacobi<M, BT, OT, DOT>(vb_grid(), A, n, dw, b, xi, xo, q, part, ctl, mode);
 }
 
 // r = b - A x
 template <class M, class BT>
-__global__ void __launch_bounds__(BS) k_residual(M A, int n, const BT *__restrict__ b,
+__device__ __forceinline__ void b_residual(VB vb, M A, int n, const BT *__restrict__ b,
                                                  const typename M::value_type *__restrict__ x,
-                                                 typename M::value_type *__restrict__ r, const Ctl *ctl)
-{
-    pdl_enter();
+                                                 typename M::value_type *__restrict__ r, const Ctl *ctl) {
     using T = typename M::value_type;
     constexpr int R = M::R;
     if (finished(ctl)) return;
@@ -741,12 +756,19 @@ __global__ void __launch_bounds__(BS) k_residual(M A, int n, const BT *__restric
     }
 }
 
-// y = R x (restriction)
-template <class M>
-__global__ void __launch_bounds__(BS) k_spmv(M Rm, int n, const typename M::value_type *__restrict__ x,
-                                             typename M::value_type *__restrict__ y, const Ctl *ctl)
+template <class M, class BT>
+__global__ void __launch_bounds__(BS) k_residual(M A, int n, const BT *__restrict__ b,
+                                                 const typename M::value_type *__restrict__ x,
+                                                 typename M::value_type *__restrict__ r, const Ctl *ctl)
 {
     pdl_enter();
+    b_residual<M, BT>(vb_grid(), A, n, b, x, r, ctl);
+}
+
+// y = R x (restriction)
+template <class M>
+__device__ __forceinline__ void b_spmv(VB vb, M Rm, int n, const typename M::value_type *__restrict__ x,
+                                             typename M::value_type *__restrict__ y, const Ctl *ctl) {
     using T = typename M::value_type;
     if (finished(ctl)) return;
     GROUP_ROWS(M, n)
@@ -759,12 +781,18 @@ __global__ void __launch_bounds__(BS) k_spmv(M Rm, int n, const typename M::valu
     }
 }
 
-// x += P e (interpolate and correct)
 template <class M>
-__global__ void __launch_bounds__(BS) k_prolong(M P, int n, const typename M::value_type *__restrict__ e,
-                                                typename M::value_type *__restrict__ x, const Ctl *ctl)
+__global__ void __launch_bounds__(BS) k_spmv(M Rm, int n, const typename M::value_type *__restrict__ x,
+                                             typename M::value_type *__restrict__ y, const Ctl *ctl)
 {
     pdl_enter();
+    b_spmv<M>(vb_grid(), Rm, n, x, y, ctl);
+}
+
+// x += P e (interpolate and correct)
+template <class M>
+__device__ __forceinline__ void b_prolong(VB vb, M P, int n, const typename M::value_type *__restrict__ e,
+                                                typename M::value_type *__restrict__ x, const Ctl *ctl) {
     using T = typename M::value_type;
     constexpr int R = M::R;
     if (finished(ctl)) return;
@@ -778,6 +806,14 @@ __global__ void __launch_bounds__(BS) k_prolong(M P, int n, const typename M::va
             st<R>(x + i, xv);
         }
     }
+}
+
+template <class M>
+__global__ void __launch_bounds__(BS) k_prolong(M P, int n, const typename M::value_type *__restrict__ e,
+                                                typename M::value_type *__restrict__ x, const Ctl *ctl)
+{
+    pdl_enter();
+    b_prolong<M>(vb_grid(), P, n, e, x, ctl);
 }
 
 // x += P e on level 0 with the implicit prolongator (ImplP), R rows a thread:
@@ -811,13 +847,11 @@ struct PImpl {
 };
 
 template <int R>
-__global__ void __launch_bounds__(BS) k_prolong_imp(PImpl P, const float *__restrict__ e, float *__restrict__ x,
-                                                    const Ctl *ctl)
-{
-    pdl_enter();
+__device__ __forceinline__ void b_prolong_imp(VB vb, PImpl P, const float *__restrict__ e, float *__restrict__ x,
+                                                    const Ctl *ctl) {
     if (finished(ctl)) return;
     const int n = P.n, nx = P.nx, sxy = P.sxy;
-    for (int i0 = R * (blockIdx.x * BS + threadIdx.x); i0 < n; i0 += R * gridDim.x * BS) {
+    for (int i0 = R * (vb.bid * BS + threadIdx.x); i0 < n; i0 += R * vb.nb * BS) {
         float acc[R];
 #pragma unroll
         for (int k = 0; k < R; ++k) acc[k] = 0.f;
@@ -867,17 +901,23 @@ __global__ void __launch_bounds__(BS) k_prolong_imp(PImpl P, const float *__rest
     }
 }
 
+template <int R>
+__global__ void __launch_bounds__(BS) k_prolong_imp(PImpl P, const float *__restrict__ e, float *__restrict__ x,
+                                                    const Ctl *ctl)
+{
+    pdl_enter();
+    b_prolong_imp<R>(vb_grid(), P, e, x, ctl);
+}
+
 // u_j = w_j r_j - sum_i f_ij s_i r_i over the six neighbours (the first half
 // of r_c = (P^T r)_c on level 0), R rows a thread, neighbours in the order
 // -z, -y, -x, +x, +y, +z
 template <int R>
-__global__ void __launch_bounds__(BS) k_restrict_u(PImpl P, const float *__restrict__ r, float *__restrict__ u,
-                                                   const Ctl *ctl)
-{
-    pdl_enter();
+__device__ __forceinline__ void b_restrict_u(VB vb, PImpl P, const float *__restrict__ r, float *__restrict__ u,
+                                                   const Ctl *ctl) {
     if (finished(ctl)) return;
     const int n = P.n, nx = P.nx, sxy = P.sxy;
-    for (int i0 = R * (blockIdx.x * BS + threadIdx.x); i0 < n; i0 += R * gridDim.x * BS) {
+    for (int i0 = R * (vb.bid * BS + threadIdx.x); i0 < n; i0 += R * vb.nb * BS) {
         float acc[R];
 #pragma unroll
         for (int k = 0; k < R; ++k) acc[k] = 0.f;
@@ -918,20 +958,26 @@ __global__ void __launch_bounds__(BS) k_restrict_u(PImpl P, const float *__restr
     }
 }
 
+template <int R>
+__global__ void __launch_bounds__(BS) k_restrict_u(PImpl P, const float *__restrict__ r, float *__restrict__ u,
+                                                   const Ctl *ctl)
+{
+    pdl_enter();
+    b_restrict_u<R>(vb_grid(), P, r, u, ctl);
+}
+
 // r_c = sum of u over the members of aggregate c: four lanes per aggregate,
 // lane g adding members g, g + 4, ... in order, then a fixed shuffle tree.
 // A lane takes its members RS_CHUNK at a time: the member indices first, then
 // the gathered u values, then the additions in order, so that the loads of a
 // chunk are in flight together instead of one dependent pair per member.
 constexpr int RS_LANES = 4, RS_CHUNK = 4;
-__global__ void __launch_bounds__(BS) k_restrict_sum(int nc, const int *__restrict__ mptr, const int *__restrict__ mem,
+__device__ __forceinline__ void b_restrict_sum(VB vb, int nc, const int *__restrict__ mptr, const int *__restrict__ mem,
                                                      const float *__restrict__ u, float *__restrict__ rc,
-                                                     const Ctl *ctl)
-{
-    pdl_enter();
+                                                     const Ctl *ctl) {
     if (finished(ctl)) return;
     const int g = threadIdx.x & (RS_LANES - 1);
-    for (int c = (int)((blockIdx.x * (long long)BS + threadIdx.x) / RS_LANES), stride = gridDim.x * (BS / RS_LANES);
+    for (int c = (int)((vb.bid * (long long)BS + threadIdx.x) / RS_LANES), stride = vb.nb * (BS / RS_LANES);
          __any_sync(0xffffffffu, c < nc); c += stride) {
         float acc = 0.f;
         if (c < nc) {
@@ -954,6 +1000,14 @@ __global__ void __launch_bounds__(BS) k_restrict_sum(int nc, const int *__restri
     }
 }
 
+__global__ void __launch_bounds__(BS) k_restrict_sum(int nc, const int *__restrict__ mptr, const int *__restrict__ mem,
+                                                     const float *__restrict__ u, float *__restrict__ rc,
+                                                     const Ctl *ctl)
+{
+    pdl_enter();
+    b_restrict_sum(vb_grid(), nc, mptr, mem, u, rc, ctl);
+}
+
 static void restrict_imp(Hier &H, const float *r, float *u, float *rc, const Ctl *ctl, cudaStream_t st)
 {
     const ImplP &I = H.p0;
@@ -974,13 +1028,11 @@ static void prolong_imp(Hier &H, const float *e, float *x, const Ctl *ctl, cudaS
 
 // x = Ainv b on the coarsest level (dense FP64 inverse), one warp per row
 template <class T>
-__global__ void __launch_bounds__(BS) k_coarse(int n, const double *__restrict__ Ainv, const T *__restrict__ b,
-                                               T *__restrict__ x, const Ctl *ctl)
-{
-    pdl_enter();
+__device__ __forceinline__ void b_coarse(VB vb, int n, const double *__restrict__ Ainv, const T *__restrict__ b,
+                                               T *__restrict__ x, const Ctl *ctl) {
     if (finished(ctl)) return;
     const int lane = threadIdx.x & 31;
-    for (int row = (blockIdx.x * BS + threadIdx.x) >> 5; row < n; row += (gridDim.x * BS) >> 5) {
+    for (int row = (vb.bid * BS + threadIdx.x) >> 5; row < n; row += (vb.nb * BS) >> 5) {
         const double *a = Ainv + (size_t)row * n;
         double s = 0.0;
         for (int j = lane; j < n; j += 32) s += a[j] * (double)b[j];
@@ -989,19 +1041,25 @@ __global__ void __launch_bounds__(BS) k_coarse(int n, const double *__restrict__
     }
 }
 
+template <class T>
+__global__ void __launch_bounds__(BS) k_coarse(int n, const double *__restrict__ Ainv, const T *__restrict__ b,
+                                               T *__restrict__ x, const Ctl *ctl)
+{
+    pdl_enter();
+    b_coarse<T>(vb_grid(), n, Ainv, b, x, ctl);
+}
+
 // Chebyshev first step: r = b - A x (r = b when x0zero), d = c0 dw r.  x is
 // gathered here, so it is not written in place: with x0zero x = d; otherwise
 // the next step (or k_axpy) adds d.  DOT: xo = x + d is the CG's z.
 template <class M, class BT, class OT, bool DOT>
-__global__ void __launch_bounds__(BS) k_cheb0(M A, int n, const typename M::value_type *__restrict__ dw,
+__device__ __forceinline__ void b_cheb0(VB vb, M A, int n, const typename M::value_type *__restrict__ dw,
                                               const BT *__restrict__ b, typename M::value_type *x,
                                               typename M::value_type *__restrict__ r,
                                               typename M::value_type *__restrict__ d, OT *__restrict__ xo,
                                               typename M::value_type c0, int x0zero,
                                               const typename M::value_type *__restrict__ q, double *part, Ctl *ctl,
-                                              int mode)
-{
-    pdl_enter();
+                                              int mode) {
     using T = typename M::value_type;
     constexpr int R = M::R;
     if (finished(ctl)) return;
@@ -1040,12 +1098,25 @@ __global__ void __launch_bounds__(BS) k_cheb0(M A, int n, const typename M::valu
             }
         }
     }
-    if constexpr (DOT) cg_rz_epilogue(lrz, lqz, part, ctl, mode);
+    if constexpr (DOT) cg_rz_epilogue(vb, lrz, lqz, part, ctl, mode);
+}
+
+template <class M, class BT, class OT, bool DOT>
+__global__ void __launch_bounds__(BS) k_cheb0(M A, int n, const typename M::value_type *__restrict__ dw,
+                                              const BT *__restrict__ b, typename M::value_type *x,
+                                              typename M::value_type *__restrict__ r,
+                                              typename M::value_type *__restrict__ d, OT *__restrict__ xo,
+                                              typename M::value_type c0, int x0zero,
+                                              const typename M::value_type *__restrict__ q, double *part, Ctl *ctl,
+                                              int mode)
+{
+    pdl_enter();
+    b_cheb0<M, BT, OT, DOT>(vb_grid(), A, n, dw, b, x, r, d, xo, c0, x0zero, q, part, ctl, mode);
 }
 
 // Chebyshev step k >= 2: r -= A d; dn = c1 d + c2 dw r; x += (add_prev ? d : 0) + dn
 template <class M, class OT, bool DOT>
-__global__ void __launch_bounds__(BS) k_chebk(M A, int n, const typename M::value_type *__restrict__ dw,
+__device__ __forceinline__ void b_chebk(VB vb, M A, int n, const typename M::value_type *__restrict__ dw,
                                               typename M::value_type *__restrict__ r,
                                               const typename M::value_type *__restrict__ d,
                                               typename M::value_type *__restrict__ dn, typename M::value_type *x,
@@ -1053,9 +1124,7 @@ __global__ void __launch_bounds__(BS) k_chebk(M A, int n, const typename M::valu
                                               typename M::value_type c2, int add_prev,
                                               const typename M::value_type *__restrict__ b0,
                                               const typename M::value_type *__restrict__ q, double *part, Ctl *ctl,
-                                              int mode)
-{
-    pdl_enter();
+                                              int mode) {
     using T = typename M::value_type;
     constexpr int R = M::R;
     if (finished(ctl)) return;
@@ -1092,7 +1161,22 @@ __global__ void __launch_bounds__(BS) k_chebk(M A, int n, const typename M::valu
             }
         }
     }
-    if constexpr (DOT) cg_rz_epilogue(lrz, lqz, part, ctl, mode);
+    if constexpr (DOT) cg_rz_epilogue(vb, lrz, lqz, part, ctl, mode);
+}
+
+template <class M, class OT, bool DOT>
+__global__ void __launch_bounds__(BS) k_chebk(M A, int n, const typename M::value_type *__restrict__ dw,
+                                              typename M::value_type *__restrict__ r,
+                                              const typename M::value_type *__restrict__ d,
+                                              typename M::value_type *__restrict__ dn, typename M::value_type *x,
+                                              OT *__restrict__ xo, typename M::value_type c1,
+                                              typename M::value_type c2, int add_prev,
+                                              const typename M::value_type *__restrict__ b0,
+                                              const typename M::value_type *__restrict__ q, double *part, Ctl *ctl,
+                                              int mode)
+{
+    pdl_enter();
+    b_chebk<M, OT, DOT>(vb_grid(), A, n, dw, r, d, dn, x, xo, c1, c2, add_prev, b0, q, part, ctl, mode);
 }
 
 // The first two Chebyshev steps from a zero guess in one pass: with
@@ -1100,7 +1184,7 @@ __global__ void __launch_bounds__(BS) k_chebk(M A, int n, const typename M::valu
 // x = d0 + d1.  r1 and d1 are stored only when more steps follow (keep).
 // DOT: x is the CG's z and (b, z), (q, z) are reduced.
 template <class M, class OT, bool DOT>
-__global__ void __launch_bounds__(BS) k_cheb_zero2(M A, int n, const typename M::value_type *__restrict__ dw,
+__device__ __forceinline__ void b_cheb_zero2(VB vb, M A, int n, const typename M::value_type *__restrict__ dw,
                                                    const typename M::value_type *__restrict__ b,
                                                    typename M::value_type *__restrict__ x,
                                                    typename M::value_type *__restrict__ r,
@@ -1108,11 +1192,9 @@ __global__ void __launch_bounds__(BS) k_cheb_zero2(M A, int n, const typename M:
                                                    typename M::value_type c0, typename M::value_type c1,
                                                    typename M::value_type c2, int keep,
                                                    const typename M::value_type *__restrict__ q, double *part,
-                                                   Ctl *ctl, int mode)
-{
+                                                   Ctl *ctl, int mode) {
     using T = typename M::value_type;
     constexpr int R = M::R;
-    pdl_enter();
     if (finished(ctl)) return;
     double lrz = 0.0, lqz = 0.0;
     GROUP_ROWS(M, n)
@@ -1148,15 +1230,35 @@ __global__ void __launch_bounds__(BS) k_cheb_zero2(M A, int n, const typename M:
             }
         }
     }
-    if constexpr (DOT) cg_rz_epilogue(lrz, lqz, part, ctl, mode);
+    if constexpr (DOT) cg_rz_epilogue(vb, lrz, lqz, part, ctl, mode);
+}
+
+template <class M, class OT, bool DOT>
+__global__ void __launch_bounds__(BS) k_cheb_zero2(M A, int n, const typename M::value_type *__restrict__ dw,
+                                                   const typename M::value_type *__restrict__ b,
+                                                   typename M::value_type *__restrict__ x,
+                                                   typename M::value_type *__restrict__ r,
+                                                   typename M::value_type *__restrict__ d, OT *__restrict__ xo,
+                                                   typename M::value_type c0, typename M::value_type c1,
+                                                   typename M::value_type c2, int keep,
+                                                   const typename M::value_type *__restrict__ q, double *part,
+                                                   Ctl *ctl, int mode)
+{
+    pdl_enter();
+    b_cheb_zero2<M, OT, DOT>(vb_grid(), A, n, dw, b, x, r, d, xo, c0, c1, c2, keep, q, part, ctl, mode);
+}
+
+template <class T>
+__device__ __forceinline__ void b_axpy(VB vb, int n, const T *__restrict__ d, T *__restrict__ x, const Ctl *ctl) {
+    if (finished(ctl)) return;
+    for (int i = vb.bid * BS + threadIdx.x; i < n; i += vb.nb * BS) x[i] += d[i];
 }
 
 template <class T>
 __global__ void __launch_bounds__(BS) k_axpy(int n, const T *__restrict__ d, T *__restrict__ x, const Ctl *ctl)
 {
     pdl_enter();
-    if (finished(ctl)) return;
-    ROWS(i, n) x[i] += d[i];
+    b_axpy<T>(vb_grid(), n, d, x, ctl);
 }
 
 // ---------------------------------------------------------- V-cycle driver --
@@ -1495,6 +1597,7 @@ template <class M>
 __global__ void __launch_bounds__(BS) k_cg_spmv_dot(M A, int n, const typename M::value_type *__restrict__ p,
                                                     typename M::value_type *__restrict__ q, double *part, Ctl *c)
 {
+    const VB vb = vb_grid();
     pdl_enter();
     using V = typename M::value_type;
     constexpr int R = M::R;
@@ -1536,19 +1639,17 @@ __global__ void __launch_bounds__(BS) k_cg_spmv_dot(M A, int n, const typename M
 // iteration: p_old is pa in even iterations (c->it even at the start) and pb
 // in odd ones, p_new the other one.
 template <class M>
-__global__ void __launch_bounds__(BS) k_cg_dir_spmv(M A, int n, const typename M::value_type *__restrict__ z,
+__device__ __forceinline__ void b_cg_dir_spmv(VB vb, M A, int n, const typename M::value_type *__restrict__ z,
                                                     typename M::value_type *pa, typename M::value_type *pb,
-                                                    typename M::value_type *__restrict__ q, double *part, Ctl *c)
-{
+                                                    typename M::value_type *__restrict__ q, double *part, Ctl *c) {
     using V = typename M::value_type;
     constexpr int R = M::R;
-    pdl_enter();
     if (finished(c)) return;
     const int odd = c->it & 1;
     const V *__restrict__ pold = odd ? pb : pa;
     V *__restrict__ pnew = odd ? pa : pb;
     if (c->it >= c->maxit) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (vb.bid == 0 && threadIdx.x == 0) {
             ctl_stop(c, GW_ERR_NOT_CONVERGED);
         }
         return;
@@ -1568,7 +1669,7 @@ __global__ void __launch_bounds__(BS) k_cg_dir_spmv(M A, int n, const typename M
             loc[0] += (double)s;
         }
     }
-    if (reduce_last<1>(loc, part, &c->cnt[0], tot) && threadIdx.x == 0) {
+    if (reduce_last<1>(vb, loc, part, &c->cnt[0], tot) && threadIdx.x == 0) {
         const double pq = tot[0];
         c->pq = pq;
         c->it += 1;
@@ -1580,21 +1681,28 @@ __global__ void __launch_bounds__(BS) k_cg_dir_spmv(M A, int n, const typename M
     }
 }
 
+template <class M>
+__global__ void __launch_bounds__(BS) k_cg_dir_spmv(M A, int n, const typename M::value_type *__restrict__ z,
+                                                    typename M::value_type *pa, typename M::value_type *pb,
+                                                    typename M::value_type *__restrict__ q, double *part, Ctl *c)
+{
+    pdl_enter();
+    b_cg_dir_spmv<M>(vb_grid(), A, n, z, pa, pb, q, part, c);
+}
+
 // x += alpha p; r -= alpha q; rr = (r, r).  Sets check when r passes the
 // stopping test, or (mixed form) when it fell below delta times the residual
 // of the last reliable update.  With pb, p is the new direction of the two
 // alternating buffers (pb after an even iteration, pa after an odd one).
 template <class V, int R>
-__global__ void __launch_bounds__(BS) k_cg_update(int n, V *__restrict__ x, V *__restrict__ r, const V *pa,
+__device__ __forceinline__ void b_cg_update(VB vb, int n, V *__restrict__ x, V *__restrict__ r, const V *pa,
                                                   const V *pb, const V *__restrict__ q, double *part, Ctl *c,
-                                                  int reliable)
-{
-    pdl_enter();
+                                                  int reliable) {
     if (finished(c)) return;
     const V *__restrict__ p = (pb && !((c->it - 1) & 1)) ? pb : pa;
     const V a = (V)c->alpha;
     double loc[1] = {0.0}, tot[1];
-    for (int i = R * (blockIdx.x * BS + threadIdx.x); i < n; i += R * gridDim.x * BS) {
+    for (int i = R * (vb.bid * BS + threadIdx.x); i < n; i += R * vb.nb * BS) {
         VecN<V, R> xv = ld_rw<R>(x + i), rv = ld_rw<R>(r + i);
         const VecN<V, R> pv = ld_ro<R>(p + i), qv = ld_ro<R>(q + i);
         V s = 0;
@@ -1608,7 +1716,7 @@ __global__ void __launch_bounds__(BS) k_cg_update(int n, V *__restrict__ x, V *_
         st<R>(x + i, xv);
         st<R>(r + i, rv);
     }
-    if (reduce_last<1>(loc, part, &c->cnt[0], tot) && threadIdx.x == 0) {
+    if (reduce_last<1>(vb, loc, part, &c->cnt[0], tot) && threadIdx.x == 0) {
         c->rr = tot[0];
         if (!isfinite(tot[0])) {
             ctl_stop(c, GW_ERR_BREAKDOWN);
@@ -1618,11 +1726,21 @@ __global__ void __launch_bounds__(BS) k_cg_update(int n, V *__restrict__ x, V *_
     }
 }
 
+template <class V, int R>
+__global__ void __launch_bounds__(BS) k_cg_update(int n, V *__restrict__ x, V *__restrict__ r, const V *pa,
+                                                  const V *pb, const V *__restrict__ q, double *part, Ctl *c,
+                                                  int reliable)
+{
+    pdl_enter();
+    b_cg_update<V, R>(vb_grid(), n, x, r, pa, pb, q, part, c, reliable);
+}
+
 // FP64 form: when the recursive residual passed, r = b - A x; stop if it passes too
 template <class M>
 __global__ void __launch_bounds__(BS) k_cg_true(M A, int n, const double *__restrict__ b, const double *__restrict__ x,
                                                 double *__restrict__ r, double *part, Ctl *c, int force)
 {
+    const VB vb = vb_grid();
     pdl_enter();
     constexpr int R = M::R;
     if (!force && (finished(c) || !c->check)) return;
@@ -1657,12 +1775,10 @@ __global__ void __launch_bounds__(BS) k_cg_true(M A, int n, const double *__rest
 
 // mixed form, reliable update part 1: x64 += xs; xs = 0
 template <int R>
-__global__ void __launch_bounds__(BS) k_rel_fold(int n, double *__restrict__ x, float *__restrict__ xs, const Ctl *c,
-                                                 int force)
-{
-    pdl_enter();
+__device__ __forceinline__ void b_rel_fold(VB vb, int n, double *__restrict__ x, float *__restrict__ xs, const Ctl *c,
+                                                 int force) {
     if (!force && (finished(c) || !c->check)) return;
-    for (int i = R * (blockIdx.x * BS + threadIdx.x); i < n; i += R * gridDim.x * BS) {
+    for (int i = R * (vb.bid * BS + threadIdx.x); i < n; i += R * vb.nb * BS) {
         VecN<double, R> xv = ld_rw<R>(x + i);
         const VecN<float, R> sv = ld_rw<R>(xs + i);
         VecN<float, R> zero;
@@ -1676,13 +1792,19 @@ __global__ void __launch_bounds__(BS) k_rel_fold(int n, double *__restrict__ x, 
     }
 }
 
+template <int R>
+__global__ void __launch_bounds__(BS) k_rel_fold(int n, double *__restrict__ x, float *__restrict__ xs, const Ctl *c,
+                                                 int force)
+{
+    pdl_enter();
+    b_rel_fold<R>(vb_grid(), n, x, xs, c, force);
+}
+
 // mixed form, reliable update part 2: r = b - A64 x64 in FP64, stored as FP32;
 // stop if ||r|| passes the test, else remember ||r||^2 for the next update
 template <class M>
-__global__ void __launch_bounds__(BS) k_rel_res(M A, int n, const double *__restrict__ b, const double *__restrict__ x,
-                                                float *__restrict__ r, double *part, Ctl *c, int force)
-{
-    pdl_enter();
+__device__ __forceinline__ void b_rel_res(VB vb, M A, int n, const double *__restrict__ b, const double *__restrict__ x,
+                                                float *__restrict__ r, double *part, Ctl *c, int force) {
     constexpr int R = M::R;
     if (!force && (finished(c) || !c->check)) return;
     double loc[1] = {0.0}, tot[1];
@@ -1701,7 +1823,7 @@ __global__ void __launch_bounds__(BS) k_rel_res(M A, int n, const double *__rest
             if (!force) st<R>(r + i, rv);
         }
     }
-    if (reduce_last<1>(loc, part, &c->cnt[0], tot) && threadIdx.x == 0) {
+    if (reduce_last<1>(vb, loc, part, &c->cnt[0], tot) && threadIdx.x == 0) {
         c->rt2 = tot[0];
         const double rel = c->bnorm2 > 0.0 ? sqrt(tot[0] / c->bnorm2) : 0.0;
         c->relres = rel;
@@ -1714,6 +1836,14 @@ __global__ void __launch_bounds__(BS) k_rel_res(M A, int n, const double *__rest
             }
         }
     }
+}
+
+template <class M>
+__global__ void __launch_bounds__(BS) k_rel_res(M A, int n, const double *__restrict__ b, const double *__restrict__ x,
+                                                float *__restrict__ r, double *part, Ctl *c, int force)
+{
+    pdl_enter();
+    b_rel_res<M>(vb_grid(), A, n, b, x, r, part, c, force);
 }
 
 // p = z + beta p
@@ -2051,6 +2181,664 @@ int pcg_run(Hier &H, double tol, int maxit, int *iters, double *relres, cudaStre
     if (iters) *iters = H.ctl_host->it;
     if (relres) *relres = H.ctl_host->relres;
     return H.ctl_host->status;
+}
+
+
+// =============================================================================
+// Batched solves (serving): the same pass of every active solve in one launch.
+//
+// Concurrent solves of different grids and fields (the sensitivity sweeps the
+// Abstract motivates) each keep their own resident hierarchy.  A batch holds
+// up to max_slots of them.  A device slot table describes every slot: per
+// level its matrices (the level-0 stencil, sliced ELL or warp-CSR on the
+// coarser levels), smoother data, vectors and Chebyshev coefficients, the
+// implicit level-0 transfer, the coarsest inverse and the CG vectors and
+// control block.  One CG iteration of the mixed form is a fixed sequence of
+// passes (the CG product and update, the reliable update, and the V-cycle's
+// passes level by level, padded to the deepest hierarchy); each pass is one
+// launch whose work list holds (slot, virtual block) items for every slot
+// that has that pass.  A slot's passes use a virtual grid fixed by its own
+// size, and its reductions use its own partial-sum array and counters, so a
+// solve gives the same bits alone and in any mix.  The iteration is captured
+// once as a CUDA graph and replayed; admission and removal of slots between
+// replays only rewrite the device slot table and work lists.  Slots finish
+// independently: a finished slot's passes return at once until it is taken.
+
+constexpr int BATCH_MAXL = 12;   // levels of a hierarchy in a batch
+constexpr int BATCH_NB_CAP = 1024;  // virtual blocks of one pass of one slot
+
+enum { BM_NONE = 0, BM_STEN4, BM_STEN2, BM_STEN1, BM_SELL, BM_CSR32 };
+
+// a matrix of a slot, dispatched on fmt inside the batched kernels
+struct BMat {
+    int fmt, nr;
+    const float *d, *ox, *oy, *oz;  // stencil (n = nr)
+    int nx, sxy;
+    const int *sp, *ci, *perm, *rp;  // sliced ELL (sp, ci, perm) or CSR (rp, ci)
+    const float *v;
+};
+
+struct BLev {
+    int n;
+    BMat A, P, R;
+    const float *dw;
+    float *x, *b, *r, *t, *d, *d2;
+    float c0, c1[8], c2[8];
+};
+
+struct BSlot {
+    int L, active;
+    BLev lv[BATCH_MAXL];
+    BMat A32;                                   // operator of the CG recurrence (level-0 stencil)
+    const double *ad, *ax, *ay, *az;            // FP64 level-0 stencil of the reliable updates
+    int a64r;                                   // its rows per thread (4, 2 or 1)
+    PImpl p0;                                   // implicit level-0 prolongator / restriction
+    int p0r;                                    // its rows per thread (4 or 1)
+    const int *mptr, *mem;
+    int nc0;                                    // aggregates of level 0 (rows of level 1)
+    const double *Ainv;
+    float *xs, *r32, *p32, *p32b, *q32, *z32;
+    double *x, *b;
+    double *part;
+    Ctl *ctl;
+};
+
+// one launch of the batched iteration: pass kind, level, Chebyshev step and
+// whether the step reads d2 and writes d (the two direction buffers alternate)
+enum {
+    BP_DIR_SPMV = 0, BP_UPDATE, BP_REL_FOLD, BP_REL_RES, BP_ZERO2, BP_CHEBK, BP_RESID, BP_RESTRICT_U,
+    BP_RESTRICT_SUM, BP_SPMV, BP_COARSE, BP_PROLONG, BP_PROLONG_IMP, BP_CHEB0, BP_CHEBK_DOT
+};
+
+struct BLaunch {
+    int kind, level, step, swap, add_prev, keep;
+};
+
+// per-slot summary written at the end of every replay
+struct BSum {
+    int done, status, it, pad;
+    double relres;
+};
+
+template <class F>
+__device__ __forceinline__ void with_bmat(const BMat &m, F f)
+{
+    switch (m.fmt) {
+    case BM_STEN4: f(MSten<float, 4>{m.d, m.ox, m.oy, m.oz, m.nr, m.nx, m.sxy}); break;
+    case BM_STEN2: f(MSten<float, 2>{m.d, m.ox, m.oy, m.oz, m.nr, m.nx, m.sxy}); break;
+    case BM_STEN1: f(MSten<float, 1>{m.d, m.ox, m.oy, m.oz, m.nr, m.nx, m.sxy}); break;
+    case BM_SELL: f(MSell<float, 1>{SV<float>{m.sp, m.ci, m.v, m.nr, m.perm}}); break;
+    case BM_CSR32: f(MCsr<float, 32>{m.rp, m.ci, m.v, m.nr}); break;
+    default: break;
+    }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(BS) kb_pass(const BSlot *__restrict__ slots, const int4 *__restrict__ work,
+                                              const int *__restrict__ wcnt, int launch, BLaunch Lc)
+{
+    pdl_enter();
+    const int cnt = wcnt[2 * launch + 1], off = wcnt[2 * launch];
+    for (int w = blockIdx.x; w < cnt; w += gridDim.x) {
+        const int4 item = work[off + w];
+        const BSlot &S = slots[item.x];
+        const VB vb{item.y, item.z};
+        const int l = Lc.level;
+        if constexpr (KIND == BP_DIR_SPMV) {
+            with_bmat(S.A32, [&](auto A) {
+                b_cg_dir_spmv(vb, A, S.lv[0].n, (const float *)S.z32, S.p32, S.p32b, S.q32, S.part, S.ctl);
+            });
+        } else if constexpr (KIND == BP_UPDATE) {
+            if (S.lv[0].n % 4 == 0)
+                b_cg_update<float, 4>(vb, S.lv[0].n, S.xs, S.r32, S.p32, S.p32b, S.q32, S.part, S.ctl, 1);
+            else
+                b_cg_update<float, 1>(vb, S.lv[0].n, S.xs, S.r32, S.p32, S.p32b, S.q32, S.part, S.ctl, 1);
+        } else if constexpr (KIND == BP_REL_FOLD) {
+            if (S.lv[0].n % 2 == 0) b_rel_fold<2>(vb, S.lv[0].n, S.x, S.xs, S.ctl, 0);
+            else b_rel_fold<1>(vb, S.lv[0].n, S.x, S.xs, S.ctl, 0);
+        } else if constexpr (KIND == BP_REL_RES) {
+            const int n = S.lv[0].n, nx = S.A32.nx, sxy = S.A32.sxy;
+            if (S.a64r == 4)
+                b_rel_res(vb, MSten<double, 4>{S.ad, S.ax, S.ay, S.az, n, nx, sxy}, n, S.b, S.x, S.r32, S.part, S.ctl, 0);
+            else if (S.a64r == 2)
+                b_rel_res(vb, MSten<double, 2>{S.ad, S.ax, S.ay, S.az, n, nx, sxy}, n, S.b, S.x, S.r32, S.part, S.ctl, 0);
+            else
+                b_rel_res(vb, MSten<double, 1>{S.ad, S.ax, S.ay, S.az, n, nx, sxy}, n, S.b, S.x, S.r32, S.part, S.ctl, 0);
+        } else if constexpr (KIND == BP_ZERO2) {
+            const BLev &v = S.lv[l];
+            const float *bl = l == 0 ? S.r32 : v.b;
+            with_bmat(v.A, [&](auto A) {
+                using M = decltype(A);
+                b_cheb_zero2<M, float, false>(vb, A, v.n, v.dw, bl, v.x, v.r, v.d, (float *)nullptr, v.c0, v.c1[1],
+                                              v.c2[1], Lc.keep, S.q32, S.part, S.ctl, 1);
+            });
+        } else if constexpr (KIND == BP_CHEBK || KIND == BP_CHEBK_DOT) {
+            const BLev &v = S.lv[l];
+            float *d = Lc.swap ? v.d2 : v.d, *dn = Lc.swap ? v.d : v.d2;
+            with_bmat(v.A, [&](auto A) {
+                using M = decltype(A);
+                if constexpr (KIND == BP_CHEBK_DOT)
+                    b_chebk<M, float, true>(vb, A, v.n, v.dw, v.r, d, dn, v.x, S.z32, v.c1[Lc.step], v.c2[Lc.step],
+                                            Lc.add_prev, (const float *)S.r32, S.q32, S.part, S.ctl, 1);
+                else
+                    b_chebk<M, float, false>(vb, A, v.n, v.dw, v.r, d, dn, v.x, (float *)nullptr, v.c1[Lc.step],
+                                             v.c2[Lc.step], Lc.add_prev, (const float *)nullptr, S.q32, S.part,
+                                             S.ctl, 1);
+            });
+        } else if constexpr (KIND == BP_CHEB0) {
+            const BLev &v = S.lv[l];
+            const float *bl = l == 0 ? S.r32 : v.b;
+            with_bmat(v.A, [&](auto A) {
+                using M = decltype(A);
+                b_cheb0<M, float, float, false>(vb, A, v.n, v.dw, bl, v.x, v.r, v.d, (float *)nullptr, v.c0, 0,
+                                                S.q32, S.part, S.ctl, 1);
+            });
+        } else if constexpr (KIND == BP_RESID) {
+            const BLev &v = S.lv[l];
+            const float *bl = l == 0 ? S.r32 : v.b;
+            with_bmat(v.A, [&](auto A) { b_residual(vb, A, v.n, bl, (const float *)v.x, v.r, S.ctl); });
+        } else if constexpr (KIND == BP_RESTRICT_U) {
+            if (S.p0r == 4) b_restrict_u<4>(vb, S.p0, S.lv[0].r, S.lv[0].t, S.ctl);
+            else b_restrict_u<1>(vb, S.p0, S.lv[0].r, S.lv[0].t, S.ctl);
+        } else if constexpr (KIND == BP_RESTRICT_SUM) {
+            b_restrict_sum(vb, S.nc0, S.mptr, S.mem, S.lv[0].t, S.lv[1].b, S.ctl);
+        } else if constexpr (KIND == BP_SPMV) {
+            const BLev &v = S.lv[l];
+            with_bmat(v.R, [&](auto R) { b_spmv(vb, R, v.R.nr, (const float *)v.r, S.lv[l + 1].b, S.ctl); });
+        } else if constexpr (KIND == BP_COARSE) {
+            const BLev &v = S.lv[l];
+            b_coarse<float>(vb, v.n, S.Ainv, v.b, v.x, S.ctl);
+        } else if constexpr (KIND == BP_PROLONG) {
+            const BLev &v = S.lv[l];
+            with_bmat(v.P, [&](auto P) { b_prolong(vb, P, v.n, (const float *)S.lv[l + 1].x, v.x, S.ctl); });
+        } else if constexpr (KIND == BP_PROLONG_IMP) {
+            if (S.p0r == 4) b_prolong_imp<4>(vb, S.p0, S.lv[1].x, S.lv[0].x, S.ctl);
+            else b_prolong_imp<1>(vb, S.p0, S.lv[1].x, S.lv[0].x, S.ctl);
+        }
+    }
+}
+
+// copies every active slot's control block into the summary array
+__global__ void kb_summary(const BSlot *__restrict__ slots, int nslots, BSum *__restrict__ out)
+{
+    pdl_enter();
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nslots; s += gridDim.x * blockDim.x) {
+        BSum o{1, GW_OK, 0, 0, 0.0};
+        if (slots[s].active) {
+            const Ctl *c = slots[s].ctl;
+            o.done = *(volatile const int *)&c->done;
+            o.status = c->status;
+            o.it = c->it;
+            o.relres = c->relres;
+        }
+        out[s] = o;
+    }
+}
+
+struct Batch {
+    int max_slots = 0, dev = 0, degree = 0, lmax = 0, graph_lmax = 0;
+    cudaStream_t st = nullptr, cap = nullptr;
+    cudaGraphExec_t g = nullptr;
+    std::vector<Hier *> slot_h;
+    std::vector<int> state;           // 0 free, 1 running, 2 finished (not yet taken)
+    std::vector<BSlot> hslots;        // host image of the slot table
+    std::vector<BLaunch> launches;    // the iteration's pass sequence for lmax levels
+    DBuf<BSlot> dslots;
+    DBuf<int4> work;
+    DBuf<int> wcnt;                   // per launch: offset and count of its items
+    DBuf<BSum> dsum;
+    BSum *hsum = nullptr;             // pinned
+    int4 *hwork = nullptr;            // pinned staging of the work lists
+    int *hwcnt = nullptr;
+    BSlot *hstage = nullptr;
+    size_t work_cap = 0;
+    long long iter_kernels = 0, launches_run = 0;
+    ~Batch()
+    {
+        if (g) cudaGraphExecDestroy(g);
+        if (hsum) host_free(hsum);
+        if (hwork) host_free(hwork);
+        if (hwcnt) host_free(hwcnt);
+        if (hstage) host_free(hstage);
+        if (cap) cudaStreamDestroy(cap);
+        if (st) cudaStreamDestroy(st);
+    }
+};
+
+static BMat bmat_of(const MatStore<float> &M)
+{
+    BMat b;
+    memset(&b, 0, sizeof b);
+    b.nr = M.nr;
+    switch (M.fmt) {
+    case FMT_STEN: {
+        const StenT<float> &S = M.sten;
+        b.fmt = (S.n % 4 == 0 && S.nx % 4 == 0) ? BM_STEN4 : (S.n % 2 == 0 && S.nx % 2 == 0) ? BM_STEN2 : BM_STEN1;
+        b.d = S.d.p, b.ox = S.ox.p, b.oy = S.oy.p, b.oz = S.oz.p;
+        b.nr = S.n, b.nx = S.nx, b.sxy = S.nx * S.ny;
+        break;
+    }
+    case FMT_SELL:
+        if (M.nnz > (long long)SELL_LONG_ROW * M.nr && GW_SELL_LANES != 1) fail(GW_ERR_ARG, "batch: unsupported lanes");
+        b.fmt = BM_SELL;
+        b.sp = M.sell.sp.p, b.ci = M.sell.ci.p, b.v = M.sell.v.p, b.perm = M.sell.perm.p;
+        b.nr = M.sell.nr;
+        break;
+    case FMT_CSR32:
+        b.fmt = BM_CSR32;
+        b.rp = M.csr.rp.p, b.ci = M.csr.ci.p, b.v = M.csr.v.p;
+        b.nr = M.csr.nr;
+        break;
+    default: fail(GW_ERR_ARG, "batch: a level format the batched kernels do not read (%d)", M.fmt);
+    }
+    return b;
+}
+
+// virtual blocks of one pass of one slot (a function of the slot alone)
+static int bnb(long long threads) { return (int)std::max(1LL, std::min<long long>((threads + BS - 1) / BS, BATCH_NB_CAP)); }
+
+static int bmat_rows_per_thread(const BMat &m) { return m.fmt == BM_STEN4 ? 4 : m.fmt == BM_STEN2 ? 2 : 1; }
+
+static long long bmat_threads(const BMat &m, int n)
+{
+    if (m.fmt == BM_CSR32) return 32LL * n;
+    return (n + bmat_rows_per_thread(m) - 1) / bmat_rows_per_thread(m);
+}
+
+static int pass_nb(const BSlot &S, const BLaunch &c)
+{
+    const int n0 = S.lv[0].n;
+    switch (c.kind) {
+    case BP_DIR_SPMV: return bnb(bmat_threads(S.A32, n0));
+    case BP_UPDATE: return bnb(n0 % 4 == 0 ? n0 / 4 : n0);
+    case BP_REL_FOLD: return bnb(n0 % 2 == 0 ? n0 / 2 : n0);
+    case BP_REL_RES: return bnb((n0 + S.a64r - 1) / S.a64r);
+    case BP_RESTRICT_U:
+    case BP_PROLONG_IMP: return bnb(n0 / S.p0r);
+    case BP_RESTRICT_SUM: return bnb(4LL * S.nc0);
+    case BP_COARSE: return bnb(32LL * S.lv[c.level].n);
+    case BP_SPMV: return bnb(bmat_threads(S.lv[c.level].R, S.lv[c.level].R.nr));
+    case BP_PROLONG: return bnb(bmat_threads(S.lv[c.level].P, S.lv[c.level].n));
+    default: return bnb(bmat_threads(S.lv[c.level].A, S.lv[c.level].n));
+    }
+}
+
+// does slot S take part in launch c
+static bool pass_has(const BSlot &S, const BLaunch &c)
+{
+    if (!S.active) return false;
+    const int l = c.level;
+    switch (c.kind) {
+    case BP_DIR_SPMV:
+    case BP_UPDATE:
+    case BP_REL_FOLD:
+    case BP_REL_RES: return true;
+    case BP_COARSE: return l == S.L - 1;
+    default: return l < S.L - 1;
+    }
+}
+
+// the pass sequence of one CG iteration for hierarchies of up to lmax levels
+// and Chebyshev degree m, one application before and after the coarse
+// correction (the order of cg_iteration, vcycle_t and smooth)
+static std::vector<BLaunch> batch_sequence(int lmax, int m)
+{
+    std::vector<BLaunch> q;
+    auto add = [&](int kind, int level, int step = 0, int swap = 0, int add_prev = 0, int keep = 0) {
+        q.push_back(BLaunch{kind, level, step, swap, add_prev, keep});
+    };
+    add(BP_DIR_SPMV, 0);
+    add(BP_UPDATE, 0);
+    add(BP_REL_FOLD, 0);
+    add(BP_REL_RES, 0);
+    for (int l = 0; l < lmax; ++l) {
+        if (l < lmax - 1) {
+            add(BP_ZERO2, l, 1, 0, 0, m > 2);
+            for (int k = 2; k < m; ++k) add(BP_CHEBK, l, k, (k % 2) ? 1 : 0, 0);  // k = 2 reads d, writes d2
+            add(BP_RESID, l);
+            if (l == 0) {
+                add(BP_RESTRICT_U, 0);
+                add(BP_RESTRICT_SUM, 0);
+            } else {
+                add(BP_SPMV, l);
+            }
+        }
+        if (l >= 1) add(BP_COARSE, l);
+    }
+    for (int l = lmax - 2; l >= 0; --l) {
+        add(l == 0 ? BP_PROLONG_IMP : BP_PROLONG, l);
+        add(BP_CHEB0, l);
+        for (int k = 1; k < m; ++k)
+            add(l == 0 && k == m - 1 ? BP_CHEBK_DOT : BP_CHEBK, l, k, (k % 2) ? 0 : 1, k == 1 ? 1 : 0);
+    }
+    return q;
+}
+
+template <int KIND>
+static void kb_launch(Batch &B, int idx, cudaStream_t s)
+{
+    launch_pdl(kb_pass<KIND>, kernel_wave((const void *)kb_pass<KIND>, BS), s, (const BSlot *)B.dslots.p,
+               (const int4 *)B.work.p, (const int *)B.wcnt.p, idx, B.launches[(size_t)idx]);
+}
+
+static void batch_enqueue_iteration(Batch &B, cudaStream_t s)
+{
+    for (int i = 0; i < (int)B.launches.size(); ++i) {
+        switch (B.launches[(size_t)i].kind) {
+        case BP_DIR_SPMV: kb_launch<BP_DIR_SPMV>(B, i, s); break;
+        case BP_UPDATE: kb_launch<BP_UPDATE>(B, i, s); break;
+        case BP_REL_FOLD: kb_launch<BP_REL_FOLD>(B, i, s); break;
+        case BP_REL_RES: kb_launch<BP_REL_RES>(B, i, s); break;
+        case BP_ZERO2: kb_launch<BP_ZERO2>(B, i, s); break;
+        case BP_CHEBK: kb_launch<BP_CHEBK>(B, i, s); break;
+        case BP_RESID: kb_launch<BP_RESID>(B, i, s); break;
+        case BP_RESTRICT_U: kb_launch<BP_RESTRICT_U>(B, i, s); break;
+        case BP_RESTRICT_SUM: kb_launch<BP_RESTRICT_SUM>(B, i, s); break;
+        case BP_SPMV: kb_launch<BP_SPMV>(B, i, s); break;
+        case BP_COARSE: kb_launch<BP_COARSE>(B, i, s); break;
+        case BP_PROLONG: kb_launch<BP_PROLONG>(B, i, s); break;
+        case BP_PROLONG_IMP: kb_launch<BP_PROLONG_IMP>(B, i, s); break;
+        case BP_CHEB0: kb_launch<BP_CHEB0>(B, i, s); break;
+        case BP_CHEBK_DOT: kb_launch<BP_CHEBK_DOT>(B, i, s); break;
+        default: break;
+        }
+    }
+    launch_pdl(kb_summary, 1, s, (const BSlot *)B.dslots.p, B.max_slots, B.dsum.p);
+    GW_CUDA(cudaMemcpyAsync(B.hsum, B.dsum.p, sizeof(BSum) * (size_t)B.max_slots, cudaMemcpyDeviceToHost, s));
+    GW_LAUNCH_CHECK();
+}
+
+// rewrites the work lists of every launch from the slot table
+static void batch_rebuild_work(Batch &B)
+{
+    const int nl = (int)B.launches.size();
+    size_t total = 0;
+    for (int i = 0; i < nl; ++i)
+        for (int s = 0; s < B.max_slots; ++s)
+            if (pass_has(B.hslots[(size_t)s], B.launches[(size_t)i])) total += (size_t)pass_nb(B.hslots[(size_t)s], B.launches[(size_t)i]);
+    if (total > B.work_cap) fail(GW_ERR_OOM, "batch: work lists exceed their capacity");
+    size_t k = 0;
+    for (int i = 0; i < nl; ++i) {
+        B.hwcnt[2 * i] = (int)k;
+        for (int s = 0; s < B.max_slots; ++s) {
+            const BSlot &S = B.hslots[(size_t)s];
+            if (!pass_has(S, B.launches[(size_t)i])) continue;
+            const int nb = pass_nb(S, B.launches[(size_t)i]);
+            for (int v = 0; v < nb; ++v) B.hwork[k++] = make_int4(s, v, nb, 0);
+        }
+        B.hwcnt[2 * i + 1] = (int)(k - (size_t)B.hwcnt[2 * i]);
+    }
+    GW_CUDA(cudaMemcpyAsync(B.wcnt.p, B.hwcnt, sizeof(int) * 2 * (size_t)nl, cudaMemcpyHostToDevice, B.st));
+    if (k) GW_CUDA(cudaMemcpyAsync(B.work.p, B.hwork, sizeof(int4) * k, cudaMemcpyHostToDevice, B.st));
+}
+
+// (re)captures the iteration graph for hierarchies of up to lmax levels
+static void batch_capture(Batch &B, int lmax)
+{
+    if (B.g && B.graph_lmax >= lmax) return;
+    lmax = std::max(lmax, B.graph_lmax);
+    std::vector<BLaunch> seq = batch_sequence(lmax, B.degree);
+    const size_t nl = seq.size();
+    // launch table and work-list capacity for this sequence
+    DBuf<int> wcnt(2 * nl);
+    size_t cap = nl * (size_t)B.max_slots * BATCH_NB_CAP;
+    DBuf<int4> work(cap);
+    int *hw = nullptr;
+    int4 *hk = nullptr;
+    GW_CUDA(host_malloc((void **)&hw, sizeof(int) * 2 * nl));
+    GW_CUDA(host_malloc((void **)&hk, sizeof(int4) * cap));
+    if (B.hwcnt) host_free(B.hwcnt);
+    if (B.hwork) host_free(B.hwork);
+    B.hwcnt = hw;
+    B.hwork = hk;
+    B.wcnt = std::move(wcnt);
+    B.work = std::move(work);
+    B.work_cap = cap;
+    B.launches = seq;
+    if (B.g) cudaGraphExecDestroy(B.g);
+    B.g = nullptr;
+    for (int i = 0; i < (int)nl; ++i) {  // kernels are loaded outside the capture
+        B.hwcnt[2 * i] = 0;
+        B.hwcnt[2 * i + 1] = 0;
+    }
+    GW_CUDA(cudaMemcpyAsync(B.wcnt.p, B.hwcnt, sizeof(int) * 2 * nl, cudaMemcpyHostToDevice, B.st));
+    batch_enqueue_iteration(B, B.st);
+    GW_CUDA(cudaStreamSynchronize(B.st));
+    cudaGraph_t g = nullptr;
+    {
+        CaptureScope scope;
+        GW_CUDA(cudaStreamBeginCapture(B.cap, cudaStreamCaptureModeThreadLocal));
+        try {
+            batch_enqueue_iteration(B, B.cap);
+        } catch (...) {
+            cudaStreamEndCapture(B.cap, &g);
+            if (g) cudaGraphDestroy(g);
+            throw;
+        }
+        GW_CUDA(cudaStreamEndCapture(B.cap, &g));
+    }
+    cudaError_t e = cudaGraphInstantiate(&B.g, g, 0);
+    if (e == cudaSuccess) B.iter_kernels = (long long)kernel_nodes(g);
+    cudaGraphDestroy(g);
+    GW_CUDA(e);
+    B.graph_lmax = lmax;
+    batch_rebuild_work(B);
+}
+
+Batch *batch_create(int max_slots)
+{
+    if (max_slots < 1 || max_slots > 256) fail(GW_ERR_ARG, "gw_batch_create: max_slots must be in 1..256");
+    std::unique_ptr<Batch> B(new Batch);
+    B->max_slots = max_slots;
+    GW_CUDA(cudaGetDevice(&B->dev));
+    GW_CUDA(cudaStreamCreateWithFlags(&B->st, cudaStreamNonBlocking));
+    GW_CUDA(cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking));
+    B->slot_h.assign((size_t)max_slots, nullptr);
+    B->state.assign((size_t)max_slots, 0);
+    B->hslots.resize((size_t)max_slots);
+    memset(B->hslots.data(), 0, sizeof(BSlot) * (size_t)max_slots);
+    B->dslots.alloc((size_t)max_slots);
+    B->dsum.alloc((size_t)max_slots);
+    GW_CUDA(host_malloc((void **)&B->hsum, sizeof(BSum) * (size_t)max_slots));
+    GW_CUDA(host_malloc((void **)&B->hstage, sizeof(BSlot) * (size_t)max_slots));
+    memcpy(B->hstage, B->hslots.data(), sizeof(BSlot) * (size_t)max_slots);
+    GW_CUDA(cudaMemcpyAsync(B->dslots.p, B->hstage, sizeof(BSlot) * (size_t)max_slots, cudaMemcpyHostToDevice, B->st));
+    GW_CUDA(cudaStreamSynchronize(B->st));
+    return B.release();
+}
+
+void batch_free(Batch *B)
+{
+    if (!B) return;
+    cudaStreamSynchronize(B->st);
+    for (Hier *H : B->slot_h)
+        if (H) H->batch = nullptr;  // solves not taken are abandoned; their hierarchies stay usable
+    delete B;
+}
+
+static void batch_upload_slots(Batch &B)
+{
+    memcpy(B.hstage, B.hslots.data(), sizeof(BSlot) * (size_t)B.max_slots);
+    GW_CUDA(cudaMemcpyAsync(B.dslots.p, B.hstage, sizeof(BSlot) * (size_t)B.max_slots, cudaMemcpyHostToDevice, B.st));
+}
+
+// Why a hierarchy cannot join a batch (nullptr: it can).
+static const char *batch_unsupported(const Hier &H, int degree)
+{
+    if (H.o.prec != GW_PREC_MIXED32 || H.o.half_storage) return "batched solves run the mixed form with FP32 storage";
+    if (H.o.smoother != GW_SMOOTH_CHEBYSHEV || H.o.nu != 1 || H.o.degree < 2)
+        return "batched solves run Chebyshev smoothing of degree >= 2 with nu = 1";
+    if (degree && H.o.degree != degree) return "every solve of a batch has the same Chebyshev degree";
+    if (H.L < 2 || H.L > BATCH_MAXL) return "batched solves need 2 to 12 levels";
+    if (!H.p0.n) return "batched solves need the implicit level-0 transfer of a 7-point grid";
+    if (H.cf[0].A.fmt != FMT_STEN || cg_op32(H).fmt != FMT_STEN || H.A64.fmt != FMT_STEN)
+        return "batched solves need the level-0 stencil";
+    return nullptr;
+}
+
+int batch_add(Batch &B, Hier &H, const double *b, double tol, int maxit)
+{
+    if (const char *why = batch_unsupported(H, B.degree)) fail(GW_ERR_ARG, "gw_batch_add: %s", why);
+    if (H.dev != B.dev) fail(GW_ERR_ARG, "gw_batch_add: the hierarchy lives on another device");
+    for (int s = 0; s < B.max_slots; ++s)
+        if (B.slot_h[(size_t)s] == &H) fail(GW_ERR_ARG, "gw_batch_add: the hierarchy is already in this batch");
+    int slot = -1;
+    for (int s = 0; s < B.max_slots; ++s)
+        if (!B.state[(size_t)s]) {
+            slot = s;
+            break;
+        }
+    if (slot < 0) fail(GW_ERR_ARG, "gw_batch_add: every slot is in use");
+    B.degree = H.o.degree;
+    // the slot's description
+    BSlot S;
+    memset(&S, 0, sizeof S);
+    S.L = H.L;
+    S.active = 1;
+    for (int l = 0; l < H.L; ++l) {
+        CycLevel<float> &c = H.cf[(size_t)l];
+        BLev &v = S.lv[l];
+        v.n = c.n;
+        if (l < H.L - 1) {
+            v.A = bmat_of(c.A);
+            if (l >= 1) {
+                v.P = bmat_of(c.P);
+                v.R = bmat_of(c.R);
+            }
+        }
+        v.dw = c.dw.p;
+        v.x = c.x.p, v.b = c.b.p, v.r = c.r.p, v.t = c.t.p, v.d = c.d.p, v.d2 = c.d2.p;
+        v.c0 = (float)c.c0;
+        for (int k = 0; k < 8; ++k) {
+            v.c1[k] = (float)c.c1[k];
+            v.c2[k] = (float)c.c2[k];
+        }
+    }
+    S.A32 = bmat_of(cg_op32(H));
+    {
+        const StenT<double> &D = H.A64.sten;
+        S.ad = D.d.p, S.ax = D.ox.p, S.ay = D.oy.p, S.az = D.oz.p;
+        constexpr int RV = sten_r<double>(), RH = RV / 2;
+        S.a64r = (D.n % RV == 0 && D.nx % RV == 0) ? RV : (D.n % RH == 0 && D.nx % RH == 0) ? RH : 1;
+    }
+    {
+        const ImplP &I = H.p0;
+        S.p0 = PImpl{I.agg, I.s.p, I.fx.p, I.fy.p, I.fz.p, I.n, I.nx, I.sxy, I.w0};
+        S.p0r = (I.n % 4 == 0 && I.nx % 4 == 0) ? 4 : 1;
+        S.mptr = I.mptr.p;
+        S.mem = I.mem.p;
+        S.nc0 = I.nc;
+    }
+    S.Ainv = H.Ainv.p;
+    S.xs = H.xs32.p, S.r32 = H.r32.p, S.p32 = H.p32.p, S.p32b = H.p32b.p, S.q32 = H.q32.p, S.z32 = H.z32.p;
+    S.x = H.x.p, S.b = H.b.p;
+    S.part = H.part.p;
+    S.ctl = H.ctl.p;
+    // the right-hand side and the start of the solve (x = 0, r = b, the first V-cycle)
+    GW_CUDA(cudaMemcpyAsync(H.b.p, b, (size_t)H.n * sizeof(double), cudaMemcpyDefault, B.st));
+    Ctl init;
+    memset(&init, 0, sizeof init);
+    init.tol2 = tol * tol;
+    init.maxit = maxit;
+    init.flexible = 1;
+    init.delta2 = H.o.delta * H.o.delta;
+    init.cond = 0;
+    *H.ctl_host = init;
+    GW_CUDA(cudaMemcpyAsync(H.ctl.p, H.ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, B.st));
+    cg_start(H, B.st);
+    H.launches += H.init_kernels;
+    B.slot_h[(size_t)slot] = &H;
+    B.state[(size_t)slot] = 1;
+    H.batch = &B;
+    B.hslots[(size_t)slot] = S;
+    B.lmax = std::max(B.lmax, H.L);
+    batch_upload_slots(B);
+    if (!B.g || B.graph_lmax < B.lmax) batch_capture(B, B.lmax);
+    else batch_rebuild_work(B);
+    GW_CUDA(cudaStreamSynchronize(B.st));  // the staging buffers are reused by the next call
+    return slot;
+}
+
+// Replays the iteration graph up to `iterations` times, stopping early once
+// some running solve has finished; returns the number of finished solves
+// waiting to be taken.
+int batch_run(Batch &B, int iterations)
+{
+    int running = 0;
+    for (int s = 0; s < B.max_slots; ++s) running += B.state[(size_t)s] == 1;
+    for (int k = 0; k < iterations && running && B.g; ++k) {
+        GW_CUDA(cudaGraphLaunch(B.g, B.st));
+        B.launches_run += B.iter_kernels;
+        GW_CUDA(cudaStreamSynchronize(B.st));
+        bool any = false;
+        for (int s = 0; s < B.max_slots; ++s)
+            if (B.state[(size_t)s] == 1 && B.hsum[s].done) {
+                B.state[(size_t)s] = 2;
+                any = true;
+            }
+        if (any) break;
+    }
+    int fin = 0;
+    for (int s = 0; s < B.max_slots; ++s) fin += B.state[(size_t)s] == 2;
+    return fin;
+}
+
+int batch_state(const Batch &B, int slot) { return slot >= 0 && slot < B.max_slots ? B.state[(size_t)slot] : -1; }
+
+// Takes a finished solve out of the batch: its heads into h (host or device),
+// its iterations and true relative residual; frees the slot.
+int batch_take(Batch &B, int slot, double *h, int *iters, double *relres)
+{
+    if (slot < 0 || slot >= B.max_slots || B.state[(size_t)slot] != 2)
+        fail(GW_ERR_ARG, "gw_batch_take: slot %d holds no finished solve", slot);
+    Hier &H = *B.slot_h[(size_t)slot];
+    Ctl *c = H.ctl.p;
+    GW_CUDA(cudaMemcpyAsync(H.ctl_host, c, sizeof(Ctl), cudaMemcpyDeviceToHost, B.st));
+    GW_CUDA(cudaStreamSynchronize(B.st));
+    if (H.ctl_host->status == GW_ERR_NOT_CONVERGED || !H.ctl_host->done) {
+        rel_update(H, 1, B.st);  // fold the correction in and state the true residual
+        GW_LAUNCH_CHECK();
+        GW_CUDA(cudaMemcpyAsync(H.ctl_host, c, sizeof(Ctl), cudaMemcpyDeviceToHost, B.st));
+        GW_CUDA(cudaStreamSynchronize(B.st));
+        if (!H.ctl_host->done) H.ctl_host->status = GW_ERR_NOT_CONVERGED;
+    }
+    if (h) GW_CUDA(cudaMemcpyAsync(h, H.x.p, (size_t)H.n * sizeof(double), cudaMemcpyDefault, B.st));
+    const int status = H.ctl_host->status;
+    if (iters) *iters = H.ctl_host->it;
+    if (relres) *relres = H.ctl_host->relres;
+    H.solves += 1;
+    memset(&B.hslots[(size_t)slot], 0, sizeof(BSlot));
+    H.batch = nullptr;
+    B.slot_h[(size_t)slot] = nullptr;
+    B.state[(size_t)slot] = 0;
+    B.lmax = 0;
+    for (int s = 0; s < B.max_slots; ++s)
+        if (B.state[(size_t)s]) B.lmax = std::max(B.lmax, B.hslots[(size_t)s].L);
+    batch_upload_slots(B);
+    batch_rebuild_work(B);
+    GW_CUDA(cudaStreamSynchronize(B.st));
+    return status;
+}
+
+long long batch_kernel_launches(const Batch &B) { return B.launches_run; }
+
+// A hierarchy that is freed while its solve is in the batch leaves it.
+void batch_forget(Batch &B, Hier *H)
+{
+    for (int s = 0; s < B.max_slots; ++s)
+        if (B.slot_h[(size_t)s] == H) {
+            cudaStreamSynchronize(B.st);
+            memset(&B.hslots[(size_t)s], 0, sizeof(BSlot));
+            B.slot_h[(size_t)s] = nullptr;
+            B.state[(size_t)s] = 0;
+            try {
+                batch_upload_slots(B);
+                batch_rebuild_work(B);
+                GW_CUDA(cudaStreamSynchronize(B.st));
+            } catch (...) {
+            }
+        }
+    H->batch = nullptr;
 }
 
 }  // namespace gw

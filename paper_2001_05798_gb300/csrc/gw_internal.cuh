@@ -362,6 +362,7 @@ struct Hier {
     long long prof_cnt[GW_PK_COUNT] = {0};
     long long launches = 0, solves = 0;
     BlockState *blk = nullptr;  // created by the first interleaved solve
+    void *batch = nullptr;      // the batch that holds this hierarchy's solve (cycle.cu), if any
     ~Hier();
 };
 
@@ -382,6 +383,18 @@ bool block_supported(const Hier &H);
 int block_solve(Hier &H, int k, const double *B, double *X, double tol, int maxit, int *iters, double *relres,
                 cudaStream_t st);
 void block_drop_graphs(BlockState *s);
+
+// Batched solves (cycle.cu): the same pass of several hierarchies' solves in
+// one launch, one captured iteration graph replayed for all of them.
+struct Batch;
+Batch *batch_create(int max_slots);
+void batch_free(Batch *B);
+int batch_add(Batch &B, Hier &H, const double *b, double tol, int maxit);  // returns the slot
+int batch_run(Batch &B, int iterations);                                   // finished solves waiting
+int batch_state(const Batch &B, int slot);                                 // 0 free, 1 running, 2 finished
+int batch_take(Batch &B, int slot, double *h, int *iters, double *relres);  // the solve's status
+long long batch_kernel_launches(const Batch &B);
+void batch_forget(Batch &B, Hier *H);
 void block_free(BlockState *s);
 
 }  // namespace gw

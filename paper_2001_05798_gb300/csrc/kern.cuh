@@ -38,6 +38,15 @@ static inline int wave_grid(const void *fn, int blocks)
 
 #define ROWS(i, n) for (int i = blockIdx.x * BS + threadIdx.x; i < (n); i += gridDim.x * BS)
 
+// The block index and block count a kernel body works with: the launch's own
+// grid, or, in a batched launch that runs one pass for several solves, the
+// virtual grid of one solve (each solve keeps its own row partition and
+// reduction order, so its results do not depend on what else runs).
+struct VB {
+    int bid, nb;
+};
+__device__ __forceinline__ VB vb_grid() { return VB{(int)blockIdx.x, (int)gridDim.x}; }
+
 // Programmatic dependent launch: every kernel of the cycle and of CG is
 // launched so that the next kernel in the stream may be scheduled while this
 // one runs; each kernel waits for its predecessors to complete (and their
@@ -93,7 +102,8 @@ __device__ __forceinline__ double block_sum(double v, double *sh)
 // Writes this block's partial sums; returns true in the last block to arrive,
 // which then holds the grand totals (summed over blocks in index order) in tot[].
 template <int K>
-__device__ __forceinline__ bool reduce_last(const double (&loc)[K], double *part, unsigned *cnt, double (&tot)[K])
+__device__ __forceinline__ bool reduce_last(VB vb, const double (&loc)[K], double *part, unsigned *cnt,
+                                            double (&tot)[K])
 {
     constexpr int W = BS / 32;
     __shared__ double sh[K][W];
@@ -110,19 +120,19 @@ __device__ __forceinline__ bool reduce_last(const double (&loc)[K], double *part
         double s = 0.0;
 #pragma unroll
         for (int q = 0; q < W; ++q) s += sh[threadIdx.x][q];
-        part[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = s;
+        part[(size_t)threadIdx.x * vb.nb + vb.bid] = s;
         __threadfence();
     }
     __syncthreads();
     if (threadIdx.x == 0) ticket = atomicAdd(cnt, 1u);
     __syncthreads();
-    if (ticket != gridDim.x - 1) return false;
+    if (ticket != (unsigned)vb.nb - 1) return false;
     __threadfence();
     // last block: warp k adds the partials of value k, lanes strided, in a fixed order
     __shared__ double fin[K];
     for (int k = w; k < K; k += W) {
         double s = 0.0;
-        for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(part + (size_t)k * gridDim.x + b);
+        for (int b = lane; b < vb.nb; b += 32) s += __ldcg(part + (size_t)k * vb.nb + b);
         s = warp_sum(s);
         if (lane == 0) fin[k] = s;
     }
@@ -131,6 +141,12 @@ __device__ __forceinline__ bool reduce_last(const double (&loc)[K], double *part
 #pragma unroll
     for (int k = 0; k < K; ++k) tot[k] = fin[k];
     return true;
+}
+
+template <int K>
+__device__ __forceinline__ bool reduce_last(const double (&loc)[K], double *part, unsigned *cnt, double (&tot)[K])
+{
+    return reduce_last<K>(vb_grid(), loc, part, cnt, tot);
 }
 
 __device__ __forceinline__ bool finished(const Ctl *c) { return c && *(volatile const int *)&c->done; }

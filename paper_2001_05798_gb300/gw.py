@@ -24,7 +24,8 @@ EXPORTS = ("gw_amg_opts_default", "gw_assemble", "gw_matrix_size", "gw_matrix_ex
            "gw_pcg_solve", "gw_vcycle", "gw_hierarchy_info", "gw_hierarchy_export", "gw_matrix_free",
            "gw_hierarchy_free", "gw_status_str", "gw_last_error", "gw_profile_enable", "gw_profile_read",
            "gw_assemble_noalloc", "gw_adjoint_gradient", "gw_misfit", "gw_hierarchy_shift",
-           "gw_pcg_solve_many", "gw_darcy_flux", "gw_hierarchy_prepare", "gw_device_allocations")
+           "gw_pcg_solve_many", "gw_darcy_flux", "gw_hierarchy_prepare", "gw_device_allocations",
+           "gw_batch_create", "gw_batch_add", "gw_batch_run", "gw_batch_state", "gw_batch_take", "gw_batch_free")
 
 PK_NAMES = ("spmv", "update", "pre1", "pre2", "resid", "restrict", "l1down", "deep", "l1up", "prolong", "post1",
             "post2", "pupdate")
@@ -100,6 +101,12 @@ def load():
         "gw_hierarchy_prepare": (i, [vp]),
         "gw_darcy_flux": (i, [P(gw_grid), vp, vp, vp, P(gw_bc), vp, vp, vp, vp, vp]),
         "gw_device_allocations": (ll, []),
+        "gw_batch_create": (i, [i, P(vp)]),
+        "gw_batch_add": (i, [vp, vp, vp, d, i, P(i)]),
+        "gw_batch_run": (i, [vp, i, P(i)]),
+        "gw_batch_state": (i, [vp, i, P(i)]),
+        "gw_batch_take": (i, [vp, i, vp, P(i), P(d)]),
+        "gw_batch_free": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -349,3 +356,62 @@ def solve(nx, ny, nz, Kx, Ky=None, Kz=None, bct=(1, 1, 0, 0, 0, 0), bcv=(1.0, 0.
     h, it, rel, st = H.solve(b, tol=tol, maxit=maxit)
     _check(st)
     return h, it, rel
+
+
+class Batch:
+    """Batched solves on resident hierarchies (include/gw.h: gw_batch_*).
+
+    add() starts a solve in a free slot, run() replays the batched iteration
+    graph, take() returns a finished solve's heads.  Hierarchies added are
+    kept alive by the batch until their solve is taken."""
+
+    def __init__(self, max_slots=8):
+        h = ctypes.c_void_p()
+        _check(load().gw_batch_create(int(max_slots), ctypes.byref(h)))
+        self.h = h
+        self.max_slots = max_slots
+        self.held = {}
+
+    def add(self, H, b, tol=1e-8, maxit=500):
+        s = ctypes.c_int()
+        _check(load().gw_batch_add(self.h, H.h, _ptr(b), float(tol), int(maxit), ctypes.byref(s)))
+        self.held[s.value] = H
+        return s.value
+
+    def run(self, iterations=1):
+        f = ctypes.c_int()
+        _check(load().gw_batch_run(self.h, int(iterations), ctypes.byref(f)))
+        return f.value
+
+    def state(self, slot):
+        st = ctypes.c_int()
+        _check(load().gw_batch_state(self.h, int(slot), ctypes.byref(st)))
+        return st.value
+
+    def finished(self):
+        return [s for s in list(self.held) if self.state(s) == 2]
+
+    def take(self, slot, h=None):
+        """Returns (h, iters, relres, status) of the finished solve in slot
+        (h: a device or host array of n doubles)."""
+        if self.state(slot) != 2:
+            raise GwError(GW_ERR_ARG, "slot %d holds no finished solve" % slot)
+        it, rel = ctypes.c_int(), ctypes.c_double()
+        st = load().gw_batch_take(self.h, int(slot), _ptr(h), ctypes.byref(it), ctypes.byref(rel))
+        self.held.pop(slot, None)
+        if st not in (GW_OK, GW_ERR_NOT_CONVERGED):
+            _check(st)
+        return h, it.value, rel.value, st
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().gw_batch_free(self.h)
+            self.h = None
+        self.held.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

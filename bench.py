@@ -594,7 +594,10 @@ def run_serve(args):
     gw.load()
     reqs = wl.serving_requests(count=args.requests, seed=4)
     warm = wl.serving_requests(count=8, seed=99)
-    srv = serve.Server(slots=args.slots, hbm_budget=120e9)
+    if args.serve_mode == "batched":
+        srv = serve.BatchedServer(slots=args.slots, setup_workers=args.setup_workers, hbm_budget=120e9)
+    else:
+        srv = serve.Server(slots=args.slots, hbm_budget=120e9)
     for f in [srv.submit(r) for r in warm]:
         f.result()
     # closed loop: everything queued at once
@@ -618,7 +621,8 @@ def run_serve(args):
     lat = np.array([o["latency_s"] for o in outs]) * 1e3
     out = {"metric": "serving stream of flow solves: solves/s and p50/p99 latency", "value": len(outs) / wall,
            "unit": "solves/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32 V-cycle + f64 CG",
-           "data": "synthetic", "requests": len(outs), "slots": args.slots,
+           "data": "synthetic", "requests": len(outs), "slots": args.slots, "mode": args.serve_mode,
+           "setup_workers": args.setup_workers if args.serve_mode == "batched" else None,
            "config": {"workload": "cubic grids side log-uniform [32,160], lnK var U[0.5,4], corr U[4,16], seed 4, "
                                   "field seed 1000+r, tol 1e-8, Poisson arrivals at 0.7 x closed-loop throughput, "
                                   "HBM budget 120 GB"},
@@ -643,7 +647,10 @@ def main():
                     help="half-precision fine stencil of the mixed form: 2 = BF16 couplings, 4 = scaled FP16")
     ap.add_argument("--side", type=int, default=SIDE, help="grid side for profiling captures (default 128)")
     ap.add_argument("--requests", type=int, default=2000, help="serving workload: number of requests")
-    ap.add_argument("--slots", type=int, default=6, help="serving workload: solves in flight")
+    ap.add_argument("--slots", type=int, default=16, help="serving workload: solves in flight")
+    ap.add_argument("--serve-mode", choices=("batched", "streams"), default="batched",
+                    help="serving workload: batched launches over a slot table, or one stream and graph per slot")
+    ap.add_argument("--setup-workers", type=int, default=6, help="serving workload, batched: concurrent setups")
     ap.add_argument("--workload", choices=("solve", "adjoint", "transient", "serve", "many", "layered"), default="solve",
                     help="solve: the 128^3 benchmark (default); adjoint: the 96^3 sensitivity case; "
                          "transient: implicit steps with a cached hierarchy; serve: the request stream; "

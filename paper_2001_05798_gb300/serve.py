@@ -118,6 +118,8 @@ class Server:
     def _admit(self):
         # called with the lock held: the oldest request, if it fits
         while True:
+            while self.pending and self.pending[0][1].cancelled():  # cancelled while waiting: dropped
+                self.pending.popleft()
             if self.pending:
                 req, fut, arr = self.pending[0]
                 need = self.estimate(req)
@@ -127,6 +129,8 @@ class Server:
                     continue
                 if self.in_use + need <= self.budget:
                     self.pending.popleft()
+                    if not fut.set_running_or_notify_cancel():
+                        continue
                     self.in_use += need
                     self.inflight += 1
                     self.peak_in_use = max(self.peak_in_use, self.in_use)
@@ -198,3 +202,183 @@ class Server:
         finally:
             gate.release_shared()
         return dict(id=req.get("id"), n=n, h=h, iters=it, relres=rel, setup_s=t1 - t0, solve_s=t2 - t1)
+
+
+class BatchedServer:
+    """Continuous batching with batched launches.
+
+    Setup workers (each on its own stream) draw a request's field, assemble
+    it and set up its hierarchy; a finished setup waits in a ready queue.  One
+    batch thread admits ready solves into free slots of a gw_batch, replays
+    the batched CG iteration (one launch per pass for every solve in flight)
+    and hands finished solves back, so requests of different sizes share
+    every launch of the iteration.  Admission to setup is FIFO by the HBM
+    budget, as in Server; a request holds its budget from the start of its
+    setup to the end of its solve.  A request whose future is cancelled while
+    it still waits is dropped at admission (a running one can no longer be
+    cancelled).  Results are the same bit for bit as the request's solve alone
+    in a batch."""
+
+    def __init__(self, slots=8, setup_workers=4, hbm_budget=120e9, device=0, tol=1e-8, maxit=500,
+                 bytes_per_cell=1500.0, iterations_per_step=2, **opts):
+        self.slots = slots
+        self.budget = float(hbm_budget)
+        self.device = device
+        self.tol, self.maxit, self.opts = tol, maxit, opts
+        self.bytes_per_cell = float(bytes_per_cell)
+        self.k = iterations_per_step
+        self.in_use = 0.0
+        self.pending = collections.deque()
+        self.ready = collections.deque()
+        self.cv = threading.Condition()
+        self.closed = False
+        self.peak_in_use = 0.0
+        self.peak_inflight = 0
+        self.inflight = 0
+        self.capture_gate = _SharedExclusive()
+        torch.cuda.set_device(device)
+        self.batch = gw.Batch(slots)
+        self.setups = [threading.Thread(target=self._setup_worker, daemon=True) for _ in range(setup_workers)]
+        self.runner = threading.Thread(target=self._batch_loop, daemon=True)
+        for t in self.setups:
+            t.start()
+        self.runner.start()
+
+    def estimate(self, req):
+        return self.bytes_per_cell * req["side"] ** 3
+
+    def submit(self, req, arrival=None):
+        fut = concurrent.futures.Future()
+        with self.cv:
+            if self.estimate(req) > self.budget:
+                fut.set_exception(MemoryError("request %s needs more than the HBM budget" % req.get("id")))
+                return fut
+            self.pending.append((req, fut, time.perf_counter() if arrival is None else arrival))
+            self.cv.notify_all()
+        return fut
+
+    def close(self):
+        with self.cv:
+            self.closed = True
+            self.cv.notify_all()
+        for t in self.setups:
+            t.join()
+        self.runner.join()
+        self.batch.close()
+
+    def _release(self, need):
+        with self.cv:
+            self.in_use -= need
+            self.inflight -= 1
+            self.cv.notify_all()
+
+    def _admit_setup(self):
+        # with the lock held: the oldest request, if it fits the budget
+        while True:
+            while self.pending and self.pending[0][1].cancelled():
+                self.pending.popleft()
+            if self.pending:
+                req, fut, arr = self.pending[0]
+                need = self.estimate(req)
+                if need > self.budget:
+                    self.pending.popleft()
+                    fut.set_exception(MemoryError("request %s needs more than the HBM budget" % req.get("id")))
+                    continue
+                if self.in_use + need <= self.budget:
+                    self.pending.popleft()
+                    if not fut.set_running_or_notify_cancel():
+                        continue
+                    self.in_use += need
+                    self.inflight += 1
+                    self.peak_in_use = max(self.peak_in_use, self.in_use)
+                    self.peak_inflight = max(self.peak_inflight, self.inflight)
+                    return req, fut, arr, need
+            elif self.closed:
+                return None
+            self.cv.wait()
+
+    def _setup_worker(self):
+        torch.cuda.set_device(self.device)
+        stream = torch.cuda.Stream()
+        while True:
+            with self.cv:
+                item = self._admit_setup()
+            if item is None:
+                return
+            req, fut, arrival, need = item
+            try:
+                s = req["side"]
+                n = s ** 3
+                t0 = time.perf_counter()
+                self.capture_gate.acquire_shared()
+                try:
+                    with torch.cuda.stream(stream):
+                        if "K" in req:
+                            K = req["K"]
+                        else:
+                            K = torch.exp(wl.lnk_field_device(s, s, s, req["var"], req["corr"], req["seed"],
+                                                              pad=FIELD_PAD))
+                        b = torch.empty(n, dtype=torch.float64, device=K.device)
+                        A, _ = gw.gw_assemble(s, s, s, K, K, K, (1, 1, 0, 0, 0, 0), (1.0, 0.0, 0, 0, 0, 0), None,
+                                              b_out=b, stream=stream)
+                        H = gw.Hierarchy(A, stream=stream, **self.opts)
+                        h = torch.empty_like(b)
+                    stream.synchronize()
+                finally:
+                    self.capture_gate.release_shared()
+                used = sum(l["bytes"] for l in H.info()) + 16 * n
+                with self.cv:
+                    self.bytes_per_cell = max(self.bytes_per_cell, 1.25 * used / n)
+                    self.ready.append(dict(req=req, fut=fut, arrival=arrival, need=need, H=H, A=A, b=b, h=h, n=n,
+                                           setup_s=time.perf_counter() - t0))
+                    self.cv.notify_all()
+            except Exception as e:  # the request fails alone
+                fut.set_exception(e)
+                self._release(need)
+
+    def _finish(self, job, slot):
+        _, it, rel, st = self.batch.take(slot, job["h"])
+        torch.cuda.synchronize()
+        done = time.perf_counter()
+        self.capture_gate.acquire_shared()
+        try:
+            del job["H"], job["A"]
+        finally:
+            self.capture_gate.release_shared()
+        if st != gw.GW_OK:
+            job["fut"].set_exception(gw.GwError(st, "request %s: relres %.3e after %d iterations"
+                                                % (job["req"].get("id"), rel, it)))
+        else:
+            job["fut"].set_result(dict(id=job["req"].get("id"), n=job["n"], h=job["h"], iters=it, relres=rel,
+                                       setup_s=job["setup_s"], solve_s=done - job["start"], arrival=job["arrival"],
+                                       done=done, latency_s=done - job["arrival"]))
+        self._release(job["need"])
+
+    def _batch_loop(self):
+        torch.cuda.set_device(self.device)
+        running = {}  # slot -> job
+        while True:
+            with self.cv:
+                while not self.ready and not running and not (self.closed and not self.inflight):
+                    self.cv.wait()
+                if self.closed and not self.inflight and not self.ready and not running:
+                    return
+                joining = []
+                while self.ready and len(running) + len(joining) < self.slots:
+                    joining.append(self.ready.popleft())
+            for job in joining:
+                self.capture_gate.acquire_exclusive()  # an add may capture the batched graph
+                try:
+                    slot = self.batch.add(job["H"], job["b"], tol=self.tol, maxit=self.maxit)
+                except Exception as e:
+                    job["fut"].set_exception(e)
+                    self._release(job["need"])
+                    continue
+                finally:
+                    self.capture_gate.release_exclusive()
+                job["start"] = time.perf_counter()
+                running[slot] = job
+            if running:
+                self.batch.run(self.k)
+                for slot in [s for s in list(running) if self.batch.state(s) == 2]:
+                    self._finish(running.pop(slot), slot)

@@ -99,3 +99,34 @@ def test_prepare_then_solve_equals_plain_solve(serve):
     h2, it2, rel2, st2 = H2.solve(bd, tol=1e-9)
     assert st1 == st2 == gw.GW_OK and it1 == it2 and rel1 == rel2
     assert torch.equal(h1, h2)
+
+
+def test_batched_server_alone_and_in_the_mix_agree(serve):
+    """The batched server: every launch of the iteration covers all solves in
+    flight; each result is the same bit for bit served alone or in the mix."""
+    from paper_2001_05798_gb300 import workload as wl
+
+    reqs = wl.serving_requests(count=8, seed=12, side_range=(16, 40))
+    s1 = serve.BatchedServer(slots=1, setup_workers=1, n_coarse=200)
+    try:
+        alone = {r["id"]: s1.submit(r).result(timeout=300) for r in reqs}
+    finally:
+        s1.close()
+    s4 = serve.BatchedServer(slots=4, setup_workers=3, n_coarse=200)
+    try:
+        futs = [s4.submit(r) for r in reqs]
+        mixed = {f.result(timeout=300)["id"]: f.result() for f in futs}
+    finally:
+        s4.close()
+    assert s4.peak_inflight >= 2
+    for r in reqs:
+        a, m = alone[r["id"]], mixed[r["id"]]
+        assert a["iters"] == m["iters"] and a["relres"] <= 1e-8
+        assert torch.equal(a["h"], m["h"])
+    r = reqs[1]
+    s = r["side"]
+    K = torch.exp(wl.lnk_field_device(s, s, s, r["var"], r["corr"], r["seed"], pad=serve.FIELD_PAD)).cpu().numpy()
+    A, b = oracle.assemble(s, s, s, K)
+    href, _, _, _ = oracle.Hierarchy(A, n_coarse=200).pcg(b, tol=1e-12)
+    h = mixed[r["id"]]["h"].cpu().numpy()
+    assert np.linalg.norm(h - href) <= 1e-6 * np.linalg.norm(href)

@@ -113,3 +113,36 @@ def test_waiting_exclusive_is_not_starved(gate_cls):
     for t in ts + [c]:
         t.join()
     assert ok
+
+
+@pytest.mark.parametrize("cls_name", ["Server", "BatchedServer"])
+def test_cancelled_requests_are_dropped_at_admission(cls_name):
+    """A request whose future is cancelled while it waits never takes budget
+    or a slot; the requests around it are admitted in order."""
+    import collections
+    import concurrent.futures
+
+    from paper_2001_05798_gb300 import serve
+
+    cls = getattr(serve, cls_name)
+    s = cls.__new__(cls)  # the admission logic only, without devices or threads
+    s.cv = threading.Condition()
+    s.pending = collections.deque()
+    s.budget, s.in_use, s.bytes_per_cell = 1e12, 0.0, 1.0
+    s.inflight = s.peak_inflight = 0
+    s.peak_in_use = 0.0
+    s.closed = False
+    futs = [concurrent.futures.Future() for _ in range(4)]
+    for k, f in enumerate(futs):
+        s.pending.append(({"id": k, "side": 4}, f, 0.0))
+    assert futs[1].cancel() and futs[2].cancel()
+    admit = s._admit if cls_name == "Server" else s._admit_setup
+    with s.cv:
+        a = admit()
+        b = admit()
+    assert [a[0]["id"], b[0]["id"]] == [0, 3]
+    assert futs[0].running() and futs[3].running()
+    assert s.inflight == 2 and s.in_use == 2 * 64.0 and not s.pending
+    s.closed = True
+    with s.cv:
+        assert admit() is None

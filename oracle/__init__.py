@@ -85,6 +85,7 @@ def _load():
         "or_shift_csr": (_vp, [_vp, _f64p]),
         "or_reuse_ok": (ctypes.c_int, [_vp, _f64p, _vp, ctypes.c_double]),
         "or_h_refresh_level0": (None, [_vp, _vp]),
+        "or_h_refresh_numeric": (None, [_vp, _vp]),
         "or_darcy_flux": (None, [ctypes.c_int] * 3 + [ctypes.c_double] * 3 + [_f64p] * 3 +
                           [_i32p, _f64p, _f64p, _f64p, _f64p, _f64p]),
         "or_cg_plain": (ctypes.c_int, [_vp, _f64p, _f64p, ctypes.c_double, ctypes.c_int,
@@ -268,6 +269,12 @@ class Hierarchy:
     def refresh_level0(self, A):
         """Keep the coarse levels; level 0 becomes A (with its smoother data redone)."""
         _load().or_h_refresh_level0(self.h, A.h)
+        self._A0 = A
+
+    def refresh_numeric(self, A):
+        """Keep the aggregates and prolongators; level 0 becomes A and every
+        coarse operator is formed again as P^T A P (same patterns)."""
+        _load().or_h_refresh_numeric(self.h, A.h)
         self._A0 = A
 
     def smooth(self, l, b, x, x0zero=False):

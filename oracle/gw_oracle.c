@@ -994,6 +994,40 @@ void or_h_refresh_level0(ohier *H, const ocsr *A)
     if (H->L > 1) smoother_setup(H, 0);
 }
 
+/*
+ * Numeric refresh of a cached hierarchy (Discussion: the preconditioner is
+ * reused while the storage term changes little): level 0 becomes A (C plus
+ * the storage diagonal, the same pattern), the aggregates and the smoothed
+ * prolongators P_l are kept, and every coarse operator is formed again by
+ * its Galerkin definition A_{l+1} = P_l^T (A_l P_l) from the new A_l; then
+ * the smoother data of every level and the coarsest LU are redone.  The
+ * pattern of each A_{l+1} does not change (A_l + diag keeps the pattern of
+ * A_l, whose diagonal is structural), so only values are replaced.
+ */
+void or_h_refresh_numeric(ohier *H, const ocsr *A)
+{
+    or_csr_free(H->A[0]);
+    H->A[0] = or_csr_from(A->nr, A->nc, A->rp, A->ci, A->v);
+    for (int l = 0; l + 1 < H->L; ++l) {
+        ocsr *AP = or_spgemm(H->A[l], H->P[l]);
+        ocsr *Ac = or_spgemm(H->R[l], AP);
+        or_csr_free(AP);
+        or_csr_free(H->A[l + 1]);
+        H->A[l + 1] = Ac;
+    }
+    for (int k = 0; k + 1 < H->L; ++k) {
+        free(H->dinv[k]);
+        H->dinv[k] = NULL;
+        smoother_setup(H, k);
+    }
+    ocsr *Ac = H->A[H->L - 1];
+    int nc = Ac->nr;
+    for (size_t i = 0; i < (size_t)nc * nc; ++i) H->lu[i] = 0.0;
+    for (int i = 0; i < nc; ++i)
+        for (int e = Ac->rp[i]; e < Ac->rp[i + 1]; ++e) H->lu[(size_t)i * nc + Ac->ci[e]] = Ac->v[e];
+    if (or_lu_factor(nc, H->lu, H->piv) != 0) H->status = OR_ERR_SETUP;
+}
+
 /* ---------------------------------------------------- Darcy face fluxes -- */
 /*
  * Darcy velocity on every face of the grid (staggered layout): vx has

@@ -622,3 +622,42 @@ def test_darcy_flux_balances_sources_per_cell():
     vz = vz.reshape(nz + 1, ny, nx)
     out = (vx[:, :, 1:] - vx[:, :, :-1]) + (vy[:, 1:, :] - vy[:, :-1, :]) + (vz[1:] - vz[:-1])
     np.testing.assert_allclose(out.ravel(), p["q"], atol=1e-10)
+
+
+def test_numeric_refresh_is_the_galerkin_product_on_kept_prolongators():
+    # the refreshed coarse operators are P^T A P of the shifted level above,
+    # with the prolongators of the original setup (dense products by numpy)
+    p = wl.problem(12, 11, 10, var=3.0, corr=3.0, seed=8)
+    C, b = asm(p)
+    d = np.diag(C.dense())
+    s = 0.02 * d * np.random.default_rng(6).random(C.nr)
+    H = oracle.Hierarchy(C, n_coarse=60)
+    L = H.nlevels
+    assert L >= 3
+    P = [H.P(l).dense() for l in range(L - 1)]
+    old = [H.A(l).dense() for l in range(L)]
+    pats = [tuple(a.copy() for a in H.A(l).arrays()[:2]) for l in range(L)]
+    A = oracle.shift(C, s)
+    H.refresh_numeric(A)
+    assert H.nlevels == L
+    new = [H.A(l).dense() for l in range(L)]
+    np.testing.assert_array_equal(new[0], C.dense() + np.diag(s))
+    for l in range(L - 1):
+        np.testing.assert_array_equal(H.P(l).dense(), P[l])
+        ref = P[l].T @ new[l] @ P[l]
+        assert np.abs(new[l + 1] - ref).max() <= 1e-13 * np.abs(ref).max()
+        rp, ci, _ = H.A(l + 1).arrays()
+        assert np.array_equal(rp, pats[l + 1][0]) and np.array_equal(ci, pats[l + 1][1])
+    # the change of level 1 is the Galerkin product of the storage diagonal
+    assert np.abs((new[1] - old[1]) - P[0].T @ np.diag(s) @ P[0]).max() <= 1e-12 * np.abs(old[1]).max()
+    # with no shift the refresh reproduces the original operators bit for bit
+    H2 = oracle.Hierarchy(C, n_coarse=60)
+    H2.refresh_numeric(C)
+    for l in range(L):
+        np.testing.assert_array_equal(H2.A(l).dense(), old[l])
+    # and the refreshed hierarchy solves the shifted system
+    rhs = b + s
+    x, it, rel, st = H.pcg(rhs, tol=1e-12)
+    assert st == 0 and rel <= 1e-12
+    ref = np.linalg.solve(A.dense(), rhs)
+    assert np.linalg.norm(x - ref) <= 1e-10 * np.linalg.norm(ref)

@@ -260,11 +260,17 @@ int gw_pcg_solve(gw_hierarchy H, const double *b, double *h, double tol, int max
 /*
  * gw_hierarchy_shift -- the implicit transient form (Eq. 2): the hierarchy
  * set up from C now solves (C + diag(s)) h = b, s_i = S_i V_i / dt (s NULL:
- * back to C).  The cached hierarchy is reused while the diagonal moved by less
- * than delta C_ii in every row since the coarse levels were built,
- * |s_i - s_built_i| < delta C_ii, the criterion of the Discussion section
- * with delta about 0.01: then only level 0 (its operator and smoother data) is
- * refreshed and *rebuilt = 0.  Otherwise the whole hierarchy is set up again
+ * back to C).  The cached aggregates and prolongators are reused while the
+ * diagonal moved by less than delta C_ii in every row since they were built,
+ * |s_i - s_built_i| < delta C_ii, the criterion of the Discussion section with
+ * delta about 0.01.  Reused, the coarse operators formed with an earlier
+ * shift s_ref are kept when every |s_i - s_ref_i| <= s_ref_i / 4 (their
+ * storage part P^T diag(s) P then stays within a factor 3/4 to 5/4 of the one
+ * they hold): only level 0 is refreshed and *rebuilt = 0.  Otherwise every
+ * coarse operator is formed again as P^T A P of the shifted level above on the
+ * kept prolongators (the same values as a setup would compute on those
+ * prolongators), with its smoother data and the coarsest inverse, and
+ * *rebuilt = 2.  When the criterion fails the whole hierarchy is set up again
  * for C + diag(s) and *rebuilt = 1.
  *   s       n doubles (host or device), s_i >= 0, or NULL.
  *   delta   in (0, 1).

@@ -2,8 +2,11 @@
 #include <math.h>
 #include <string.h>
 
+#include <stdlib.h>
+
 #include <memory>
 #include <new>
+
 
 #include "gw_internal.cuh"
 
@@ -19,6 +22,7 @@ struct gw_hierarchy_s {
     gw::DCSR shifted;           // C + diag(s) while a transient shift is applied
     gw::DBuf<double> s_built;   // shift the coarse levels were built with (empty: none)
     gw::DBuf<double> s_now;     // shift now applied (empty: none)
+    gw::DBuf<double> s_ref;     // shift the coarse operators were last formed with (empty: none)
 };
 
 namespace gw {
@@ -183,19 +187,159 @@ void refresh_level0(Hier &H, const DCSR &A, cudaStream_t st)
     GW_CUDA(cudaStreamSynchronize(st));
 }
 
+void refresh_numeric(Hier &H, const DCSR &A, cudaStream_t st)
+{
+    H.A0 = &A;
+    const int L = H.L;
+    for (int l = 0; l + 1 < L; ++l) {
+        const DCSR &Al = l == 0 ? A : H.A[(size_t)l];
+        DCSR AP, Ac;
+        setup_spgemm(Al, H.P[(size_t)l], AP, st);
+        setup_spgemm(H.R[(size_t)l], AP, Ac, st);
+        if (Ac.nnz != H.A[(size_t)l + 1].nnz) fail(GW_ERR_SETUP, "refresh: the pattern of level %d changed", l + 1);
+        H.A[(size_t)l + 1] = std::move(Ac);
+    }
+    for (int l = 0; l + 1 < L; ++l) store_level(H, l, l == 0 ? A : H.A[(size_t)l], nullptr, nullptr, st);
+    setup_dense_inverse(H.A[(size_t)L - 1], H.Ainv, st);
+    if (H.o.prec != GW_PREC_FP64) to_store<double>(A, H.A64, FMT_STEN, H.gnx, H.gny, H.gnz, st);
+    drop_graphs(H);
+    GW_CUDA(cudaStreamSynchronize(st));
+}
+
+// ------------------------------------------------------ hierarchy checks --
+// Every setup scans the stored hierarchy for non-finite values (a coarse
+// operator, a prolongator, the coarsest inverse), so that a bad input or a
+// breakdown in the setup is reported there, not as a stalled solve.  With the
+// environment variable GW_VALIDATE=1 it also checks every index array the
+// cycle kernels gather through (CSR row pointers and columns of all levels,
+// the sliced-ELL columns, the implicit level-0 transfer's aggregate and
+// member lists) against its bounds.  The checks count violations on the
+// device and report them as GW_ERR_SETUP; nothing asserts on the GPU.
+__global__ void k_nonfinite(long long n, const double *__restrict__ v, int *__restrict__ bad)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        if (!isfinite(v[i])) atomicAdd(bad, 1);
+}
+
+__global__ void k_check_csr(int nr, int nc, long long nnz, const int *__restrict__ rp, const int *__restrict__ ci,
+                            int *__restrict__ bad)
+{
+    for (long long ii = blockIdx.x * (long long)blockDim.x + threadIdx.x; ii < nr; ii += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)ii;
+        const int a = rp[i], b = rp[i + 1];
+        if (a < 0 || b < a || b > nnz || (i == 0 && a != 0) || (i == nr - 1 && b != nnz)) {
+            atomicAdd(bad, 1);
+            continue;
+        }
+        for (int e = a; e < b; ++e)
+            if (ci[e] < 0 || ci[e] >= nc || (e > a && ci[e] <= ci[e - 1])) atomicAdd(bad, 1);
+    }
+}
+
+__global__ void k_check_range(long long n, const int *__restrict__ x, int lo, int hi, int *__restrict__ bad)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        if (x[i] < lo || x[i] >= hi) atomicAdd(bad, 1);
+}
+
+static int grid_of(long long n) { return (int)std::max(1LL, std::min<long long>((n + 255) / 256, 152LL * 16)); }
+
+static void check_hierarchy(Hier &H, cudaStream_t st)
+{
+    // non-finite scan: one counter per array, read back together
+    const int L = H.L;
+    DBuf<int> cnt((size_t)2 * L + 1);
+    GW_CUDA(cudaMemsetAsync(cnt.p, 0, cnt.bytes(), st));
+    for (int l = 1; l < L; ++l) {
+        const DCSR &A = H.A[(size_t)l];
+        gw_launch(k_nonfinite, grid_of(A.nnz), 256, 0, st, (long long)A.nnz, (const double *)A.v.p, cnt.p + l);
+    }
+    for (int l = 0; l + 1 < L; ++l) {
+        const DCSR &P = H.P[(size_t)l];
+        gw_launch(k_nonfinite, grid_of(P.nnz), 256, 0, st, (long long)P.nnz, (const double *)P.v.p, cnt.p + L + l);
+    }
+    const long long nc2 = (long long)H.info[(size_t)L - 1].n * H.info[(size_t)L - 1].n;
+    gw_launch(k_nonfinite, grid_of(nc2), 256, 0, st, nc2, (const double *)H.Ainv.p, cnt.p + 2 * L);
+    GW_LAUNCH_CHECK();
+    std::vector<int> c((size_t)2 * L + 1);
+    GW_CUDA(cudaMemcpyAsync(c.data(), cnt.p, cnt.bytes(), cudaMemcpyDeviceToHost, st));
+    GW_CUDA(cudaStreamSynchronize(st));
+    for (int l = 1; l < L; ++l)
+        if (c[(size_t)l]) fail(GW_ERR_SETUP, "setup: non-finite entries in the operator of level %d", l);
+    for (int l = 0; l + 1 < L; ++l) {
+        if (c[(size_t)L + l]) fail(GW_ERR_SETUP, "setup: non-finite entries in the prolongator of level %d", l);
+        const gw_level_info &li = H.info[(size_t)l];
+        if (!isfinite(li.lambda_max) || !isfinite(li.jacobi_w) || !isfinite(li.omega_p))
+            fail(GW_ERR_SETUP, "setup: non-finite smoother or prolongator weights on level %d", l);
+    }
+    if (c[(size_t)2 * L]) fail(GW_ERR_SETUP, "setup: non-finite entries in the coarsest-level inverse");
+    DBuf<int> bad(1);
+    auto count = [&](auto launch) {
+        GW_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
+        launch();
+        GW_LAUNCH_CHECK();
+        return read_int(bad.p, st);
+    };
+    static const bool validate = [] {
+        const char *e = getenv("GW_VALIDATE");
+        return e && e[0] == '1';
+    }();
+    if (!validate) return;
+    auto csr = [&](const char *what, int l, int nr, int nc, long long nnz, const int *rp, const int *ci) {
+        if (count([&] { gw_launch(k_check_csr, grid_of(nr), 256, 0, st, nr, nc, nnz, rp, ci, bad.p); }))
+            fail(GW_ERR_SETUP, "validation: %s of level %d has row pointers or columns out of bounds", what, l);
+    };
+    auto range = [&](const char *what, int l, long long n, const int *x, int lo, int hi) {
+        if (n > 0 && count([&] { gw_launch(k_check_range, grid_of(n), 256, 0, st, n, x, lo, hi, bad.p); }))
+            fail(GW_ERR_SETUP, "validation: %s of level %d out of [%d, %d)", what, l, lo, hi);
+    };
+    for (int l = 0; l < H.L; ++l) {
+        const DCSR &A = l == 0 ? *H.A0 : H.A[(size_t)l];
+        csr("the operator", l, A.nr, A.nc, A.nnz, A.rp.p, A.ci.p);
+        if (l + 1 < H.L) {
+            const DCSR &P = H.P[(size_t)l], &R = H.R[(size_t)l];
+            csr("the prolongator", l, P.nr, P.nc, P.nnz, P.rp.p, P.ci.p);
+            csr("the restriction", l, R.nr, R.nc, R.nnz, R.rp.p, R.ci.p);
+            range("the aggregate ids", l, H.info[(size_t)l].n, H.agg[(size_t)l].p, 0, H.info[(size_t)l].naggregates);
+        }
+    }
+    // the cycle's own storage of the levels
+    auto cyc = [&](auto &C) {
+        for (int l = 1; l + 1 < H.L; ++l) {
+            for (const auto *M : {&C[(size_t)l].A, &C[(size_t)l].P, &C[(size_t)l].R}) {
+                if (M->fmt == FMT_SELL && M->sell.stored) {
+                    range("a sliced-ELL column array", l, M->sell.stored, M->sell.ci.p, 0, std::max(1, M->nc));
+                    if (M->sell.perm.p) range("a sliced-ELL row permutation", l, M->nr, M->sell.perm.p, 0, M->nr);
+                } else if (M->fmt == FMT_CSR4 || M->fmt == FMT_CSR8 || M->fmt == FMT_CSR32) {
+                    csr("a warp-CSR matrix", l, M->csr.nr, M->csr.nc, M->csr.nnz, M->csr.rp.p, M->csr.ci.p);
+                }
+            }
+        }
+    };
+    if (H.o.prec == GW_PREC_FP64) cyc(H.cd);
+    else cyc(H.cf);
+    if (H.p0.n) {
+        range("the implicit transfer's aggregate ids", 0, H.p0.n, H.p0.agg, 0, H.p0.nc);
+        range("the implicit transfer's member lists", 0, H.p0.n, H.p0.mem.p, 0, H.p0.n);
+        csr("the implicit transfer's member pointers", 0, H.p0.nc, H.p0.n, H.p0.n, H.p0.mptr.p, H.p0.mem.p);
+    }
+}
+
 // Smoothed-aggregation setup (see setup.cu for the stages).  Levels are added
 // while the level has more than n_coarse unknowns and fewer than max_levels
 // levels exist; a level whose aggregation keeps more than 0.9 of its unknowns
 // (or finds none) becomes the coarsest.  theta halves per level.
 void build_hierarchy(Hier &H, cudaStream_t st)
 {
+    NvtxRange range("gw setup");
     const gw_amg_opts &o = H.o;
     int nsm = 0;
     GW_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, H.dev));
     H.max_blocks = std::max(1, std::min(RED_MAX_BLOCKS, nsm * GW_BLOCKS_PER_SM));
     H.A.clear();
     H.A.emplace_back();  // placeholder for level 0 (the matrix handle's CSR)
-    std::vector<DCSR> R;
+    std::vector<DCSR> &R = H.R;
+    R.clear();
     auto Al = [&](int l) -> const DCSR & { return l == 0 ? *H.A0 : H.A[(size_t)l]; };
     double th = o.theta;
     int l = 0;
@@ -209,6 +353,9 @@ void build_hierarchy(Hier &H, cudaStream_t st)
         H.agg.emplace_back();
         H.root.emplace_back();
         if (A.nr <= o.n_coarse || l + 1 >= o.max_levels) break;
+        char nm[48];
+        snprintf(nm, sizeof nm, "gw setup level %d", l);
+        NvtxRange lrange(nm);
         DBuf<unsigned char> S;
         setup_strength(A, th * th, S, st);
         H.info[(size_t)l].mis_rounds = setup_mis2(A, S.p, o.seed, l, H.root[(size_t)l], o.mis_max_rounds, st);
@@ -287,6 +434,7 @@ void build_hierarchy(Hier &H, cudaStream_t st)
     GW_CUDA(host_malloc((void **)&H.ctl_host, sizeof(Ctl)));
     memset(H.ctl_host, 0, sizeof(Ctl));
     H.info[0].bytes += f64 ? 7LL * n * 8 : 2LL * n * 8 + 6LL * n * 4;
+    check_hierarchy(H, st);
     GW_CUDA(cudaStreamSynchronize(st));
 }
 
@@ -323,6 +471,20 @@ __global__ void k_reuse_check(int n, const int *__restrict__ rp, const int *__re
     }
 }
 
+// The coarse operators formed with the shift s_ref stay while every
+// |s_i - s_ref_i| <= gamma s_ref_i: their storage part P^T diag(s) P then
+// stays within the factors 1 -/+ gamma of the one they hold (s_ref = 0 only
+// for s = 0).
+__global__ void k_coarse_check(int n, const double *__restrict__ s, const double *__restrict__ sr, double gamma,
+                               int *__restrict__ bad)
+{
+    for (long long ii = blockIdx.x * (long long)blockDim.x + threadIdx.x; ii < n; ii += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)ii;
+        const double a = s ? s[i] : 0.0, r = sr ? sr[i] : 0.0;
+        if (!(fabs(a - r) <= gamma * r) && !(a == 0.0 && r == 0.0)) atomicAdd(bad, 1);
+    }
+}
+
 // A = C + diag(s) on a copy of C's pattern
 __global__ void k_shift_diag(int n, const int *__restrict__ rp, const int *__restrict__ ci, double *__restrict__ v,
                              const double *__restrict__ s)
@@ -333,6 +495,8 @@ __global__ void k_shift_diag(int n, const int *__restrict__ rp, const int *__res
             if (ci[e] == i) v[e] = v[e] + s[i];
     }
 }
+
+constexpr double SHIFT_COARSE_GAMMA = 0.25;
 
 #define GW_API_BEGIN try {
 #define GW_API_END                                    \
@@ -619,14 +783,32 @@ int gw_hierarchy_shift(gw_hierarchy H, const double *s, double delta, int *rebui
         GW_LAUNCH_CHECK();
     }
     if (reuse) {
+        // keep the coarse operators if the shift stayed close to theirs,
+        // else form them again on the kept aggregates and prolongators
+        GW_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
+        gw_launch(k_coarse_check, gb, 256, 0, st, n, (const double *)snew.p, (const double *)H->s_ref.p,
+                  SHIFT_COARSE_GAMMA, bad.p);
+        GW_LAUNCH_CHECK();
+        const bool keep_coarse = read_int(bad.p, st) == 0;
         if (s) {
             H->shifted = std::move(A);
             target = &H->shifted;
         }
-        refresh_level0(*H->h, *target, st);
+        if (keep_coarse) {
+            refresh_level0(*H->h, *target, st);
+        } else {
+            refresh_numeric(*H->h, *target, st);
+            if (s) {
+                H->s_ref.alloc((size_t)n);
+                GW_CUDA(cudaMemcpyAsync(H->s_ref.p, snew.p, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+            } else {
+                H->s_ref.release();
+            }
+        }
         if (s) H->s_now = std::move(snew);
         else H->s_now.release();
-        if (rebuilt) *rebuilt = 0;
+        GW_CUDA(cudaStreamSynchronize(st));
+        if (rebuilt) *rebuilt = keep_coarse ? 0 : 2;
     } else {
         const gw_amg_opts o = H->h->o;
         if (s) target = &A;
@@ -638,10 +820,13 @@ int gw_hierarchy_shift(gw_hierarchy H, const double *s, double delta, int *rebui
             H->h->A0 = &H->shifted;
             H->s_built.alloc((size_t)n);
             GW_CUDA(cudaMemcpyAsync(H->s_built.p, snew.p, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+            H->s_ref.alloc((size_t)n);
+            GW_CUDA(cudaMemcpyAsync(H->s_ref.p, snew.p, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
             H->s_now = std::move(snew);
         } else {
             H->shifted = DCSR();
             H->s_built.release();
+            H->s_ref.release();
             H->s_now.release();
         }
         GW_CUDA(cudaStreamSynchronize(st));

@@ -642,16 +642,13 @@ template <int R, class T, class OT>
 __device__ __forceinline__ void dot_rows(int i, const T *b, const OT (&z)[R], const T *q, double &lrz, double &lqz)
 {
     const VecN<T, R> bb = ld_ro<R>(b + i);
-    T s = 0;
+    T zz[R];
 #pragma unroll
-    for (int k = 0; k < R; ++k) s += bb.v[k] * (T)z[k];
-    lrz += (double)s;
+    for (int k = 0; k < R; ++k) zz[k] = (T)z[k];
+    dot_add<R>(lrz, bb.v, zz);
     if (q) {
         const VecN<T, R> qq = ld_ro<R>(q + i);
-        T t = 0;
-#pragma unroll
-        for (int k = 0; k < R; ++k) t += qq.v[k] * (T)z[k];
-        lqz += (double)t;
+        dot_add<R>(lqz, qq.v, zz);
     }
 }
 
@@ -1663,10 +1660,7 @@ __device__ __forceinline__ void b_cg_dir_spmv(VB vb, M A, int n, const typename 
             st<R>(q + i, qi);
             const VecN<V, R> pi = GDir<V>{z, pold, beta}.template vec<R>(i);
             st<R>(pnew + i, pi);
-            V s = 0;
-#pragma unroll
-            for (int k = 0; k < R; ++k) s += pi.v[k] * qi.v[k];
-            loc[0] += (double)s;
+            dot_add<R>(loc[0], pi.v, qi.v);
         }
     }
     if (reduce_last<1>(vb, loc, part, &c->cnt[0], tot) && threadIdx.x == 0) {
@@ -1705,14 +1699,12 @@ __device__ __forceinline__ void b_cg_update(VB vb, int n, V *__restrict__ x, V *
     for (int i = R * (vb.bid * BS + threadIdx.x); i < n; i += R * vb.nb * BS) {
         VecN<V, R> xv = ld_rw<R>(x + i), rv = ld_rw<R>(r + i);
         const VecN<V, R> pv = ld_ro<R>(p + i), qv = ld_ro<R>(q + i);
-        V s = 0;
 #pragma unroll
         for (int k = 0; k < R; ++k) {
             xv.v[k] += a * pv.v[k];
             rv.v[k] -= a * qv.v[k];
-            s += rv.v[k] * rv.v[k];
         }
-        loc[0] += (double)s;
+        dot_add<R>(loc[0], rv.v, rv.v);
         st<R>(x + i, xv);
         st<R>(r + i, rv);
     }
@@ -2131,6 +2123,7 @@ void pcg_prepare(Hier &H) { ensure_graphs(H); }
 
 int pcg_run(Hier &H, double tol, int maxit, int *iters, double *relres, cudaStream_t st)
 {
+    NvtxRange range("gw solve");
     Ctl *c = H.ctl.p;
     ensure_graphs(H);
     Ctl init;
@@ -2764,6 +2757,7 @@ int batch_add(Batch &B, Hier &H, const double *b, double tol, int maxit)
 // waiting to be taken.
 int batch_run(Batch &B, int iterations)
 {
+    NvtxRange range("gw batch replays");
     int running = 0;
     for (int s = 0; s < B.max_slots; ++s) running += B.state[(size_t)s] == 1;
     for (int k = 0; k < iterations && running && B.g; ++k) {

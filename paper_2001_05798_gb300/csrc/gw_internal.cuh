@@ -13,9 +13,20 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "gw.h"
 
 namespace gw {
+
+// A named NVTX range for the lifetime of the object (setup levels, solves,
+// batch replays); it costs nothing unless a profiler is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // ------------------------------------------------------------------ errors --
 struct Error {
@@ -323,6 +334,7 @@ struct Hier {
     int L = 0;
     std::vector<DCSR> A;       // A[l] for l >= 1 (A[0] is *A0)
     std::vector<DCSR> P;       // P[l] for l < L-1
+    std::vector<DCSR> R;       // R[l] = P[l]^T, kept for numeric refreshes
     std::vector<DBuf<int>> agg;
     std::vector<DBuf<unsigned char>> root;
     std::vector<gw_level_info> info;
@@ -373,6 +385,10 @@ inline const MatStore<float> &cg_op32(const Hier &H) { return H.A32.nr ? H.A32 :
 
 void build_hierarchy(Hier &H, cudaStream_t st);
 void refresh_level0(Hier &H, const DCSR &A, cudaStream_t st);
+// level 0 becomes A and every coarse operator is formed again as
+// P_l^T A_l P_l on the kept prolongators (same patterns), with the smoother
+// data of every level and the coarsest inverse redone
+void refresh_numeric(Hier &H, const DCSR &A, cudaStream_t st);
 void vcycle_enqueue(Hier &H, const double *r, double *z, Ctl *ctl, bool dot, cudaStream_t st);
 int pcg_run(Hier &H, double tol, int maxit, int *iters, double *relres, cudaStream_t st);
 void pcg_prepare(Hier &H);  // capture the solver's graphs now

@@ -77,6 +77,43 @@ static void launch_pdl(void (*kernel)(KArgs...), int grid, cudaStream_t st, Args
 
 
 // ------------------------------------------------------------- reductions --
+// A thread's share of an FP32 dot product without FP32 rounding of the sum:
+// each product is split exactly into p + e (e by a fused multiply-add) and
+// the products are added in two FP32 words by the error-free TwoSum, which
+// keeps about 46 bits; the pair is then added to the FP64 accumulator.  FP32
+// operations only (FP64 throughput is scarce on this GPU); explicitly rounded
+// intrinsics keep the compiler from contracting the transformations.
+struct Sum2 {
+    float hi = 0.f, lo = 0.f;
+};
+__device__ __forceinline__ void sum2_prod(Sum2 &s, float x, float y)
+{
+    const float p = __fmul_rn(x, y);
+    const float e = __fmaf_rn(x, y, -p);
+    const float t = __fadd_rn(s.hi, p);
+    const float bp = __fsub_rn(t, s.hi);
+    const float err = __fadd_rn(__fsub_rn(s.hi, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+    s.hi = t;
+    s.lo = __fadd_rn(s.lo, __fadd_rn(err, e));
+}
+__device__ __forceinline__ double sum2_value(const Sum2 &s) { return (double)s.hi + (double)s.lo; }
+
+// the dot product of R consecutive entries, added to an FP64 accumulator
+template <int R, class T, class U>
+__device__ __forceinline__ void dot_add(double &acc, const T (&a)[R], const U (&b)[R])
+{
+    if constexpr (sizeof(T) == 4 && sizeof(U) == 4) {
+        Sum2 s;
+#pragma unroll
+        for (int k = 0; k < R; ++k) sum2_prod(s, (float)a[k], (float)b[k]);
+        acc += sum2_value(s);
+    } else {
+        double s = 0.0;
+#pragma unroll
+        for (int k = 0; k < R; ++k) s += (double)a[k] * (double)b[k];
+        acc += s;
+    }
+}
 __device__ __forceinline__ double warp_sum(double v)
 {
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);

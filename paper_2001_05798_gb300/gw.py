@@ -323,10 +323,11 @@ class Hierarchy:
         return X, list(its), list(rels), st
 
     def shift(self, s, delta=0.01, stream=None):
-        """Solve (C + diag(s)) from now on; returns True if the hierarchy was rebuilt."""
+        """Solve (C + diag(s)) from now on; returns 0 (hierarchy kept, level 0
+        refreshed), 2 (coarse operators formed again) or 1 (rebuilt)."""
         rb = ctypes.c_int()
         _check(load().gw_hierarchy_shift(self.h, _ptr(s), float(delta), ctypes.byref(rb), _stream(stream)))
-        return bool(rb.value)
+        return rb.value
 
     def profile(self, on=True):
         _check(load().gw_profile_enable(self.h, int(bool(on))))

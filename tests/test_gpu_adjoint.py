@@ -111,13 +111,29 @@ def test_adjoint_96_cubed_against_finite_differences_and_oracle(gw):
     J = ((h[obs_t.long()] - hobs) ** 2).sum()
     J.backward()
     g = lnK.grad.cpu().numpy()
-    eps = 1e-4
-    for i in wl.cells(side ** 3, 20, 8):
+
+    def J64(lnK):  # FP64 form solved to 1e-13: the misfit to about 1e-12
+        return gw.gw_misfit(heads(lnK, side, side, side, tol=1e-13, prec=gw.GW_PREC_FP64), obs_t, hobs)
+
+    def fd(i, eps):
         lp, lm = lnK0.clone(), lnK0.clone()
         lp[i] += eps
         lm[i] -= eps
-        fd = (J_of(lp) - J_of(lm)) / (2 * eps)
-        assert fd == pytest.approx(g[i], rel=2e-3, abs=1e-6 * np.abs(g).max())
+        return (J64(lp) - J64(lm)) / (2 * eps)
+
+    # the 20 seeded cells, the cells of largest sensitivity and the most
+    # sensitive cells on the Dirichlet faces (x = 0, x = side - 1), where the
+    # boundary transmissibility term enters; Richardson-extrapolated central
+    # differences (truncation O(eps^4)) with eps = 2e-3 and 1e-3
+    gmax = np.abs(g).max()
+    xs = np.arange(side ** 3) % side
+    face = np.flatnonzero((xs == 0) | (xs == side - 1))
+    cells = list(wl.cells(side ** 3, 20, 8)) + list(np.argsort(-np.abs(g))[:6])
+    cells += list(face[np.argsort(-np.abs(g[face]))[:4]])
+    for i in cells:
+        i = int(i)
+        rich = (4.0 * fd(i, 1e-3) - fd(i, 2e-3)) / 3.0
+        assert abs(rich - g[i]) <= 1e-5 * abs(g[i]) + 1e-6 * gmax, (i, rich, g[i])
     # the oracle's adjoint on the oracle's own solves
     A, b = oracle.assemble(side, side, side, p["Kx"])
     Ho = oracle.Hierarchy(A)

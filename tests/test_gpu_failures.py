@@ -92,3 +92,31 @@ def test_non_finite_column_of_a_block_solve(gw, system):
     # the good columns alone still solve to the tolerance afterwards
     X, its, rels, st = H.solve_many(torch.stack([b, 0.5 * b]).contiguous(), tol=1e-8)
     assert st == gw.GW_OK and max(rels) <= 1e-8
+
+
+def test_index_validation_of_every_level(gw):
+    """GW_VALIDATE=1 checks every index array the cycle kernels gather through
+    (all levels' CSR row pointers and columns, sliced-ELL columns and row
+    permutations, the implicit level-0 transfer's lists) after the setup; the
+    variable is read once per process, so the check runs in a child process."""
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "import torch\n"
+            "from paper_2001_05798_gb300 import gw, workload as wl\n"
+            "for shape, prec in (((33, 31, 29), 1), ((20, 18, 16), 0), ((64, 64, 32), 1)):\n"
+            "    p = wl.problem(*shape, var=3.0, corr=4.0, seed=2)\n"
+            "    n = shape[0] * shape[1] * shape[2]\n"
+            "    K = torch.from_numpy(p['Kx']).cuda()\n"
+            "    b = torch.empty(n, dtype=torch.float64, device='cuda')\n"
+            "    A, _ = gw.gw_assemble(*shape, K, K, K, p['bct'], p['bcv'], None, b_out=b)\n"
+            "    H = gw.Hierarchy(A, n_coarse=64, prec=prec)\n"
+            "    h, it, rel, st = H.solve(b, tol=1e-8)\n"
+            "    assert st == 0 and rel <= 1e-8, (st, rel)\n"
+            "print('validated')\n") % root
+    env = dict(os.environ, GW_VALIDATE="1")
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0 and "validated" in r.stdout, r.stdout + r.stderr

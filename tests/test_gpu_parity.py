@@ -248,12 +248,19 @@ def test_full_size_128_cubed_sigma4(gw, prec):
     Ho = oracle.Hierarchy(Ao)
     info = H.info()
     assert [l["n"] for l in info] == Ho.stats()["n"]
-    agg, root, (arp, aci, av), _ = H.export_level(0)
-    oagg, oroot, _ = Ho.level(0)
-    assert np.array_equal(agg, oagg) and np.array_equal(root, oroot)
-    _, _, (arp1, aci1, av1), _ = H.export_level(1)
-    orp1, oci1, ov1 = Ho.A(1).arrays()
-    assert np.array_equal(arp1, orp1) and np.array_equal(aci1, oci1) and np.array_equal(av1, ov1)
+    # every level bit for bit: aggregates, roots, P_l and A_l
+    for l in range(len(info)):
+        agg, root, (arp, aci, av), P = H.export_level(l)
+        orp, oci, ov = Ho.A(l).arrays()
+        assert np.array_equal(arp, orp) and np.array_equal(aci, oci), l
+        assert np.array_equal(av.view(np.uint64), ov.view(np.uint64)), l
+        if P is not None:
+            oagg, oroot, _ = Ho.level(l)
+            assert np.array_equal(agg, oagg) and np.array_equal(root, oroot), l
+            prp, pci, pv = P
+            qrp, qci, qv = Ho.P(l).arrays()
+            assert np.array_equal(prp, qrp) and np.array_equal(pci, qci), l
+            assert np.array_equal(pv.view(np.uint64), qv.view(np.uint64)), l
     href, _, _, _ = Ho.pcg(bo, tol=1e-12)
     assert np.linalg.norm(h.cpu().numpy() - href) / np.linalg.norm(href) <= REL_ERR
 

@@ -661,3 +661,55 @@ def test_numeric_refresh_is_the_galerkin_product_on_kept_prolongators():
     assert st == 0 and rel <= 1e-12
     ref = np.linalg.solve(A.dense(), rhs)
     assert np.linalg.norm(x - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+def _smoother_propagator(H, l, smoother, degree, nu):
+    """Error propagator of one smoothing application on level l from the
+    smoothers' closed forms: (I - w D^-1 A)^nu for damped Jacobi with the
+    Gershgorin weight, and p_m(D^-1 A)^nu for Chebyshev of degree m on
+    [lam/30, 1.1 lam], p_m(t) = T_m((b + a - 2t)/(b - a)) / T_m((b + a)/(b - a)),
+    evaluated by an eigendecomposition of D^-1/2 A D^-1/2."""
+    A = H.A(l).dense()
+    n = A.shape[0]
+    d = np.diag(A)
+    sc = H.scalars(l)
+    if smoother == 0:
+        E1 = np.eye(n) - sc["jacobi_w"] * (A / d[:, None])
+    else:
+        lam = sc["lam"]
+        a, b = lam / 30.0, 1.1 * lam
+        s = 1.0 / np.sqrt(d)
+        w, V = np.linalg.eigh(s[:, None] * A * s[None, :])
+        Tm = [0.0] * degree + [1.0]  # T_m in the Chebyshev basis (numpy's chebval)
+        p = np.polynomial.chebyshev.chebval((b + a - 2 * w) / (b - a), Tm)
+        p = p / np.polynomial.chebyshev.chebval((b + a) / (b - a), Tm)
+        E1 = (s[:, None] * (V * p) @ V.T) / s[None, :]  # D^-1/2 f(S) D^1/2
+    return np.linalg.matrix_power(E1, nu)
+
+
+def _vcycle_matrix(H, l, smoother, degree, nu):
+    """The V-cycle from level l down as a matrix B_l: on the coarsest level the
+    exact inverse, above it I - B_l A_l = E (I - P_l B_{l+1} P_l^T A_l) E."""
+    A = H.A(l).dense()
+    if l == H.nlevels - 1:
+        return np.linalg.inv(A)
+    P = H.P(l).dense()
+    Bc = _vcycle_matrix(H, l + 1, smoother, degree, nu)
+    E = _smoother_propagator(H, l, smoother, degree, nu)
+    n = A.shape[0]
+    Mid = np.eye(n) - P @ Bc @ P.T @ A
+    return (np.eye(n) - E @ Mid @ E) @ np.linalg.inv(A)
+
+
+@pytest.mark.parametrize("smoother,degree,nu", [(0, 1, 1), (0, 1, 2), (1, 2, 1), (1, 3, 2)])
+def test_vcycle_is_the_multigrid_error_propagator(smoother, degree, nu):
+    # the oracle's V-cycle, applied to unit vectors, equals the dense product
+    # of smoother, coarse-correction and smoother error propagators on every level
+    p = wl.problem(9, 8, 7, var=3.0, corr=3.0, seed=6, wells_count=2, wells_seed=1)
+    A, b = asm(p)
+    H = oracle.Hierarchy(A, smoother=smoother, degree=degree, nu=nu, n_coarse=20)
+    assert H.status == 0 and H.nlevels >= 3
+    n = A.nr
+    Bo = np.column_stack([H.vcycle(e) for e in np.eye(n)])
+    Bref = _vcycle_matrix(H, 0, smoother, degree, nu)
+    assert np.abs(Bo - Bref).max() <= 1e-10 * np.abs(Bref).max()

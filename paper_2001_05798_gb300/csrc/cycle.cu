@@ -1374,7 +1374,7 @@ static void smooth(Hier &H, std::vector<CycLevel<T>> &C, int l, const T *b, bool
                 for (int k = 2; k < m; ++k) {
                     const bool f3 = fin && k == m - 1;
                     timed(H, kind(), st, [&] {
-                        H.prof_bytes += vbytes(H, amat + dn * sx * 6.0 + (f3 ? dn * sx * (q ? 2.0 : 1.0) : 0.0));
+                        H.prof_bytes += vbytes(H, amat + dn * sx * 7.0 + (f3 ? dn * sx * (q ? 2.0 : 1.0) : 0.0));
                         if (f3)
                             launch_pdl(k_chebk<M, T, true>, g, st, A, n, lv.dw.p, lv.r.p, d, dnx, lv.x.p, zout,
                                        (T)lv.c1[k], (T)lv.c2[k], 0, b, q, part, ctl, mode);
@@ -1404,7 +1404,7 @@ static void smooth(Hier &H, std::vector<CycLevel<T>> &C, int l, const T *b, bool
                 const bool f2 = fin && k == m - 1;
                 const int add_prev = (k == 1 && !zero) ? 1 : 0;
                 timed(H, kind(), st, [&] {
-                    H.prof_bytes += vbytes(H, amat + dn * sx * 6.0 + (f2 ? dn * sx * (q ? 2.0 : 1.0) : 0.0));
+                    H.prof_bytes += vbytes(H, amat + dn * sx * 7.0 + (f2 ? dn * sx * (q ? 2.0 : 1.0) : 0.0));
                     if (f2)
                         launch_pdl(k_chebk<M, T, true>, g, st, A, n, lv.dw.p, lv.r.p, d, dnx, lv.x.p, zout,
                                    (T)lv.c1[k], (T)lv.c2[k], add_prev, b, q, part, ctl, mode);
@@ -1928,7 +1928,7 @@ static void cg_iteration(Hier &H, int parity, cudaStream_t st)
     const MatStore<float> &A32 = cg_op32(H);
     (void)parity;
     timed(H, GW_PK_SPMV, st, [&] {
-        H.prof_bytes += vbytes(H, mat_bytes(A32) + 20.0 * dn);
+        H.prof_bytes += vbytes(H, mat_bytes(A32) + 16.0 * dn);  // z, p_old read; p_new, q written
         with_mat(A32, [&](auto A) {
             using M = decltype(A);
             launch_pdl(k_cg_dir_spmv<M>, grid_for<M>(H, n), st, A, n, (const float *)H.z32.p, H.p32.p, H.p32b.p,

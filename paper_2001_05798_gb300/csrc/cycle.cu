@@ -1735,7 +1735,11 @@ __global__ void __launch_bounds__(BS) k_cg_true(M A, int n, const double *__rest
     const VB vb = vb_grid();
     pdl_enter();
     constexpr int R = M::R;
-    if (!force && (finished(c) || !c->check)) return;
+    if (!force && finished(c)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) ctl_end_loop(c);
+        return;
+    }
+    if (!force && !c->check) return;
     double loc[1] = {0.0}, tot[1];
     GROUP_ROWS(M, n)
     {
@@ -1759,6 +1763,7 @@ __global__ void __launch_bounds__(BS) k_cg_true(M A, int n, const double *__rest
         } else if (tot[0] <= c->tol2 * c->bnorm2) {
             c->relres = rel;
             ctl_stop(c, GW_OK);
+            ctl_end_loop(c);
         } else {
             c->check = 0;
         }
@@ -1798,7 +1803,11 @@ template <class M>
 __device__ __forceinline__ void b_rel_res(VB vb, M A, int n, const double *__restrict__ b, const double *__restrict__ x,
                                                 float *__restrict__ r, double *part, Ctl *c, int force) {
     constexpr int R = M::R;
-    if (!force && (finished(c) || !c->check)) return;
+    if (!force && finished(c)) {
+        if (vb.bid == 0 && threadIdx.x == 0) ctl_end_loop(c);
+        return;
+    }
+    if (!force && !c->check) return;
     double loc[1] = {0.0}, tot[1];
     GROUP_ROWS(M, n)
     {
@@ -1822,6 +1831,7 @@ __device__ __forceinline__ void b_rel_res(VB vb, M A, int n, const double *__res
         if (!force) {
             if (tot[0] <= c->tol2 * c->bnorm2) {
                 ctl_stop(c, GW_OK);
+                ctl_end_loop(c);
             } else {
                 c->rmax2 = tot[0];
                 c->check = 0;

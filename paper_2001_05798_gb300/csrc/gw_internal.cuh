@@ -229,7 +229,8 @@ struct Ctl {
     int it, maxit, done, status, check, flexible;
     unsigned int cnt[8];  // arrival counters of the last-block reductions
     // handle of the while node of the solve's graph (0 when the solve does
-    // not run under one): the kernel that finishes the solve sets it to 0
+    // not run under one): the last kernel of the iteration sets it to 0 once
+    // the solve is done
     unsigned long long cond;
 };
 

@@ -188,13 +188,21 @@ __device__ __forceinline__ bool reduce_last(const double (&loc)[K], double *part
 
 __device__ __forceinline__ bool finished(const Ctl *c) { return c && *(volatile const int *)&c->done; }
 
-// Ends the solve with the given status; under a graph while node also ends
-// the loop (one thread of one kernel calls this, so the condition is never
-// set concurrently).
+// Ends the solve with the given status.  Under a graph while node the loop
+// itself is ended by the kernel that checks the true residual (k_rel_res, or
+// k_cg_true in the FP64 form): it stops the loop when it finds the solve done
+// on entry, or when it finds it converged, so that the heavy kernels make no
+// device graph call (profilers skip kernels that make one).
 __device__ __forceinline__ void ctl_stop(Ctl *c, int status)
 {
     c->status = status;
     c->done = 1;
+}
+
+// ends the while loop of the solve's graph (one thread: the condition is
+// never set concurrently)
+__device__ __forceinline__ void ctl_end_loop(const Ctl *c)
+{
     if (c->cond) cudaGraphSetConditional((cudaGraphConditionalHandle)c->cond, 0u);
 }
 

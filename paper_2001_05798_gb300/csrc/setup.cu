@@ -847,17 +847,25 @@ void setup_spgemm(const DCSR &L, const DCSR &Rm, DCSR &C, cudaStream_t st)
 }
 
 // ---------------------------------------------------------- coarsest level --
-// Dense inverse of the coarsest level by Gauss-Jordan elimination with
-// partial pivoting on the augmented matrix W = [A | I] (n x 2n, row-major):
-// after step k column k of the left half is e_k, and after n steps the right
-// half is the inverse.  Each step is two launches: one block picks the pivot
-// (largest |W_ik|, i >= k, lowest index on ties), swaps it into row k, scales
-// that row and copies it and the multipliers W_ik aside; then the whole GPU
-// subtracts m_i times the pivot row from every other row.  The O(n^3)
-// FP64 work so runs on every SM instead of one.
-// The 2n launches of the elimination run back to back with programmatic
-// dependent launch: each kernel may be scheduled while its predecessor runs
-// and waits for it (and its writes) before touching memory.
+// Dense inverse of the coarsest level by block Gauss-Jordan elimination in
+// place, without pivoting (the coarsest operator is a Galerkin product of
+// the SPD level-0 operator with a full-rank prolongator, so it is SPD, and
+// elimination without pivoting is stable on SPD matrices; a pivot that is
+// not positive and finite reports the matrix as singular).  M (n x n,
+// row-major) starts as A; for each panel K of GJB consecutive indices:
+//   Q = (M_KK)^-1,
+//   M_IJ -= M_IK Q M_KJ  (I, J outside K),
+//   M_KJ  = Q M_KJ,  M_IK = -M_IK Q,  M_KK = Q,
+// and after the last panel M = A^-1.  Each panel is two launches: one block
+// per 32-column tile J inverts M_KK (every block the same way, in shared
+// memory), forms the new row panel Q M_KJ and copies the old column panel
+// M_JK aside; then one block per 32 x 32 tile of M applies the update.  The
+// n^3 FP64 multiply-adds so run on every SM, in 2 n / GJB launches.  The
+// launches run back to back with programmatic dependent launch: each kernel
+// may be scheduled while its predecessor runs and waits for it (and its
+// writes) before touching memory.
+constexpr int GJB = 32;
+
 __device__ __forceinline__ void gj_enter()
 {
     asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -880,92 +888,119 @@ static void gj_launch(void (*kernel)(KArgs...), int grid, int block, cudaStream_
     GW_CUDA(cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...));
 }
 
-__global__ void __launch_bounds__(1024) k_gj_pivot(int n, int k, double *__restrict__ W, double *__restrict__ prow,
-                                                   double *__restrict__ m, int *__restrict__ singular)
+// Inverse of the bk x bk pivot block in shared memory (row stride GJB+1),
+// in-place Gauss-Jordan without pivoting; 256 threads.  Returns false (for
+// every thread) if a pivot is not positive and finite.
+__device__ bool gj_invert_block(double (*a)[GJB + 1], double *col, int bk)
 {
-    __shared__ double sv[1024];
-    __shared__ int si[1024];
-    const int tid = threadIdx.x, bs = blockDim.x, w2 = 2 * n;
-    gj_enter();
-    if (*singular) return;
-    double best = -1.0;
-    int bi = n;
-    for (int i = k + tid; i < n; i += bs) {
-        const double t = fabs(W[(size_t)i * w2 + k]);
-        if (t > best) {
-            best = t;
-            bi = i;
-        }
-    }
-    sv[tid] = best;
-    si[tid] = bi;
+    const int tid = threadIdx.x;
+    __shared__ int bad;
+    if (tid == 0) bad = 0;
     __syncthreads();
-    for (int off = bs >> 1; off > 0; off >>= 1) {
-        if (tid < off) {
-            const double o = sv[tid + off];
-            const int oi = si[tid + off];
-            if (o > sv[tid] || (o == sv[tid] && oi < si[tid])) {
-                sv[tid] = o;
-                si[tid] = oi;
-            }
+    for (int p = 0; p < bk; ++p) {
+        const double piv = a[p][p];
+        if (!(piv > 0.0) || !isfinite(piv)) {
+            if (tid == 0) bad = 1;
+            break;  // uniform: every thread read the same pivot
+        }
+        if (tid < bk) col[tid] = a[tid][p];
+        __syncthreads();
+        // row p scaled by 1/piv, with its diagonal entry replaced by 1/piv
+        if (tid < bk) a[p][tid] = (tid == p ? 1.0 : a[p][tid]) / piv;
+        __syncthreads();
+        for (int t = tid; t < bk * bk; t += blockDim.x) {
+            const int i = t / bk, j = t % bk;
+            if (i != p) a[i][j] = (j == p ? 0.0 : a[i][j]) - col[i] * a[p][j];
         }
         __syncthreads();
     }
-    const int p = si[0];
-    if (!(sv[0] > 0.0) || !isfinite(sv[0])) {
-        if (tid == 0) *singular = 1;
+    __syncthreads();
+    return bad == 0;
+}
+
+// One block per 32-index tile J: Q = (M_KK)^-1, Rn[:, J] = Q M_KJ, Cs[J, :]
+// = M_JK (old values); block 0 also stores Q.
+__global__ void __launch_bounds__(256) k_bgj_panel(int n, int k0, int bk, const double *__restrict__ M,
+                                                   double *__restrict__ Q, double *__restrict__ Rn,
+                                                   double *__restrict__ Cs, int *__restrict__ singular)
+{
+    __shared__ double a[GJB][GJB + 1], t[GJB][GJB + 1];
+    __shared__ double col[GJB];
+    const int tid = threadIdx.x, j0 = blockIdx.x * GJB, bj = min(GJB, n - j0);
+    gj_enter();
+    if (*(volatile const int *)singular) return;
+    for (int e = tid; e < GJB * GJB; e += blockDim.x) {
+        const int i = e / GJB, j = e % GJB;
+        a[i][j] = i < bk && j < bk ? M[(size_t)(k0 + i) * n + k0 + j] : 0.0;
+        t[i][j] = i < bk && j < bj ? M[(size_t)(k0 + i) * n + j0 + j] : 0.0;
+    }
+    __syncthreads();
+    // old column panel rows of this tile
+    for (int e = tid; e < GJB * GJB; e += blockDim.x) {
+        const int i = e / GJB, j = e % GJB;
+        if (i < bj && j < bk) Cs[(size_t)(j0 + i) * GJB + j] = M[(size_t)(j0 + i) * n + k0 + j];
+    }
+    if (!gj_invert_block(a, col, bk)) {
+        if (tid == 0) atomicExch(singular, 1);
         return;
     }
-    if (p != k)
-        for (int j = tid; j < w2; j += bs) {
-            const double t = W[(size_t)k * w2 + j];
-            W[(size_t)k * w2 + j] = W[(size_t)p * w2 + j];
-            W[(size_t)p * w2 + j] = t;
-        }
-    __syncthreads();
-    const double pv = W[(size_t)k * w2 + k];
-    __syncthreads();
-    for (int j = tid; j < w2; j += bs) {
-        const double t = j < k ? 0.0 : W[(size_t)k * w2 + j] / pv;
-        prow[j] = t;
-        W[(size_t)k * w2 + j] = t;
+    if (blockIdx.x == 0)
+        for (int e = tid; e < GJB * GJB; e += blockDim.x) Q[e] = a[e / GJB][e % GJB];
+    // Rn[:, J] = Q M_KJ, terms in ascending inner index
+    for (int e = tid; e < bk * bj; e += blockDim.x) {
+        const int i = e / bj, j = e % bj;
+        double s = 0.0;
+        for (int q = 0; q < bk; ++q) s = fma(a[i][q], t[q][j], s);
+        Rn[(size_t)i * n + j0 + j] = s;
     }
-    for (int i = tid; i < n; i += bs) m[i] = i == k ? 0.0 : W[(size_t)i * w2 + k];
 }
 
-__global__ void k_gj_elim(int n, int k, double *__restrict__ W, const double *__restrict__ prow,
-                          const double *__restrict__ m, const int *__restrict__ singular)
+// One block per 32 x 32 tile (I, J) of M: the panel update above.
+__global__ void __launch_bounds__(256) k_bgj_update(int n, int k0, int bk, double *__restrict__ M,
+                                                    const double *__restrict__ Q, const double *__restrict__ Rn,
+                                                    const double *__restrict__ Cs, const int *__restrict__ singular)
 {
+    __shared__ double c[GJB][GJB + 1], r[GJB][GJB + 1];
+    const int tid = threadIdx.x;
+    const int nt = (n + GJB - 1) / GJB;
+    const int ti = blockIdx.x / nt, tj = blockIdx.x % nt;
+    const int i0 = ti * GJB, j0 = tj * GJB, bi = min(GJB, n - i0), bj = min(GJB, n - j0);
+    const int kt = k0 / GJB;
     gj_enter();
-    if (*singular) return;
-    const int w2 = 2 * n, cols = w2 - k;
-    const long long total = (long long)n * cols;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-         t += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(t / cols), j = k + (int)(t % cols);
-        const double mi = m[i];
-        if (i == k || mi == 0.0) continue;
-        W[(size_t)i * w2 + j] -= mi * prow[j];
+    if (*(volatile const int *)singular) return;
+    if (ti == kt && tj == kt) {
+        for (int e = tid; e < bk * bk; e += blockDim.x)
+            M[(size_t)(k0 + e / bk) * n + k0 + e % bk] = Q[(e / bk) * GJB + e % bk];
+        return;
     }
-}
-
-__global__ void k_gj_copy(int n, const double *__restrict__ W, double *__restrict__ X)
-{
-    GRID_STRIDE(t, (long long)n * n)
-    {
-        const int i = (int)(t / n), j = (int)(t % n);
-        X[t] = W[(size_t)i * 2 * n + n + j];
+    if (ti == kt) {
+        for (int e = tid; e < bk * bj; e += blockDim.x)
+            M[(size_t)(k0 + e / bj) * n + j0 + e % bj] = Rn[(size_t)(e / bj) * n + j0 + e % bj];
+        return;
+    }
+    // c = old M_IK (bi x bk); r = Rn[:, J] (bk x bj), or Q for the tile in column K
+    for (int e = tid; e < GJB * GJB; e += blockDim.x) {
+        const int i = e / GJB, j = e % GJB;
+        c[i][j] = i < bi && j < bk ? Cs[(size_t)(i0 + i) * GJB + j] : 0.0;
+        r[i][j] = i < bk && j < bj ? (tj == kt ? Q[i * GJB + j] : Rn[(size_t)i * n + j0 + j]) : 0.0;
+    }
+    __syncthreads();
+    for (int e = tid; e < bi * bj; e += blockDim.x) {
+        const int i = e / bj, j = e % bj;
+        double s = 0.0;
+        for (int q = 0; q < bk; ++q) s = fma(c[i][q], r[q][j], s);
+        double *m = M + (size_t)(i0 + i) * n + j0 + j;
+        *m = tj == kt ? -s : *m - s;
     }
 }
 
 __global__ void k_gj_fill(int n, const int *__restrict__ rp, const int *__restrict__ ci, const double *__restrict__ v,
-                          double *__restrict__ W)
+                          double *__restrict__ M)
 {
     GRID_STRIDE(ii, n)
     {
         const int i = (int)ii;
-        for (int e = rp[i]; e < rp[i + 1]; ++e) W[(size_t)i * 2 * n + ci[e]] = v[e];
-        W[(size_t)i * 2 * n + n + i] = 1.0;
+        for (int e = rp[i]; e < rp[i + 1]; ++e) M[(size_t)i * n + ci[e]] = v[e];
     }
 }
 
@@ -973,26 +1008,22 @@ void setup_dense_inverse(const DCSR &A, DBuf<double> &Ainv, cudaStream_t st)
 {
     const int n = A.nr;
     if (n > 4096) fail(GW_ERR_SETUP, "coarsest level has %d unknowns (more than 4096)", n);
-    DBuf<double> W((size_t)n * 2 * n), prow((size_t)2 * n), m((size_t)n);
+    const int nt = (n + GJB - 1) / GJB;
+    DBuf<double> Q((size_t)GJB * GJB), Rn((size_t)GJB * n), Cs((size_t)nt * GJB * GJB);
     DBuf<int> sing(1);
     Ainv.alloc((size_t)n * n);
-    GW_CUDA(cudaMemsetAsync(W.p, 0, W.bytes(), st));
+    GW_CUDA(cudaMemsetAsync(Ainv.p, 0, Ainv.bytes(), st));
     GW_CUDA(cudaMemsetAsync(sing.p, 0, sizeof(int), st));
-    gw_launch(k_gj_fill, nblk(n, 128), 128, 0, st, n, A.rp.p, A.ci.p, A.v.p, W.p);
-    int sms = 0, dev = 0;
-    GW_CUDA(cudaGetDevice(&dev));
-    GW_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    for (int k = 0; k < n; ++k) {
-        gj_launch(k_gj_pivot, 1, 1024, st, n, k, W.p, prow.p, m.p, (int *)sing.p);
-        const long long total = (long long)n * (2 * n - k);
-        const int g = (int)std::max(1LL, std::min<long long>((total + 255) / 256, 8LL * std::max(1, sms)));
-        gj_launch(k_gj_elim, g, 256, st, n, k, W.p, (const double *)prow.p, (const double *)m.p, (const int *)sing.p);
+    gw_launch(k_gj_fill, nblk(n, 128), 128, 0, st, n, A.rp.p, A.ci.p, A.v.p, Ainv.p);
+    GW_LAUNCH_CHECK();
+    for (int k0 = 0; k0 < n; k0 += GJB) {
+        const int bk = std::min(GJB, n - k0);
+        gj_launch(k_bgj_panel, nt, 256, st, n, k0, bk, (const double *)Ainv.p, Q.p, Rn.p, Cs.p, (int *)sing.p);
+        gj_launch(k_bgj_update, nt * nt, 256, st, n, k0, bk, Ainv.p, (const double *)Q.p, (const double *)Rn.p,
+                  (const double *)Cs.p, (const int *)sing.p);
     }
     GW_LAUNCH_CHECK();
     if (read_int(sing.p, st)) fail(GW_ERR_SETUP, "coarsest-level matrix (%d unknowns) is singular", n);
-    gw_launch(k_gj_copy, nblk((long long)n * n, 256), 256, 0, st, n, W.p, Ainv.p);
-    GW_LAUNCH_CHECK();
-    GW_CUDA(cudaStreamSynchronize(st));
 }
 
 // ------------------------------------------------- smoother data (per level) --

@@ -391,6 +391,14 @@ int gw_profile_enable(gw_hierarchy H, int on);
 /* Copies the counters gathered since the last reset; reset != 0 clears them. */
 int gw_profile_read(gw_hierarchy H, gw_profile *out, int reset);
 
+/*
+ * Free a handle.  Device memory goes back to the library's memory pool (in
+ * stream order, without synchronising the device); the pool keeps it for
+ * the next allocation.  Every call that uses a handle finishes its device
+ * work before it returns, except gw_vcycle: let the work of a gw_vcycle
+ * call finish before freeing its hierarchy.  A matrix must outlive the
+ * hierarchies set up on it.
+ */
 void gw_matrix_free(gw_matrix A);
 void gw_hierarchy_free(gw_hierarchy H);
 
@@ -447,8 +455,9 @@ const char *gw_status_str(int status);
 const char *gw_last_error(void);
 
 /*
- * gw_device_allocations -- the number of device allocations (cudaMalloc and
- * cudaMallocAsync calls) the library has made in this process so far.  It
+ * gw_device_allocations -- the number of device allocations (from the
+ * library's memory pool, or cudaMalloc outside a call that takes a stream)
+ * the library has made in this process so far.  It
  * lets a caller check that a sequence of calls allocated nothing, for
  * example gw_assemble_noalloc.  Not part of the paper's method.
  */

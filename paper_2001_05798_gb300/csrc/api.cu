@@ -577,6 +577,7 @@ int gw_assemble(const gw_grid *grid, const double *Kx, const double *Ky, const d
     }
     if (ndir == 0) fail(GW_ERR_ARG, "gw_assemble: no Dirichlet face, the system is singular");
     cudaStream_t st = (cudaStream_t)stream;
+    AllocStream alloc_scope(st);
     const size_t n = (size_t)n64;
     int dev = 0;
     GW_CUDA(cudaGetDevice(&dev));
@@ -621,6 +622,7 @@ int gw_matrix_export(gw_matrix A, int *rowptr, int *col, double *val, void *stre
     if (!A) fail(GW_ERR_ARG, "gw_matrix_export: null matrix");
     DeviceGuard g(A->dev);
     cudaStream_t st = (cudaStream_t)stream;
+    AllocStream alloc_scope(st);
     if (rowptr) to_device(rowptr, A->A.rp.p, ((size_t)A->A.nr + 1) * sizeof(int), st);
     if (col) to_device(col, A->A.ci.p, (size_t)A->A.nnz * sizeof(int), st);
     if (val) to_device(val, A->A.v.p, (size_t)A->A.nnz * sizeof(double), st);
@@ -661,6 +663,7 @@ int gw_amg_setup(gw_matrix A, const gw_amg_opts *opts, gw_hierarchy *H_out, void
     if (!(o.delta > 0.0 && o.delta < 1.0)) fail(GW_ERR_ARG, "gw_amg_setup: delta must be in (0, 1)");
     DeviceGuard g(A->dev);
     cudaStream_t st = (cudaStream_t)stream;
+    AllocStream alloc_scope(st);
     gw_hierarchy h = new gw_hierarchy_s;
     try {
         h->base = A;
@@ -684,6 +687,7 @@ int gw_pcg_solve(gw_hierarchy H, const double *b, double *h, double tol, int max
     Hier &hh = *H->h;
     DeviceGuard g(hh.dev);
     cudaStream_t st = (cudaStream_t)stream;
+    AllocStream alloc_scope(st);
     const size_t bytes = (size_t)hh.n * sizeof(double);
     GW_CUDA(cudaMemcpyAsync(hh.b.p, b, bytes, cudaMemcpyDefault, st));
     status = pcg_run(hh, tol, maxit, iters, relres, st);
@@ -720,6 +724,7 @@ int gw_pcg_solve_many(gw_hierarchy H, int k, const double *B, double *X, double 
     Hier &hh = *H->h;
     DeviceGuard g(hh.dev);
     cudaStream_t st = (cudaStream_t)stream;
+    AllocStream alloc_scope(st);
     const size_t n = (size_t)hh.n, bytes = n * sizeof(double);
     if (k > 1 && block_supported(hh)) {
         worst = block_solve(hh, k, B, X, tol, maxit, iters, relres, st);
@@ -756,6 +761,7 @@ int gw_hierarchy_shift(gw_hierarchy H, const double *s, double delta, int *rebui
     gw_matrix C = H->base;
     DeviceGuard g(C->dev);
     cudaStream_t st = (cudaStream_t)stream;
+    AllocStream alloc_scope(st);
     const int n = C->A.nr;
     const int gb = (int)std::min<long long>(((long long)n + 255) / 256, 152LL * 16);
     DBuf<double> snew;
@@ -843,6 +849,7 @@ int gw_vcycle(gw_hierarchy H, const double *r, double *z, void *stream)
     if (!is_device_ptr(r) || !is_device_ptr(z)) fail(GW_ERR_ARG, "gw_vcycle: r and z must be device pointers");
     DeviceGuard g(H->h->dev);
     cudaStream_t st = (cudaStream_t)stream;
+    AllocStream alloc_scope(st);
     vcycle_enqueue(*H->h, r, z, nullptr, false, st);
     GW_CUDA(cudaStreamSynchronize(st));
     GW_API_END
@@ -866,6 +873,7 @@ int gw_hierarchy_export(gw_hierarchy H, int level, int *agg, unsigned char *root
     if (level < 0 || level >= hh.L) fail(GW_ERR_ARG, "gw_hierarchy_export: level out of range");
     DeviceGuard g(hh.dev);
     cudaStream_t st = (cudaStream_t)stream;
+    AllocStream alloc_scope(st);
     const DCSR &A = level == 0 ? *hh.A0 : hh.A[(size_t)level];
     const size_t n = (size_t)A.nr;
     if (agg && hh.agg[(size_t)level].p) to_device(agg, hh.agg[(size_t)level].p, n * sizeof(int), st);

@@ -414,6 +414,7 @@ extern "C" int gw_adjoint_gradient(const gw_grid *grid, const double *Kx, const 
             G.bcv[f] = bc->value[f];
         }
         cudaStream_t st = (cudaStream_t)stream;
+        AllocStream alloc_scope(st);
         const int grid_b = (int)std::min<long long>((n64 + 255) / 256, 152LL * 16);
         gw_launch(k_adj_grad, grid_b, 256, 0, st, G, Kx, ky, kz, h, lambda, grad);
         GW_LAUNCH_CHECK();
@@ -435,6 +436,7 @@ extern "C" int gw_misfit(int n, const double *h, int nobs, const int *obs, const
         if (n < 1 || nobs < 0 || nobs > (1 << 24) || !h || !J || (nobs && (!obs || !hobs)))
             fail(GW_ERR_ARG, "gw_misfit: bad argument");
         cudaStream_t st = (cudaStream_t)stream;
+        AllocStream alloc_scope(st);
         DBuf<double> jd(1);
         if (dJdh) {
             gw_launch(k_zero, (int)std::min<long long>((n + 255) / 256, 152LL * 16), 256, 0, st, n, dJdh);
@@ -482,6 +484,7 @@ extern "C" int gw_darcy_flux(const gw_grid *grid, const double *Kx, const double
         }
         if ((long long)nx * ny * nz > 0x7fffffffLL) fail(GW_ERR_ARG, "gw_darcy_flux: more than 2^31 - 1 cells");
         cudaStream_t st = (cudaStream_t)stream;
+        AllocStream alloc_scope(st);
         const long long n = (long long)nx * ny * nz;
         const int gb = (int)std::min<long long>((n + 255) / 256, 152LL * 8);
         gw_launch(k_darcy, gb, 256, 0, st, G, K[0], K[1], K[2], h, v[0], v[1], v[2]);

@@ -2681,6 +2681,7 @@ static const char *batch_unsupported(const Hier &H, int degree)
 
 int batch_add(Batch &B, Hier &H, const double *b, double tol, int maxit)
 {
+    AllocStream alloc_scope(B.st);
     if (const char *why = batch_unsupported(H, B.degree)) fail(GW_ERR_ARG, "gw_batch_add: %s", why);
     if (H.dev != B.dev) fail(GW_ERR_ARG, "gw_batch_add: the hierarchy lives on another device");
     for (int s = 0; s < B.max_slots; ++s)
@@ -2767,6 +2768,7 @@ int batch_add(Batch &B, Hier &H, const double *b, double tol, int maxit)
 // waiting to be taken.
 int batch_run(Batch &B, int iterations)
 {
+    AllocStream alloc_scope(B.st);
     NvtxRange range("gw batch replays");
     int running = 0;
     for (int s = 0; s < B.max_slots; ++s) running += B.state[(size_t)s] == 1;
@@ -2793,6 +2795,7 @@ int batch_state(const Batch &B, int slot) { return slot >= 0 && slot < B.max_slo
 // its iterations and true relative residual; frees the slot.
 int batch_take(Batch &B, int slot, double *h, int *iters, double *relres)
 {
+    AllocStream alloc_scope(B.st);
     if (slot < 0 || slot >= B.max_slots || B.state[(size_t)slot] != 2)
         fail(GW_ERR_ARG, "gw_batch_take: slot %d holds no finished solve", slot);
     Hier &H = *B.slot_h[(size_t)slot];

@@ -49,14 +49,39 @@ const char *last_error_cstr();
 #define GW_LAUNCH_CHECK() GW_CUDA(cudaGetLastError())
 
 // ------------------------------------------------- allocation vs capture --
-// cudaFree (and cudaFreeHost) synchronise the device, which invalidates a
-// graph capture that another thread has in progress.  Every allocation and
-// free of the library therefore waits while a capture is in progress, and a
-// capture waits for allocations in flight.
-cudaError_t dev_malloc(void **p, size_t bytes);
-void dev_free(void *p);
+// Device memory comes from a library-owned memory pool per device through
+// stream-ordered allocation: a buffer is taken on the stream of the API call
+// in progress on this thread (AllocStream, set by every entry point that takes
+// a stream) and given back on the stream of the call that releases it, after
+// that call's earlier work.  Buffers released outside any call (a handle
+// freed) go back on a library stream of the device: every call that uses a
+// handle's buffers has finished its device work when it returns, except
+// gw_vcycle, whose work the caller lets finish before freeing the hierarchy.
+// The pool keeps the memory it has, so that neither an allocation nor a free
+// goes to the driver or synchronises the device once the pool has grown.
+// Without an AllocStream (buffers made outside an API call) plain cudaMalloc
+// and cudaFree are used.  cudaFree and cudaFreeHost synchronise the device,
+// which invalidates a graph capture that another thread has in progress:
+// every allocation and free of the library therefore waits while a capture
+// is in progress, and a capture waits for allocations in flight.
+cudaError_t dev_malloc(void **p, size_t bytes, int *pool_dev);
+void dev_free(void *p, int pool_dev);
+// the same on an explicit stream, for a buffer used and released within one
+// stream's work
+cudaError_t dev_malloc_on(void **p, size_t bytes, cudaStream_t st);
+void dev_free_on(void *p, cudaStream_t st);
 cudaError_t host_malloc(void **p, size_t bytes);
 void host_free(void *p);
+struct AllocStream {
+    explicit AllocStream(cudaStream_t st);
+    ~AllocStream();
+    AllocStream(const AllocStream &) = delete;
+    AllocStream &operator=(const AllocStream &) = delete;
+
+  private:
+    cudaStream_t prev_;
+    bool prev_on_;
+};
 // Device allocations made by the library so far (cudaMalloc and
 // cudaMallocAsync calls), for callers that must check that a call allocates
 // nothing.
@@ -78,32 +103,41 @@ template <class T>
 struct DBuf {
     T *p = nullptr;
     size_t n = 0;
+    int pdev = -1;  // device of the pool it came from, -1 for cudaMalloc
     DBuf() = default;
     explicit DBuf(size_t n_) { alloc(n_); }
     void alloc(size_t n_)
     {
         release();
+        if (n_) GW_CUDA(dev_malloc((void **)&p, n_ * sizeof(T), &pdev));
         n = n_;
-        if (n) GW_CUDA(dev_malloc((void **)&p, n * sizeof(T)));
     }
     void release()
     {
-        if (p) dev_free(p);
+        if (p) dev_free(p, pdev);
         p = nullptr;
         n = 0;
+        pdev = -1;
     }
     ~DBuf() { release(); }
     DBuf(const DBuf &) = delete;
     DBuf &operator=(const DBuf &) = delete;
-    DBuf(DBuf &&o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+    DBuf(DBuf &&o) noexcept : p(o.p), n(o.n), pdev(o.pdev)
+    {
+        o.p = nullptr;
+        o.n = 0;
+        o.pdev = -1;
+    }
     DBuf &operator=(DBuf &&o) noexcept
     {
         if (this != &o) {
             release();
             p = o.p;
             n = o.n;
+            pdev = o.pdev;
             o.p = nullptr;
             o.n = 0;
+            o.pdev = -1;
         }
         return *this;
     }

@@ -1,5 +1,6 @@
 // util.cu -- error plumbing, device scan and small host helpers of libgw.
 #include <stdarg.h>
+#include <string.h>
 
 #include <atomic>
 #include <condition_variable>
@@ -35,19 +36,93 @@ static std::atomic<long long> g_device_allocs{0};
 
 long long device_allocations() { return g_device_allocs.load(); }
 
-cudaError_t dev_malloc(void **p, size_t bytes)
+static thread_local cudaStream_t t_alloc_stream = nullptr;
+static thread_local bool t_alloc_on = false;
+
+AllocStream::AllocStream(cudaStream_t st) : prev_(t_alloc_stream), prev_on_(t_alloc_on)
+{
+    t_alloc_stream = st;
+    t_alloc_on = true;
+}
+
+AllocStream::~AllocStream()
+{
+    t_alloc_stream = prev_;
+    t_alloc_on = prev_on_;
+}
+
+constexpr int POOL_DEVS = 64;
+struct DevPool {
+    cudaMemPool_t pool = nullptr;
+    cudaStream_t free_st = nullptr;  // releases made outside any call
+};
+static DevPool g_pool[POOL_DEVS];
+
+// with g_alloc_mu held
+static DevPool &pool_of(int dev)
+{
+    DevPool &d = g_pool[dev];
+    if (!d.pool) {
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof props);
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        GW_CUDA(cudaMemPoolCreate(&d.pool, &props));
+        unsigned long long keep = ~0ULL;
+        GW_CUDA(cudaMemPoolSetAttribute(d.pool, cudaMemPoolAttrReleaseThreshold, &keep));
+        GW_CUDA(cudaStreamCreateWithFlags(&d.free_st, cudaStreamNonBlocking));
+    }
+    return d;
+}
+
+static int current_pool_device()
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= POOL_DEVS) return -1;
+    return dev;
+}
+
+cudaError_t dev_malloc(void **p, size_t bytes, int *pool_dev)
 {
     std::unique_lock<std::mutex> lk(g_alloc_mu);
     g_alloc_cv.wait(lk, [] { return g_captures == 0; });
     g_device_allocs.fetch_add(1);
-    return cudaMalloc(p, bytes);
+    *pool_dev = -1;
+    const int dev = t_alloc_on ? current_pool_device() : -1;
+    if (dev < 0) return cudaMalloc(p, bytes);
+    const cudaError_t e = cudaMallocFromPoolAsync(p, bytes, pool_of(dev).pool, t_alloc_stream);
+    if (e == cudaSuccess) *pool_dev = dev;
+    return e;
 }
 
-void dev_free(void *p)
+void dev_free(void *p, int pool_dev)
 {
     std::unique_lock<std::mutex> lk(g_alloc_mu);
     g_alloc_cv.wait(lk, [] { return g_captures == 0; });
-    cudaFree(p);
+    if (pool_dev < 0) {
+        cudaFree(p);
+        return;
+    }
+    cudaFreeAsync(p, t_alloc_on ? t_alloc_stream : pool_of(pool_dev).free_st);
+}
+
+cudaError_t dev_malloc_on(void **p, size_t bytes, cudaStream_t st)
+{
+    std::unique_lock<std::mutex> lk(g_alloc_mu);
+    g_alloc_cv.wait(lk, [] { return g_captures == 0; });
+    g_device_allocs.fetch_add(1);
+    const int dev = current_pool_device();
+    if (dev < 0) return cudaMallocAsync(p, bytes, st);
+    return cudaMallocFromPoolAsync(p, bytes, pool_of(dev).pool, st);
+}
+
+void dev_free_on(void *p, cudaStream_t st)
+{
+    std::unique_lock<std::mutex> lk(g_alloc_mu);
+    g_alloc_cv.wait(lk, [] { return g_captures == 0; });
+    cudaFreeAsync(p, st);
 }
 
 cudaError_t host_malloc(void **p, size_t bytes)
@@ -154,8 +229,7 @@ void exclusive_scan(const int *in, int *out, int n, cudaStream_t st)
     }
     int nb = (n + SCAN_CHUNK - 1) / SCAN_CHUNK;
     int *bsum = nullptr;
-    g_device_allocs.fetch_add(1);
-    GW_CUDA(cudaMallocAsync((void **)&bsum, (size_t)(nb + 1) * sizeof(int), st));
+    GW_CUDA(dev_malloc_on((void **)&bsum, (size_t)(nb + 1) * sizeof(int), st));
     gw_launch(k_scan_block, nb, SCAN_BS, 0, st, in, out, bsum, n);
     GW_LAUNCH_CHECK();
     if (nb > 1) {
@@ -167,7 +241,7 @@ void exclusive_scan(const int *in, int *out, int n, cudaStream_t st)
         gw_launch(k_set_at, 1, 1, 0, st, out + n, bsum);
     }
     GW_LAUNCH_CHECK();
-    GW_CUDA(cudaFreeAsync(bsum, st));
+    dev_free_on(bsum, st);
 }
 
 // Same scan, with the block totals kept in caller-provided device memory of

@@ -723,15 +723,16 @@ __device__ int sg_build_set(const int *__restrict__ lrp, const int *__restrict__
 
 // Distinct columns of every row (table per row sized by its own bound), and
 // their maximum, which sizes the numeric pass's tables.
-__global__ void k_sg_symbolic(int nr, const int *__restrict__ lrp, const int *__restrict__ lci,
-                              const int *__restrict__ rrp, const int *__restrict__ rci, int H, int *__restrict__ cnt,
-                              int *__restrict__ overflow, int *__restrict__ maxu)
+__global__ void k_sg_symbolic(int nr, const int *__restrict__ rows, const int *__restrict__ lrp,
+                              const int *__restrict__ lci, const int *__restrict__ rrp, const int *__restrict__ rci,
+                              int H, int *__restrict__ cnt, int *__restrict__ overflow, int *__restrict__ maxu)
 {
     extern __shared__ int sg_smem[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, W = blockDim.x >> 5;
     int *keys = sg_smem + (size_t)w * H;
     int best = 0;
-    for (long long row = (long long)blockIdx.x * W + w; row < nr; row += (long long)gridDim.x * W) {
+    for (long long rr = (long long)blockIdx.x * W + w; rr < nr; rr += (long long)gridDim.x * W) {
+        const int row = rows ? rows[rr] : (int)rr;
         const int Hr = sg_row_table(lrp, lci, rrp, (int)row, H, lane);
         int u = sg_build_set(lrp, lci, rrp, rci, (int)row, keys, Hr, lane);
         if (lane == 0) {
@@ -744,10 +745,10 @@ __global__ void k_sg_symbolic(int nr, const int *__restrict__ lrp, const int *__
     if (lane == 0 && best > 0) atomicMax(maxu, best);
 }
 
-__global__ void k_sg_numeric(int nr, const int *__restrict__ lrp, const int *__restrict__ lci,
-                             const double *__restrict__ lv, const int *__restrict__ rrp, const int *__restrict__ rci,
-                             const double *__restrict__ rv, int H, const int *__restrict__ crp, int *__restrict__ cci,
-                             double *__restrict__ cv)
+__global__ void k_sg_numeric(int nr, const int *__restrict__ rows, const int *__restrict__ lrp,
+                             const int *__restrict__ lci, const double *__restrict__ lv, const int *__restrict__ rrp,
+                             const int *__restrict__ rci, const double *__restrict__ rv, int H,
+                             const int *__restrict__ crp, int *__restrict__ cci, double *__restrict__ cv)
 {
     extern __shared__ int sg_smem[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, W = blockDim.x >> 5;
@@ -757,7 +758,7 @@ __global__ void k_sg_numeric(int nr, const int *__restrict__ lrp, const int *__r
     int *list = keys + H;
     double *acc = (double *)(list + H);
     for (long long rr = (long long)blockIdx.x * W + w; rr < nr; rr += (long long)gridDim.x * W) {
-        const int row = (int)rr;
+        const int row = rows ? rows[rr] : (int)rr;
         sg_build_set(lrp, lci, rrp, rci, row, keys, H, lane);
         // compact the table into list (any order), then rank-sort into keys
         int u = 0;
@@ -799,50 +800,189 @@ __global__ void k_sg_numeric(int nr, const int *__restrict__ lrp, const int *__r
     }
 }
 
+// Short rows, one thread each: the distinct columns of the row kept as a
+// sorted list in shared memory (entry t of thread x at [t * SGT_BS + x], so
+// the threads of a warp touch distinct banks).  Symbolic: counts the row's
+// distinct columns; a row with more than SGT_CAP of them goes to the warp
+// kernels' row list instead.  Numeric: inserts each product L(i,k) Rm(k,c)
+// in L's column order k, so every output entry receives its terms in
+// ascending k, the same sums as the warp kernel forms.
+constexpr int SGT_BS = 128, SGT_CAP = 64;
+
+__device__ __forceinline__ int sgt_find(const int *list, int u, int c)
+{
+    int lo = 0, hi = u;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (list[mid * SGT_BS] < c) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(SGT_BS) k_sgt_symbolic(int nr, const int *__restrict__ lrp, const int *__restrict__ lci,
+                                                        const int *__restrict__ rrp, const int *__restrict__ rci,
+                                                        int *__restrict__ cnt, int *__restrict__ long_rows,
+                                                        int *__restrict__ nlong, int *__restrict__ maxu)
+{
+    __shared__ int sl[SGT_CAP * SGT_BS];
+    int *list = sl + threadIdx.x;
+    int best = 0;
+    GRID_STRIDE(ii, nr)
+    {
+        const int i = (int)ii;
+        int u = 0;
+        bool over = false;
+        for (int e = lrp[i]; e < lrp[i + 1] && !over; ++e) {
+            const int k = lci[e];
+            for (int f = rrp[k]; f < rrp[k + 1]; ++f) {
+                const int c = rci[f];
+                const int pos = sgt_find(list, u, c);
+                if (pos < u && list[pos * SGT_BS] == c) continue;
+                if (u == SGT_CAP) {
+                    over = true;
+                    break;
+                }
+                for (int t = u; t > pos; --t) list[t * SGT_BS] = list[(t - 1) * SGT_BS];
+                list[pos * SGT_BS] = c;
+                ++u;
+            }
+        }
+        if (over) {
+            long_rows[atomicAdd(nlong, 1)] = i;
+        } else {
+            cnt[i] = u;
+            best = max(best, u);
+        }
+    }
+    if (best > 0) atomicMax(maxu, best);
+}
+
+template <int CAP>
+__global__ void __launch_bounds__(SGT_BS) k_sgt_numeric(int nr, const int *__restrict__ lrp, const int *__restrict__ lci,
+                                                       const double *__restrict__ lv, const int *__restrict__ rrp,
+                                                       const int *__restrict__ rci, const double *__restrict__ rv,
+                                                       const int *__restrict__ crp, int *__restrict__ cci,
+                                                       double *__restrict__ cv)
+{
+    extern __shared__ double sgt_smem[];  // acc[CAP * SGT_BS] doubles, then list[CAP * SGT_BS] ints
+    double *acc = sgt_smem + threadIdx.x;
+    int *list = (int *)(sgt_smem + CAP * SGT_BS) + threadIdx.x;
+    GRID_STRIDE(ii, nr)
+    {
+        const int i = (int)ii;
+        const int o = crp[i], cnt = crp[i + 1] - o;
+        if (cnt > CAP) continue;  // a long row: the warp kernel's
+        int u = 0;
+        for (int e = lrp[i]; e < lrp[i + 1]; ++e) {
+            const int k = lci[e];
+            const double a = lv[e];
+            for (int f = rrp[k]; f < rrp[k + 1]; ++f) {
+                const int c = rci[f];
+                const int pos = sgt_find(list, u, c);
+                if (!(pos < u && list[pos * SGT_BS] == c)) {
+                    for (int t = u; t > pos; --t) {
+                        list[t * SGT_BS] = list[(t - 1) * SGT_BS];
+                        acc[t * SGT_BS] = acc[(t - 1) * SGT_BS];
+                    }
+                    list[pos * SGT_BS] = c;
+                    acc[pos * SGT_BS] = 0.0;
+                    ++u;
+                }
+                acc[pos * SGT_BS] = __dadd_rn(acc[pos * SGT_BS], __dmul_rn(a, rv[f]));
+            }
+        }
+        for (int t = 0; t < u; ++t) {
+            cci[o + t] = list[t * SGT_BS];
+            cv[o + t] = acc[t * SGT_BS];
+        }
+    }
+}
+
 void setup_spgemm(const DCSR &L, const DCSR &Rm, DCSR &C, cudaStream_t st)
 {
-    DBuf<int> maxub(1), ovf(1), maxu(1);
-    GW_CUDA(cudaMemsetAsync(maxub.p, 0, sizeof(int), st));
-    GW_CUDA(cudaMemsetAsync(ovf.p, 0, sizeof(int), st));
-    GW_CUDA(cudaMemsetAsync(maxu.p, 0, sizeof(int), st));
-    gw_launch(k_sg_bound, nblk(L.nr, 256), 256, 0, st, L.nr, Rm.nc, L.rp.p, L.ci.p, Rm.rp.p, maxub.p);
-    GW_LAUNCH_CHECK();
-    const int ub = read_int(maxub.p, st);
-    int H = 32;
-    while (H < 2 * ub && H < SG_HMAX) H <<= 1;
-    // warps per block so that a block's tables stay within 96 KB
-    const int W = (int)std::max<size_t>(1, std::min<size_t>(8, (96u << 10) / ((size_t)H * sizeof(int))));
-    const size_t smem_sym = (size_t)W * H * sizeof(int);
+    // 0: long rows, 1: their count, 2: largest distinct count of the short rows,
+    // 3: bound of the long rows, 4: overflow, 5: largest distinct count of the long rows
+    DBuf<int> ctr(6), long_rows;
+    GW_CUDA(cudaMemsetAsync(ctr.p, 0, ctr.bytes(), st));
+    C.nr = L.nr;
+    C.nc = Rm.nc;
+    C.rp.alloc((size_t)C.nr + 1);
+    // A thread a row pays off for many short rows (the level-0 products A P
+    // with about 24 products a row, 2M rows); with few rows or hundreds of
+    // products a row a warp a row is faster.  Products a row estimated from
+    // the mean row lengths.
+    const double per_row = L.nr ? (double)L.nnz / L.nr * ((double)Rm.nnz / std::max(1, Rm.nr)) : 0.0;
+    const bool thread_rows = L.nr >= 32768 && per_row <= 128.0;
+    const int gt = nblk(L.nr, SGT_BS, 152LL * 64);
+    int nlong = L.nr, mu_short = 0;
+    if (thread_rows) {
+        long_rows.alloc((size_t)L.nr);
+        gw_launch(k_sgt_symbolic, gt, SGT_BS, 0, st, L.nr, L.rp.p, L.ci.p, Rm.rp.p, Rm.ci.p, C.rp.p, long_rows.p,
+                  ctr.p + 1, ctr.p + 2);
+        GW_LAUNCH_CHECK();
+        int hc[2];
+        GW_CUDA(cudaMemcpyAsync(hc, ctr.p + 1, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        GW_CUDA(cudaStreamSynchronize(st));
+        nlong = hc[0];
+        mu_short = hc[1];
+    }
+    const int *rows = thread_rows ? (const int *)long_rows.p : nullptr;
     // The attribute is global to the kernel, and setups may run concurrently on
     // several threads: always set the same value, the largest any launch uses.
     GW_CUDA(cudaFuncSetAttribute(k_sg_symbolic, cudaFuncAttributeMaxDynamicSharedMemorySize, SG_SMEM_MAX));
     GW_CUDA(cudaFuncSetAttribute(k_sg_numeric, cudaFuncAttributeMaxDynamicSharedMemorySize, SG_SMEM_MAX));
-    if (smem_sym > (size_t)SG_SMEM_MAX)
-        fail(GW_ERR_SETUP, "SpGEMM shared memory %zu exceeds %d", smem_sym, SG_SMEM_MAX);
-    C.nr = L.nr;
-    C.nc = Rm.nc;
-    C.rp.alloc((size_t)C.nr + 1);
-    const int grid = (int)std::max(1LL, std::min<long long>(((long long)L.nr + W - 1) / W, 152LL * 64));
-    gw_launch(k_sg_symbolic, grid, 32 * W, smem_sym, st, L.nr, L.rp.p, L.ci.p, Rm.rp.p, Rm.ci.p, H, C.rp.p, ovf.p,
-              maxu.p);
-    GW_LAUNCH_CHECK();
-    if (read_int(ovf.p, st)) fail(GW_ERR_SETUP, "SpGEMM row has more than %d distinct columns", H / 2);
-    // the numeric pass knows every row's distinct count: tables of twice the largest
-    const int mu = read_int(maxu.p, st);
-    int Hn = 32;
-    while (Hn < 2 * mu) Hn <<= 1;
-    const size_t per_warp_num = (size_t)Hn * 12;
-    const int Wn = (int)std::max<size_t>(1, std::min<size_t>(8, (96u << 10) / per_warp_num));
-    const size_t smem_num = (size_t)Wn * per_warp_num;
-    if (smem_num > (size_t)SG_SMEM_MAX) fail(GW_ERR_SETUP, "SpGEMM shared memory %zu exceeds %d", smem_num, SG_SMEM_MAX);
-    const int grid_n = (int)std::max(1LL, std::min<long long>(((long long)L.nr + Wn - 1) / Wn, 152LL * 64));
+    int Hn = 0, Wn = 0;
+    if (nlong > 0) {
+        // rows with more than SGT_CAP distinct columns: a warp each
+        gw_launch(k_sg_bound, nblk(L.nr, 256), 256, 0, st, L.nr, Rm.nc, L.rp.p, L.ci.p, Rm.rp.p, ctr.p + 3);
+        GW_LAUNCH_CHECK();
+        const int ub = read_int(ctr.p + 3, st);
+        int H = 32;
+        while (H < 2 * ub && H < SG_HMAX) H <<= 1;
+        // warps per block so that a block's tables stay within 96 KB
+        const int W = (int)std::max<size_t>(1, std::min<size_t>(8, (96u << 10) / ((size_t)H * sizeof(int))));
+        const size_t smem_sym = (size_t)W * H * sizeof(int);
+        if (smem_sym > (size_t)SG_SMEM_MAX)
+            fail(GW_ERR_SETUP, "SpGEMM shared memory %zu exceeds %d", smem_sym, SG_SMEM_MAX);
+        const int grid = (int)std::max(1LL, std::min<long long>(((long long)nlong + W - 1) / W, 152LL * 64));
+        gw_launch(k_sg_symbolic, grid, 32 * W, smem_sym, st, nlong, rows, L.rp.p, L.ci.p,
+                  Rm.rp.p, Rm.ci.p, H, C.rp.p, ctr.p + 4, ctr.p + 5);
+        GW_LAUNCH_CHECK();
+        int hl[2];
+        GW_CUDA(cudaMemcpyAsync(hl, ctr.p + 4, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        GW_CUDA(cudaStreamSynchronize(st));
+        if (hl[0]) fail(GW_ERR_SETUP, "SpGEMM row has more than %d distinct columns", H / 2);
+        // the numeric pass knows every row's distinct count: tables of twice the largest
+        Hn = 32;
+        while (Hn < 2 * hl[1]) Hn <<= 1;
+        const size_t per_warp_num = (size_t)Hn * 12;
+        Wn = (int)std::max<size_t>(1, std::min<size_t>(8, (96u << 10) / per_warp_num));
+        if ((size_t)Wn * per_warp_num > (size_t)SG_SMEM_MAX)
+            fail(GW_ERR_SETUP, "SpGEMM shared memory %zu exceeds %d", (size_t)Wn * per_warp_num, SG_SMEM_MAX);
+    }
     exclusive_scan(C.rp.p, C.rp.p, C.nr, st);
     C.nnz = read_int(C.rp.p + C.nr, st);
     C.ci.alloc((size_t)C.nnz);
     C.v.alloc((size_t)C.nnz);
-    gw_launch(k_sg_numeric, grid_n, 32 * Wn, smem_num, st, L.nr, L.rp.p, L.ci.p, L.v.p, Rm.rp.p, Rm.ci.p, Rm.v.p, Hn, C.rp.p,
-                                                  C.ci.p, C.v.p);
-    GW_LAUNCH_CHECK();
+    if (mu_short > 0) {
+        auto numeric = [&](auto kernel, int cap) {
+            GW_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SGT_CAP * SGT_BS * 12));
+            gw_launch(kernel, gt, SGT_BS, (size_t)cap * SGT_BS * 12, st, L.nr, L.rp.p, L.ci.p, L.v.p, Rm.rp.p,
+                      Rm.ci.p, Rm.v.p, C.rp.p, C.ci.p, C.v.p);
+        };
+        if (mu_short <= 16) numeric(k_sgt_numeric<16>, 16);
+        else if (mu_short <= 32) numeric(k_sgt_numeric<32>, 32);
+        else numeric(k_sgt_numeric<SGT_CAP>, SGT_CAP);
+        GW_LAUNCH_CHECK();
+    }
+    if (nlong > 0) {
+        const size_t smem_num = (size_t)Wn * Hn * 12;
+        const int grid_n = (int)std::max(1LL, std::min<long long>(((long long)nlong + Wn - 1) / Wn, 152LL * 64));
+        gw_launch(k_sg_numeric, grid_n, 32 * Wn, smem_num, st, nlong, rows, L.rp.p, L.ci.p,
+                  L.v.p, Rm.rp.p, Rm.ci.p, Rm.v.p, Hn, C.rp.p, C.ci.p, C.v.p);
+        GW_LAUNCH_CHECK();
+    }
     GW_CUDA(cudaStreamSynchronize(st));
 }
 

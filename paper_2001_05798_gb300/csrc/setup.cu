@@ -468,6 +468,140 @@ __global__ void k_p_fill(int n, const int *__restrict__ rp, const int *__restric
     }
 }
 
+// The same two passes with a warp per row, for levels whose rows are long
+// (the thread-per-row passes above are quadratic in the row length).  The
+// row's member aggregates (j = i or strong) go to shared memory; an entry is
+// the first occurrence of its aggregate if no earlier entry has it; the
+// first occurrences are counted, and each one's column is its rank among
+// them, its value the sum over the row's entries of that aggregate in
+// ascending j, as in k_p_fill.  Rows of more than PW_MAX entries take the
+// serial path on lane 0.
+constexpr int PW_MAX = 256, PW_WARPS = 8;
+
+__device__ void pw_load(int i, int e0, int len, const int *__restrict__ ci, const unsigned char *__restrict__ S,
+                        const int *__restrict__ agg, int *sagg, unsigned char *sfirst, int lane)
+{
+    for (int t = lane; t < len; t += 32) {
+        const int j = ci[e0 + t];
+        sagg[t] = p_member(i, j, S[e0 + t]) ? agg[j] : -1;
+    }
+    __syncwarp();
+    for (int t = lane; t < len; t += 32) {
+        const int a = sagg[t];
+        bool first = a >= 0;
+        for (int u = 0; u < t && first; ++u)
+            if (sagg[u] == a) first = false;
+        sfirst[t] = first;
+    }
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(32 * PW_WARPS) k_p_count_w(int n, const int *__restrict__ rp,
+                                                            const int *__restrict__ ci,
+                                                            const unsigned char *__restrict__ S,
+                                                            const int *__restrict__ agg,
+                                                            const unsigned char *__restrict__ hs,
+                                                            int *__restrict__ cnt)
+{
+    __shared__ int sagg_all[PW_WARPS][PW_MAX];
+    __shared__ unsigned char sfirst_all[PW_WARPS][PW_MAX];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (long long ii = (long long)blockIdx.x * PW_WARPS + w; ii < n; ii += (long long)gridDim.x * PW_WARPS) {
+        const int i = (int)ii, e0 = rp[i], len = rp[i + 1] - e0;
+        if (!hs[i]) {
+            if (lane == 0) cnt[i] = 1;
+            continue;
+        }
+        int c = 0;
+        if (len > PW_MAX) {
+            if (lane == 0) {
+                for (int e = e0; e < e0 + len; ++e) {
+                    const int j = ci[e];
+                    if (!p_member(i, j, S[e])) continue;
+                    const int a = agg[j];
+                    bool dup = false;
+                    for (int f = e0; f < e && !dup; ++f)
+                        if (p_member(i, ci[f], S[f]) && agg[ci[f]] == a) dup = true;
+                    if (!dup) ++c;
+                }
+                cnt[i] = c;
+            }
+            continue;
+        }
+        pw_load(i, e0, len, ci, S, agg, sagg_all[w], sfirst_all[w], lane);
+        for (int t = lane; t < len; t += 32) c += sfirst_all[w][t];
+        for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
+        if (lane == 0) cnt[i] = c;
+        __syncwarp();
+    }
+}
+
+__global__ void __launch_bounds__(32 * PW_WARPS) k_p_fill_w(int n, const int *__restrict__ rp,
+                                                           const int *__restrict__ ci, const double *__restrict__ v,
+                                                           const unsigned char *__restrict__ S,
+                                                           const int *__restrict__ agg,
+                                                           const unsigned char *__restrict__ hs,
+                                                           const double *__restrict__ aF, double omega,
+                                                           const int *__restrict__ prp, int *__restrict__ pci,
+                                                           double *__restrict__ pv)
+{
+    __shared__ int sagg_all[PW_WARPS][PW_MAX];
+    __shared__ unsigned char sfirst_all[PW_WARPS][PW_MAX];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int *sagg = sagg_all[w];
+    unsigned char *sfirst = sfirst_all[w];
+    for (long long ii = (long long)blockIdx.x * PW_WARPS + w; ii < n; ii += (long long)gridDim.x * PW_WARPS) {
+        const int i = (int)ii, e0 = rp[i], len = rp[i + 1] - e0;
+        const int o = prp[i], ai = agg[i];
+        if (!hs[i]) {
+            if (lane == 0) {
+                pci[o] = ai;
+                pv[o] = 1.0;
+            }
+            continue;
+        }
+        const double s = __ddiv_rn(omega, aF[i]);
+        if (len > PW_MAX) {
+            if (lane == 0) {
+                const int cnt = prp[i + 1] - o;
+                int last = -1;
+                for (int t = 0; t < cnt; ++t) {
+                    int c = 0x7fffffff;
+                    for (int e = e0; e < e0 + len; ++e) {
+                        const int j = ci[e];
+                        if (!p_member(i, j, S[e])) continue;
+                        const int a = agg[j];
+                        if (a > last && a < c) c = a;
+                    }
+                    double acc = 0.0;
+                    for (int e = e0; e < e0 + len; ++e) {
+                        const int j = ci[e];
+                        if (!p_member(i, j, S[e]) || agg[j] != c) continue;
+                        acc = __dadd_rn(acc, j == i ? aF[i] : v[e]);
+                    }
+                    pci[o + t] = c;
+                    pv[o + t] = __dsub_rn(c == ai ? 1.0 : 0.0, __dmul_rn(s, acc));
+                    last = c;
+                }
+            }
+            continue;
+        }
+        pw_load(i, e0, len, ci, S, agg, sagg, sfirst, lane);
+        for (int t = lane; t < len; t += 32) {
+            if (!sfirst[t]) continue;
+            const int a = sagg[t];
+            int rank = 0;
+            for (int u = 0; u < len; ++u) rank += sfirst[u] && sagg[u] < a;
+            double acc = 0.0;
+            for (int u = t; u < len; ++u)
+                if (sagg[u] == a) acc = __dadd_rn(acc, ci[e0 + u] == i ? aF[i] : v[e0 + u]);
+            pci[o + rank] = a;
+            pv[o + rank] = __dsub_rn(a == ai ? 1.0 : 0.0, __dmul_rn(s, acc));
+        }
+        __syncwarp();
+    }
+}
+
 void setup_smooth_p(const DCSR &A, const unsigned char *S, const int *agg, int nagg, DCSR &P, double *omega,
                     double *rho, cudaStream_t st)
 {
@@ -490,13 +624,22 @@ void setup_smooth_p(const DCSR &A, const unsigned char *S, const int *agg, int n
     P.nr = n;
     P.nc = nagg;
     P.rp.alloc((size_t)n + 1);
-    gw_launch(k_p_count, g, 256, 0, st, n, A.rp.p, A.ci.p, S, agg, hs.p, P.rp.p);
+    // a warp a row where rows are long (the coarse levels), a thread a row otherwise
+    const bool warp_rows = n > 0 && (double)A.nnz / n > 12.0;
+    const int gw_ = (int)std::max(1LL, std::min<long long>(((long long)n + PW_WARPS - 1) / PW_WARPS, 152LL * 64));
+    if (warp_rows) gw_launch(k_p_count_w, gw_, 32 * PW_WARPS, 0, st, n, A.rp.p, A.ci.p, S, agg, hs.p, P.rp.p);
+    else gw_launch(k_p_count, g, 256, 0, st, n, A.rp.p, A.ci.p, S, agg, hs.p, P.rp.p);
     GW_LAUNCH_CHECK();
     exclusive_scan(P.rp.p, P.rp.p, n, st);
     P.nnz = read_int(P.rp.p + n, st);
     P.ci.alloc((size_t)P.nnz);
     P.v.alloc((size_t)P.nnz);
-    gw_launch(k_p_fill, g, 256, 0, st, n, A.rp.p, A.ci.p, A.v.p, S, agg, hs.p, aF.p, *omega, P.rp.p, P.ci.p, P.v.p);
+    if (warp_rows)
+        gw_launch(k_p_fill_w, gw_, 32 * PW_WARPS, 0, st, n, A.rp.p, A.ci.p, A.v.p, S, agg, hs.p, aF.p, *omega, P.rp.p,
+                  P.ci.p, P.v.p);
+    else
+        gw_launch(k_p_fill, g, 256, 0, st, n, A.rp.p, A.ci.p, A.v.p, S, agg, hs.p, aF.p, *omega, P.rp.p, P.ci.p,
+                  P.v.p);
     GW_LAUNCH_CHECK();
 }
 
@@ -1214,21 +1357,31 @@ __global__ void k_pow_start(int n, uint64_t seed, int level, double *__restrict_
     }
 }
 
-// w = D^-1 A v and per-block partial sums of w.w
-__global__ void k_pow_step(int n, const int *__restrict__ rp, const int *__restrict__ ci, const double *__restrict__ a,
-                           const double *__restrict__ d, const double *__restrict__ v, double scale,
-                           double *__restrict__ w, double *__restrict__ part)
+// w = D^-1 A v and per-block partial sums of w.w; G lanes a row
+template <int G>
+__global__ void __launch_bounds__(256) k_pow_step(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                                                  const double *__restrict__ a, const double *__restrict__ d,
+                                                  const double *__restrict__ v, double *__restrict__ w,
+                                                  double *__restrict__ part)
 {
     __shared__ double sh[256];
+    const int lane = threadIdx.x & (G - 1);
     double loc = 0.0;
-    GRID_STRIDE(ii, n)
-    {
+    const long long groups = (long long)gridDim.x * (blockDim.x / G);
+    // whole warps stay in the loop (the groups' shuffles need every lane)
+    for (long long ii = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / G;
+         G == 1 ? ii < n : __any_sync(0xffffffffu, ii < n); ii += groups) {
         const int i = (int)ii;
         double s = 0.0;
-        for (int e = rp[i]; e < rp[i + 1]; ++e) s += a[e] * (v[ci[e]] * scale);
-        s /= d[i];
-        w[i] = s;
-        loc += s * s;
+        if (ii < n)
+            for (int e = rp[i] + lane; e < rp[i + 1]; e += G) s += a[e] * v[ci[e]];
+#pragma unroll
+        for (int off = G / 2; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off, G);
+        if (lane == 0 && ii < n) {
+            s /= d[i];
+            w[i] = s;
+            loc += s * s;
+        }
     }
     sh[threadIdx.x] = loc;
     __syncthreads();
@@ -1239,48 +1392,38 @@ __global__ void k_pow_step(int n, const int *__restrict__ rp, const int *__restr
     if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
 }
 
-__global__ void k_sumsq(int n, const double *__restrict__ v, double *__restrict__ part)
-{
-    __shared__ double sh[256];
-    double loc = 0.0;
-    GRID_STRIDE(i, n) loc += v[i] * v[i];
-    sh[threadIdx.x] = loc;
-    __syncthreads();
-    for (int off = 128; off > 0; off >>= 1) {
-        if (threadIdx.x < off) sh[threadIdx.x] += sh[threadIdx.x + off];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
-}
-
-static double host_sum(const DBuf<double> &part, int nb, cudaStream_t st)
-{
-    std::vector<double> h((size_t)nb);
-    GW_CUDA(cudaMemcpyAsync(h.data(), part.p, (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, st));
-    GW_CUDA(cudaStreamSynchronize(st));
-    double s = 0.0;
-    for (int i = 0; i < nb; ++i) s += h[(size_t)i];
-    return s;
-}
-
-// lambda_max(D^-1 A) by 10 power iterations from a hashed start vector
+// lambda_max(D^-1 A) by 10 power iterations from a hashed start vector:
+// x_{k+1} = D^-1 A x_k without normalising (the spectral radius of D^-1 A is
+// a few units at most, so ten steps stay far from overflow), and
+// lambda = |x_10| / |x_9|, the same estimate as normalised iterations give.
+// The ten steps run back to back; the host reads the two last norms once.
 double setup_power_lambda(const DCSR &A, const double *diag, uint64_t seed, int level, cudaStream_t st)
 {
-    const int n = A.nr, g = nblk(n, 256, 1024);
-    DBuf<double> v((size_t)n), w((size_t)n), part((size_t)g);
-    gw_launch(k_pow_start, g, 256, 0, st, n, seed, level, v.p);
-    gw_launch(k_sumsq, g, 256, 0, st, n, v.p, part.p);
+    const int n = A.nr;
+    const double per_row = n ? (double)A.nnz / n : 0.0;
+    const int G = per_row <= 12.0 ? 1 : per_row <= 48.0 ? 8 : 32;
+    const int g = nblk((long long)n * G, 256, 1024);
+    DBuf<double> v((size_t)n), w((size_t)n), part((size_t)2 * g);
+    gw_launch(k_pow_start, nblk(n, 256, 1024), 256, 0, st, n, seed, level, v.p);
     GW_LAUNCH_CHECK();
-    double scale = 1.0 / sqrt(host_sum(part, g, st));
-    double lam = 0.0;
     for (int it = 0; it < 10; ++it) {
-        gw_launch(k_pow_step, g, 256, 0, st, n, A.rp.p, A.ci.p, A.v.p, diag, v.p, scale, w.p, part.p);
+        double *pp = part.p + (size_t)(it & 1) * g;
+        if (G == 1) gw_launch(k_pow_step<1>, g, 256, 0, st, n, A.rp.p, A.ci.p, A.v.p, diag, v.p, w.p, pp);
+        else if (G == 8) gw_launch(k_pow_step<8>, g, 256, 0, st, n, A.rp.p, A.ci.p, A.v.p, diag, v.p, w.p, pp);
+        else gw_launch(k_pow_step<32>, g, 256, 0, st, n, A.rp.p, A.ci.p, A.v.p, diag, v.p, w.p, pp);
         GW_LAUNCH_CHECK();
-        lam = sqrt(host_sum(part, g, st));
         std::swap(v, w);
-        scale = 1.0 / lam;
     }
-    return lam;
+    // it = 8 wrote |x_9|^2 into the first half, it = 9 |x_10|^2 into the second
+    std::vector<double> h((size_t)2 * g);
+    GW_CUDA(cudaMemcpyAsync(h.data(), part.p, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    GW_CUDA(cudaStreamSynchronize(st));
+    double s9 = 0.0, s10 = 0.0;
+    for (int b = 0; b < g; ++b) {
+        s9 += h[(size_t)b];
+        s10 += h[(size_t)g + b];
+    }
+    return s9 > 0.0 ? sqrt(s10 / s9) : 0.0;
 }
 
 // ------------------------------------------------------- sliced ELL format --

@@ -236,6 +236,7 @@ class BatchedServer:
         self.peak_inflight = 0
         self.inflight = 0
         self.capture_gate = _SharedExclusive()
+        self.graph_levels = 0  # depth of the batched graph captured so far
         torch.cuda.set_device(device)
         self.batch = gw.Batch(slots)
         self.setups = [threading.Thread(target=self._setup_worker, daemon=True) for _ in range(setup_workers)]
@@ -326,19 +327,19 @@ class BatchedServer:
                     stream.synchronize()
                 finally:
                     self.capture_gate.release_shared()
-                used = sum(l["bytes"] for l in H.info()) + 16 * n
+                info = H.info()
+                used = sum(l["bytes"] for l in info) + 16 * n
                 with self.cv:
                     self.bytes_per_cell = max(self.bytes_per_cell, 1.25 * used / n)
                     self.ready.append(dict(req=req, fut=fut, arrival=arrival, need=need, H=H, A=A, b=b, h=h, n=n,
-                                           setup_s=time.perf_counter() - t0))
+                                           L=len(info), setup_s=time.perf_counter() - t0))
                     self.cv.notify_all()
             except Exception as e:  # the request fails alone
                 fut.set_exception(e)
                 self._release(need)
 
     def _finish(self, job, slot):
-        _, it, rel, st = self.batch.take(slot, job["h"])
-        torch.cuda.synchronize()
+        _, it, rel, st = self.batch.take(slot, job["h"])  # returns with the batch's stream synchronised
         done = time.perf_counter()
         self.capture_gate.acquire_shared()
         try:
@@ -367,15 +368,21 @@ class BatchedServer:
                 while self.ready and len(running) + len(joining) < self.slots:
                     joining.append(self.ready.popleft())
             for job in joining:
-                self.capture_gate.acquire_exclusive()  # an add may capture the batched graph
+                # an add captures the batched graph again only for a hierarchy deeper
+                # than every one before it: only then must the setup workers pause
+                capture = job["L"] > self.graph_levels
+                if capture:
+                    self.capture_gate.acquire_exclusive()
                 try:
                     slot = self.batch.add(job["H"], job["b"], tol=self.tol, maxit=self.maxit)
+                    self.graph_levels = max(self.graph_levels, job["L"])
                 except Exception as e:
                     job["fut"].set_exception(e)
                     self._release(job["need"])
                     continue
                 finally:
-                    self.capture_gate.release_exclusive()
+                    if capture:
+                        self.capture_gate.release_exclusive()
                 job["start"] = time.perf_counter()
                 running[slot] = job
             if running:

@@ -310,6 +310,7 @@ __device__ __forceinline__ bool reduce_cols(const double (&loc)[NV][CW], double 
     __threadfence();
     for (int q = w; q < NV * KB; q += W) {
         double s = 0.0;
+#pragma unroll 8
         for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(part + (size_t)q * gridDim.x + b);
         s = warp_sum(s);
         if (lane == 0) tot[q] = s;

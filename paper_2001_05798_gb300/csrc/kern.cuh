@@ -165,13 +165,24 @@ __device__ __forceinline__ bool reduce_last(VB vb, const double (&loc)[K], doubl
     __syncthreads();
     if (ticket != (unsigned)vb.nb - 1) return false;
     __threadfence();
-    // last block: warp k adds the partials of value k, lanes strided, in a fixed order
+    // last block: every thread adds the partials b = t, t + BS, ... (their
+    // loads issued together), then the warps' shuffle trees and the warps in
+    // order, a fixed order for a given block count
     __shared__ double fin[K];
-    for (int k = w; k < K; k += W) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
         double s = 0.0;
-        for (int b = lane; b < vb.nb; b += 32) s += __ldcg(part + (size_t)k * vb.nb + b);
+#pragma unroll 8
+        for (int b = threadIdx.x; b < vb.nb; b += BS) s += __ldcg(part + (size_t)k * vb.nb + b);
         s = warp_sum(s);
-        if (lane == 0) fin[k] = s;
+        if (lane == 0) sh[k][w] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < K) {
+        double s = 0.0;
+#pragma unroll
+        for (int q = 0; q < W; ++q) s += sh[threadIdx.x][q];
+        fin[threadIdx.x] = s;
     }
     if (threadIdx.x == 0) *cnt = 0u;
     __syncthreads();

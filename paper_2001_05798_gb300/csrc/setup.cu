@@ -13,6 +13,7 @@
 // fused, and every sum runs in ascending column order of its row -- the same
 // order a serial FP64 implementation follows -- so aggregates, patterns and
 // values match such an implementation exactly.
+#include <stdlib.h>
 #include <string.h>
 
 #include "gw_internal.cuh"
@@ -26,6 +27,23 @@ static inline int nblk(long long n, int bs, long long cap = 152LL * 32)
 }
 
 #define GRID_STRIDE(i, n) for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (n); i += (long long)gridDim.x * blockDim.x)
+
+// Row-parallel form of the SpGEMM and prolongator passes: chosen per product
+// from the row counts and lengths (0), or forced to a thread a row (1) or a
+// warp a row (2) by GW_SETUP_FORMS=thread|warp in the environment, read once,
+// so that tests can check both forms against the oracle on any problem.  Both
+// forms give the same bits.
+static int setup_forms()
+{
+    static const int f = [] {
+        const char *e = getenv("GW_SETUP_FORMS");
+        if (!e) return 0;
+        if (!strcmp(e, "thread")) return 1;
+        if (!strcmp(e, "warp")) return 2;
+        return 0;
+    }();
+    return f;
+}
 
 // SplitMix64 (Steele, Lea & Flood 2014): finaliser of x + golden gamma.
 __device__ __forceinline__ uint64_t smix64(uint64_t x)
@@ -625,7 +643,7 @@ void setup_smooth_p(const DCSR &A, const unsigned char *S, const int *agg, int n
     P.nc = nagg;
     P.rp.alloc((size_t)n + 1);
     // a warp a row where rows are long (the coarse levels), a thread a row otherwise
-    const bool warp_rows = n > 0 && (double)A.nnz / n > 12.0;
+    const bool warp_rows = setup_forms() ? setup_forms() == 2 : n > 0 && (double)A.nnz / n > 12.0;
     const int gw_ = (int)std::max(1LL, std::min<long long>(((long long)n + PW_WARPS - 1) / PW_WARPS, 152LL * 64));
     if (warp_rows) gw_launch(k_p_count_w, gw_, 32 * PW_WARPS, 0, st, n, A.rp.p, A.ci.p, S, agg, hs.p, P.rp.p);
     else gw_launch(k_p_count, g, 256, 0, st, n, A.rp.p, A.ci.p, S, agg, hs.p, P.rp.p);
@@ -1056,7 +1074,7 @@ void setup_spgemm(const DCSR &L, const DCSR &Rm, DCSR &C, cudaStream_t st)
     // products a row a warp a row is faster.  Products a row estimated from
     // the mean row lengths.
     const double per_row = L.nr ? (double)L.nnz / L.nr * ((double)Rm.nnz / std::max(1, Rm.nr)) : 0.0;
-    const bool thread_rows = L.nr >= 32768 && per_row <= 128.0;
+    const bool thread_rows = setup_forms() ? setup_forms() == 1 : L.nr >= 32768 && per_row <= 128.0;
     const int gt = nblk(L.nr, SGT_BS, 152LL * 64);
     int nlong = L.nr, mu_short = 0;
     if (thread_rows) {

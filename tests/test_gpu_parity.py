@@ -135,6 +135,27 @@ def test_setup_bit_exact_other_seed(gw):
     compare_setup(gw, PROBLEMS["3d_het_20"](), n_coarse=64, seed=12345)
 
 
+@pytest.mark.parametrize("form", ["thread", "warp"])
+def test_setup_bit_exact_in_each_row_form(gw, form):
+    """The SpGEMM and the smoothed-prolongator passes have a thread-per-row and
+    a warp-per-row form (the library picks one per product from the row
+    counts and lengths, so small problems would only see one of them);
+    GW_SETUP_FORMS forces either on every product, including the thread
+    form's hand-over of rows with more than 64 distinct columns to the warp
+    form.  Every level stays bit-exact with the oracle.  The variable is read
+    once per process, so the setup tests run again in a child process."""
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, GW_SETUP_FORMS=form)
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-m", "gpu", "-p", "no:cacheprovider",
+                        "-k", "setup_bit_exact and not each_row_form", os.path.join(root, "tests", "test_gpu_parity.py")],
+                       env=env, cwd=root, capture_output=True, text=True, timeout=1200)
+    assert r.returncode == 0 and " passed" in r.stdout, r.stdout[-3000:] + r.stderr[-3000:]
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("smoother,nu", [(0, 1), (0, 2), (1, 1), (1, 2)])
 def test_solve_parity(gw, prec, smoother, nu):

@@ -146,3 +146,83 @@ def test_cancelled_requests_are_dropped_at_admission(cls_name):
     s.closed = True
     with s.cv:
         assert admit() is None
+
+
+def test_batched_admission_takes_the_exclusive_side_only_to_recapture(monkeypatch):
+    """The batch thread makes the setup workers pause (the exclusive side of
+    the gate) only for an admission whose hierarchy is deeper than any the
+    batched graph was captured for: only such an add captures again.  A
+    failed add fails its request alone and leaves the captured depth as it
+    was.  Driven on the CPU with a stand-in batch."""
+    import collections
+    import concurrent.futures
+
+    from paper_2001_05798_gb300 import serve
+
+    monkeypatch.setattr(serve.torch.cuda, "set_device", lambda d: None)
+
+    class Gate:
+        def __init__(self):
+            self.log = []
+
+        def acquire_exclusive(self):
+            self.log.append("x+")
+
+        def release_exclusive(self):
+            self.log.append("x-")
+
+        def acquire_shared(self):
+            pass
+
+        def release_shared(self):
+            pass
+
+    class Batch:
+        def __init__(self):
+            self.state_of, self.next, self.order = {}, 0, []
+
+        def add(self, H, b, tol, maxit):
+            if H == "bad":
+                raise RuntimeError("refused")
+            s = self.next
+            self.next += 1
+            self.state_of[s] = 2  # finished at the next look
+            self.order.append(H)
+            return s
+
+        def run(self, k):
+            pass
+
+        def state(self, s):
+            return self.state_of.get(s, 0)
+
+        def take(self, s, h):
+            del self.state_of[s]
+            return h, 7, 1e-9, 0
+
+    s = serve.BatchedServer.__new__(serve.BatchedServer)
+    s.cv = threading.Condition()
+    s.ready = collections.deque()
+    s.closed = True
+    s.slots, s.k, s.tol, s.maxit, s.device = 2, 1, 1e-8, 100, 0
+    s.capture_gate = Gate()
+    s.graph_levels = 0
+    s.batch = Batch()
+    depths = [3, 3, 4, 2, 4, 6, 5]
+    names = ["h%d" % k for k in range(len(depths))]
+    names[5] = "bad"
+    futs = []
+    for k, (L, H) in enumerate(zip(depths, names)):
+        f = concurrent.futures.Future()
+        f.set_running_or_notify_cancel()
+        futs.append(f)
+        s.ready.append(dict(req={"id": k}, fut=f, arrival=0.0, need=1.0, H=H, A=None, b=None, h=None, n=8, L=L,
+                            setup_s=0.0))
+    s.in_use, s.inflight = float(len(depths)), len(depths)
+    s._batch_loop()
+    # exclusive only for depths 3 (first capture), 4 and 6 (refused: its try still held the side), then 5
+    assert s.capture_gate.log == ["x+", "x-"] * 4
+    assert s.batch.order == ["h0", "h1", "h2", "h3", "h4", "h6"]
+    assert s.graph_levels == 5 and s.inflight == 0 and s.in_use == 0.0
+    assert isinstance(futs[5].exception(), RuntimeError)
+    assert all(f.result()["iters"] == 7 for k, f in enumerate(futs) if k != 5)

@@ -471,6 +471,52 @@ def run_transient(args):
     print(json.dumps(out), flush=True)
 
 
+def run_setup(args):
+    """Secondary workload: the AMG setup alone (strength, MIS-2 aggregation,
+    smoothed prolongators, Galerkin products, coarse inverse, cycle storage)
+    on the heterogeneous field (lnK var 4, corr 8) for cubes of side 32 to 160,
+    the sizes of the serving stream.  One step = gw_amg_setup of the resident
+    matrix; the hierarchy is freed after each step (its free is timed apart)."""
+    import torch
+
+    from paper_2001_05798_gb300 import build, gw, workload as wl
+
+    torch.cuda.set_device(0)
+    build.build()
+    gw.load()
+    sides = [int(x) for x in args.setup_sides.split(",")]
+    res = {}
+    for side in sides:
+        p = wl.heterogeneous_3d(side=side, var=4.0, corr=8.0, seed=1)
+        n = side ** 3
+        K = torch.from_numpy(p["Kx"]).cuda()
+        b = torch.empty(n, dtype=torch.float64, device="cuda")
+        A, _ = gw.gw_assemble(side, side, side, K, K, K, p["bct"], p["bcv"], None, b_out=b)
+        torch.cuda.synchronize()
+        times, frees = [], []
+        for k in range(max(args.warmup, 3) + args.steps):
+            t0 = time.perf_counter()
+            H = gw.Hierarchy(A)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            levels = [l["n"] for l in H.info()]
+            del H
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            if k >= max(args.warmup, 3):
+                times.append((t1 - t0) * 1e3)
+                frees.append((t2 - t1) * 1e3)
+        res[str(side)] = {"p50_ms": float(np.median(times)), "min_ms": float(np.min(times)),
+                          "free_ms": float(np.median(frees)), "levels": levels}
+    big = str(max(sides))
+    out = {"metric": "AMG setup ms (gw_amg_setup, mixed form) per cube side", "value": res[big]["p50_ms"],
+           "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
+           "dtype": "f64 setup", "data": "synthetic",
+           "config": {"workload": "cubes of side %s, lnK var 4 corr 8 seed 1, x faces 1/0; value = side %s"
+                                  % (args.setup_sides, big)}, "setup": res}
+    print(json.dumps(out), flush=True)
+
+
 def run_many(args):
     """Secondary workload: k = 8 right-hand sides (the benchmark's b and seven
     well scenarios of 6 random wells each, rate U[-1e-3, 1e-3]) on one 128^3
@@ -745,7 +791,9 @@ def main():
     ap.add_argument("--serve-mode", choices=("batched", "streams"), default="batched",
                     help="serving workload: batched launches over a slot table, or one stream and graph per slot")
     ap.add_argument("--setup-workers", type=int, default=6, help="serving workload, batched: concurrent setups")
-    ap.add_argument("--workload", choices=("solve", "adjoint", "transient", "serve", "many", "layered", "baseline"),
+    ap.add_argument("--setup-sides", default="32,64,96,128,160", help="setup workload: cube sides")
+    ap.add_argument("--workload", choices=("solve", "adjoint", "transient", "serve", "many", "layered", "baseline",
+                                           "setup"),
                     default="solve",
                     help="solve: the 128^3 benchmark (default); adjoint: the 96^3 sensitivity case; "
                          "transient: implicit steps with a cached hierarchy; serve: the request stream; "
@@ -765,6 +813,8 @@ def main():
         run_transient(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "setup":
+        run_setup(args)
     elif args.workload == "many":
         run_many(args)
     elif args.workload == "layered":

@@ -639,7 +639,7 @@ __device__ __forceinline__ void cg_rz_epilogue(VB vb, double lrz, double lqz, do
 // (b, z) and (q, z) contributions of R rows: products summed in T over the
 // R rows, then accumulated in FP64 across rows and threads
 template <int R, class T, class OT>
-__device__ __forceinline__ void dot_rows(int i, const T *b, const OT (&z)[R], const T *q, double &lrz, double &lqz)
+__device__ __forceinline__ void dot_rows(int i, const T *b, const OT (&z)[R], const T *q, DAcc &lrz, DAcc &lqz)
 {
     const VecN<T, R> bb = ld_ro<R>(b + i);
     T zz[R];
@@ -697,7 +697,7 @@ __device__ __forceinline__ void b_jacobi(VB vb, M A, int n, const typename M::va
     using T = typename M::value_type;
     constexpr int R = M::R;
     if (finished(ctl)) return;
-    double lrz = 0.0, lqz = 0.0;
+    DAcc lrz, lqz;
     GROUP_ROWS(M, n)
     {
         VecN<T, R> ax;
@@ -719,7 +719,7 @@ __device__ __forceinline__ void b_jacobi(VB vb, M A, int n, const typename M::va
             if constexpr (DOT) dot_rows<R>(i, b, out, q, lrz, lqz);
         }
     }
-    if constexpr (DOT) cg_rz_epilogue(vb, lrz, lqz, part, ctl, mode);
+    if constexpr (DOT) cg_rz_epilogue(vb, dacc_value(lrz), dacc_value(lqz), part, ctl, mode);
 }
 
 template <class M, class BT, class OT, bool DOT>
@@ -1060,7 +1060,7 @@ __device__ __forceinline__ void b_cheb0(VB vb, M A, int n, const typename M::val
     using T = typename M::value_type;
     constexpr int R = M::R;
     if (finished(ctl)) return;
-    double lrz = 0.0, lqz = 0.0;
+    DAcc lrz, lqz;
     GROUP_ROWS(M, n)
     {
         VecN<T, R> ax;
@@ -1095,7 +1095,7 @@ __device__ __forceinline__ void b_cheb0(VB vb, M A, int n, const typename M::val
             }
         }
     }
-    if constexpr (DOT) cg_rz_epilogue(vb, lrz, lqz, part, ctl, mode);
+    if constexpr (DOT) cg_rz_epilogue(vb, dacc_value(lrz), dacc_value(lqz), part, ctl, mode);
 }
 
 template <class M, class BT, class OT, bool DOT>
@@ -1125,7 +1125,7 @@ __device__ __forceinline__ void b_chebk(VB vb, M A, int n, const typename M::val
     using T = typename M::value_type;
     constexpr int R = M::R;
     if (finished(ctl)) return;
-    double lrz = 0.0, lqz = 0.0;
+    DAcc lrz, lqz;
     GROUP_ROWS(M, n)
     {
         const VecN<T, R> ad = A.dot(i, lane, GVec<T, T>{d});
@@ -1158,7 +1158,7 @@ __device__ __forceinline__ void b_chebk(VB vb, M A, int n, const typename M::val
             }
         }
     }
-    if constexpr (DOT) cg_rz_epilogue(vb, lrz, lqz, part, ctl, mode);
+    if constexpr (DOT) cg_rz_epilogue(vb, dacc_value(lrz), dacc_value(lqz), part, ctl, mode);
 }
 
 template <class M, class OT, bool DOT>
@@ -1193,7 +1193,7 @@ __device__ __forceinline__ void b_cheb_zero2(VB vb, M A, int n, const typename M
     using T = typename M::value_type;
     constexpr int R = M::R;
     if (finished(ctl)) return;
-    double lrz = 0.0, lqz = 0.0;
+    DAcc lrz, lqz;
     GROUP_ROWS(M, n)
     {
         const VecN<T, R> ad = A.dot(i, lane, GProdC<T, T>{dw, b, c0});
@@ -1227,7 +1227,7 @@ __device__ __forceinline__ void b_cheb_zero2(VB vb, M A, int n, const typename M
             }
         }
     }
-    if constexpr (DOT) cg_rz_epilogue(vb, lrz, lqz, part, ctl, mode);
+    if constexpr (DOT) cg_rz_epilogue(vb, dacc_value(lrz), dacc_value(lqz), part, ctl, mode);
 }
 
 template <class M, class OT, bool DOT>
@@ -1652,7 +1652,7 @@ __device__ __forceinline__ void b_cg_dir_spmv(VB vb, M A, int n, const typename 
         return;
     }
     const V beta = (V)c->beta;
-    double loc[1] = {0.0}, tot[1];
+    DAcc acc;
     GROUP_ROWS(M, n)
     {
         const VecN<V, R> qi = A.dot(i, lane, GDir<V>{z, pold, beta});
@@ -1660,9 +1660,10 @@ __device__ __forceinline__ void b_cg_dir_spmv(VB vb, M A, int n, const typename 
             st<R>(q + i, qi);
             const VecN<V, R> pi = GDir<V>{z, pold, beta}.template vec<R>(i);
             st<R>(pnew + i, pi);
-            dot_add<R>(loc[0], pi.v, qi.v);
+            dot_add<R>(acc, pi.v, qi.v);
         }
     }
+    double loc[1] = {dacc_value(acc)}, tot[1];
     if (reduce_last<1>(vb, loc, part, &c->cnt[0], tot) && threadIdx.x == 0) {
         const double pq = tot[0];
         c->pq = pq;
@@ -1695,7 +1696,7 @@ __device__ __forceinline__ void b_cg_update(VB vb, int n, V *__restrict__ x, V *
     if (finished(c)) return;
     const V *__restrict__ p = (pb && !((c->it - 1) & 1)) ? pb : pa;
     const V a = (V)c->alpha;
-    double loc[1] = {0.0}, tot[1];
+    DAcc acc;
     for (int i = R * (vb.bid * BS + threadIdx.x); i < n; i += R * vb.nb * BS) {
         VecN<V, R> xv = ld_rw<R>(x + i), rv = ld_rw<R>(r + i);
         const VecN<V, R> pv = ld_ro<R>(p + i), qv = ld_ro<R>(q + i);
@@ -1704,10 +1705,11 @@ __device__ __forceinline__ void b_cg_update(VB vb, int n, V *__restrict__ x, V *
             xv.v[k] += a * pv.v[k];
             rv.v[k] -= a * qv.v[k];
         }
-        dot_add<R>(loc[0], rv.v, rv.v);
+        dot_add<R>(acc, rv.v, rv.v);
         st<R>(x + i, xv);
         st<R>(r + i, rv);
     }
+    double loc[1] = {dacc_value(acc)}, tot[1];
     if (reduce_last<1>(vb, loc, part, &c->cnt[0], tot) && threadIdx.x == 0) {
         c->rr = tot[0];
         if (!isfinite(tot[0])) {

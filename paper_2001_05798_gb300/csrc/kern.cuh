@@ -80,7 +80,7 @@ static void launch_pdl(void (*kernel)(KArgs...), int grid, cudaStream_t st, Args
 // A thread's share of an FP32 dot product without FP32 rounding of the sum:
 // each product is split exactly into p + e (e by a fused multiply-add) and
 // the products are added in two FP32 words by the error-free TwoSum, which
-// keeps about 46 bits; the pair is then added to the FP64 accumulator.  FP32
+// keeps about 46 bits; the pair becomes an FP64 value at the reduction.  FP32
 // operations only (FP64 throughput is scarce on this GPU); explicitly rounded
 // intrinsics keep the compiler from contracting the transformations.
 struct Sum2 {
@@ -98,20 +98,29 @@ __device__ __forceinline__ void sum2_prod(Sum2 &s, float x, float y)
 }
 __device__ __forceinline__ double sum2_value(const Sum2 &s) { return (double)s.hi + (double)s.lo; }
 
-// the dot product of R consecutive entries, added to an FP64 accumulator
+// A thread's running share of a dot product over all its rows: for FP32
+// operands the error-free pair above, carried from row block to row block
+// and turned into FP64 once, when the block reduces (one conversion a thread
+// instead of one a row block: FP64 issue, about 2 operations a cycle an SM,
+// is the scarce unit on this GPU); for FP64 operands a plain FP64 sum.
+struct DAcc {
+    Sum2 s;
+    double d = 0.0;
+};
+__device__ __forceinline__ double dacc_value(const DAcc &a) { return a.d + sum2_value(a.s); }
+
+// adds the dot product of R consecutive entries
 template <int R, class T, class U>
-__device__ __forceinline__ void dot_add(double &acc, const T (&a)[R], const U (&b)[R])
+__device__ __forceinline__ void dot_add(DAcc &acc, const T (&a)[R], const U (&b)[R])
 {
     if constexpr (sizeof(T) == 4 && sizeof(U) == 4) {
-        Sum2 s;
 #pragma unroll
-        for (int k = 0; k < R; ++k) sum2_prod(s, (float)a[k], (float)b[k]);
-        acc += sum2_value(s);
+        for (int k = 0; k < R; ++k) sum2_prod(acc.s, (float)a[k], (float)b[k]);
     } else {
         double s = 0.0;
 #pragma unroll
         for (int k = 0; k < R; ++k) s += (double)a[k] * (double)b[k];
-        acc += s;
+        acc.d += s;
     }
 }
 __device__ __forceinline__ double warp_sum(double v)

@@ -366,16 +366,36 @@ __device__ __forceinline__ void rz_cols(const double (&loc)[2][CW], double *part
     if (threadIdx.x == 0) refresh_done<KB>(c);
 }
 
+// A thread's per-column dot-product shares are error-free FP32 pairs carried
+// over all its rows (FP32 operations only) and become FP64 once, before the
+// block reduction, as in the single-vector passes.
+template <int NV, int CW>
+__device__ __forceinline__ void pairs_to_double(const Sum2 (&a)[NV][CW], double (&d)[NV][CW])
+{
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+        for (int u = 0; u < CW; ++u) d[v][u] = sum2_value(a[v][u]);
+}
+
+template <int KB, int CW>
+__device__ __forceinline__ void rz_cols(const Sum2 (&acc)[2][CW], double *part, BlkCtl *c, int mode)
+{
+    double loc[2][CW];
+    pairs_to_double(acc, loc);
+    rz_cols<KB, CW>(loc, part, c, mode);
+}
+
 template <int CW>
-__device__ __forceinline__ void dot_cols(const float *b, const CV<float, CW> &z, const float *q, double (&loc)[2][CW])
+__device__ __forceinline__ void dot_cols(const float *b, const CV<float, CW> &z, const float *q, Sum2 (&loc)[2][CW])
 {
     const CV<float, CW> bb = cld<CW>(b);
 #pragma unroll
-    for (int u = 0; u < CW; ++u) loc[0][u] += (double)(bb.v[u] * z.v[u]);
+    for (int u = 0; u < CW; ++u) sum2_prod(loc[0][u], bb.v[u], z.v[u]);
     if (q) {
         const CV<float, CW> qq = cld<CW>(q);
 #pragma unroll
-        for (int u = 0; u < CW; ++u) loc[1][u] += (double)(qq.v[u] * z.v[u]);
+        for (int u = 0; u < CW; ++u) sum2_prod(loc[1][u], qq.v[u], z.v[u]);
     }
 }
 
@@ -394,7 +414,7 @@ __global__ void __launch_bounds__(BS) kb_cheb_zero2(M A, int n, const float *__r
 {
     pdl_enter();
     if (bfinished(c)) return;
-    double loc[2][CW] = {};
+    Sum2 loc[2][CW];
     BLOCK_ROWS(n, KB, CW)
     {
         const CV<float, CW> ad = A.template dot<CW>(i, BProd<CW, KB>{dw, b + off, c0});
@@ -433,7 +453,7 @@ __global__ void __launch_bounds__(BS) kb_cheb0(M A, int n, const float *__restri
 {
     pdl_enter();
     if (bfinished(c)) return;
-    double loc[2][CW] = {};
+    Sum2 loc[2][CW];
     BLOCK_ROWS(n, KB, CW)
     {
         CV<float, CW> ax;
@@ -479,7 +499,7 @@ __global__ void __launch_bounds__(BS) kb_chebk(M A, int n, const float *__restri
 {
     pdl_enter();
     if (bfinished(c)) return;
-    double loc[2][CW] = {};
+    Sum2 loc[2][CW];
     BLOCK_ROWS(n, KB, CW)
     {
         const CV<float, CW> ad = A.template dot<CW>(i, BVec<float, CW, KB>{d + off});
@@ -513,7 +533,7 @@ __global__ void __launch_bounds__(BS) kb_jacobi(M A, int n, const float *__restr
 {
     pdl_enter();
     if (bfinished(c)) return;
-    double loc[2][CW] = {};
+    Sum2 loc[2][CW];
     BLOCK_ROWS(n, KB, CW)
     {
         CV<float, CW> ax, xv;
@@ -712,7 +732,7 @@ __global__ void __launch_bounds__(BS) kb_dir_spmv(M A, int n, const float *__res
     pdl_enter();
     if (bfinished(c)) return;
     __shared__ double tot[KB];
-    double loc[1][CW] = {};
+    Sum2 acc[1][CW];
     CV<float, CW> beta;  // a thread keeps its columns: the grid stride is a multiple of KB / CW
 #pragma unroll
     for (int u = 0; u < CW; ++u) beta.v[u] = (float)c->col[first_col<KB, CW>() + u].beta;
@@ -725,8 +745,10 @@ __global__ void __launch_bounds__(BS) kb_dir_spmv(M A, int n, const float *__res
         cst<CW>(q + e, qi);
         cst<CW>(pnew + e, pi);
 #pragma unroll
-        for (int u = 0; u < CW; ++u) loc[0][u] += (double)(pi.v[u] * qi.v[u]);
+        for (int u = 0; u < CW; ++u) sum2_prod(acc[0][u], pi.v[u], qi.v[u]);
     }
+    double loc[1][CW];
+    pairs_to_double(acc, loc);
     if (!reduce_cols<KB, CW, 1>(loc, part, &c->cnt[0], tot)) return;
     if (threadIdx.x < KB) {
         Ctl &cj = c->col[threadIdx.x];
@@ -757,7 +779,7 @@ __global__ void __launch_bounds__(BS) kb_update(int n, float *__restrict__ xs, f
     pdl_enter();
     if (bfinished(c)) return;
     __shared__ double tot[KB];
-    double loc[1][CW] = {};
+    Sum2 acc[1][CW];
     CV<float, CW> a;
 #pragma unroll
     for (int u = 0; u < CW; ++u) a.v[u] = (float)c->col[first_col<KB, CW>() + u].alpha;
@@ -770,11 +792,13 @@ __global__ void __launch_bounds__(BS) kb_update(int n, float *__restrict__ xs, f
         for (int u = 0; u < CW; ++u) {
             xv.v[u] += a.v[u] * pv.v[u];
             rv.v[u] -= a.v[u] * qv.v[u];
-            loc[0][u] += (double)(rv.v[u] * rv.v[u]);
+            sum2_prod(acc[0][u], rv.v[u], rv.v[u]);
         }
         cst<CW>(xs + e, xv);
         cst<CW>(r + e, rv);
     }
+    double loc[1][CW];
+    pairs_to_double(acc, loc);
     if (!reduce_cols<KB, CW, 1>(loc, part, &c->cnt[0], tot)) return;
     if (threadIdx.x < KB) {
         Ctl &cj = c->col[threadIdx.x];

@@ -16,6 +16,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <type_traits>
+
 #include "gw_internal.cuh"
 
 namespace gw {
@@ -33,6 +35,23 @@ static inline int nblk(long long n, int bs, long long cap = 152LL * 32)
 // warp a row (2) by GW_SETUP_FORMS=thread|warp in the environment, read once,
 // so that tests can check both forms against the oracle on any problem.  Both
 // forms give the same bits.
+// Lanes that share a row in the per-row setup passes: one for the short rows
+// of the fine grid, a group of 8 or a warp for the long rows of the coarse
+// levels (a thread walking a row of a hundred entries alone leaves a
+// 6k-row level on a few dozen SMs).
+static int row_lanes(const DCSR &A)
+{
+    const double per_row = A.nr ? (double)A.nnz / A.nr : 0.0;
+    return per_row <= 12.0 ? 1 : per_row <= 48.0 ? 8 : 32;
+}
+
+// Rows handed to groups of G lanes; whole warps stay in the loop when G > 1
+// (the groups' shuffles need every lane), so the row index may be >= n.
+#define GROUP_LOOP(G, ii, n)                                                                       \
+    for (long long ii = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / (G),                \
+                   ii##_step = (long long)gridDim.x * (blockDim.x / (G));                        \
+         (G) == 1 ? ii < (n) : __any_sync(0xffffffffu, ii < (n)); ii += ii##_step)
+
 static int setup_forms()
 {
     static const int f = [] {
@@ -102,15 +121,18 @@ __global__ void k_diag(int n, const int *__restrict__ rp, const int *__restrict_
 }
 
 // (i,j) strong iff a_ij^2 > theta2 * (a_ii * a_jj), i != j
+template <int G>
 __global__ void k_strength_raw(int n, const int *__restrict__ rp, const int *__restrict__ ci,
                                const double *__restrict__ v, const double *__restrict__ d, double theta2,
                                unsigned char *__restrict__ raw)
 {
-    GRID_STRIDE(ii, n)
+    const int lane = threadIdx.x & (G - 1);
+    GROUP_LOOP(G, ii, n)
     {
+        if (ii >= n) continue;
         const int i = (int)ii;
         const double di = d[i];
-        for (int e = rp[i]; e < rp[i + 1]; ++e) {
+        for (int e = rp[i] + lane; e < rp[i + 1]; e += G) {
             const int j = ci[e];
             if (j == i) {
                 raw[e] = 0;
@@ -139,13 +161,16 @@ __device__ __forceinline__ int row_find(const int *__restrict__ rp, const int *_
 }
 
 // S = raw OR raw^T
+template <int G>
 __global__ void k_strength_sym(int n, const int *__restrict__ rp, const int *__restrict__ ci,
                                const unsigned char *__restrict__ raw, unsigned char *__restrict__ S)
 {
-    GRID_STRIDE(ii, n)
+    const int lane = threadIdx.x & (G - 1);
+    GROUP_LOOP(G, ii, n)
     {
+        if (ii >= n) continue;
         const int i = (int)ii;
-        for (int e = rp[i]; e < rp[i + 1]; ++e) {
+        for (int e = rp[i] + lane; e < rp[i + 1]; e += G) {
             const int j = ci[e];
             unsigned char s = raw[e];
             if (!s && j != i) {
@@ -163,8 +188,17 @@ void setup_strength(const DCSR &A, double theta2, DBuf<unsigned char> &S, cudaSt
     DBuf<unsigned char> raw((size_t)A.nnz + 1);
     S.alloc((size_t)A.nnz + 1);
     gw_launch(k_diag, nblk(A.nr, 256), 256, 0, st, A.nr, A.rp.p, A.ci.p, A.v.p, d.p);
-    gw_launch(k_strength_raw, nblk(A.nr, 256), 256, 0, st, A.nr, A.rp.p, A.ci.p, A.v.p, d.p, theta2, raw.p);
-    gw_launch(k_strength_sym, nblk(A.nr, 256), 256, 0, st, A.nr, A.rp.p, A.ci.p, raw.p, S.p);
+    const int G = row_lanes(A), gg = nblk((long long)A.nr * G, 256);
+    if (G == 1) {
+        gw_launch(k_strength_raw<1>, gg, 256, 0, st, A.nr, A.rp.p, A.ci.p, A.v.p, d.p, theta2, raw.p);
+        gw_launch(k_strength_sym<1>, gg, 256, 0, st, A.nr, A.rp.p, A.ci.p, raw.p, S.p);
+    } else if (G == 8) {
+        gw_launch(k_strength_raw<8>, gg, 256, 0, st, A.nr, A.rp.p, A.ci.p, A.v.p, d.p, theta2, raw.p);
+        gw_launch(k_strength_sym<8>, gg, 256, 0, st, A.nr, A.rp.p, A.ci.p, raw.p, S.p);
+    } else {
+        gw_launch(k_strength_raw<32>, gg, 256, 0, st, A.nr, A.rp.p, A.ci.p, A.v.p, d.p, theta2, raw.p);
+        gw_launch(k_strength_sym<32>, gg, 256, 0, st, A.nr, A.rp.p, A.ci.p, raw.p, S.p);
+    }
     GW_LAUNCH_CHECK();
     GW_CUDA(cudaStreamSynchronize(st));
 }
@@ -177,86 +211,135 @@ void setup_strength(const DCSR &A, double theta2, DBuf<unsigned char> &S, cudaSt
 // visiting the nodes in descending priority (Blelloch, Fineman & Shun 2012).
 enum : unsigned char { MIS_UNDECIDED = 0, MIS_ROOT = 1, MIS_OUT = 2 };
 
+// the larger of two (key, index) candidates, -1 meaning none (a strict
+// total order, so the maximum over a group does not depend on its order)
+__device__ __forceinline__ void prio_take(uint64_t &bk, int &bi, uint64_t k, int i)
+{
+    if (i >= 0 && (bi < 0 || prio_gt(k, i, bk, bi))) {
+        bk = k;
+        bi = i;
+    }
+}
+
+template <int G>
+__device__ __forceinline__ void prio_group_max(uint64_t &bk, int &bi)
+{
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) {
+        const uint64_t k = __shfl_xor_sync(0xffffffffu, (unsigned long long)bk, off, G);
+        const int i = __shfl_xor_sync(0xffffffffu, bi, off, G);
+        prio_take(bk, bi, k, i);
+    }
+}
+
+template <int G>
+__device__ __forceinline__ bool group_any(bool f)
+{
+    unsigned v = f ? 1u : 0u;
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) v |= __shfl_xor_sync(0xffffffffu, v, off, G);
+    return v != 0;
+}
+
+// m1(i) = max undecided (key, index) over {i} and its strong neighbours
+template <int G>
 __global__ void k_mis_max1(int n, const int *__restrict__ rp, const int *__restrict__ ci,
                            const unsigned char *__restrict__ S, const unsigned char *__restrict__ state,
                            uint64_t seed, int level, unsigned long long *__restrict__ mk, int *__restrict__ mi)
 {
-    GRID_STRIDE(ii, n)
+    const int lane = threadIdx.x & (G - 1);
+    GROUP_LOOP(G, ii, n)
     {
         const int i = (int)ii;
         uint64_t bk = 0;
         int bi = -1;
-        if (state[i] == MIS_UNDECIDED) {
-            bk = prio_key(seed, level, i);
-            bi = i;
-        }
-        for (int e = rp[i]; e < rp[i + 1]; ++e) {
-            if (!S[e]) continue;
-            const int j = ci[e];
-            if (state[j] != MIS_UNDECIDED) continue;
-            const uint64_t k = prio_key(seed, level, j);
-            if (bi < 0 || prio_gt(k, j, bk, bi)) {
-                bk = k;
-                bi = j;
+        if (ii < n) {
+            if (lane == 0 && state[i] == MIS_UNDECIDED) prio_take(bk, bi, prio_key(seed, level, i), i);
+            for (int e = rp[i] + lane; e < rp[i + 1]; e += G) {
+                if (!S[e]) continue;
+                const int j = ci[e];
+                if (state[j] != MIS_UNDECIDED) continue;
+                prio_take(bk, bi, prio_key(seed, level, j), j);
             }
         }
-        mk[i] = bk;
-        mi[i] = bi;
+        prio_group_max<G>(bk, bi);
+        if (lane == 0 && ii < n) {
+            mk[i] = bk;
+            mi[i] = bi;
+        }
     }
 }
 
+// an undecided i whose m2 = max of m1 over {i} and its strong neighbours is
+// i itself becomes a root
+template <int G>
 __global__ void k_mis_select(int n, const int *__restrict__ rp, const int *__restrict__ ci,
                              const unsigned char *__restrict__ S, unsigned char *__restrict__ state,
                              const unsigned long long *__restrict__ mk, const int *__restrict__ mi)
 {
-    GRID_STRIDE(ii, n)
+    const int lane = threadIdx.x & (G - 1);
+    GROUP_LOOP(G, ii, n)
     {
         const int i = (int)ii;
-        if (state[i] != MIS_UNDECIDED) continue;
-        uint64_t bk = mk[i];
-        int bi = mi[i];
-        for (int e = rp[i]; e < rp[i + 1]; ++e) {
-            if (!S[e]) continue;
-            const int j = ci[e];
-            const int ji = mi[j];
-            if (ji < 0) continue;
-            const uint64_t k = mk[j];
-            if (bi < 0 || prio_gt(k, ji, bk, bi)) {
-                bk = k;
-                bi = ji;
+        const bool live = ii < n && state[i] == MIS_UNDECIDED;
+        uint64_t bk = 0;
+        int bi = -1;
+        if (live) {
+            if (lane == 0) prio_take(bk, bi, mk[i], mi[i]);
+            for (int e = rp[i] + lane; e < rp[i + 1]; e += G) {
+                if (!S[e]) continue;
+                const int j = ci[e];
+                prio_take(bk, bi, mk[j], mi[j]);
             }
         }
-        if (bi == i) state[i] = MIS_ROOT;
+        prio_group_max<G>(bk, bi);
+        if (lane == 0 && live && bi == i) state[i] = MIS_ROOT;
     }
 }
 
+// near1(i): i is a root or has a strong neighbour that is one
+template <int G>
 __global__ void k_mis_near1(int n, const int *__restrict__ rp, const int *__restrict__ ci,
                             const unsigned char *__restrict__ S, const unsigned char *__restrict__ state,
                             unsigned char *__restrict__ near1)
 {
-    GRID_STRIDE(ii, n)
+    const int lane = threadIdx.x & (G - 1);
+    GROUP_LOOP(G, ii, n)
     {
         const int i = (int)ii;
-        unsigned char f = state[i] == MIS_ROOT;
-        for (int e = rp[i]; e < rp[i + 1] && !f; ++e)
-            if (S[e] && state[ci[e]] == MIS_ROOT) f = 1;
-        near1[i] = f;
+        bool f = false;
+        if (ii < n) {
+            f = lane == 0 && state[i] == MIS_ROOT;
+            for (int e = rp[i] + lane; e < rp[i + 1] && !f; e += G)
+                if (S[e] && state[ci[e]] == MIS_ROOT) f = true;
+        }
+        f = group_any<G>(f);
+        if (lane == 0 && ii < n) near1[i] = f;
     }
 }
 
+// an undecided node within two hops of a root leaves; the others are counted
+template <int G>
 __global__ void k_mis_remove(int n, const int *__restrict__ rp, const int *__restrict__ ci,
                              const unsigned char *__restrict__ S, unsigned char *__restrict__ state,
                              const unsigned char *__restrict__ near1, int *__restrict__ undecided)
 {
-    GRID_STRIDE(ii, n)
+    const int lane = threadIdx.x & (G - 1);
+    GROUP_LOOP(G, ii, n)
     {
         const int i = (int)ii;
-        if (state[i] != MIS_UNDECIDED) continue;
-        bool f = near1[i];
-        for (int e = rp[i]; e < rp[i + 1] && !f; ++e)
-            if (S[e] && near1[ci[e]]) f = true;
-        if (f) state[i] = MIS_OUT;
-        else atomicAdd(undecided, 1);
+        const bool live = ii < n && state[i] == MIS_UNDECIDED;
+        bool f = false;
+        if (live) {
+            f = lane == 0 && near1[i];
+            for (int e = rp[i] + lane; e < rp[i + 1] && !f; e += G)
+                if (S[e] && near1[ci[e]]) f = true;
+        }
+        f = group_any<G>(f);
+        if (lane == 0 && live) {
+            if (f) state[i] = MIS_OUT;
+            else atomicAdd(undecided, 1);
+        }
     }
 }
 
@@ -275,15 +358,22 @@ int setup_mis2(const DCSR &A, const unsigned char *S, uint64_t seed, int level, 
     root.alloc((size_t)n);
     GW_CUDA(cudaMemsetAsync(state.p, 0, (size_t)n, st));
     const int g = nblk(n, 256);
+    const int G = row_lanes(A), gg = nblk((long long)n * G, 256);
+    auto mis_round = [&](auto lanes) {
+        constexpr int L = decltype(lanes)::value;
+        gw_launch(k_mis_max1<L>, gg, 256, 0, st, n, A.rp.p, A.ci.p, S, state.p, seed, level, mk.p, mi.p);
+        gw_launch(k_mis_select<L>, gg, 256, 0, st, n, A.rp.p, A.ci.p, S, state.p, mk.p, mi.p);
+        gw_launch(k_mis_near1<L>, gg, 256, 0, st, n, A.rp.p, A.ci.p, S, state.p, near1.p);
+        gw_launch(k_mis_remove<L>, gg, 256, 0, st, n, A.rp.p, A.ci.p, S, state.p, near1.p, cnt.p);
+    };
     int rounds = 0;
     for (;;) {
         if (rounds >= max_rounds) fail(GW_ERR_SETUP, "MIS-2 did not finish in %d rounds on level %d", max_rounds, level);
         ++rounds;
         GW_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int), st));
-        gw_launch(k_mis_max1, g, 256, 0, st, n, A.rp.p, A.ci.p, S, state.p, seed, level, mk.p, mi.p);
-        gw_launch(k_mis_select, g, 256, 0, st, n, A.rp.p, A.ci.p, S, state.p, mk.p, mi.p);
-        gw_launch(k_mis_near1, g, 256, 0, st, n, A.rp.p, A.ci.p, S, state.p, near1.p);
-        gw_launch(k_mis_remove, g, 256, 0, st, n, A.rp.p, A.ci.p, S, state.p, near1.p, cnt.p);
+        if (G == 1) mis_round(std::integral_constant<int, 1>());
+        else if (G == 8) mis_round(std::integral_constant<int, 8>());
+        else mis_round(std::integral_constant<int, 32>());
         GW_LAUNCH_CHECK();
         if (read_int(cnt.p, st) == 0) break;
     }

@@ -82,9 +82,8 @@ struct AllocStream {
     cudaStream_t prev_;
     bool prev_on_;
 };
-// Device allocations made by the library so far (cudaMalloc and
-// cudaMallocAsync calls), for callers that must check that a call allocates
-// nothing.
+// Device allocations made by the library so far (from its pool or by
+// cudaMalloc), for callers that must check that a call allocates nothing.
 long long device_allocations();
 // Outside this thread's own capture: waits until no other thread of the
 // library captures, and keeps captures from starting while the returned

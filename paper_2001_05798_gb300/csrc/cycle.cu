@@ -849,43 +849,61 @@ __device__ __forceinline__ void b_prolong_imp(VB vb, PImpl P, const float *__res
     if (finished(ctl)) return;
     const int n = P.n, nx = P.nx, sxy = P.sxy;
     for (int i0 = R * (vb.bid * BS + threadIdx.x); i0 < n; i0 += R * vb.nb * BS) {
+        // every aggregate id first, then every gather of e, so that the loads
+        // of the six neighbours are in flight together; the sums keep the
+        // order -z, -y, -x, +x, +y, +z
+        const bool zm = i0 >= sxy, ym = i0 >= nx, xm = i0 >= 1, xp = i0 + R < n, yp = i0 + nx < n,
+                   zp = i0 + sxy < n;
+        const VecN<int, R> ai = ld_int<R>(P.agg + i0);
+        VecN<int, R> azm, aym, ayp, azp;
+        int axm = 0, axp = 0;
+        if (zm) azm = ld_int<R>(P.agg + i0 - sxy);
+        if (ym) aym = ld_int<R>(P.agg + i0 - nx);
+        if (xm) axm = __ldg(P.agg + i0 - 1);
+        if (xp) axp = __ldg(P.agg + i0 + R);
+        if (yp) ayp = ld_int<R>(P.agg + i0 + nx);
+        if (zp) azp = ld_int<R>(P.agg + i0 + sxy);
+        VecN<float, R> ev, ezm, eym, eyp, ezp;
+        float exm = 0.f, exp_ = 0.f;
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            ev.v[k] = __ldg(e + ai.v[k]);
+            ezm.v[k] = zm ? __ldg(e + azm.v[k]) : 0.f;
+            eym.v[k] = ym ? __ldg(e + aym.v[k]) : 0.f;
+            eyp.v[k] = yp ? __ldg(e + ayp.v[k]) : 0.f;
+            ezp.v[k] = zp ? __ldg(e + azp.v[k]) : 0.f;
+        }
+        if (xm) exm = __ldg(e + axm);
+        if (xp) exp_ = __ldg(e + axp);
         float acc[R];
 #pragma unroll
         for (int k = 0; k < R; ++k) acc[k] = 0.f;
-        if (i0 >= sxy) {
+        if (zm) {
             const VecN<float, R> c = ld_ro<R>(P.fz + i0 - sxy);
-            const VecN<int, R> a = ld_int<R>(P.agg + i0 - sxy);
 #pragma unroll
-            for (int k = 0; k < R; ++k) acc[k] += c.v[k] * __ldg(e + a.v[k]);
+            for (int k = 0; k < R; ++k) acc[k] += c.v[k] * ezm.v[k];
         }
-        if (i0 >= nx) {
+        if (ym) {
             const VecN<float, R> c = ld_ro<R>(P.fy + i0 - nx);
-            const VecN<int, R> a = ld_int<R>(P.agg + i0 - nx);
 #pragma unroll
-            for (int k = 0; k < R; ++k) acc[k] += c.v[k] * __ldg(e + a.v[k]);
+            for (int k = 0; k < R; ++k) acc[k] += c.v[k] * eym.v[k];
         }
-        const VecN<int, R> ai = ld_int<R>(P.agg + i0);
-        VecN<float, R> ev;
-#pragma unroll
-        for (int k = 0; k < R; ++k) ev.v[k] = __ldg(e + ai.v[k]);
         const VecN<float, R> cx = ld_ro<R>(P.fx + i0);
-        if (i0 >= 1) acc[0] += __ldg(P.fx + i0 - 1) * __ldg(e + __ldg(P.agg + i0 - 1));
+        if (xm) acc[0] += __ldg(P.fx + i0 - 1) * exm;
 #pragma unroll
         for (int k = 1; k < R; ++k) acc[k] += cx.v[k - 1] * ev.v[k - 1];
 #pragma unroll
         for (int k = 0; k < R - 1; ++k) acc[k] += cx.v[k] * ev.v[k + 1];
-        if (i0 + R < n) acc[R - 1] += cx.v[R - 1] * __ldg(e + __ldg(P.agg + i0 + R));
-        if (i0 + nx < n) {
+        if (xp) acc[R - 1] += cx.v[R - 1] * exp_;
+        if (yp) {
             const VecN<float, R> c = ld_ro<R>(P.fy + i0);
-            const VecN<int, R> a = ld_int<R>(P.agg + i0 + nx);
 #pragma unroll
-            for (int k = 0; k < R; ++k) acc[k] += c.v[k] * __ldg(e + a.v[k]);
+            for (int k = 0; k < R; ++k) acc[k] += c.v[k] * eyp.v[k];
         }
-        if (i0 + sxy < n) {
+        if (zp) {
             const VecN<float, R> c = ld_ro<R>(P.fz + i0);
-            const VecN<int, R> a = ld_int<R>(P.agg + i0 + sxy);
 #pragma unroll
-            for (int k = 0; k < R; ++k) acc[k] += c.v[k] * __ldg(e + a.v[k]);
+            for (int k = 0; k < R; ++k) acc[k] += c.v[k] * ezp.v[k];
         }
         const VecN<float, R> sv = ld_ro<R>(P.s + i0);
         VecN<float, R> xv = ld_rw<R>(x + i0);

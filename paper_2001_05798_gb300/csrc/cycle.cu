@@ -34,6 +34,11 @@ namespace gw {
 #define GW_SELL_UNROLL 1
 #endif
 constexpr int SELL_UNROLL = GW_SELL_UNROLL;
+// chunks of a sliced-ELL row read before their gathers (a thread per row)
+#ifndef GW_SELL_BATCH
+#define GW_SELL_BATCH 2
+#endif
+constexpr int SELL_BATCH = GW_SELL_BATCH;
 
 // ------------------------------------------------------------ matrix views --
 // R consecutive values handled by one thread (R = 4 floats or 2 doubles is
@@ -235,6 +240,56 @@ struct MSell {
         using VI = typename VecT<T>::I;
         constexpr int V = SellV<T>::V;
         T acc = 0;
+        if constexpr (G == 1) {
+            // a thread per row: SELL_BATCH chunks' values and columns first,
+            // then their gathers, then the products in chunk order, so that
+            // a batch's loads are in flight together
+            if (r < a.nr || G == 1) {
+                const int s = r >> 5, rl = r & 31;
+                const int base = a.sp[s];
+                const int nch = (a.sp[s + 1] - base) / (SELL_C * V);
+                const VV *vv = reinterpret_cast<const VV *>(a.v + base) + rl;
+                const VI *cc = reinterpret_cast<const VI *>(a.ci + base) + rl;
+                for (int c0 = 0; c0 < nch; c0 += SELL_BATCH) {
+                    VV x[SELL_BATCH];
+                    VI j[SELL_BATCH];
+#pragma unroll
+                    for (int b = 0; b < SELL_BATCH; ++b)
+                        if (c0 + b < nch) {
+                            x[b] = __ldg(vv + (c0 + b) * SELL_C);
+                            j[b] = __ldg(cc + (c0 + b) * SELL_C);
+                        }
+                    T g[SELL_BATCH][V];
+#pragma unroll
+                    for (int b = 0; b < SELL_BATCH; ++b)
+                        if (c0 + b < nch) {
+                            if constexpr (V == 4) {
+                                g[b][0] = f(j[b].x);
+                                g[b][1] = f(j[b].y);
+                                g[b][2] = f(j[b].z);
+                                g[b][3] = f(j[b].w);
+                            } else {
+                                g[b][0] = f(j[b].x);
+                                g[b][1] = f(j[b].y);
+                            }
+                        }
+#pragma unroll
+                    for (int b = 0; b < SELL_BATCH; ++b)
+                        if (c0 + b < nch) {
+                            if constexpr (V == 4) {
+                                acc += x[b].x * g[b][0];
+                                acc += x[b].y * g[b][1];
+                                acc += x[b].z * g[b][2];
+                                acc += x[b].w * g[b][3];
+                            } else {
+                                acc += x[b].x * g[b][0];
+                                acc += x[b].y * g[b][1];
+                            }
+                        }
+                }
+            }
+            return VecN<T, 1>{{acc}};
+        }
         if (G == 1 || r < a.nr) {
             const int s = r >> 5, rl = r & 31;
             const int base = a.sp[s];

@@ -146,10 +146,32 @@ struct BSell {
         CV<T, CW> acc;
 #pragma unroll
         for (int u = 0; u < CW; ++u) acc.v[u] = 0;
-        for (int c = 0; c < nch; ++c) {
-            const int e0 = base + c * SELL_C * V + lane * V;
+        // two chunks at a time: values and columns, then the gathers, then the
+        // products in chunk order, so that a row's loads overlap
+        for (int c = 0; c < nch; c += 2) {
+            const bool two = c + 1 < nch;
+            const int e0 = base + c * SELL_C * V + lane * V, e1 = e0 + SELL_C * V;
+            T a0[V], a1[V];
+            int j0[V], j1[V];
 #pragma unroll
-            for (int k = 0; k < V; ++k) cacc(acc, __ldg(v + e0 + k), f(__ldg(ci + e0 + k)));
+            for (int k = 0; k < V; ++k) {
+                a0[k] = __ldg(v + e0 + k);
+                j0[k] = __ldg(ci + e0 + k);
+                a1[k] = two ? __ldg(v + e1 + k) : T(0);
+                j1[k] = two ? __ldg(ci + e1 + k) : 0;
+            }
+            decltype(f(0)) g0[V], g1[V];
+#pragma unroll
+            for (int k = 0; k < V; ++k) {
+                g0[k] = f(j0[k]);
+                if (two) g1[k] = f(j1[k]);
+            }
+#pragma unroll
+            for (int k = 0; k < V; ++k) cacc(acc, a0[k], g0[k]);
+            if (two) {
+#pragma unroll
+                for (int k = 0; k < V; ++k) cacc(acc, a1[k], g1[k]);
+            }
         }
         return acc;
     }

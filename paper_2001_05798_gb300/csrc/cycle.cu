@@ -1770,9 +1770,22 @@ __device__ __forceinline__ void b_cg_update(VB vb, int n, V *__restrict__ x, V *
     const V *__restrict__ p = (pb && !((c->it - 1) & 1)) ? pb : pa;
     const V a = (V)c->alpha;
     DAcc acc;
-    for (int i = R * (vb.bid * BS + threadIdx.x); i < n; i += R * vb.nb * BS) {
-        VecN<V, R> xv = ld_rw<R>(x + i), rv = ld_rw<R>(r + i);
+    // two of the thread's row groups per step, all their loads issued first
+    // (the second group's loads no longer wait for the first's); the groups
+    // are added to the dot in the same order as one at a time
+    const int stride = R * vb.nb * BS;
+    for (int i = R * (vb.bid * BS + threadIdx.x); i < n; i += 2 * stride) {
+        const int i2 = i + stride;
+        const bool two = i2 < n;
+        VecN<V, R> xv = ld_rw<R>(x + i), rv = ld_rw<R>(r + i), xv2, rv2;
         const VecN<V, R> pv = ld_ro<R>(p + i), qv = ld_ro<R>(q + i);
+        VecN<V, R> pv2, qv2;
+        if (two) {
+            xv2 = ld_rw<R>(x + i2);
+            rv2 = ld_rw<R>(r + i2);
+            pv2 = ld_ro<R>(p + i2);
+            qv2 = ld_ro<R>(q + i2);
+        }
 #pragma unroll
         for (int k = 0; k < R; ++k) {
             xv.v[k] += a * pv.v[k];
@@ -1781,6 +1794,16 @@ __device__ __forceinline__ void b_cg_update(VB vb, int n, V *__restrict__ x, V *
         dot_add<R>(acc, rv.v, rv.v);
         st<R>(x + i, xv);
         st<R>(r + i, rv);
+        if (two) {
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                xv2.v[k] += a * pv2.v[k];
+                rv2.v[k] -= a * qv2.v[k];
+            }
+            dot_add<R>(acc, rv2.v, rv2.v);
+            st<R>(x + i2, xv2);
+            st<R>(r + i2, rv2);
+        }
     }
     double loc[1] = {dacc_value(acc)}, tot[1];
     if (reduce_last<1>(vb, loc, part, &c->cnt[0], tot) && threadIdx.x == 0) {

@@ -651,11 +651,24 @@ static void with_mat(const MatStore<T> &M, F f)
     }
 }
 
+// Row blocks a thread's loop takes per unrolled step: two for the FP32
+// level-0 stencil (the second block's loads then overlap the first's; the
+// sliced-ELL and CSR forms measured slower unrolled), one otherwise.
+template <class M>
+struct RowUnroll {
+    static constexpr int v = 1;
+};
+template <>
+struct RowUnroll<MSten<float, 4>> {
+    static constexpr int v = 2;
+};
+
 // Row blocks of M::R rows handled by groups of M::G lanes.  The loop keeps
 // whole warps together (so the group reductions may shuffle); a group whose
 // block starts at or past n does no epilogue.
 #define GROUP_ROWS(M, n)                                                                                  \
     const int lane = M::G == 1 ? 0 : (int)(threadIdx.x & (M::G - 1));                                    \
+    _Pragma("unroll (RowUnroll<M>::v)")                                                                  \
     for (int i = (int)((vb.bid * (long long)BS + threadIdx.x) / M::G) * M::R,                             \
              stride_ = vb.nb * (BS / M::G) * M::R;                                                        \
          M::G == 1 ? (i < (n)) : __any_sync(0xffffffffu, i < (n)); i += stride_)

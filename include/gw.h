@@ -224,17 +224,23 @@ int gw_matrix_export(gw_matrix A, int *rowptr, int *col, double *val, void *stre
  * gw_amg_setup -- the AMG setup phase (Introduction): strength graph,
  * deterministic parallel MIS-2 aggregation with hashed seeded priorities,
  * tentative prolongator, one damped-Jacobi smoothing of it, Galerkin coarse
- * operators A_{l+1} = P^T A_l P by a two-pass SpGEMM, and a dense LU inverse
- * of the coarsest level; then the V-cycle storage in the chosen precision.
- * All of it runs in CUDA kernels.  The aggregates and the P and A_{l+1}
- * patterns and values are the same as a serial FP64 implementation that
- * sums in the stated order (no fused multiply-add in these stages).
+ * operators A_{l+1} = P^T A_l P by a two-pass SpGEMM, and a dense inverse of
+ * the (SPD) coarsest level by block Gauss-Jordan elimination without
+ * pivoting; then the V-cycle storage in the chosen precision.  All of it
+ * runs in CUDA kernels.  The aggregates and the P and A_{l+1} patterns and
+ * values are the same as a serial FP64 implementation that sums in the
+ * stated order (no fused multiply-add in these stages).
+ * Environment, read once per process, for checks and tests: GW_VALIDATE=1
+ * adds index validation of every level after the setup (GW_ERR_SETUP on a
+ * bad index); GW_SETUP_FORMS=thread|warp forces one of the two row-parallel
+ * forms of the SpGEMM and prolongator passes (the library otherwise picks
+ * one per product; both give the same bits).
  *   A     assembled matrix; the hierarchy keeps a reference to it (freeing A
  *         before H is the caller's error).
  *   opts  host struct or NULL for the defaults.
  * Errors: GW_ERR_ARG (bad option), GW_ERR_OOM, GW_ERR_SETUP (MIS-2 round cap
  * reached, a node left unaggregated, coarsest level above 4096 unknowns or
- * singular), GW_ERR_CUDA.
+ * with a pivot that is not positive), GW_ERR_CUDA.
  */
 int gw_amg_setup(gw_matrix A, const gw_amg_opts *opts, gw_hierarchy *H_out, void *stream);
 
